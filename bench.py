@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Throughput of the gather-and-refine scoring path (QPS, p50/p99 batch latency).
+
+One step = one batch of queries through all four steps (top centroids, gather,
+refine, top-k) on synthetic data shaped like the passage-ranking workload
+(1M docs, ~70M tokens, 262,144 bf16 centroids, 16-byte PQ codes, batches of
+64 queries x 32 tokens, k = 10). Every reported number states its accuracy
+against the FP64 oracle on a sample of the timed queries.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+this path) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "msmarco-1M"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--kc", type=int, default=40)
+    ap.add_argument("--kd", type=int, default=1000)
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
+    ap.add_argument("--oracle-queries", type=int, default=16)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_workload(name, device, rank, world, log):
+    """Index (cached on local disk) + the query stream."""
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        if rank == 0:
+            ix = synth.load_or_make(name, device=device, log=log)
+        dist.barrier()
+        if rank != 0:
+            ix = synth.load_or_make(name, device=device, log=log)
+    else:
+        ix = synth.load_or_make(name, device=device, log=log)
+    return ix
+
+
+def oracle_check(ix, qs, ntok, gi, gs, k, kc, kd, nsample):
+    """Top-10 overlap and score error of the GPU result vs the FP64 oracle on a sample."""
+    from oracle import Oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    O = Oracle(ix)
+    qoff = np.concatenate([[0], np.cumsum(ntok)])
+    sel = np.arange(min(nsample, len(ntok)))
+    rows = np.concatenate([np.arange(qoff[u], qoff[u + 1]) for u in sel])
+    t0 = time.perf_counter()
+    res = O.search(qs[rows], ntok[sel], k, kc, kd)
+    dt = time.perf_counter() - t0
+    ov, err = [], []
+    for j, u in enumerate(sel):
+        g = gi[u * k:(u + 1) * k]
+        o = res["ids"][j * k:(j + 1) * k]
+        a = set(g[:10].tolist()) - {-1}
+        b = set(o[:10].tolist()) - {-1}
+        ov.append(len(a & b) / max(1, len(b)))
+        os_ = res["scores"][j * k:(j + 1) * k]
+        m = np.isfinite(os_)
+        err.append(float(np.max(np.abs(gs[u * k:(u + 1) * k][m] - os_[m]) / np.maximum(1, np.abs(os_[m])))
+                   if m.any() else 0.0))
+    return {"queries": int(len(sel)), "overlap_at_10": float(np.mean(ov)), "min_overlap_at_10": float(np.min(ov)),
+            "max_rel_score_err": float(np.max(err))}, dt, len(sel)
+
+
+def algorithmic_traffic(T_idx, ix, params, dq, ntok, k, kc, kd, torch):
+    """Per-launch algorithmic bytes of gather and refine for one batch (counted, not modelled)."""
+    R = int(ntok.sum())
+    nq = len(ntok)
+    top = torch.empty((R, kc), dtype=torch.int32, device="cuda")
+    tops = torch.empty((R, kc), dtype=torch.float32, device="cuda")
+    T_idx.top_centroids(params, dq, top, tops)
+    cid = torch.empty((nq, kd), dtype=torch.int32, device="cuda")
+    cs = torch.empty((nq, kd), dtype=torch.float32, device="cuda")
+    nc = torch.empty(nq, dtype=torch.int32, device="cuda")
+    T_idx.gather(params, dq, ntok, top, cid, cs, nc)
+    torch.cuda.synchronize()
+    off = ix["_list_off"]
+    t = top.cpu().numpy()
+    lens = (off[t + 1] - off[t]).astype(np.int64)
+    entries = int(lens.sum())
+    D = ix["doc_offsets"].shape[0] - 1
+    gather_bytes = entries * 4 + R * kc * 8 + nq * D * 4
+    cand = cid.cpu().numpy()
+    doff = ix["doc_offsets"]
+    c = cand[cand >= 0]
+    ntoks = int((doff[c + 1] - doff[c]).sum())
+    M = ix["pq_codebooks"].shape[0]
+    cbytes = 2 if ix["centroid_dtype"] == "bf16" else 4
+    refine_bytes = ntoks * (4 + M + 2 + 128 * cbytes)
+    return {"list_entries": entries, "gather_bytes": gather_bytes, "refine_tokens": ntoks,
+            "refine_bytes": refine_bytes, "select_bytes": nq * D * 4}
+
+
+def run_ours(a):
+    import torch
+    import paper_2604_28142_b300 as T
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    log = (lambda m: print(f"[bench] {m}", file=sys.stderr, flush=True)) if rank == 0 else None
+    cfg = synth.CONFIGS[a.workload]
+    t0 = time.time()
+    ix = load_workload(a.workload, "cuda", rank, world, log)
+    if log:
+        log(f"index ready in {time.time() - t0:.1f}s: T={ix['doc_offsets'][-1]}")
+    G = T.Index(ix, local)
+    if a.precision == "auto":
+        prec = T.PREC_BF16 if T.lib().tachiom_version() and _tc_ok(T) else T.PREC_FP32
+    else:
+        prec = T.PREC_BF16 if a.precision == "bf16" else T.PREC_FP32
+    params = T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=prec)
+    nb = a.warmup + a.steps
+    q = synth.make_queries(cfg, n_queries=nb * a.batch, seed=cfg.query_seed + 7919 * rank, ntok_min=32,
+                           ntok_max=32)
+    qs, ntok = q["queries"], q["ntok"]
+    qoff = np.concatenate([[0], np.cumsum(ntok)])
+    batches = []
+    for b in range(nb):
+        lo, hi = b * a.batch, (b + 1) * a.batch
+        batches.append((torch.from_numpy(qs[qoff[lo]:qoff[hi]]).cuda(), ntok[lo:hi].copy()))
+    kk = np.full(a.batch, a.k, np.int32)
+    out_i = [torch.empty(a.batch * a.k, dtype=torch.int32, device="cuda") for _ in range(nb)]
+    out_s = [torch.empty(a.batch * a.k, dtype=torch.float32, device="cuda") for _ in range(nb)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for b in range(a.warmup):
+        G.search(params, batches[b][0], batches[b][1], kk, out_i[b], out_s[b])
+    torch.cuda.synchronize()
+    if a.profile_only:
+        for b in range(a.warmup, nb):
+            G.search(params, batches[b][0], batches[b][1], kk, out_i[b], out_s[b])
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_only": True}))
+        return
+    # ---- timed region (device-resident inputs) ----
+    T.profile_enable(True)
+    T.profile_read()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for s in range(a.steps):
+            b = a.warmup + s
+            flush.zero_()  # L2 flush between steps, outside the step's events
+            evs[s][0].record(stream)
+            G.search(params, batches[b][0], batches[b][1], kk, out_i[b], out_s[b])
+            evs[s][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    prof = T.profile_read()
+    T.profile_enable(False)
+    step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
+    tot_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    flags = G.stream_status()
+    queries_total = a.steps * a.batch * world
+    qps = queries_total / (tot_ms / 1e3)
+    # ---- end to end through the host-buffer entry point ----
+    e2e = None
+    if not a.no_e2e:
+        hq = [qs[qoff[(a.warmup + s) * a.batch]:qoff[(a.warmup + s + 1) * a.batch]] for s in range(a.steps)]
+        for s in range(min(2, a.steps)):
+            G.search_host(params, hq[s], batches[a.warmup + s][1], kk)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for s in range(a.steps):
+            G.search_host(params, hq[s], batches[a.warmup + s][1], kk)
+        e2e_s = time.perf_counter() - t1
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = int(hq[0].nbytes) + (4 * a.batch + 2) * 4
+        d2h = a.batch * a.k * 8
+        e2e = {"value": queries_total / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    # ---- accuracy on a sample of the timed queries, and the oracle's own time ----
+    b0 = a.warmup
+    gi = out_i[b0].cpu().numpy()
+    gs = out_s[b0].cpu().numpy()
+    qb = qs[qoff[b0 * a.batch]:qoff[(b0 + 1) * a.batch]]
+    acc, odt, on = oracle_check(ix, qb, batches[b0][1], gi, gs, a.k, a.kc, a.kd, a.oracle_queries)
+    # ---- roofline of the dominant launcher ----
+    ix["_list_off"] = G.lists()[0]
+    traffic = algorithmic_traffic(G, ix, params, batches[b0][0], batches[b0][1], a.k, a.kc, a.kd, torch)
+    import json as _j
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = _j.load(open(pk))
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (launches, ms) = dom
+    per_launch_ms = ms / max(1, launches)
+    clocks = clk.summary()
+    if name == "gather":
+        roof = {"kernel": "k_gather", "bound": "hbm", "achieved": traffic["gather_bytes"] / (per_launch_ms * 1e-3) / 1e9,
+                "peak": hbm_peak, "unit": "GB/s"}
+    elif name == "refine":
+        roof = {"kernel": "k_refine", "bound": "hbm", "achieved": traffic["refine_bytes"] / (per_launch_ms * 1e-3) / 1e9,
+                "peak": hbm_peak, "unit": "GB/s"}
+    elif name == "select_kd":
+        roof = {"kernel": "k_sel_*", "bound": "hbm", "achieved": traffic["select_bytes"] / (per_launch_ms * 1e-3) / 1e9,
+                "peak": hbm_peak, "unit": "GB/s"}
+    elif name == "topc_f32_scan":
+        R = a.batch * 32
+        C = ix["centroids"].shape[0]
+        fl = 2.0 * R * C * 128
+        sm = clocks.get("sm_mhz") or 1900.0
+        peak_alu = 148 * 128 * 2 * sm * 1e6 / 1e12
+        roof = {"kernel": "k_topc_f32_scan", "bound": "alu", "achieved": fl / (per_launch_ms * 1e-3) / 1e12,
+                "peak": peak_alu, "unit": "TFLOP/s"}
+        peak_src = "derived: 148 SMs x 128 FP32 lanes x 2 x median SM clock"
+    else:
+        R = a.batch * 32
+        C = ix["centroids"].shape[0]
+        fl = 2.0 * R * C * 128
+        pk_t = peaks.get("bf16_tflops", 1800.0)
+        roof = {"kernel": name, "bound": "tensor", "achieved": fl / (per_launch_ms * 1e-3) / 1e12,
+                "peak": pk_t, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["peak_source"] = peak_src
+    roof["traffic"] = None
+    roof["per_launch_ms"] = per_launch_ms
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    lat = step_ms
+    line = {
+        "metric": "QPS at top-10 overlap >=0.99 vs FP64 oracle; p50/p99 latency ms",
+        "value": qps,
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": float(lat.mean()),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16/f32" if prec == T.PREC_BF16 else "f32",
+        "data": "synthetic (seeded generator shaped like the passage-ranking workload)",
+        "config": {"workload": f"{a.workload}: {ix['doc_offsets'].shape[0] - 1} docs, {int(ix['doc_offsets'][-1])} "
+                               f"tokens, C={ix['centroids'].shape[0]} {ix['centroid_dtype']}, PQ {ix['pq_codebooks'].shape[0]}x8b",
+                   "batch": a.batch, "tokens_per_query": 32, "k": a.k, "kappa_c": a.kc, "kappa_d": a.kd,
+                   "precision": "bf16" if prec == T.PREC_BF16 else "fp32",
+                   "l2": "flushed between steps (256 MiB write outside the step's events)",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "note": "per batch; every query of a batch completes with its batch"},
+        "accuracy": acc,
+        "stage_ms_per_step": {k: v[1] / a.steps for k, v in prof.items()},
+        "status_flags": flags,
+        "roofline": roof,
+        "traffic_counts": traffic,
+        "cpu_baseline": {"value": on / odt, "unit": "queries/s", "cores": ncores, "kind": "oracle",
+                         "sample": f"{on} queries of the first timed batch, full cascade in FP64, OpenMP over queries"},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": _count_launches(prof),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _count_launches(prof):
+    # kernels per launcher call: select_kd launches 8 kernels, topc_merge 2, others 1
+    per = {"select_kd": 8, "topc_merge": 2}
+    return sum(v[0] * per.get(k, 1) for k, v in prof.items())
+
+
+def _tc_ok(T):
+    return os.environ.get("TACHIOM_NO_TC") is None and _probe_tc(T)
+
+
+def _probe_tc(T):
+    import ctypes
+    try:
+        f = T.lib().tachiom_tc_available
+    except AttributeError:
+        return False
+    f.restype = ctypes.c_int
+    return bool(f())
+
+
+def run_reference(a):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    from oracle import Oracle
+    cfg = synth.CONFIGS[a.workload]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    ix = synth.load_or_make(a.workload, device=dev)
+    O = Oracle(ix)
+    per_step = 8
+    nb = a.warmup + a.steps
+    q = synth.make_queries(cfg, n_queries=nb * per_step, seed=cfg.query_seed, ntok_min=32, ntok_max=32)
+    qs, ntok = q["queries"], q["ntok"]
+    qoff = np.concatenate([[0], np.cumsum(ntok)])
+    times = []
+    for b in range(nb):
+        lo, hi = b * per_step, (b + 1) * per_step
+        t0 = time.perf_counter()
+        O.search(qs[qoff[lo]:qoff[hi]], ntok[lo:hi], a.k, a.kc, a.kd)
+        if b >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    qps = a.steps * per_step / tot
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {
+        "impl": "reference",
+        "metric": "QPS at top-10 overlap >=0.99 vs FP64 oracle; p50/p99 latency ms",
+        "value": qps, "unit": "queries/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded generator shaped like the passage-ranking workload)",
+        "config": {"workload": a.workload, "batch": per_step, "tokens_per_query": 32, "k": a.k,
+                   "kappa_c": a.kc, "kappa_d": a.kd},
+        "latency_ms": {"p50": float(np.percentile(times, 50) * 1e3), "p99": float(np.percentile(times, 99) * 1e3)},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": ncores, "kind": "oracle",
+                         "sample": f"{per_step} queries per step, full cascade in FP64, OpenMP over queries"},
+        "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

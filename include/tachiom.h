@@ -1,0 +1,212 @@
+/*
+ * tachiom.h: C ABI of the B300 gather-and-refine scoring library.
+ *
+ * The library scores multivector (late-interaction) queries against an index
+ * built the way TACHIOM (arXiv 2604.28142) builds one: per-token-type
+ * centroids, the centroid id of every document token, PQ-coded normalised
+ * residuals and their norms (Sec. 2.1, "Residuals Compression"; Sec. 2.2,
+ * "Index Structure"). A search runs the four steps of Sec. 2.2 on one GPU:
+ *
+ *   (a) every query token against every centroid, keeping each token's
+ *       kappa_c best (Sec. 2.2, Gather step 1; exact, not a graph search);
+ *   (b) inverted-list gather and centroid-only late interaction,
+ *       S~(q,d) = sum_i max_{j in Top_i : d in L_j} <q_i, c_j> (Gather steps
+ *       2-4), truncated to the kappa_d best documents;
+ *   (c) refinement of those candidates with the full MaxSim on centroid plus
+ *       PQ-coded residual, S(q,d) = sum_i max_{t in d} (<q_i, c_a(t)> +
+ *       rho_t <q_i, r^_t>), the residual term read from per-query lookup
+ *       tables in the query-token-major layout (Sec. 2.2, Refine);
+ *   (d) the k best documents by S.
+ *
+ * Conventions shared by every call:
+ *   - Plain pointers and sizes only. "Host" pointers are read during the call
+ *     and may be freed when it returns. "Device" pointers are CUDA device
+ *     memory of the index's device, owned by the caller.
+ *   - A `stream` argument is a cudaStream_t (NULL = the legacy default stream).
+ *     Calls taking a stream are asynchronous on it: argument errors return
+ *     synchronously; conditions found on the device (a capacity overflow
+ *     that took the slow path, a row whose reduced-precision top-kappa_c was
+ *     recomputed in FP32) are reported later by tachiom_stream_status.
+ *   - Ties at every cut (kappa_c, kappa_d, k) are broken by the lower id.
+ *   - A row of results that has fewer than k documents is padded with doc id
+ *     -1 and score -inf.
+ *   - Every call returns a tachiom_status; on failure tachiom_last_error()
+ *     returns a message for the calling thread.
+ *   - One index may be searched concurrently from several host threads on
+ *     different streams; each stream gets its own scratch memory.
+ */
+#ifndef TACHIOM_H
+#define TACHIOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TACHIOM_OK = 0,
+  TACHIOM_ERR_INVALID = 1,  /* bad argument or malformed index */
+  TACHIOM_ERR_OOM = 2,      /* device or host allocation failed */
+  TACHIOM_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+  TACHIOM_ERR_CAPACITY = 4, /* a size is beyond a compiled-in maximum */
+  TACHIOM_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
+  TACHIOM_ERR_BUSY = 6      /* the index is being freed */
+} tachiom_status;
+
+/* storage type of the centroid table */
+enum { TACHIOM_DTYPE_F32 = 0, TACHIOM_DTYPE_BF16 = 1 };
+
+/* arithmetic of step (a); steps (b)-(d) always accumulate in FP32 */
+enum {
+  TACHIOM_PREC_FP32 = 0, /* FP32 CUDA-core products: the plain comparator path */
+  TACHIOM_PREC_BF16 = 1  /* BF16 tensor-core products with FP32 accumulation, then the
+                            candidates near each row's kappa_c boundary rescored in FP32 */
+};
+
+/* device status flags, OR-ed per stream since the last tachiom_stream_status */
+enum {
+  TACHIOM_FLAG_TOPC_RESCUED = 1u << 0,   /* a row's candidate buffer overflowed in step (a);
+                                            that row was recomputed exactly */
+  TACHIOM_FLAG_SELECT_TIES = 1u << 1,    /* the kappa_d cut fell in a run of exactly equal
+                                            scores wider than the fast buffer; the ordered
+                                            tie pass ran */
+  TACHIOM_FLAG_CAPACITY = 1u << 2,       /* a buffer overflow that could not be rescued: the
+                                            affected query's result may be incomplete */
+  TACHIOM_FLAG_BAD_INPUT = 1u << 3       /* a device-side range check failed */
+};
+
+typedef struct tachiom_index tachiom_index; /* opaque, owned by the library */
+
+/* Index description. Every pointer is a HOST pointer read during
+ * tachiom_index_load only; the library keeps its own device copies.
+ * Layouts are row-major and packed.                                         */
+typedef struct {
+  int32_t dim;                 /* embedding dimension; must be 128 */
+  int64_t n_centroids;         /* C >= 1 */
+  int64_t n_docs;              /* D >= 1, D < 2^31 */
+  int64_t n_tokens;            /* T = doc_offsets[D] */
+  int32_t pq_m;                /* PQ subspaces M: 8, 16 or 32 (d/M dims each) */
+  int32_t pq_nbits;            /* bits per code; must be 8 (256 codewords) */
+  int32_t centroid_dtype;      /* TACHIOM_DTYPE_F32 or TACHIOM_DTYPE_BF16 */
+  const void *centroids;       /* [C x dim] fp32, or bf16 bit patterns (uint16) */
+  const int32_t *centroid_type;/* [C] token-type id of each centroid; may be NULL */
+  const int64_t *doc_offsets;  /* [D+1] CSR over tokens: doc d owns [off[d], off[d+1]) */
+  const int32_t *token_centroid;/* [T] centroid id a(t) of every token, in [0, C) */
+  const float *pq_codebooks;   /* [M x 256 x dim/M] codewords of the normalised residual */
+  const uint8_t *pq_codes;     /* [T x M] one byte per token and subspace */
+  const uint16_t *residual_norms;/* [T] fp16 bit patterns of rho_t; NULL means rho_t = 1
+                                    (the codes then encode the raw residual) */
+} tachiom_index_desc;
+
+/* Copy an index to `cuda_device` and build its inverted lists L_j (document
+ * ids of the tokens assigned to c_j, Sec. 2.2 "Index Structure";
+ * deduplicated, ascending). Validates the CSR and every id; on any failure
+ * nothing is leaked and *out is left NULL. Blocking.                        */
+tachiom_status tachiom_index_load(const tachiom_index_desc *desc, int cuda_device,
+                                  tachiom_index **out);
+
+/* Release an index and all scratch memory it allocated. The caller must have
+ * synchronised every stream that used it. NULL is accepted.                */
+tachiom_status tachiom_index_free(tachiom_index *index);
+
+/* Read-only facts about a loaded index (any pointer may be NULL).          */
+tachiom_status tachiom_index_info(const tachiom_index *index, int64_t *n_centroids,
+                                  int64_t *n_docs, int64_t *n_tokens, int64_t *n_list_entries,
+                                  int32_t *pq_m, int64_t *device_bytes);
+
+/* Copy the inverted lists back to the host: off [C+1] int64, docs
+ * [n_list_entries] int32 (host buffers owned by the caller). Blocking.     */
+tachiom_status tachiom_index_lists(const tachiom_index *index, int64_t *h_off, int32_t *h_docs);
+
+typedef struct {
+  int32_t kappa_c;    /* centroids kept per query token, 1..128 */
+  int32_t kappa_d;    /* candidates refined per query, 1..4096; 0 means max(1000, 4 max_k) capped
+                         at 4096 */
+  int32_t precision;  /* TACHIOM_PREC_* for step (a) */
+  int32_t plan_id;    /* -1: the library picks launch shapes; >= 0: a fixed plan (autotuner) */
+} tachiom_search_params;
+
+/* The whole path, steps (a)-(d), for a batch of nq queries.
+ *   d_queries  device fp32 [sum(ntok) x 128], query q's tokens at rows
+ *              [sum_{p<q} ntok_p, +ntok_q); unit norm expected, not checked
+ *   h_ntok     host int32 [nq], each 1..32
+ *   h_k        host int32 [nq], each 1..kappa_d
+ *   d_out_ids / d_out_scores  device int32 / fp32 [sum(k)], row q at
+ *              [sum_{p<q} k_p, +k_q), sorted by (score desc, doc asc)
+ * nq may be 0 (nothing is launched). Asynchronous on `stream`.             */
+tachiom_status tachiom_search(tachiom_index *index, const tachiom_search_params *params,
+                              const float *d_queries, const int32_t *h_ntok, const int32_t *h_k,
+                              int32_t nq, int32_t *d_out_ids, float *d_out_scores, void *stream);
+
+/* Same as tachiom_search with HOST queries and HOST outputs: the library copies
+ * the queries in and the results out on `stream` (through pinned staging it
+ * owns) and returns after the stream has finished the batch. Blocking.     */
+tachiom_status tachiom_search_host(tachiom_index *index, const tachiom_search_params *params,
+                                   const float *h_queries, const int32_t *h_ntok,
+                                   const int32_t *h_k, int32_t nq, int32_t *h_out_ids,
+                                   float *h_out_scores, void *stream);
+
+/* ---- single steps, for replaying one step on given inputs ---- */
+
+/* Step (a) alone (Sec. 2.2, Gather step 1, exhaustive): for each of nrows
+ * device fp32 rows [nrows x 128], the kappa_c best centroids by (FP32 score
+ * desc, id asc): d_top_ids int32 / d_top_scores fp32 [nrows x kappa_c].
+ * With TACHIOM_PREC_BF16 the products run in BF16 and the result is rescored
+ * in FP32, so the output is the FP32 path's. Asynchronous.                 */
+tachiom_status tachiom_top_centroids(tachiom_index *index, const tachiom_search_params *params,
+                                     const float *d_rows, int32_t nrows, int32_t *d_top_ids,
+                                     float *d_top_scores, void *stream);
+
+/* Step (b) alone (Sec. 2.2, Gather steps 2-4 and the kappa_d truncation) on
+ * given top centroids. d_top_ids int32 [sum(ntok) x kappa_c] (entries < 0
+ * are skipped; the FP32 scores are recomputed from the ids). Writes, per
+ * query, the kappa_d best documents by (S~ desc, doc asc) to d_cand_ids
+ * int32 / d_cand_scores fp32 [nq x kappa_d] (padded with -1 / -inf) and their
+ * count to d_ncand int32 [nq]. Asynchronous.                                */
+tachiom_status tachiom_gather(tachiom_index *index, const tachiom_search_params *params,
+                              const float *d_queries, const int32_t *h_ntok, int32_t nq,
+                              const int32_t *d_top_ids, int32_t *d_cand_ids,
+                              float *d_cand_scores, int32_t *d_ncand, void *stream);
+
+/* Steps (c)-(d) alone (Sec. 2.2, Refine; then top-k) on given candidates:
+ * d_cand_ids int32 [nq x kappa_d] (entries < 0 are skipped), outputs as in
+ * tachiom_search. Asynchronous.                                             */
+tachiom_status tachiom_refine(tachiom_index *index, const tachiom_search_params *params,
+                              const float *d_queries, const int32_t *h_ntok, const int32_t *h_k,
+                              int32_t nq, const int32_t *d_cand_ids, int32_t *d_out_ids,
+                              float *d_out_scores, void *stream);
+
+/* Synchronise `stream`, then return and clear the TACHIOM_FLAG_* bits raised
+ * by work on that stream. Blocking.                                         */
+tachiom_status tachiom_stream_status(tachiom_index *index, void *stream, uint32_t *h_flags);
+
+/* ---- timing of the library's own launches ----
+ * When enabled, every launcher records a CUDA event pair around its kernels on
+ * the launching stream (not while the stream is being captured into a graph).
+ * tachiom_profile_read synchronises `stream`, then returns, per launcher name in
+ * first-launch order, the number of launches and their summed device time
+ * since the previous read, and forgets them. `out` is a host array of `cap`
+ * entries; *n_out receives the number written.                              */
+typedef struct {
+  char name[32];
+  int32_t launches;
+  double total_ms;
+} tachiom_profile_entry;
+
+tachiom_status tachiom_profile_enable(int on);
+tachiom_status tachiom_profile_read(void *stream, tachiom_profile_entry *out, int32_t cap,
+                                    int32_t *n_out);
+
+/* Message of the last failed call on this thread ("" if none).             */
+const char *tachiom_last_error(void);
+
+/* Library version string. */
+const char *tachiom_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TACHIOM_H */

@@ -1,0 +1,223 @@
+"""ctypes binding of the C ABI in include/tachiom.h (argument marshalling only).
+
+Every function of the header is exposed under its own name on `lib()`; the
+`Index` class is a thin owner of a `tachiom_index*` whose methods take torch
+CUDA tensors (for device pointers and the current stream) or numpy arrays (for
+host buffers) and call those functions. No step of the search runs in Python.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+TACHIOM_OK = 0
+DTYPE_F32, DTYPE_BF16 = 0, 1
+PREC_FP32, PREC_BF16 = 0, 1
+FLAG_TOPC_RESCUED, FLAG_SELECT_TIES, FLAG_CAPACITY, FLAG_BAD_INPUT = 1, 2, 4, 8
+
+_STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "CAPACITY", 5: "TIMEOUT", 6: "BUSY"}
+
+
+class TachiomError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tachiom {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Desc(ct.Structure):
+    _fields_ = [
+        ("dim", ct.c_int32), ("n_centroids", ct.c_int64), ("n_docs", ct.c_int64),
+        ("n_tokens", ct.c_int64), ("pq_m", ct.c_int32), ("pq_nbits", ct.c_int32),
+        ("centroid_dtype", ct.c_int32), ("centroids", ct.c_void_p), ("centroid_type", ct.c_void_p),
+        ("doc_offsets", ct.c_void_p), ("token_centroid", ct.c_void_p),
+        ("pq_codebooks", ct.c_void_p), ("pq_codes", ct.c_void_p), ("residual_norms", ct.c_void_p),
+    ]
+
+
+class SearchParams(ct.Structure):
+    _fields_ = [("kappa_c", ct.c_int32), ("kappa_d", ct.c_int32), ("precision", ct.c_int32),
+                ("plan_id", ct.c_int32)]
+
+    def __init__(self, kappa_c=40, kappa_d=0, precision=PREC_FP32, plan_id=-1):
+        super().__init__(kappa_c, kappa_d, precision, plan_id)
+
+
+class ProfileEntry(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int32), ("total_ms", ct.c_double)]
+
+
+def profile_enable(on: bool = True):
+    _check(lib().tachiom_profile_enable(1 if on else 0))
+
+
+def profile_read(stream=None) -> dict:
+    """{launcher name: (launches, total device ms)} since the previous read (synchronises)."""
+    buf = (ProfileEntry * 64)()
+    n = ct.c_int32()
+    _check(lib().tachiom_profile_read(_stream(stream), buf, 64, ct.byref(n)))
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(n.value)}
+
+
+def lib_path() -> str:
+    return os.environ.get("TACHIOM_LIB", os.path.join(_HERE, "libtachiom.so"))
+
+
+_LIB = None
+
+
+def lib():
+    """Load libtachiom.so (fails loudly when it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libtachiom.so not found at {path}: run paper_2604_28142_b300/build.py")
+    L = ct.CDLL(path)
+    P, I32, I64, U32p = ct.c_void_p, ct.c_int32, ct.c_int64, ct.POINTER(ct.c_uint32)
+    sig = {
+        "tachiom_index_load": ([ct.POINTER(_Desc), ct.c_int, ct.POINTER(ct.c_void_p)], ct.c_int),
+        "tachiom_index_free": ([P], ct.c_int),
+        "tachiom_index_info": ([P, P, P, P, P, P, P], ct.c_int),
+        "tachiom_index_lists": ([P, P, P], ct.c_int),
+        "tachiom_search": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P], ct.c_int),
+        "tachiom_search_host": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P], ct.c_int),
+        "tachiom_top_centroids": ([P, ct.POINTER(SearchParams), P, I32, P, P, P], ct.c_int),
+        "tachiom_gather": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P, P, P], ct.c_int),
+        "tachiom_refine": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
+        "tachiom_stream_status": ([P, P, U32p], ct.c_int),
+        "tachiom_profile_enable": ([ct.c_int], ct.c_int),
+        "tachiom_profile_read": ([P, ct.POINTER(ProfileEntry), I32, ct.POINTER(ct.c_int32)], ct.c_int),
+        "tachiom_last_error": ([], ct.c_char_p),
+        "tachiom_version": ([], ct.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = L
+    return L
+
+
+def _check(st: int):
+    if st != TACHIOM_OK:
+        raise TachiomError(st, lib().tachiom_last_error().decode(errors="replace"))
+
+
+def _hp(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def _dp(t):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ct.c_void_p(stream.cuda_stream)
+
+
+class Index:
+    """A loaded index (tachiom_index_load / tachiom_index_free)."""
+
+    def __init__(self, ix: dict, device: int = 0):
+        L = lib()
+        cd = DTYPE_BF16 if ix.get("centroid_dtype") == "bf16" else DTYPE_F32
+        self._keep = {
+            "centroids": np.ascontiguousarray(ix["centroids"]),
+            "doc_offsets": np.ascontiguousarray(ix["doc_offsets"], dtype=np.int64),
+            "token_centroid": np.ascontiguousarray(ix["token_centroid"], dtype=np.int32),
+            "pq_codebooks": np.ascontiguousarray(ix["pq_codebooks"], dtype=np.float32),
+            "pq_codes": np.ascontiguousarray(ix["pq_codes"], dtype=np.uint8),
+        }
+        ct_ = ix.get("centroid_type")
+        rn = ix.get("residual_norms")
+        self._keep["centroid_type"] = None if ct_ is None else np.ascontiguousarray(ct_, dtype=np.int32)
+        self._keep["residual_norms"] = None if rn is None else np.ascontiguousarray(rn, dtype=np.uint16)
+        k = self._keep
+        C = k["centroids"].shape[0]
+        D = k["doc_offsets"].shape[0] - 1
+        T = k["token_centroid"].shape[0]
+        M = k["pq_codebooks"].shape[0]
+        d = _Desc(128, C, D, T, M, 8, cd, _hp(k["centroids"]), _hp(k["centroid_type"]),
+                  _hp(k["doc_offsets"]), _hp(k["token_centroid"]), _hp(k["pq_codebooks"]),
+                  _hp(k["pq_codes"]), _hp(k["residual_norms"]))
+        h = ct.c_void_p()
+        _check(L.tachiom_index_load(ct.byref(d), device, ct.byref(h)))
+        self.h = h
+        self.device = device
+        self.C, self.D, self.T, self.M = C, D, T, M
+        self._keep = None  # the library holds its own copies
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tachiom_index_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        v = [ct.c_int64(), ct.c_int64(), ct.c_int64(), ct.c_int64(), ct.c_int32(), ct.c_int64()]
+        _check(lib().tachiom_index_info(self.h, *[ct.byref(x) for x in v]))
+        keys = ["n_centroids", "n_docs", "n_tokens", "n_list_entries", "pq_m", "device_bytes"]
+        return {k: x.value for k, x in zip(keys, v)}
+
+    def lists(self):
+        n = self.info()["n_list_entries"]
+        off = np.empty(self.C + 1, np.int64)
+        docs = np.empty(max(n, 1), np.int32)
+        _check(lib().tachiom_index_lists(self.h, _hp(off), _hp(docs)))
+        return off, docs[:n]
+
+    # ---- the calls that take device tensors (torch) -----------------------------
+    def search(self, params: SearchParams, queries, ntok: np.ndarray, k: np.ndarray, out_ids,
+               out_scores, stream=None):
+        ntok = np.ascontiguousarray(ntok, dtype=np.int32)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        _check(lib().tachiom_search(self.h, ct.byref(params), _dp(queries), _hp(ntok), _hp(k),
+                                    int(ntok.shape[0]), _dp(out_ids), _dp(out_scores), _stream(stream)))
+
+    def search_host(self, params: SearchParams, queries: np.ndarray, ntok, k, stream=None):
+        queries = np.ascontiguousarray(queries, dtype=np.float32)
+        ntok = np.ascontiguousarray(ntok, dtype=np.int32)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        tot = int(k.sum())
+        ids = np.empty(max(tot, 1), np.int32)
+        sc = np.empty(max(tot, 1), np.float32)
+        _check(lib().tachiom_search_host(self.h, ct.byref(params), _hp(queries), _hp(ntok), _hp(k),
+                                         int(ntok.shape[0]), _hp(ids), _hp(sc), _stream(stream)))
+        return ids[:tot], sc[:tot]
+
+    def top_centroids(self, params: SearchParams, rows, top_ids, top_scores, stream=None):
+        _check(lib().tachiom_top_centroids(self.h, ct.byref(params), _dp(rows), int(rows.shape[0]),
+                                           _dp(top_ids), _dp(top_scores), _stream(stream)))
+
+    def gather(self, params: SearchParams, queries, ntok, top_ids, cand_ids, cand_scores, ncand,
+               stream=None):
+        ntok = np.ascontiguousarray(ntok, dtype=np.int32)
+        _check(lib().tachiom_gather(self.h, ct.byref(params), _dp(queries), _hp(ntok),
+                                    int(ntok.shape[0]), _dp(top_ids), _dp(cand_ids), _dp(cand_scores),
+                                    _dp(ncand), _stream(stream)))
+
+    def refine(self, params: SearchParams, queries, ntok, k, cand_ids, out_ids, out_scores, stream=None):
+        ntok = np.ascontiguousarray(ntok, dtype=np.int32)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        _check(lib().tachiom_refine(self.h, ct.byref(params), _dp(queries), _hp(ntok), _hp(k),
+                                    int(ntok.shape[0]), _dp(cand_ids), _dp(out_ids), _dp(out_scores),
+                                    _stream(stream)))
+
+    def stream_status(self, stream=None) -> int:
+        f = ct.c_uint32()
+        _check(lib().tachiom_stream_status(self.h, _stream(stream), ct.byref(f)))
+        return f.value

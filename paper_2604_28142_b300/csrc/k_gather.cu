@@ -1,0 +1,330 @@
+// Step (b): inverted-list gather and centroid-only late interaction
+// (Sec. 2.2, Gather steps 2-4), then the kappa_d truncation.
+//
+// k_gather: one CTA per (query, range of R documents). For each query token i
+// in ascending order it walks, for every j in Top_i, the slice of L_j that
+// falls in its range (lists are doc-sorted and a per-(list, range) offset
+// table locates the slice) and keeps
+//     s~_i(d) = max_{j in Top_i : d in L_j} <q_i, c_j>
+// in a shared-memory word per document (atomicMax on an order-preserving
+// key); a second walk of the same slices hands each reached document's max
+// to exactly one thread (atomicExch), which adds it to S~(q, d). Tokens are
+// folded in ascending i, so S~ is summed in a fixed order and the candidate
+// scores are bit-identical run to run. The range's S~ values go to a dense
+// per-query array (-inf = not reached), and a 4096-bin histogram of their
+// keys goes to the query's histogram for the selection.
+//
+// Selection of the kappa_d best (S~ desc, doc asc): the histogram locates the
+// bin that holds the kappa_d-th key; up to two more histogram levels narrow
+// it when that bin is wide; every key at or above the cut is collected and
+// sorted exactly. A cut inside a run of equal keys wider than the buffer
+// takes the ordered tie pass (lowest doc ids first).
+#include "tachiom_internal.cuh"
+
+namespace tachiom {
+
+constexpr int G_THREADS = 1024;
+
+__global__ void __launch_bounds__(G_THREADS, 1)
+k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
+         const float *__restrict__ top_s, int kc, const int64_t *__restrict__ list_off,
+         const int32_t *__restrict__ list_doc, const int32_t *__restrict__ list_roff, int nr1,
+         int64_t D, int RD, int64_t C, float *__restrict__ dense, uint32_t *__restrict__ hist,
+         uint32_t *__restrict__ flags) {
+  extern __shared__ __align__(16) uint32_t gsm[];
+  uint32_t *best = gsm;                                   // [RD] max key of the current token
+  float *S = reinterpret_cast<float *>(gsm + RD);         // [RD] running S~
+  uint32_t *h = gsm + 2 * RD;                             // [NBINS1]
+  __shared__ int64_t seg_base[MAX_KC];
+  __shared__ uint32_t seg_key[MAX_KC];
+  __shared__ int seg_pref[MAX_KC + 1];
+
+  const int r = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
+  const int64_t r0 = (int64_t)r * RD;
+  const int nd = (int)min((int64_t)RD, D - r0);
+  for (int x = tid; x < RD; x += G_THREADS) {
+    best[x] = 0u;
+    S[x] = -INFINITY;
+  }
+  for (int b = tid; b < NBINS1; b += G_THREADS) h[b] = 0u;
+  const int row_b = qoff[q], row_e = qoff[q + 1];
+  __syncthreads();
+
+  for (int i = row_b; i < row_e; i++) {
+    if (tid < kc) {
+      int32_t j = top_ids[(int64_t)i * kc + tid];
+      int len = 0;
+      if (j >= C) {
+        atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
+        j = -1;
+      }
+      if (j >= 0) {
+        int lo = list_roff[(int64_t)j * nr1 + r], hi = list_roff[(int64_t)j * nr1 + r + 1];
+        seg_base[tid] = list_off[j] + lo;
+        seg_key[tid] = fkey(top_s[(int64_t)i * kc + tid]);
+        len = hi - lo;
+      }
+      seg_pref[tid + 1] = len;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      seg_pref[0] = 0;
+      for (int u = 0; u < kc; u++) seg_pref[u + 1] += seg_pref[u];
+    }
+    __syncthreads();
+    const int total = seg_pref[kc];
+    // pass 1: per-document max over the retrieved centroids (step 3)
+    for (int e = tid; e < total; e += G_THREADS) {
+      int lo = 0, hi = kc;  // find seg with pref[seg] <= e < pref[seg+1]
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (seg_pref[mid] <= e) lo = mid; else hi = mid;
+      }
+      int32_t d = list_doc[seg_base[lo] + (e - seg_pref[lo])];
+      atomicMax(&best[d - r0], seg_key[lo]);
+    }
+    __syncthreads();
+    // pass 2: fold the max into S~ once per reached document (step 4)
+    for (int e = tid; e < total; e += G_THREADS) {
+      int lo = 0, hi = kc;
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (seg_pref[mid] <= e) lo = mid; else hi = mid;
+      }
+      int32_t d = list_doc[seg_base[lo] + (e - seg_pref[lo])];
+      uint32_t v = atomicExch(&best[d - r0], 0u);
+      if (v) {
+        float s = funkey(v), cur = S[d - r0];
+        S[d - r0] = (cur == -INFINITY) ? s : cur + s;
+      }
+    }
+    __syncthreads();
+  }
+  float *out = dense + (int64_t)q * D + r0;
+  for (int x = tid; x < nd; x += G_THREADS) {
+    float v = S[x];
+    out[x] = v;
+    if (v != -INFINITY) atomicAdd(&h[fkey(v) >> 20], 1u);
+  }
+  __syncthreads();
+  uint32_t *hq = hist + (int64_t)q * NBINS1;
+  for (int b = tid; b < NBINS1; b += G_THREADS)
+    if (h[b]) atomicAdd(&hq[b], h[b]);
+}
+
+tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, const int32_t *top_ids,
+                             const float *top_s, int kc, float *dense, uint32_t *hist, uint32_t *flags,
+                             cudaStream_t s) {
+  if (nq <= 0) return TACHIOM_OK;
+  TPROF("gather", s);
+  TCUDA(cudaMemsetAsync(hist, 0, (size_t)nq * NBINS1 * 4, s));
+  size_t smem = (size_t)ix.range_docs * 8 + NBINS1 * 4;
+  TCUDA(cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(ix.n_ranges, nq);
+  k_gather<<<grid, G_THREADS, smem, s>>>(meta_qoff, top_ids, top_s, kc, ix.list_off, ix.list_doc,
+                                         ix.list_roff, ix.n_ranges + 1, ix.D, ix.range_docs, ix.C, dense, hist,
+                                         flags);
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// kappa_d selection
+// state[q][*]: 0 prefix (key bits fixed so far), 1 level reached (1..3), 2 above
+// (count of keys strictly above the current bin range), 3 done, 4 kmin (collect
+// keys >= kmin), 5 collected count, 6 tie mode, 7 spare.
+constexpr int S_PREFIX = 0, S_LEVEL = 1, S_ABOVE = 2, S_DONE = 3, S_KMIN = 4, S_CNT = 5, S_TIES = 6;
+constexpr int SEL_CHUNK = 8192;
+constexpr int SEL_THREADS = 256;
+
+// level L bins: L1 key>>20 (4096), L2 (key>>8)&0xfff (4096), L3 key&0xff (256)
+__device__ __forceinline__ int level_shift(int L) { return L == 1 ? 20 : (L == 2 ? 8 : 0); }
+__device__ __forceinline__ int level_bins(int L) { return L == 3 ? 256 : 4096; }
+
+__global__ void k_sel_find(const uint32_t *__restrict__ hist, uint32_t *__restrict__ state, int kd, int L,
+                           uint32_t *__restrict__ flags) {
+  const int q = blockIdx.x;
+  uint32_t *st = state + (int64_t)q * 8;
+  if (threadIdx.x != 0) return;
+  if (L == 1) {
+    st[S_PREFIX] = 0; st[S_LEVEL] = 1; st[S_ABOVE] = 0; st[S_DONE] = 0; st[S_KMIN] = 1;
+    st[S_CNT] = 0; st[S_TIES] = 0;
+  } else if (st[S_DONE]) {
+    return;
+  }
+  const uint32_t *hq = hist + (int64_t)q * NBINS1;
+  const int nb = level_bins(L);
+  uint32_t above = st[S_ABOVE];
+  uint32_t need = (uint32_t)kd > above ? (uint32_t)kd - above : 0;
+  uint32_t cum = 0;
+  int b = nb - 1;
+  for (; b >= 0; b--) {
+    if (cum + hq[b] >= need) break;
+    cum += hq[b];
+  }
+  const int sh = level_shift(L);
+  uint32_t prefix = st[S_PREFIX];
+  if (b < 0) {
+    // fewer keys than needed in the whole range: take everything in it
+    uint32_t lo_key = (L == 1) ? 1u : (prefix << (sh + (L == 2 ? 12 : 8)));
+    st[S_KMIN] = lo_key == 0 ? 1u : lo_key;
+    st[S_DONE] = 1;
+    return;
+  }
+  // the cut lies in bin b
+  uint32_t newprefix = (L == 1) ? (uint32_t)b : ((prefix << (L == 2 ? 12 : 8)) | (uint32_t)b);
+  uint32_t kmin = newprefix << sh;
+  if (kmin == 0) kmin = 1;
+  st[S_PREFIX] = newprefix;
+  st[S_LEVEL] = L;
+  st[S_ABOVE] = above + cum;
+  st[S_KMIN] = kmin;
+  if (above + cum + hq[b] <= (uint32_t)SEL_CAP) {
+    st[S_DONE] = 1;
+  } else if (L == 3) {
+    // exact key reached and still too many equal keys: ordered tie pass
+    st[S_DONE] = 1;
+    st[S_TIES] = 1;
+    atomicOr(flags, TACHIOM_FLAG_SELECT_TIES);
+  }
+}
+
+__global__ void __launch_bounds__(SEL_THREADS)
+k_sel_hist(const float *__restrict__ dense, int64_t D, const uint32_t *__restrict__ state,
+           uint32_t *__restrict__ hist, int L) {
+  const int q = blockIdx.y;
+  const uint32_t *st = state + (int64_t)q * 8;
+  if (st[S_DONE]) return;
+  __shared__ uint32_t h[NBINS1];
+  const int nb = level_bins(L);
+  for (int b = threadIdx.x; b < nb; b += SEL_THREADS) h[b] = 0u;
+  __syncthreads();
+  const uint32_t prefix = st[S_PREFIX];
+  const int psh = (L == 2) ? 20 : 8;  // bits above this level's bins
+  const int sh = level_shift(L);
+  const int64_t b0 = (int64_t)blockIdx.x * SEL_CHUNK;
+  const int64_t e0 = min(D, b0 + SEL_CHUNK);
+  const float *dq = dense + (int64_t)q * D;
+  for (int64_t x = b0 + threadIdx.x; x < e0; x += SEL_THREADS) {
+    float v = dq[x];
+    if (v == -INFINITY) continue;
+    uint32_t k = fkey(v);
+    if ((k >> psh) == prefix) atomicAdd(&h[(k >> sh) & (nb - 1)], 1u);
+  }
+  __syncthreads();
+  uint32_t *hq = hist + (int64_t)q * NBINS1;
+  for (int b = threadIdx.x; b < nb; b += SEL_THREADS)
+    if (h[b]) atomicAdd(&hq[b], h[b]);
+}
+
+__global__ void __launch_bounds__(SEL_THREADS)
+k_sel_collect(const float *__restrict__ dense, int64_t D, uint32_t *__restrict__ state,
+              uint64_t *__restrict__ selbuf, uint32_t *__restrict__ flags) {
+  const int q = blockIdx.y;
+  uint32_t *st = state + (int64_t)q * 8;
+  const uint32_t kmin = st[S_KMIN];
+  const bool ties = st[S_TIES] != 0;
+  const int64_t b0 = (int64_t)blockIdx.x * SEL_CHUNK;
+  const int64_t e0 = min(D, b0 + SEL_CHUNK);
+  const float *dq = dense + (int64_t)q * D;
+  uint64_t *buf = selbuf + (int64_t)q * SEL_CAP;
+  for (int64_t x = b0 + threadIdx.x; x < e0; x += SEL_THREADS) {
+    float v = dq[x];
+    if (v == -INFINITY) continue;
+    uint32_t k = fkey(v);
+    if (ties ? (k > kmin) : (k >= kmin)) {
+      uint32_t pos = atomicAdd(&st[S_CNT], 1u);
+      if (pos < (uint32_t)SEL_CAP) buf[pos] = comp_key(v, (int32_t)x);
+      else atomicOr(flags, TACHIOM_FLAG_CAPACITY);
+    }
+  }
+}
+
+// ordered pass for a cut inside a long run of equal keys: the lowest doc ids win
+__global__ void __launch_bounds__(1024)
+k_sel_ties(const float *__restrict__ dense, int64_t D, uint32_t *__restrict__ state,
+           uint64_t *__restrict__ selbuf, int kd) {
+  const int q = blockIdx.x;
+  uint32_t *st = state + (int64_t)q * 8;
+  if (!st[S_TIES]) return;
+  __shared__ int s_taken;
+  __shared__ int warp_cnt[32];
+  const uint32_t kmin = st[S_KMIN];
+  const float *dq = dense + (int64_t)q * D;
+  uint64_t *buf = selbuf + (int64_t)q * SEL_CAP;
+  const int base = (int)umin(st[S_CNT], (uint32_t)SEL_CAP);
+  const int need = kd - base;
+  if (threadIdx.x == 0) s_taken = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t c0 = 0; c0 < D; c0 += 1024) {
+    if (s_taken >= need) break;
+    int64_t x = c0 + threadIdx.x;
+    bool hit = x < D && dq[x] != -INFINITY && fkey(dq[x]) == kmin;
+    unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) warp_cnt[warp] = __popc(m);
+    __syncthreads();
+    int before = s_taken;
+    for (int w = 0; w < warp; w++) before += warp_cnt[w];
+    before += __popc(m & ((1u << lane) - 1));
+    if (hit && before < need && base + before < SEL_CAP) buf[base + before] = comp_key(dq[x], (int32_t)x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < 32; w++) t += warp_cnt[w];
+      s_taken += t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st[S_CNT] = (uint32_t)(base + min(s_taken, need));
+}
+
+__global__ void __launch_bounds__(1024)
+k_sel_sort(uint32_t *__restrict__ state, uint64_t *__restrict__ selbuf, int kd, int32_t *__restrict__ cand,
+           float *__restrict__ cand_s, int32_t *__restrict__ ncand) {
+  extern __shared__ __align__(16) uint64_t ssm[];
+  const int q = blockIdx.x;
+  const uint32_t *st = state + (int64_t)q * 8;
+  const int n = (int)umin(st[S_CNT], (uint32_t)SEL_CAP);
+  const int np = next_pow2(max(n, 2));
+  const uint64_t *buf = selbuf + (int64_t)q * SEL_CAP;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) ssm[i] = i < n ? buf[i] : 0ull;
+  __syncthreads();
+  block_sort_desc(ssm, np);
+  const int m = min(n, kd);
+  for (int i = threadIdx.x; i < kd; i += blockDim.x) {
+    uint64_t v = i < m ? ssm[i] : 0ull;
+    cand[(int64_t)q * kd + i] = v ? comp_id(v) : -1;
+    cand_s[(int64_t)q * kd + i] = v ? comp_score(v) : -INFINITY;
+  }
+  if (threadIdx.x == 0) ncand[q] = m;
+}
+
+tachiom_status launch_select_kd(const Index &ix, int nq, int kd, const float *dense, const uint32_t *hist,
+                                uint32_t *hist2, uint32_t *state, uint64_t *selbuf, int32_t *cand,
+                                float *cand_s, int32_t *ncand, uint32_t *flags, cudaStream_t s) {
+  if (nq <= 0) return TACHIOM_OK;
+  TPROF("select_kd", s);
+  const int64_t D = ix.D;
+  dim3 grid((unsigned)((D + SEL_CHUNK - 1) / SEL_CHUNK), nq);
+  k_sel_find<<<nq, 32, 0, s>>>(hist, state, kd, 1, flags);
+  TLAUNCH();
+  for (int L = 2; L <= 3; L++) {
+    TCUDA(cudaMemsetAsync(hist2, 0, (size_t)nq * NBINS1 * 4, s));
+    k_sel_hist<<<grid, SEL_THREADS, 0, s>>>(dense, D, state, hist2, L);
+    TLAUNCH();
+    k_sel_find<<<nq, 32, 0, s>>>(hist2, state, kd, L, flags);
+    TLAUNCH();
+  }
+  k_sel_collect<<<grid, SEL_THREADS, 0, s>>>(dense, D, state, selbuf, flags);
+  TLAUNCH();
+  k_sel_ties<<<nq, 1024, 0, s>>>(dense, D, state, selbuf, kd);
+  TLAUNCH();
+  size_t smem = (size_t)SEL_CAP * 8;
+  TCUDA(cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_sel_sort<<<nq, 1024, smem, s>>>(state, selbuf, kd, cand, cand_s, ncand);
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
+}  // namespace tachiom

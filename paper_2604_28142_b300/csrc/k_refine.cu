@@ -1,0 +1,267 @@
+// Steps (c) and (d): PQ-ADC refinement with full MaxSim (Sec. 2.2, Refine) and
+// the final top-k.
+//
+//   S(q,d) = sum_i max_{t in d} ( <q_i, c_a(t)> + rho_t * sum_m T[m][code_{t,m}][i] )
+//   T[m][j][i] = <q_i^(m), w_{m,j}>                  (ADC lookup tables)
+//
+// The tables use the paper's query-token-major layout (Sec. 2.2, "Distance
+// Table Layout"): subspace m, then codeword j, then a contiguous micro-block of
+// query tokens, so one code of one document token fetches the distances of
+// all the CTA's query tokens from consecutive words. A full table for 32
+// query tokens (M x 256 x 32 fp32 = 512 KB at M = 16) does not fit in shared
+// memory, so a CTA owns a group of G = 128 / M query tokens (a 128 KB table)
+// and the per-group partial sums of the max are added in ascending group
+// order by the final kernel.
+//
+// Work mapping: a CTA = (query, token group, slice of candidates); a warp
+// takes one candidate document at a time with one lane per document token;
+// each lane loads its token's codes with 16-byte vector loads, its residual
+// norm and its centroid row, and keeps a running max per query token of the
+// group; a butterfly max across the lanes finishes the document.
+#include <cuda_fp16.h>
+
+#include "tachiom_internal.cuh"
+
+namespace tachiom {
+
+constexpr int R_THREADS = 512;
+constexpr int R_DOCS_PER_CTA = 128;
+
+int refine_groups(int M) { return (MAX_NTOK + (128 / M) - 1) / (128 / M); }
+
+__device__ __forceinline__ float half_bits_to_float(uint16_t h) {
+  return __half2float(__ushort_as_half(h));
+}
+
+template <int M, bool BF16C>
+__global__ void __launch_bounds__(R_THREADS, 1)
+k_refine(const float *__restrict__ queries, const int32_t *__restrict__ meta, int nq,
+         const int32_t *__restrict__ cand, int kd, const int64_t *__restrict__ doc_off,
+         const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
+         const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
+         const float *__restrict__ cent_f32, const __nv_bfloat16 *__restrict__ cent_bf16,
+         float *__restrict__ part, int ngroups, int64_t D, uint32_t *__restrict__ flags) {
+  constexpr int G = 128 / M;   // query tokens per CTA
+  constexpr int DS = 128 / M;  // dims per subspace
+  extern __shared__ __align__(16) float rsm[];
+  float *tab = rsm;                   // [M][256][G]
+  float *qs = tab + M * 256 * G;      // [G][128]
+
+  const int q = blockIdx.z, grp = blockIdx.y;
+  const int *qoff = meta;
+  const int ntok = meta[3 * nq + 2 + q];
+  const int i0 = grp * G;
+  if (i0 >= ntok) return;
+  const int ng = min(G, ntok - i0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  const float *qrow = queries + (int64_t)(qoff[q] + i0) * DIM;
+  for (int x = tid; x < G * DIM; x += R_THREADS) qs[x] = (x / DIM < ng) ? qrow[x] : 0.f;
+  __syncthreads();
+  // K0: the group's tables, T[m][j][g] = <q_g^(m), w_{m,j}>
+  for (int mj = tid; mj < M * 256; mj += R_THREADS) {
+    const int m = mj / 256;
+    const float *w = codebooks + (int64_t)mj * DS;
+    float wv[DS];
+#pragma unroll
+    for (int u = 0; u < DS; u++) wv[u] = w[u];
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+      float a = 0.f;
+#pragma unroll
+      for (int u = 0; u < DS; u++) a = fmaf(qs[g * DIM + m * DS + u], wv[u], a);
+      tab[mj * G + g] = a;
+    }
+  }
+  __syncthreads();
+
+  // K4: candidates of this CTA's slice, one warp per document
+  const int s_begin = blockIdx.x * R_DOCS_PER_CTA;
+  const int s_end = min(kd, s_begin + R_DOCS_PER_CTA);
+  for (int slot = s_begin + warp; slot < s_end; slot += R_THREADS / 32) {
+    const int32_t d = cand[(int64_t)q * kd + slot];
+    if (d < 0) continue;
+    if (d >= D) {
+      if (lane == 0) {
+        atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
+        part[((int64_t)q * ngroups + grp) * kd + slot] = 0.f;
+      }
+      continue;
+    }
+    const int64_t tb = doc_off[d], te = doc_off[d + 1];
+    float mx[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) mx[g] = -INFINITY;
+    for (int64_t t = tb + lane; t < te; t += 32) {
+      // codes: M bytes per token, 16-byte vector loads
+      uint8_t cb[M];
+      if constexpr (M == 8) {
+        uint2 v = *reinterpret_cast<const uint2 *>(codes + t * M);
+        *reinterpret_cast<uint2 *>(cb) = v;
+      } else {
+#pragma unroll
+        for (int u = 0; u < M / 16; u++) {
+          uint4 v = *reinterpret_cast<const uint4 *>(codes + t * M + u * 16);
+          *reinterpret_cast<uint4 *>(cb + u * 16) = v;
+        }
+      }
+      const float rho = half_bits_to_float(rnorm[t]);
+      const int32_t j = tok_cid[t];
+      // centroid contribution <q_g, c_j>
+      float ct[G];
+#pragma unroll
+      for (int g = 0; g < G; g++) ct[g] = 0.f;
+      if (BF16C) {
+        const uint4 *crow = reinterpret_cast<const uint4 *>(cent_bf16 + (int64_t)j * DIM);
+#pragma unroll 2
+        for (int k8 = 0; k8 < DIM / 8; k8++) {
+          uint4 u = crow[k8];
+          float c[8] = {__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                        __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u),
+                        __uint_as_float(u.z << 16), __uint_as_float(u.z & 0xffff0000u),
+                        __uint_as_float(u.w << 16), __uint_as_float(u.w & 0xffff0000u)};
+#pragma unroll
+          for (int g = 0; g < G; g++) {
+            const float4 qa = *reinterpret_cast<const float4 *>(&qs[g * DIM + k8 * 8]);
+            const float4 qb = *reinterpret_cast<const float4 *>(&qs[g * DIM + k8 * 8 + 4]);
+            float a = ct[g];
+            a = fmaf(qa.x, c[0], a); a = fmaf(qa.y, c[1], a); a = fmaf(qa.z, c[2], a); a = fmaf(qa.w, c[3], a);
+            a = fmaf(qb.x, c[4], a); a = fmaf(qb.y, c[5], a); a = fmaf(qb.z, c[6], a); a = fmaf(qb.w, c[7], a);
+            ct[g] = a;
+          }
+        }
+      } else {
+        const float4 *crow = reinterpret_cast<const float4 *>(cent_f32 + (int64_t)j * DIM);
+#pragma unroll 4
+        for (int k4 = 0; k4 < DIM / 4; k4++) {
+          float4 c = crow[k4];
+#pragma unroll
+          for (int g = 0; g < G; g++) {
+            const float4 qa = *reinterpret_cast<const float4 *>(&qs[g * DIM + k4 * 4]);
+            float a = ct[g];
+            a = fmaf(qa.x, c.x, a); a = fmaf(qa.y, c.y, a); a = fmaf(qa.z, c.z, a); a = fmaf(qa.w, c.w, a);
+            ct[g] = a;
+          }
+        }
+      }
+      // residual contribution from the tables (micro-block of G query tokens per code)
+      float rs[G];
+#pragma unroll
+      for (int g = 0; g < G; g++) rs[g] = 0.f;
+#pragma unroll
+      for (int m = 0; m < M; m++) {
+        const float *blk = tab + (m * 256 + cb[m]) * G;
+        if constexpr (G % 4 == 0) {
+#pragma unroll
+          for (int g4 = 0; g4 < G / 4; g4++) {
+            float4 v = *reinterpret_cast<const float4 *>(blk + g4 * 4);
+            rs[g4 * 4 + 0] += v.x; rs[g4 * 4 + 1] += v.y; rs[g4 * 4 + 2] += v.z; rs[g4 * 4 + 3] += v.w;
+          }
+        } else {
+#pragma unroll
+          for (int g = 0; g < G; g++) rs[g] += blk[g];
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < G; g++) mx[g] = fmaxf(mx[g], fmaf(rho, rs[g], ct[g]));
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx[g] = fmaxf(mx[g], __shfl_xor_sync(0xffffffffu, mx[g], o));
+    }
+    if (lane == 0) {
+      float sum = 0.f;
+      if (te > tb) {
+#pragma unroll
+        for (int g = 0; g < G; g++)
+          if (g < ng) sum += mx[g];
+      }
+      part[((int64_t)q * ngroups + grp) * kd + slot] = sum;
+    }
+  }
+}
+
+template <int M>
+static tachiom_status launch_refine_m(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                      const int32_t *cand, int kd, float *part, uint32_t *flags,
+                                      cudaStream_t s) {
+  constexpr int G = 128 / M;
+  const int ngroups = refine_groups(M);
+  size_t smem = ((size_t)M * 256 * G + (size_t)G * DIM) * 4;
+  dim3 grid((kd + R_DOCS_PER_CTA - 1) / R_DOCS_PER_CTA, ngroups, nq);
+  if (ix.cdtype == TACHIOM_DTYPE_BF16) {
+    TCUDA(cudaFuncSetAttribute(k_refine<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_refine<M, true><<<grid, R_THREADS, smem, s>>>(queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid,
+                                                     ix.codes, ix.rnorm, ix.codebooks, ix.cent_f32,
+                                                     ix.cent_bf16, part, ngroups, ix.D, flags);
+  } else {
+    TCUDA(cudaFuncSetAttribute(k_refine<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_refine<M, false><<<grid, R_THREADS, smem, s>>>(queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid,
+                                                      ix.codes, ix.rnorm, ix.codebooks, ix.cent_f32,
+                                                      ix.cent_bf16, part, ngroups, ix.D, flags);
+  }
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
+tachiom_status launch_refine(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                             const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s) {
+  if (nq <= 0) return TACHIOM_OK;
+  TPROF("refine", s);
+  switch (ix.M) {
+    case 8: return launch_refine_m<8>(ix, queries, meta, nq, cand, kd, part, flags, s);
+    case 16: return launch_refine_m<16>(ix, queries, meta, nq, cand, kd, part, flags, s);
+    case 32: return launch_refine_m<32>(ix, queries, meta, nq, cand, kd, part, flags, s);
+  }
+  return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
+}
+
+// ---------------------------------------------------------------------------------
+// step (d): S = sum of the group partials (ascending group), then the first k by
+// (S desc, doc asc); rows padded with (-1, -inf)
+__global__ void __launch_bounds__(1024)
+k_final_topk(const int32_t *__restrict__ meta, int nq, const int32_t *__restrict__ cand, int kd,
+             const float *__restrict__ part, int ngroups, int G, int32_t *__restrict__ out_ids,
+             float *__restrict__ out_s) {
+  extern __shared__ __align__(16) uint64_t fsm[];
+  const int q = blockIdx.x;
+  const int ntok = meta[3 * nq + 2 + q];
+  const int k = meta[2 * nq + 2 + q];
+  const int koff = meta[nq + 1 + q];
+  const int gq = (ntok + G - 1) / G;
+  const int np = next_pow2(max(kd, 2));
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    uint64_t v = 0ull;
+    if (i < kd) {
+      int32_t d = cand[(int64_t)q * kd + i];
+      if (d >= 0) {
+        float s = 0.f;
+        for (int g = 0; g < gq; g++) s += part[((int64_t)q * ngroups + g) * kd + i];
+        v = comp_key(s, d);
+      }
+    }
+    fsm[i] = v;
+  }
+  __syncthreads();
+  block_sort_desc(fsm, np);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    uint64_t v = i < np ? fsm[i] : 0ull;
+    out_ids[koff + i] = v ? comp_id(v) : -1;
+    out_s[koff + i] = v ? comp_score(v) : -INFINITY;
+  }
+}
+
+tachiom_status launch_final_topk(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
+                                 const float *part, int32_t *out_ids, float *out_s, cudaStream_t s) {
+  if (nq <= 0) return TACHIOM_OK;
+  TPROF("final_topk", s);
+  size_t smem = (size_t)next_pow2(std::max(kd, 2)) * 8;
+  TCUDA(cudaFuncSetAttribute(k_final_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_final_topk<<<nq, 1024, smem, s>>>(meta, nq, cand, kd, part, refine_groups(ix.M), 128 / ix.M, out_ids,
+                                      out_s);
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
+}  // namespace tachiom

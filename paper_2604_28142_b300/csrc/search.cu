@@ -1,0 +1,492 @@
+// Search orchestration: per-stream scratch, launch plans, and the C-ABI
+// entry points that run steps (a)-(d) of Sec. 2.2 on one stream.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "tachiom_internal.cuh"
+
+namespace tachiom {
+
+// ---- workspace ---------------------------------------------------------------------
+void ws_destroy(Workspace *w) {
+  if (!w) return;
+  for (void *p : w->blocks) cudaFree(p);
+  if (w->h_meta) cudaFreeHost(w->h_meta);
+  if (w->h_rows) cudaFreeHost(w->h_rows);
+  if (w->h_out_ids) cudaFreeHost(w->h_out_ids);
+  if (w->h_out_s) cudaFreeHost(w->h_out_s);
+  if (w->meta_done) cudaEventDestroy(w->meta_done);
+  delete w;
+}
+
+tachiom_status ws_get(Index *ix, cudaStream_t stream, Workspace **out) {
+  std::lock_guard<std::mutex> g(ix->mu);
+  auto it = ix->ws.find(stream);
+  if (it != ix->ws.end()) {
+    *out = it->second;
+    return TACHIOM_OK;
+  }
+  Workspace *w = new Workspace();
+  w->stream = stream;
+  w->device = ix->device;
+  if (cudaEventCreateWithFlags(&w->meta_done, cudaEventDisableTiming) != cudaSuccess) {
+    delete w;
+    return fail(TACHIOM_ERR_CUDA, "cudaEventCreate failed");
+  }
+  if (cudaMalloc(&w->d_flags, 4) != cudaSuccess || cudaMemset(w->d_flags, 0, 4) != cudaSuccess) {
+    cudaGetLastError();
+    ws_destroy(w);
+    return fail(TACHIOM_ERR_OOM, "cudaMalloc of the status word failed");
+  }
+  w->blocks.push_back(w->d_flags);
+  ix->ws[stream] = w;
+  *out = w;
+  return TACHIOM_OK;
+}
+
+struct Need {
+  int64_t nq = 0, rows = 0, kc = 0, kd = 0, split_entries = 0, dense = 0;
+};
+
+// (Re)allocate the device scratch for a batch. Growth synchronises the stream
+// first, so memory still in use by earlier work on it is never freed early.
+static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
+  bool grow = n.nq > w->cap_q || n.rows > w->cap_rows || n.kc > w->cap_kc || n.kd > w->cap_kd ||
+              n.split_entries > w->cap_split_entries || n.dense > w->cap_dense;
+  if (!grow) return TACHIOM_OK;
+  TCUDA(cudaStreamSynchronize(w->stream));
+  for (void *p : w->blocks)
+    if (p != w->d_flags) cudaFree(p);
+  w->blocks.clear();
+  w->blocks.push_back(w->d_flags);
+  int64_t nq = std::max<int64_t>(n.nq, w->cap_q), rows = std::max<int64_t>(n.rows, w->cap_rows);
+  int64_t kc = std::max<int64_t>(n.kc, w->cap_kc), kd = std::max<int64_t>(n.kd, w->cap_kd);
+  int64_t se = std::max<int64_t>(n.split_entries, w->cap_split_entries);
+  int64_t dn = std::max<int64_t>(n.dense, w->cap_dense);
+  const int groups = refine_groups(32);  // the largest group count of any pq_m
+  auto al = [&](void **p, size_t bytes) -> tachiom_status {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TACHIOM_ERR_OOM, "scratch allocation of %zu bytes failed", bytes);
+    }
+    w->blocks.push_back(*p);
+    return TACHIOM_OK;
+  };
+  tachiom_status st;
+#define AL(ptr, bytes)                               \
+  if ((st = al((void **)&(ptr), (size_t)(bytes)))) { \
+    w->cap_q = w->cap_rows = 0;                      \
+    return st;                                       \
+  }
+  AL(w->d_meta, (4 * nq + 2) * 4);
+  AL(w->d_rows_f32, rows * DIM * 4);
+  AL(w->d_rows_bf16, rows * DIM * 2);
+  AL(w->d_split, se * 8);
+  AL(w->d_split_cnt, (se + rows) * 4);
+  AL(w->d_top_ids, rows * kc * 4);
+  AL(w->d_top_s, rows * kc * 4);
+  AL(w->d_dense, dn * 4);
+  AL(w->d_hist, nq * NBINS1 * 4);
+  AL(w->d_hist2, nq * NBINS1 * 4);
+  AL(w->d_selstate, nq * 8 * 4);
+  AL(w->d_selbuf, nq * (int64_t)SEL_CAP * 8);
+  AL(w->d_cand, nq * kd * 4);
+  AL(w->d_cand_s, nq * kd * 4);
+  AL(w->d_ncand, nq * 4);
+  AL(w->d_part, nq * groups * kd * 4);
+  AL(w->d_out_ids, nq * kd * 4);
+  AL(w->d_out_s, nq * kd * 4);
+#undef AL
+  w->cap_q = nq;
+  w->cap_rows = rows;
+  w->cap_kc = kc;
+  w->cap_kd = kd;
+  w->cap_split_entries = se;
+  w->cap_dense = dn;
+  return TACHIOM_OK;
+}
+
+static tachiom_status host_reserve(Workspace *w, int64_t meta_ints) {
+  if (meta_ints <= w->cap_meta) return TACHIOM_OK;
+  if (w->h_meta) {
+    cudaEventSynchronize(w->meta_done);
+    cudaFreeHost(w->h_meta);
+  }
+  w->h_meta = nullptr;
+  w->cap_meta = 0;
+  if (cudaMallocHost((void **)&w->h_meta, (size_t)meta_ints * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TACHIOM_ERR_OOM, "pinned host allocation failed");
+  }
+  w->cap_meta = meta_ints;
+  return TACHIOM_OK;
+}
+
+// ---- plan -----------------------------------------------------------------------------
+struct Plan {
+  int splits;   // centroid slices of step (a)
+  int capout;   // survivors a slice hands to the merge, per row
+};
+
+static int sm_count(int dev) {
+  static int cached[64] = {0};
+  if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+  int n = 148;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  if (dev >= 0 && dev < 64) cached[dev] = n;
+  return n;
+}
+
+static Plan make_plan(const Index &ix, int rows, int kc, int precision, int plan_id) {
+  Plan p;
+  const int sms = sm_count(ix.device);
+  const int row_tiles = (rows + 31) / 32;
+  // enough CTAs for two waves, each slice at least one 128-centroid tile
+  int splits = std::max(1, (2 * sms + row_tiles - 1) / row_tiles);
+  int64_t max_splits = (ix.C + 127) / 128;
+  splits = (int)std::min<int64_t>(splits, max_splits);
+  p.capout = kc + 64;
+  splits = std::min(splits, std::max(1, 16384 / p.capout));
+  if (plan_id >= 0) {
+    // plan_id encodes an explicit slice count (autotuner)
+    splits = std::max(1, std::min(plan_id, (int)std::min<int64_t>(max_splits, 16384 / p.capout)));
+  }
+  p.splits = splits;
+  (void)precision;
+  return p;
+}
+
+struct Batch {
+  int nq = 0;
+  int rows = 0;
+  int max_k = 0;
+  int64_t total_k = 0;
+};
+
+static tachiom_status check_batch(const int32_t *h_ntok, const int32_t *h_k, int nq, int kd_limit,
+                                  Batch *b) {
+  if (nq < 0) return fail(TACHIOM_ERR_INVALID, "nq < 0");
+  if (nq > 0 && !h_ntok) return fail(TACHIOM_ERR_INVALID, "h_ntok is NULL");
+  b->nq = nq;
+  int64_t rows = 0, tk = 0;
+  int mk = 0;
+  for (int i = 0; i < nq; i++) {
+    if (h_ntok[i] < 1 || h_ntok[i] > MAX_NTOK)
+      return fail(TACHIOM_ERR_INVALID, "ntok[%d] = %d out of [1, %d]", i, h_ntok[i], MAX_NTOK);
+    rows += h_ntok[i];
+    if (h_k) {
+      if (h_k[i] < 1 || (kd_limit > 0 && h_k[i] > kd_limit))
+        return fail(TACHIOM_ERR_INVALID, "k[%d] = %d out of [1, kappa_d]", i, h_k[i]);
+      tk += h_k[i];
+      mk = std::max(mk, h_k[i]);
+    }
+  }
+  if (rows > (1 << 30) || tk > (1LL << 31) - 1) return fail(TACHIOM_ERR_CAPACITY, "batch too large");
+  b->rows = (int)rows;
+  b->total_k = tk;
+  b->max_k = mk;
+  return TACHIOM_OK;
+}
+
+static tachiom_status check_params(const tachiom_search_params *p) {
+  if (!p) return fail(TACHIOM_ERR_INVALID, "params is NULL");
+  if (p->kappa_c < 1 || p->kappa_c > MAX_KC)
+    return fail(TACHIOM_ERR_INVALID, "kappa_c = %d out of [1, %d]", p->kappa_c, MAX_KC);
+  if (p->kappa_d < 0 || p->kappa_d > MAX_KD)
+    return fail(TACHIOM_ERR_INVALID, "kappa_d = %d out of [0, %d]", p->kappa_d, MAX_KD);
+  if (p->precision != TACHIOM_PREC_FP32 && p->precision != TACHIOM_PREC_BF16)
+    return fail(TACHIOM_ERR_INVALID, "unknown precision %d", p->precision);
+  return TACHIOM_OK;
+}
+
+static int resolve_kd(const tachiom_search_params *p, int max_k) {
+  if (p->kappa_d > 0) return p->kappa_d;
+  return std::min(MAX_KD, std::max(1000, 4 * max_k));
+}
+
+// upload qoff | koff | k | ntok through pinned staging
+static tachiom_status upload_meta(Workspace *w, const int32_t *h_ntok, const int32_t *h_k, int nq) {
+  tachiom_status st = host_reserve(w, 4 * (int64_t)nq + 2);
+  if (st) return st;
+  TCUDA(cudaEventSynchronize(w->meta_done));
+  int32_t *m = w->h_meta;
+  m[0] = 0;
+  m[nq + 1] = 0;
+  for (int i = 0; i < nq; i++) {
+    m[i + 1] = m[i] + h_ntok[i];
+    int k = h_k ? h_k[i] : 0;
+    m[nq + 2 + i] = m[nq + 1 + i] + k;
+    m[2 * nq + 2 + i] = k;
+    m[3 * nq + 2 + i] = h_ntok[i];
+  }
+  TCUDA(cudaMemcpyAsync(w->d_meta, m, (size_t)(4 * nq + 2) * 4, cudaMemcpyHostToDevice, w->stream));
+  TCUDA(cudaEventRecord(w->meta_done, w->stream));
+  return TACHIOM_OK;
+}
+
+// step (a) into w->d_top_ids / d_top_s
+static tachiom_status run_topc(Index *ix, Workspace *w, const tachiom_search_params *p, const float *rows,
+                               int nrows, const Plan &plan) {
+  const int kc = p->kappa_c;
+  tachiom_status st;
+  if (p->precision == TACHIOM_PREC_BF16 && topc_tc_supported()) {
+    if ((st = launch_quantize_bf16(rows, w->d_rows_bf16, (int64_t)nrows * DIM, w->stream))) return st;
+    // per-score error of BF16 queries times exact or BF16 centroids: |e| <= 2^-8 * ||c_j||
+    // (both operands rounded, unit-norm query) plus FP32 accumulation; the window is twice it
+    const float delta = ldexpf(1.f, -8) * ix->cnorm_max + 1e-5f;
+    if ((st = launch_topc_tc(*ix, w->d_rows_bf16, nrows, kc, plan.splits, plan.capout, 2.f * delta,
+                             w->d_split, w->d_split_cnt, w->d_flags, w->stream)))
+      return st;
+    return launch_topc_merge(*ix, rows, nrows, kc, plan.splits, plan.capout, w->d_split, w->d_split_cnt,
+                             2.f * delta, 1, w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
+  }
+  if ((st = launch_topc_f32(*ix, rows, nrows, kc, plan.splits, plan.capout, w->d_split, w->d_split_cnt,
+                            w->d_flags, w->stream)))
+    return st;
+  return launch_topc_merge(*ix, rows, nrows, kc, plan.splits, plan.capout, w->d_split, w->d_split_cnt, 0.f, 0,
+                           w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+static tachiom_status search_device(Index *ix, const tachiom_search_params *p, const float *d_queries,
+                                    const int32_t *h_ntok, const int32_t *h_k, int nq, int32_t *d_out_ids,
+                                    float *d_out_scores, cudaStream_t stream, Workspace **wout) {
+  tachiom_status st;
+  if ((st = check_params(p))) return st;
+  Batch b;
+  if ((st = check_batch(h_ntok, h_k, nq, 0, &b))) return st;
+  if (nq > 0 && !h_k) return fail(TACHIOM_ERR_INVALID, "h_k is NULL");
+  const int kd = resolve_kd(p, b.max_k);
+  if (b.max_k > kd) return fail(TACHIOM_ERR_INVALID, "k (%d) > kappa_d (%d)", b.max_k, kd);
+  if (nq > 0 && (!d_queries || !d_out_ids || !d_out_scores))
+    return fail(TACHIOM_ERR_INVALID, "NULL device buffer");
+  Workspace *w;
+  if ((st = ws_get(ix, stream, &w))) return st;
+  if (wout) *wout = w;
+  if (nq == 0) return TACHIOM_OK;
+  Plan plan = make_plan(*ix, b.rows, p->kappa_c, p->precision, p->plan_id);
+  Need n;
+  n.nq = nq;
+  n.rows = b.rows;
+  n.kc = p->kappa_c;
+  n.kd = kd;
+  n.split_entries = (int64_t)b.rows * plan.splits * plan.capout;
+  n.dense = (int64_t)nq * ix->D;
+  if ((st = ws_reserve(ix, w, n))) return st;
+  if ((st = upload_meta(w, h_ntok, h_k, nq))) return st;
+  if ((st = run_topc(ix, w, p, d_queries, b.rows, plan))) return st;
+  if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, p->kappa_c, w->d_dense, w->d_hist,
+                          w->d_flags, stream)))
+    return st;
+  if ((st = launch_select_kd(*ix, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
+                             w->d_cand, w->d_cand_s, w->d_ncand, w->d_flags, stream)))
+    return st;
+  if ((st = launch_refine(*ix, d_queries, w->d_meta, nq, w->d_cand, kd, w->d_part, w->d_flags, stream)))
+    return st;
+  return launch_final_topk(*ix, w->d_meta, nq, w->d_cand, kd, w->d_part, d_out_ids, d_out_scores, stream);
+}
+
+}  // namespace tachiom
+
+using namespace tachiom;
+
+static Index *as_index(tachiom_index *p) { return reinterpret_cast<Index *>(p); }
+
+extern "C" tachiom_status tachiom_search(tachiom_index *index, const tachiom_search_params *params,
+                                         const float *d_queries, const int32_t *h_ntok, const int32_t *h_k,
+                                         int32_t nq, int32_t *d_out_ids, float *d_out_scores, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
+  DeviceGuard g(ix->device);
+  return search_device(ix, params, d_queries, h_ntok, h_k, nq, d_out_ids, d_out_scores,
+                       (cudaStream_t)stream, nullptr);
+}
+
+extern "C" tachiom_status tachiom_search_host(tachiom_index *index, const tachiom_search_params *params,
+                                              const float *h_queries, const int32_t *h_ntok,
+                                              const int32_t *h_k, int32_t nq, int32_t *h_out_ids,
+                                              float *h_out_scores, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
+  DeviceGuard g(ix->device);
+  tachiom_status st;
+  if ((st = check_params(params))) return st;
+  Batch b;
+  if ((st = check_batch(h_ntok, h_k, nq, 0, &b))) return st;
+  if (nq == 0) return TACHIOM_OK;
+  if (!h_queries || !h_k || !h_out_ids || !h_out_scores) return fail(TACHIOM_ERR_INVALID, "NULL host buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w;
+  if ((st = ws_get(ix, s, &w))) return st;
+  const int kd = resolve_kd(params, b.max_k);
+  Plan plan = make_plan(*ix, b.rows, params->kappa_c, params->precision, params->plan_id);
+  Need n;
+  n.nq = nq;
+  n.rows = b.rows;
+  n.kc = params->kappa_c;
+  n.kd = std::max<int64_t>(kd, (b.total_k + nq - 1) / nq + 1);
+  n.split_entries = (int64_t)b.rows * plan.splits * plan.capout;
+  n.dense = (int64_t)nq * ix->D;
+  if ((st = ws_reserve(ix, w, n))) return st;
+  if (b.total_k > w->cap_q * w->cap_kd) return fail(TACHIOM_ERR_CAPACITY, "sum(k) beyond scratch");
+  // pinned staging for queries and results
+  int64_t qbytes = (int64_t)b.rows * DIM;
+  if (qbytes > w->cap_h_rows) {
+    TCUDA(cudaStreamSynchronize(s));
+    if (w->h_rows) cudaFreeHost(w->h_rows);
+    w->h_rows = nullptr;
+    w->cap_h_rows = 0;
+    if (cudaMallocHost((void **)&w->h_rows, (size_t)qbytes * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TACHIOM_ERR_OOM, "pinned host allocation failed");
+    }
+    w->cap_h_rows = qbytes;
+  }
+  if (b.total_k > w->cap_h_out) {
+    TCUDA(cudaStreamSynchronize(s));
+    if (w->h_out_ids) cudaFreeHost(w->h_out_ids);
+    if (w->h_out_s) cudaFreeHost(w->h_out_s);
+    w->h_out_ids = nullptr;
+    w->h_out_s = nullptr;
+    w->cap_h_out = 0;
+    if (cudaMallocHost((void **)&w->h_out_ids, (size_t)b.total_k * 4) != cudaSuccess ||
+        cudaMallocHost((void **)&w->h_out_s, (size_t)b.total_k * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TACHIOM_ERR_OOM, "pinned host allocation failed");
+    }
+    w->cap_h_out = b.total_k;
+  }
+  TCUDA(cudaStreamSynchronize(s));
+  memcpy(w->h_rows, h_queries, (size_t)qbytes * 4);
+  TCUDA(cudaMemcpyAsync(w->d_rows_f32, w->h_rows, (size_t)qbytes * 4, cudaMemcpyHostToDevice, s));
+  if ((st = search_device(ix, params, w->d_rows_f32, h_ntok, h_k, nq, w->d_out_ids, w->d_out_s, s, nullptr)))
+    return st;
+  TCUDA(cudaMemcpyAsync(w->h_out_ids, w->d_out_ids, (size_t)b.total_k * 4, cudaMemcpyDeviceToHost, s));
+  TCUDA(cudaMemcpyAsync(w->h_out_s, w->d_out_s, (size_t)b.total_k * 4, cudaMemcpyDeviceToHost, s));
+  TCUDA(cudaStreamSynchronize(s));
+  memcpy(h_out_ids, w->h_out_ids, (size_t)b.total_k * 4);
+  memcpy(h_out_scores, w->h_out_s, (size_t)b.total_k * 4);
+  return TACHIOM_OK;
+}
+
+extern "C" tachiom_status tachiom_top_centroids(tachiom_index *index, const tachiom_search_params *params,
+                                                const float *d_rows, int32_t nrows, int32_t *d_top_ids,
+                                                float *d_top_scores, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
+  DeviceGuard g(ix->device);
+  tachiom_status st;
+  if ((st = check_params(params))) return st;
+  if (nrows < 0) return fail(TACHIOM_ERR_INVALID, "nrows < 0");
+  if (nrows == 0) return TACHIOM_OK;
+  if (!d_rows || !d_top_ids || !d_top_scores) return fail(TACHIOM_ERR_INVALID, "NULL device buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w;
+  if ((st = ws_get(ix, s, &w))) return st;
+  Plan plan = make_plan(*ix, nrows, params->kappa_c, params->precision, params->plan_id);
+  Need n;
+  n.nq = 1;
+  n.rows = nrows;
+  n.kc = params->kappa_c;
+  n.kd = 1;
+  n.split_entries = (int64_t)nrows * plan.splits * plan.capout;
+  n.dense = 0;
+  if ((st = ws_reserve(ix, w, n))) return st;
+  if ((st = run_topc(ix, w, params, d_rows, nrows, plan))) return st;
+  TCUDA(cudaMemcpyAsync(d_top_ids, w->d_top_ids, (size_t)nrows * params->kappa_c * 4, cudaMemcpyDeviceToDevice, s));
+  TCUDA(cudaMemcpyAsync(d_top_scores, w->d_top_s, (size_t)nrows * params->kappa_c * 4, cudaMemcpyDeviceToDevice, s));
+  return TACHIOM_OK;
+}
+
+extern "C" tachiom_status tachiom_gather(tachiom_index *index, const tachiom_search_params *params,
+                                         const float *d_queries, const int32_t *h_ntok, int32_t nq,
+                                         const int32_t *d_top_ids, int32_t *d_cand_ids, float *d_cand_scores,
+                                         int32_t *d_ncand, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
+  DeviceGuard g(ix->device);
+  tachiom_status st;
+  if ((st = check_params(params))) return st;
+  Batch b;
+  if ((st = check_batch(h_ntok, nullptr, nq, 0, &b))) return st;
+  if (nq == 0) return TACHIOM_OK;
+  if (!d_queries || !d_top_ids || !d_cand_ids || !d_cand_scores || !d_ncand)
+    return fail(TACHIOM_ERR_INVALID, "NULL device buffer");
+  const int kd = resolve_kd(params, 0);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w;
+  if ((st = ws_get(ix, s, &w))) return st;
+  Need n;
+  n.nq = nq;
+  n.rows = b.rows;
+  n.kc = params->kappa_c;
+  n.kd = kd;
+  n.dense = (int64_t)nq * ix->D;
+  if ((st = ws_reserve(ix, w, n))) return st;
+  if ((st = upload_meta(w, h_ntok, nullptr, nq))) return st;
+  if ((st = launch_score_pairs(*ix, d_queries, b.rows, d_top_ids, params->kappa_c, w->d_top_s, s))) return st;
+  if ((st = launch_gather(*ix, w->d_meta, nq, d_top_ids, w->d_top_s, params->kappa_c, w->d_dense, w->d_hist,
+                          w->d_flags, s)))
+    return st;
+  return launch_select_kd(*ix, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
+                          d_cand_ids, d_cand_scores, d_ncand, w->d_flags, s);
+}
+
+extern "C" tachiom_status tachiom_refine(tachiom_index *index, const tachiom_search_params *params,
+                                         const float *d_queries, const int32_t *h_ntok, const int32_t *h_k,
+                                         int32_t nq, const int32_t *d_cand_ids, int32_t *d_out_ids,
+                                         float *d_out_scores, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
+  DeviceGuard g(ix->device);
+  tachiom_status st;
+  if ((st = check_params(params))) return st;
+  Batch b;
+  if ((st = check_batch(h_ntok, h_k, nq, 0, &b))) return st;
+  if (nq == 0) return TACHIOM_OK;
+  if (!h_k) return fail(TACHIOM_ERR_INVALID, "h_k is NULL");
+  const int kd = resolve_kd(params, b.max_k);
+  if (b.max_k > kd) return fail(TACHIOM_ERR_INVALID, "k > kappa_d");
+  if (!d_queries || !d_cand_ids || !d_out_ids || !d_out_scores) return fail(TACHIOM_ERR_INVALID, "NULL device buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w;
+  if ((st = ws_get(ix, s, &w))) return st;
+  Need n;
+  n.nq = nq;
+  n.rows = b.rows;
+  n.kc = params->kappa_c;
+  n.kd = kd;
+  if ((st = ws_reserve(ix, w, n))) return st;
+  if ((st = upload_meta(w, h_ntok, h_k, nq))) return st;
+  if ((st = launch_refine(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, w->d_part, w->d_flags, s))) return st;
+  return launch_final_topk(*ix, w->d_meta, nq, d_cand_ids, kd, w->d_part, d_out_ids, d_out_scores, s);
+}
+
+extern "C" tachiom_status tachiom_stream_status(tachiom_index *index, void *stream, uint32_t *h_flags) {
+  Index *ix = as_index(index);
+  if (!ix || !h_flags) return fail(TACHIOM_ERR_INVALID, "NULL argument");
+  DeviceGuard g(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w;
+  tachiom_status st;
+  if ((st = ws_get(ix, s, &w))) return st;
+  TCUDA(cudaStreamSynchronize(s));
+  TCUDA(cudaMemcpy(h_flags, w->d_flags, 4, cudaMemcpyDeviceToHost));
+  TCUDA(cudaMemset(w->d_flags, 0, 4));
+  return TACHIOM_OK;
+}

@@ -1,0 +1,219 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/tachiom.h"
+
+namespace tachiom {
+
+constexpr int DIM = 128;
+constexpr int MAX_NTOK = 32;   // query tokens per query
+constexpr int MAX_KC = 128;    // kappa_c
+constexpr int MAX_KD = 4096;   // kappa_d
+constexpr int NBINS1 = 4096;   // first-level histogram of the kappa_d selection
+constexpr int SEL_CAP = 16384; // candidates a query's exact kappa_d sort takes at once
+
+// ---- errors -----------------------------------------------------------------
+void set_error(const char *fmt, ...);
+tachiom_status fail(tachiom_status st, const char *fmt, ...);
+
+#define TCUDA(call)                                                                    \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return ::tachiom::fail(TACHIOM_ERR_CUDA, "%s failed: %s (%s:%d)", #call,         \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);              \
+  } while (0)
+
+#define TLAUNCH()                                                                      \
+  do {                                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                               \
+    if (e_ != cudaSuccess)                                                             \
+      return ::tachiom::fail(TACHIOM_ERR_CUDA, "kernel launch failed: %s (%s:%d)",     \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);              \
+  } while (0)
+
+// ---- ordered keys --------------------------------------------------------------
+// fkey maps float order onto uint32 order (0 is never produced: it marks "empty").
+__device__ __forceinline__ uint32_t fkey(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float funkey(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+// (score desc, id asc) as one descending uint64; 0 sorts after every real entry.
+__device__ __forceinline__ uint64_t comp_key(float s, int32_t id) {
+  return ((uint64_t)fkey(s) << 32) | (uint32_t)(~(uint32_t)id);
+}
+__device__ __forceinline__ int32_t comp_id(uint64_t c) { return (int32_t)(~(uint32_t)(c & 0xffffffffu)); }
+__device__ __forceinline__ float comp_score(uint64_t c) { return funkey((uint32_t)(c >> 32)); }
+
+// Descending bitonic sort of n (power of two) uint64 in shared memory by the whole block.
+__device__ __forceinline__ void block_sort_desc(uint64_t *a, int n) {
+  for (int k = 2; k <= n; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          uint64_t x = a[i], y = a[l];
+          bool desc = (i & k) == 0;
+          if (desc ? (x < y) : (x > y)) { a[i] = y; a[l] = x; }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// Same, by one warp (lane stride), for n <= a few hundred.
+__device__ __forceinline__ void warp_sort_desc(uint64_t *a, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 2; k <= n; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < n; i += 32) {
+        int l = i ^ j;
+        if (l > i) {
+          uint64_t x = a[i], y = a[l];
+          bool desc = (i & k) == 0;
+          if (desc ? (x < y) : (x > y)) { a[i] = y; a[l] = x; }
+        }
+      }
+      __syncwarp();
+    }
+}
+
+__host__ __device__ inline int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// ---- index ------------------------------------------------------------------------
+struct Workspace;
+
+struct Index {
+  int device = 0;
+  int64_t C = 0, D = 0, T = 0;
+  int M = 16, ds = 8;
+  int cdtype = TACHIOM_DTYPE_F32;
+  float *cent_f32 = nullptr;            // [C x 128] FP32 values of the stored centroids
+  __nv_bfloat16 *cent_bf16 = nullptr;   // [C x 128] BF16 operand of the tensor-core path
+  float cnorm_max = 0.f;                // max_j ||c_j|| (error bound of the BF16 path)
+  int32_t *cent_type = nullptr;         // [C] or null
+  int64_t *doc_off = nullptr;           // [D+1]
+  int32_t *tok_cid = nullptr;           // [T]
+  uint8_t *codes = nullptr;             // [T x M]
+  uint16_t *rnorm = nullptr;            // [T] fp16 bits (1.0 everywhere when absent)
+  float *codebooks = nullptr;           // [M x 256 x ds]
+  int64_t *list_off = nullptr;          // [C+1]
+  int32_t *list_doc = nullptr;          // [n_list]
+  int64_t n_list = 0;
+  int range_docs = 0;                   // documents per gather range
+  int n_ranges = 0;
+  int32_t *list_roff = nullptr;         // [C x (n_ranges+1)] offset in L_j of the first doc
+                                        // of each range
+  size_t device_bytes = 0;
+  std::mutex mu;
+  std::unordered_map<cudaStream_t, Workspace *> ws;
+};
+
+// scratch of one stream, grown on demand
+struct Workspace {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<void *> blocks;          // device allocations, freed with the workspace
+  // capacities
+  int64_t cap_rows = 0, cap_q = 0, cap_kc = 0, cap_kd = 0, cap_split_entries = 0;
+  int64_t cap_dense = 0;
+  // device buffers
+  int32_t *d_meta = nullptr;           // qoff [B+1] | koff [B+1] | k [B] | ntok [B]
+  float *d_rows_f32 = nullptr;         // staging of host queries (search_host)
+  __nv_bfloat16 *d_rows_bf16 = nullptr;// [rows x 128]
+  uint64_t *d_split = nullptr;         // [rows x splits x capout] candidates of step (a)
+  int32_t *d_split_cnt = nullptr;      // [rows x splits]
+  int32_t *d_top_ids = nullptr;        // [rows x kc]
+  float *d_top_s = nullptr;            // [rows x kc]
+  float *d_dense = nullptr;            // [B x D] S~ per query (-inf: not reached)
+  uint32_t *d_hist = nullptr;          // [B x NBINS1]
+  uint32_t *d_hist2 = nullptr;         // [B x NBINS1]
+  uint32_t *d_selstate = nullptr;      // [B x 8]
+  uint64_t *d_selbuf = nullptr;        // [B x SEL_CAP]
+  int32_t *d_cand = nullptr;           // [B x kd]
+  float *d_cand_s = nullptr;           // [B x kd]
+  int32_t *d_ncand = nullptr;          // [B]
+  float *d_part = nullptr;             // [B x groups x kd] refine partial sums
+  int32_t *d_out_ids = nullptr;        // staging for search_host
+  float *d_out_s = nullptr;
+  uint32_t *d_flags = nullptr;         // status word
+  // host pinned staging
+  int32_t *h_meta = nullptr;
+  int64_t cap_meta = 0;
+  float *h_rows = nullptr;
+  int64_t cap_h_rows = 0;
+  int32_t *h_out_ids = nullptr;
+  float *h_out_s = nullptr;
+  int64_t cap_h_out = 0;
+  cudaEvent_t meta_done = nullptr;     // host staging reusable once this fires
+};
+
+// lifecycle helpers (search.cu)
+tachiom_status ws_get(Index *ix, cudaStream_t stream, Workspace **out);
+void ws_destroy(Workspace *w);
+
+// ---- per-launcher timing (tachiom_profile_enable) -----------------------------------
+class ProfScope {
+ public:
+  ProfScope(const char *name, cudaStream_t s);
+  ~ProfScope();
+
+ private:
+  const char *name_;
+  cudaStream_t s_;
+  void *a_;
+};
+#define TPROF_CAT2(a, b) a##b
+#define TPROF_CAT(a, b) TPROF_CAT2(a, b)
+#define TPROF(name, s) ::tachiom::ProfScope TPROF_CAT(prof_scope_, __LINE__)(name, s)
+
+// ---- kernel launchers (one per translation unit) -----------------------------------
+// step (a)
+tachiom_status launch_quantize_bf16(const float *rows, __nv_bfloat16 *out, int64_t n, cudaStream_t s);
+tachiom_status launch_topc_f32(const Index &ix, const float *rows, int nrows, int kc, int splits,
+                               int capout, uint64_t *split, int32_t *split_cnt, uint32_t *flags,
+                               cudaStream_t s);
+tachiom_status launch_topc_merge(const Index &ix, const float *rows, int nrows, int kc, int splits,
+                                 int capout, const uint64_t *split, const int32_t *split_cnt,
+                                 float margin, int rescore, int32_t *top_ids, float *top_s,
+                                 uint32_t *flags, cudaStream_t s);
+tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc,
+                              int splits, int capout, float margin, uint64_t *split,
+                              int32_t *split_cnt, uint32_t *flags, cudaStream_t s);
+int topc_tc_supported();
+tachiom_status launch_score_pairs(const Index &ix, const float *rows, int nrows, const int32_t *ids,
+                                  int kc, float *scores, cudaStream_t s);
+// step (b)
+tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, const int32_t *top_ids,
+                             const float *top_s, int kc, float *dense, uint32_t *hist,
+                             uint32_t *flags, cudaStream_t s);
+tachiom_status launch_select_kd(const Index &ix, int nq, int kd, const float *dense,
+                                const uint32_t *hist, uint32_t *hist2, uint32_t *state,
+                                uint64_t *selbuf, int32_t *cand, float *cand_s, int32_t *ncand,
+                                uint32_t *flags, cudaStream_t s);
+// steps (c), (d)
+tachiom_status launch_refine(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                             const int32_t *cand, int kd, float *part, uint32_t *flags,
+                             cudaStream_t s);
+tachiom_status launch_final_topk(const Index &ix, const int32_t *meta, int nq, const int32_t *cand,
+                                 int kd, const float *part, int32_t *out_ids, float *out_s,
+                                 cudaStream_t s);
+int refine_groups(int M);
+
+}  // namespace tachiom

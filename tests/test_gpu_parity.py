@@ -1,0 +1,253 @@
+"""CUDA path against the FP64 oracle, stage by stage and end to end (needs a GPU).
+
+Stages are replayed: each GPU stage runs on the oracle's own upstream result,
+so a near-tie upstream cannot hide or fake a bug downstream. Rankings are
+compared with the gap-aware rules of tests/compare.py. Tolerance: scores of
+the FP32 path within 1e-5 relative to the oracle (FP32 dot products of
+128-term unit vectors are accurate to ~1e-7; S sums at most 32 of them).
+"""
+import numpy as np
+import pytest
+
+import synth
+from compare import check_ranking, overlap
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL_FP32 = 1e-5
+GAP = 1e-4
+
+
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+class Case:
+    def __init__(self, name, ix, q, kc, kd, k):
+        import paper_2604_28142_b300 as T
+        from oracle import Oracle
+        self.name, self.ix, self.kc, self.kd, self.k = name, ix, kc, kd, k
+        self.q, self.ntok = q["queries"], q["ntok"]
+        self.nq = len(self.ntok)
+        self.qoff = np.concatenate([[0], np.cumsum(self.ntok)]).astype(np.int64)
+        self.O = Oracle(ix)
+        self.G = T.Index(ix, 0)
+        self.T = T
+        self.dq = torch.from_numpy(self.q).cuda()
+
+    def params(self, prec=0, kd=None, kc=None):
+        return self.T.SearchParams(kappa_c=kc or self.kc, kappa_d=kd or self.kd, precision=prec)
+
+
+_CASES = {}
+
+
+def get_case(name):
+    _cuda()
+    if name in _CASES:
+        return _CASES[name]
+    if name == "tiny":
+        cfg = synth.CONFIGS["tiny"]
+        ix = synth.load_or_make("tiny", device="cpu")
+        q = synth.make_queries(cfg)
+        c = Case(name, ix, q, cfg.kappa_c, cfg.kappa_d, cfg.k)
+    elif name in ("small", "small32"):
+        cfg = synth.CONFIGS[name]
+        ix = synth.load_or_make(name, device="cuda")
+        q = synth.make_queries(cfg)
+        c = Case(name, ix, q, cfg.kappa_c, cfg.kappa_d, cfg.k)
+    elif name == "random_edges":
+        ix = synth.random_index(3001, 777, len_min=0, len_max=40, seed=5, empty_docs=50)
+        q = synth.random_queries(9, 1, 32, seed=6)
+        c = Case(name, ix, q, 7, 300, 25)
+    else:
+        raise KeyError(name)
+    _CASES[name] = c
+    return c
+
+
+CASES = ["tiny", "small", "small32", "random_edges"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_inverted_lists_bit_exact(name):
+    c = get_case(name)
+    o_off, o_docs = c.O.lists()
+    g_off, g_docs = c.G.lists()
+    assert np.array_equal(o_off, g_off)
+    assert np.array_equal(o_docs, g_docs)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_step_a_top_centroids_fp32(name):
+    c = get_case(name)
+    R = c.q.shape[0]
+    ids = torch.empty((R, c.kc), dtype=torch.int32, device="cuda")
+    sc = torch.empty((R, c.kc), dtype=torch.float32, device="cuda")
+    c.G.top_centroids(c.params(), c.dq, ids, sc)
+    torch.cuda.synchronize()
+    o_ids, o_s = c.O.top_centroids(c.q, c.kc)
+    gi, gs = ids.cpu().numpy(), sc.cpu().numpy()
+    for r in range(R):
+        check_ranking(gi[r], gs[r], o_ids[r], o_s[r], RTOL_FP32, GAP, what=f"row {r}")
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_step_b_gather_replay(name):
+    c = get_case(name)
+    o_ids, _ = c.O.top_centroids(c.q, c.kc)
+    top = torch.from_numpy(o_ids).cuda()
+    cid = torch.empty((c.nq, c.kd), dtype=torch.int32, device="cuda")
+    cs = torch.empty((c.nq, c.kd), dtype=torch.float32, device="cuda")
+    nc = torch.empty(c.nq, dtype=torch.int32, device="cuda")
+    c.G.gather(c.params(), c.dq, c.ntok, top, cid, cs, nc)
+    torch.cuda.synchronize()
+    gi, gs, gn = cid.cpu().numpy(), cs.cpu().numpy(), nc.cpu().numpy()
+    for u in range(c.nq):
+        docs, s = c.O.gather(c.q[c.qoff[u]:c.qoff[u + 1]], o_ids[c.qoff[u]:c.qoff[u + 1]])
+        od, os_ = c.O.select(docs, s, c.kd)
+        want_i = np.full(c.kd, -1, np.int32)
+        want_s = np.full(c.kd, -np.inf)
+        want_i[:len(od)] = od
+        want_s[:len(od)] = os_
+        assert gn[u] == len(od)
+        check_ranking(gi[u], gs[u], want_i, want_s, RTOL_FP32, GAP, what=f"query {u}",
+                      exact_scores=dict(zip(docs.tolist(), s.tolist())))
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_step_b_reached_set_bit_exact(name):
+    # with kappa_d above the pool size the candidates are every reached doc: integer work
+    c = get_case(name)
+    o_ids, _ = c.O.top_centroids(c.q, c.kc)
+    top = torch.from_numpy(o_ids).cuda()
+    kd = 4096
+    cid = torch.empty((c.nq, kd), dtype=torch.int32, device="cuda")
+    cs = torch.empty((c.nq, kd), dtype=torch.float32, device="cuda")
+    nc = torch.empty(c.nq, dtype=torch.int32, device="cuda")
+    c.G.gather(c.params(kd=kd), c.dq, c.ntok, top, cid, cs, nc)
+    torch.cuda.synchronize()
+    gi, gn = cid.cpu().numpy(), nc.cpu().numpy()
+    checked = 0
+    for u in range(c.nq):
+        docs, _ = c.O.gather(c.q[c.qoff[u]:c.qoff[u + 1]], o_ids[c.qoff[u]:c.qoff[u + 1]])
+        if len(docs) > kd:
+            continue
+        checked += 1
+        assert gn[u] == len(docs)
+        assert np.array_equal(np.sort(gi[u][:gn[u]]), docs)
+        assert np.all(gi[u][gn[u]:] == -1)
+    assert checked > 0 or name in ("small", "small32")
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_step_cd_refine_replay(name):
+    c = get_case(name)
+    res = c.O.search(c.q, c.ntok, c.k, c.kc, c.kd, stages=True)
+    cand = torch.from_numpy(np.ascontiguousarray(res["cand_ids"])).cuda()
+    kk = np.full(c.nq, c.k, np.int32)
+    oi = torch.empty(c.nq * c.k, dtype=torch.int32, device="cuda")
+    os_ = torch.empty(c.nq * c.k, dtype=torch.float32, device="cuda")
+    c.G.refine(c.params(), c.dq, c.ntok, kk, cand, oi, os_)
+    torch.cuda.synchronize()
+    gi, gs = oi.cpu().numpy(), os_.cpu().numpy()
+    for u in range(c.nq):
+        sl = slice(u * c.k, (u + 1) * c.k)
+        cd = res["cand_ids"][u]
+        cd = cd[cd >= 0]
+        rs = c.O.refine(c.q[c.qoff[u]:c.qoff[u + 1]], cd)
+        check_ranking(gi[sl], gs[sl], res["ids"][sl], res["scores"][sl], RTOL_FP32, GAP,
+                      what=f"query {u}", exact_scores=dict(zip(cd.tolist(), rs.tolist())))
+
+
+def _search(c, prec=0, kk=None):
+    kk = np.full(c.nq, c.k, np.int32) if kk is None else kk
+    tot = int(kk.sum())
+    oi = torch.empty(tot, dtype=torch.int32, device="cuda")
+    os_ = torch.empty(tot, dtype=torch.float32, device="cuda")
+    c.G.search(c.params(prec), c.dq, c.ntok, kk, oi, os_)
+    torch.cuda.synchronize()
+    return oi.cpu().numpy(), os_.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_search_end_to_end_fp32(name):
+    c = get_case(name)
+    gi, gs = _search(c)
+    res = c.O.search(c.q, c.ntok, c.k, c.kc, c.kd)
+    ov = []
+    for u in range(c.nq):
+        sl = slice(u * c.k, (u + 1) * c.k)
+        check_ranking(gi[sl], gs[sl], res["ids"][sl], res["scores"][sl], RTOL_FP32, GAP, what=f"query {u}")
+        ov.append(overlap(gi[sl], res["ids"][sl], 10))
+    assert np.mean(ov) >= 0.99, ov
+    assert c.G.stream_status() & ~0b10 == 0
+
+
+@pytest.mark.parametrize("name", ["tiny", "random_edges"])
+def test_search_deterministic_and_batch_invariant(name):
+    c = get_case(name)
+    a = _search(c)
+    b = _search(c)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.int32), b[1].view(np.int32))
+    # each query alone gives the same bits as inside the batch
+    for u in range(0, c.nq, 3):
+        qq = torch.from_numpy(c.q[c.qoff[u]:c.qoff[u + 1]]).cuda()
+        oi = torch.empty(c.k, dtype=torch.int32, device="cuda")
+        os_ = torch.empty(c.k, dtype=torch.float32, device="cuda")
+        c.G.search(c.params(), qq, c.ntok[u:u + 1], np.array([c.k], np.int32), oi, os_)
+        torch.cuda.synchronize()
+        sl = slice(u * c.k, (u + 1) * c.k)
+        assert np.array_equal(oi.cpu().numpy(), a[0][sl])
+        assert np.array_equal(os_.cpu().numpy().view(np.int32), a[1][sl].view(np.int32))
+
+
+def test_search_host_matches_device():
+    c = get_case("tiny")
+    gi, gs = _search(c)
+    hi, hs = c.G.search_host(c.params(), c.q, c.ntok, np.full(c.nq, c.k, np.int32))
+    assert np.array_equal(gi, hi) and np.array_equal(gs, hs)
+
+
+def test_uneven_k_and_padding():
+    c = get_case("random_edges")
+    kk = np.array([1, 300, 5, 17, 2, 300, 40, 9, 299], np.int32)
+    gi, gs = _search(c, kk=kk)
+    res = c.O.search(c.q, c.ntok, kk, c.kc, c.kd)
+    off = np.concatenate([[0], np.cumsum(kk)])
+    for u in range(c.nq):
+        sl = slice(off[u], off[u + 1])
+        check_ranking(gi[sl], gs[sl], res["ids"][sl], res["scores"][sl], RTOL_FP32, GAP, what=f"query {u}")
+
+
+def test_all_centroids_and_tiny_kappa():
+    c = get_case("random_edges")
+    # kappa_c = 128 on C = 777, kappa_d = 1
+    kc, kd, k = 128, 1, 1
+    tot = c.nq * k
+    oi = torch.empty(tot, dtype=torch.int32, device="cuda")
+    os_ = torch.empty(tot, dtype=torch.float32, device="cuda")
+    c.G.search(c.params(kc=kc, kd=kd), c.dq, c.ntok, np.full(c.nq, k, np.int32), oi, os_)
+    torch.cuda.synchronize()
+    res = c.O.search(c.q, c.ntok, k, kc, kd)
+    check_ranking(oi.cpu().numpy(), os_.cpu().numpy(), res["ids"], res["scores"], RTOL_FP32, GAP)
+
+
+def test_empty_batch_is_noop():
+    c = get_case("tiny")
+    c.G.search(c.params(), c.dq, np.zeros(0, np.int32), np.zeros(0, np.int32), None, None)
+
+
+def test_bad_arguments_rejected():
+    import paper_2604_28142_b300 as T
+    c = get_case("tiny")
+    oi = torch.empty(16, dtype=torch.int32, device="cuda")
+    os_ = torch.empty(16, dtype=torch.float32, device="cuda")
+    with pytest.raises(T.TachiomError):
+        c.G.search(c.params(), c.dq, np.array([33], np.int32), np.array([1], np.int32), oi, os_)
+    with pytest.raises(T.TachiomError):
+        c.G.search(c.params(kc=0), c.dq, np.array([3], np.int32), np.array([1], np.int32), oi, os_)
+    with pytest.raises(T.TachiomError):
+        c.G.search(c.params(kd=5), c.dq, np.array([3], np.int32), np.array([6], np.int32), oi, os_)
