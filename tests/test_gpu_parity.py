@@ -38,7 +38,8 @@ class Case:
         self.dq = torch.from_numpy(self.q).cuda()
 
     def params(self, prec=0, kd=None, kc=None):
-        return self.T.SearchParams(kappa_c=kc or self.kc, kappa_d=kd or self.kd, precision=prec)
+        return self.T.SearchParams(kappa_c=self.kc if kc is None else kc,
+                                   kappa_d=self.kd if kd is None else kd, precision=prec)
 
 
 _CASES = {}
