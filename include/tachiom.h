@@ -178,6 +178,30 @@ tachiom_status tachiom_refine(tachiom_index *index, const tachiom_search_params 
                               int32_t nq, const int32_t *d_cand_ids, int32_t *d_out_ids,
                               float *d_out_scores, void *stream);
 
+/* tachiom_refine without allocating. The paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory during a call, for
+ * example a process whose device memory is handed out in advance by a
+ * fixed-budget allocator, a plug-in living inside another framework's memory
+ * pool, or a latency-critical thread that must not block in cudaMalloc (which
+ * can synchronise the whole device). tachiom_refine takes its scratch from a
+ * per-stream workspace that grows with cudaMalloc; this call instead uses one
+ * static device array compiled into the library (2 MiB + 4 KiB, held on every
+ * device that loads the library until the process exits) and calls no
+ * cudaMalloc, cudaFree, pinned-host or heap allocation.
+ *   Same arguments and results as tachiom_refine, with these limits:
+ *   nq <= 64 and params->kappa_d given explicitly in 1..1024; larger sizes
+ *   return TACHIOM_ERR_CAPACITY with a message, and nothing is launched.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before capturing any stream. Every call shares the one array: calls whose
+ *   work overlaps on the GPU (other streams, other host threads) race on it,
+ *   so serialise them. Device-side range-check flags raised by this call are
+ *   not reported by tachiom_stream_status. Asynchronous on `stream`.       */
+tachiom_status tachiom_refine_noalloc(tachiom_index *index, const tachiom_search_params *params,
+                                      const float *d_queries, const int32_t *h_ntok,
+                                      const int32_t *h_k, int32_t nq, const int32_t *d_cand_ids,
+                                      int32_t *d_out_ids, float *d_out_scores, void *stream);
+
 /* Synchronise `stream`, then return and clear the TACHIOM_FLAG_* bits raised
  * by work on that stream. Blocking.                                         */
 tachiom_status tachiom_stream_status(tachiom_index *index, void *stream, uint32_t *h_flags);

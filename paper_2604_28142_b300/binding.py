@@ -90,6 +90,7 @@ def lib():
         "tachiom_top_centroids": ([P, ct.POINTER(SearchParams), P, I32, P, P, P], ct.c_int),
         "tachiom_gather": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P, P, P], ct.c_int),
         "tachiom_refine": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
+        "tachiom_refine_noalloc": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
         "tachiom_stream_status": ([P, P, U32p], ct.c_int),
         "tachiom_profile_enable": ([ct.c_int], ct.c_int),
         "tachiom_profile_read": ([P, ct.POINTER(ProfileEntry), I32, ct.POINTER(ct.c_int32)], ct.c_int),
