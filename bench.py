@@ -192,7 +192,7 @@ def run_ours(a):
         log(f"index ready in {time.time() - t0:.1f}s: T={ix['doc_offsets'][-1]}")
     G = T.Index(ix, local)
     if a.precision == "auto":
-        prec = T.PREC_BF16 if T.lib().tachiom_version() and _tc_ok(T) else T.PREC_FP32
+        prec = T.PREC_BF16 if T.tc_available() else T.PREC_FP32
     else:
         prec = T.PREC_BF16 if a.precision == "bf16" else T.PREC_FP32
     params = T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=prec)
@@ -362,20 +362,6 @@ def _count_launches(prof):
     # kernels per launcher call: select_kd launches 8 kernels, topc_merge 2, others 1
     per = {"select_kd": 8, "topc_merge": 2}
     return sum(v[0] * per.get(k, 1) for k, v in prof.items())
-
-
-def _tc_ok(T):
-    return os.environ.get("TACHIOM_NO_TC") is None and _probe_tc(T)
-
-
-def _probe_tc(T):
-    import ctypes
-    try:
-        f = T.lib().tachiom_tc_available
-    except AttributeError:
-        return False
-    f.restype = ctypes.c_int
-    return bool(f())
 
 
 def run_reference(a):

@@ -74,7 +74,9 @@ enum {
                                             tie pass ran */
   TACHIOM_FLAG_CAPACITY = 1u << 2,       /* a buffer overflow that could not be rescued: the
                                             affected query's result may be incomplete */
-  TACHIOM_FLAG_BAD_INPUT = 1u << 3       /* a device-side range check failed */
+  TACHIOM_FLAG_BAD_INPUT = 1u << 3,      /* a device-side range check failed */
+  TACHIOM_FLAG_TIMEOUT = 1u << 4         /* a bounded wait inside a kernel gave up; the
+                                            results of that call are not valid */
 };
 
 typedef struct tachiom_index tachiom_index; /* opaque, owned by the library */
@@ -225,6 +227,19 @@ tachiom_status tachiom_profile_read(void *stream, tachiom_profile_entry *out, in
 
 /* Message of the last failed call on this thread ("" if none).             */
 const char *tachiom_last_error(void);
+
+/* 1 when the current device runs the tensor-core step (a) (compute capability
+ * 10.3, the library's only target), else 0; TACHIOM_PREC_BF16 then uses the
+ * FP32 CUDA-core path.                                                      */
+int tachiom_tc_available(void);
+
+/* Diagnostics of the tensor-core step (a): the BF16 x BF16 -> FP32 score of
+ * each of nrows device fp32 rows (rounded to BF16 on the way) against every
+ * centroid, written to d_out [nrows x C] fp32 (device, caller-owned). Used by
+ * the tests to check the error bound the FP32 repair relies on.
+ * TACHIOM_ERR_INVALID when the device has no tensor-core path.              */
+tachiom_status tachiom_debug_tc_scores(tachiom_index *index, const float *d_rows, int32_t nrows,
+                                       float *d_out, void *stream);
 
 /* Library version string. */
 const char *tachiom_version(void);

@@ -17,4 +17,5 @@ from .binding import (  # noqa: F401
     lib_path,
     profile_enable,
     profile_read,
+    tc_available,
 )

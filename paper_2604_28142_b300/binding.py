@@ -63,6 +63,11 @@ def profile_read(stream=None) -> dict:
     return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(n.value)}
 
 
+def tc_available() -> bool:
+    """True when the current device runs the tensor-core step (a)."""
+    return bool(lib().tachiom_tc_available())
+
+
 def lib_path() -> str:
     return os.environ.get("TACHIOM_LIB", os.path.join(_HERE, "libtachiom.so"))
 
@@ -92,6 +97,8 @@ def lib():
         "tachiom_refine": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
         "tachiom_refine_noalloc": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
         "tachiom_stream_status": ([P, P, U32p], ct.c_int),
+        "tachiom_debug_tc_scores": ([P, P, I32, P, P], ct.c_int),
+        "tachiom_tc_available": ([], ct.c_int),
         "tachiom_profile_enable": ([ct.c_int], ct.c_int),
         "tachiom_profile_read": ([P, ct.POINTER(ProfileEntry), I32, ct.POINTER(ct.c_int32)], ct.c_int),
         "tachiom_last_error": ([], ct.c_char_p),
@@ -217,6 +224,9 @@ class Index:
         _check(lib().tachiom_refine(self.h, ct.byref(params), _dp(queries), _hp(ntok), _hp(k),
                                     int(ntok.shape[0]), _dp(cand_ids), _dp(out_ids), _dp(out_scores),
                                     _stream(stream)))
+
+    def debug_tc_scores(self, rows, out, stream=None):
+        _check(lib().tachiom_debug_tc_scores(self.h, _dp(rows), int(rows.shape[0]), _dp(out), _stream(stream)))
 
     def stream_status(self, stream=None) -> int:
         f = ct.c_uint32()

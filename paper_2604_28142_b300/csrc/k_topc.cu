@@ -241,6 +241,10 @@ k_topc_merge(const float *__restrict__ rows, int nrows, const float *__restrict_
       int v = split_cnt[(int64_t)r * splits + sp];
       if (v & (1 << 30)) lo = 1;
       v &= (1 << 30) - 1;
+      if (v > capout) {  // a slice's list overflowed: the row takes the exact fallback
+        lo = 1;
+        v = capout;
+      }
       offs[sp] = o;
       o += v;
     }

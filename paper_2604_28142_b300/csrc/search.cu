@@ -46,14 +46,14 @@ tachiom_status ws_get(Index *ix, cudaStream_t stream, Workspace **out) {
 }
 
 struct Need {
-  int64_t nq = 0, rows = 0, kc = 0, kd = 0, split_entries = 0, dense = 0;
+  int64_t nq = 0, rows = 0, kc = 0, kd = 0, split_entries = 0, dense = 0, gmax = 0;
 };
 
 // (Re)allocate the device scratch for a batch. Growth synchronises the stream
 // first, so memory still in use by earlier work on it is never freed early.
 static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   bool grow = n.nq > w->cap_q || n.rows > w->cap_rows || n.kc > w->cap_kc || n.kd > w->cap_kd ||
-              n.split_entries > w->cap_split_entries || n.dense > w->cap_dense;
+              n.split_entries > w->cap_split_entries || n.dense > w->cap_dense || n.gmax > w->cap_gmax;
   if (!grow) return TACHIOM_OK;
   TCUDA(cudaStreamSynchronize(w->stream));
   for (void *p : w->blocks)
@@ -64,6 +64,7 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   int64_t kc = std::max<int64_t>(n.kc, w->cap_kc), kd = std::max<int64_t>(n.kd, w->cap_kd);
   int64_t se = std::max<int64_t>(n.split_entries, w->cap_split_entries);
   int64_t dn = std::max<int64_t>(n.dense, w->cap_dense);
+  int64_t gm = std::max<int64_t>(n.gmax, w->cap_gmax);
   const int groups = refine_groups(32);  // the largest group count of any pq_m
   auto al = [&](void **p, size_t bytes) -> tachiom_status {
     if (bytes == 0) bytes = 16;
@@ -89,6 +90,8 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   AL(w->d_top_ids, rows * kc * 4);
   AL(w->d_top_s, rows * kc * 4);
   AL(w->d_dense, dn * 4);
+  AL(w->d_gmax, gm * 4);
+  AL(w->d_tau, rows * 4);
   AL(w->d_hist, nq * NBINS1 * 4);
   AL(w->d_hist2, nq * NBINS1 * 4);
   AL(w->d_selstate, nq * 8 * 4);
@@ -106,6 +109,7 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   w->cap_kd = kd;
   w->cap_split_entries = se;
   w->cap_dense = dn;
+  w->cap_gmax = gm;
   return TACHIOM_OK;
 }
 
@@ -227,21 +231,43 @@ static tachiom_status upload_meta(Workspace *w, const int32_t *h_ntok, const int
   return TACHIOM_OK;
 }
 
+static bool use_tc(const tachiom_search_params *p) {
+  return p->precision == TACHIOM_PREC_BF16 && topc_tc_supported();
+}
+
+// Bound on |BF16 product score - FP32 score| for a unit-norm query row:
+// rounding the query to BF16 moves each product by at most 2^-9 |q_k c_k|
+// (relative), so the sum moves by at most 2^-9 ||q|| ||c_j||; FP32-stored
+// centroids are rounded too (another 2^-9). The bound used doubles that and
+// adds an absolute term for the accumulation.
+static float bf16_delta(const Index &ix) {
+  const float rel = ix.cdtype == TACHIOM_DTYPE_BF16 ? ldexpf(1.f, -8) : ldexpf(1.f, -7);
+  return rel * ix.cnorm_max + 1e-5f;
+}
+
+// scratch sizes of step (a) for a batch
+static void need_topc(const Index &ix, const tachiom_search_params *p, int rows, const Plan &plan, Need *n) {
+  if (use_tc(p)) {
+    n->split_entries = (int64_t)rows * topc_tc_capg();
+    n->gmax = (int64_t)topc_tc_gmax_elems(ix.C, rows);
+  } else {
+    n->split_entries = (int64_t)rows * plan.splits * plan.capout;
+  }
+}
+
 // step (a) into w->d_top_ids / d_top_s
 static tachiom_status run_topc(Index *ix, Workspace *w, const tachiom_search_params *p, const float *rows,
                                int nrows, const Plan &plan) {
   const int kc = p->kappa_c;
   tachiom_status st;
-  if (p->precision == TACHIOM_PREC_BF16 && topc_tc_supported()) {
+  if (use_tc(p)) {
     if ((st = launch_quantize_bf16(rows, w->d_rows_bf16, (int64_t)nrows * DIM, w->stream))) return st;
-    // per-score error of BF16 queries times exact or BF16 centroids: |e| <= 2^-8 * ||c_j||
-    // (both operands rounded, unit-norm query) plus FP32 accumulation; the window is twice it
-    const float delta = ldexpf(1.f, -8) * ix->cnorm_max + 1e-5f;
-    if ((st = launch_topc_tc(*ix, w->d_rows_bf16, nrows, kc, plan.splits, plan.capout, 2.f * delta,
-                             w->d_split, w->d_split_cnt, w->d_flags, w->stream)))
+    const float margin = 2.f * bf16_delta(*ix);
+    if ((st = launch_topc_tc(*ix, w->d_rows_bf16, nrows, kc, margin, w->d_gmax, w->d_tau, w->d_split_cnt,
+                             w->d_split, w->d_flags, w->stream)))
       return st;
-    return launch_topc_merge(*ix, rows, nrows, kc, plan.splits, plan.capout, w->d_split, w->d_split_cnt,
-                             2.f * delta, 1, w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
+    return launch_topc_merge(*ix, rows, nrows, kc, 1, topc_tc_capg(), w->d_split, w->d_split_cnt, margin, 1,
+                             w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
   }
   if ((st = launch_topc_f32(*ix, rows, nrows, kc, plan.splits, plan.capout, w->d_split, w->d_split_cnt,
                             w->d_flags, w->stream)))
@@ -285,7 +311,7 @@ static tachiom_status search_device(Index *ix, const tachiom_search_params *p, c
   n.rows = b.rows;
   n.kc = p->kappa_c;
   n.kd = kd;
-  n.split_entries = (int64_t)b.rows * plan.splits * plan.capout;
+  need_topc(*ix, p, b.rows, plan, &n);
   n.dense = (int64_t)nq * ix->D;
   if ((st = ws_reserve(ix, w, n))) return st;
   if ((st = upload_meta(w, h_ntok, h_k, nq))) return st;
@@ -340,7 +366,7 @@ extern "C" tachiom_status tachiom_search_host(tachiom_index *index, const tachio
   n.rows = b.rows;
   n.kc = params->kappa_c;
   n.kd = std::max<int64_t>(kd, (b.total_k + nq - 1) / nq + 1);
-  n.split_entries = (int64_t)b.rows * plan.splits * plan.capout;
+  need_topc(*ix, params, b.rows, plan, &n);
   n.dense = (int64_t)nq * ix->D;
   if ((st = ws_reserve(ix, w, n))) return st;
   if (b.total_k > w->cap_q * w->cap_kd) return fail(TACHIOM_ERR_CAPACITY, "sum(k) beyond scratch");
@@ -404,7 +430,7 @@ extern "C" tachiom_status tachiom_top_centroids(tachiom_index *index, const tach
   n.rows = nrows;
   n.kc = params->kappa_c;
   n.kd = 1;
-  n.split_entries = (int64_t)nrows * plan.splits * plan.capout;
+  need_topc(*ix, params, nrows, plan, &n);
   n.dense = 0;
   if ((st = ws_reserve(ix, w, n))) return st;
   if ((st = run_topc(ix, w, params, d_rows, nrows, plan))) return st;
@@ -489,4 +515,26 @@ extern "C" tachiom_status tachiom_stream_status(tachiom_index *index, void *stre
   TCUDA(cudaMemcpy(h_flags, w->d_flags, 4, cudaMemcpyDeviceToHost));
   TCUDA(cudaMemset(w->d_flags, 0, 4));
   return TACHIOM_OK;
+}
+
+extern "C" tachiom_status tachiom_debug_tc_scores(tachiom_index *index, const float *d_rows, int32_t nrows,
+                                                  float *d_out, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
+  if (!topc_tc_supported()) return fail(TACHIOM_ERR_INVALID, "no tensor-core step (a) on this device");
+  if (nrows < 0 || (nrows > 0 && (!d_rows || !d_out))) return fail(TACHIOM_ERR_INVALID, "bad arguments");
+  if (nrows == 0) return TACHIOM_OK;
+  DeviceGuard g(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w;
+  tachiom_status st;
+  if ((st = ws_get(ix, s, &w))) return st;
+  Need n;
+  n.nq = 1;
+  n.rows = nrows;
+  n.kc = 1;
+  n.kd = 1;
+  if ((st = ws_reserve(ix, w, n))) return st;
+  if ((st = launch_quantize_bf16(d_rows, w->d_rows_bf16, (int64_t)nrows * DIM, s))) return st;
+  return launch_topc_tc_raw(*ix, w->d_rows_bf16, nrows, d_out, w->d_flags, s);
 }

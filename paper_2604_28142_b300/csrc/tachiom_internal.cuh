@@ -138,6 +138,9 @@ struct Workspace {
   float *d_rows_f32 = nullptr;         // staging of host queries (search_host)
   __nv_bfloat16 *d_rows_bf16 = nullptr;// [rows x 128]
   uint64_t *d_split = nullptr;         // [rows x splits x capout] candidates of step (a)
+  uint32_t *d_gmax = nullptr;          // tensor-core path: group maxima of pass 1
+  uint32_t *d_tau = nullptr;           // tensor-core path: per-row lower bound of the cut
+  int64_t cap_gmax = 0;
   int32_t *d_split_cnt = nullptr;      // [rows x splits]
   int32_t *d_top_ids = nullptr;        // [rows x kc]
   float *d_top_s = nullptr;            // [rows x kc]
@@ -193,10 +196,14 @@ tachiom_status launch_topc_merge(const Index &ix, const float *rows, int nrows, 
                                  int capout, const uint64_t *split, const int32_t *split_cnt,
                                  float margin, int rescore, int32_t *top_ids, float *top_s,
                                  uint32_t *flags, cudaStream_t s);
-tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc,
-                              int splits, int capout, float margin, uint64_t *split,
-                              int32_t *split_cnt, uint32_t *flags, cudaStream_t s);
+tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, float margin,
+                              uint32_t *gmax, uint32_t *tau, int32_t *cnt, uint64_t *cand, uint32_t *flags,
+                              cudaStream_t s);
 int topc_tc_supported();
+tachiom_status launch_topc_tc_raw(const Index &ix, const __nv_bfloat16 *rows, int nrows, float *out,
+                                  uint32_t *flags, cudaStream_t s);
+int topc_tc_capg();
+size_t topc_tc_gmax_elems(int64_t C, int rows);
 tachiom_status launch_score_pairs(const Index &ix, const float *rows, int nrows, const int32_t *ids,
                                   int kc, float *scores, cudaStream_t s);
 // step (b)

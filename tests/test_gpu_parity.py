@@ -252,3 +252,88 @@ def test_bad_arguments_rejected():
         c.G.search(c.params(kc=0), c.dq, np.array([3], np.int32), np.array([1], np.int32), oi, os_)
     with pytest.raises(T.TachiomError):
         c.G.search(c.params(kd=5), c.dq, np.array([3], np.int32), np.array([6], np.int32), oi, os_)
+
+
+# ---------------------------------------------------------------- tensor-core step (a)
+
+def _tc():
+    import paper_2604_28142_b300 as T
+    if not T.tc_available():
+        pytest.skip("no tensor-core step (a) on this device")
+
+
+def _widened(ix):
+    c = ix["centroids"]
+    if ix["centroid_dtype"] == "bf16":
+        return (c.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return c.astype(np.float64)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "random_edges"])
+def test_tc_scores_within_error_bound(name):
+    # every BF16 tensor-core score is within the delta the FP32 repair assumes
+    _cuda()
+    _tc()
+    c = get_case(name)
+    R = min(c.q.shape[0], 300)
+    C = c.G.C
+    out = torch.empty((R, C), dtype=torch.float32, device="cuda")
+    c.G.debug_tc_scores(c.dq[:R], out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    Cw = _widened(c.ix)
+    exact = c.q[:R].astype(np.float64) @ Cw.T
+    cmax = np.linalg.norm(Cw, axis=1).max()
+    rel = 2.0 ** -8 if c.ix["centroid_dtype"] == "bf16" else 2.0 ** -7
+    delta = rel * cmax + 1e-5
+    err = np.abs(got - exact)
+    assert err.max() <= delta, (err.max(), delta)
+    # and the bound is not vacuous: the scores do carry BF16 rounding error
+    assert err.max() > 0
+    assert c.G.stream_status() == 0
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_step_a_bf16_equals_fp32(name):
+    _cuda()
+    _tc()
+    c = get_case(name)
+    R = c.q.shape[0]
+    res = []
+    for prec in (0, 1):
+        ids = torch.empty((R, c.kc), dtype=torch.int32, device="cuda")
+        sc = torch.empty((R, c.kc), dtype=torch.float32, device="cuda")
+        c.G.top_centroids(c.params(prec), c.dq, ids, sc)
+        torch.cuda.synchronize()
+        res.append((ids.cpu().numpy(), sc.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1].view(np.int32), res[1][1].view(np.int32))
+    assert c.G.stream_status() & 16 == 0  # no timeout
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_search_bf16_equals_fp32(name):
+    _cuda()
+    _tc()
+    c = get_case(name)
+    a = _search(c, prec=0)
+    b = _search(c, prec=1)
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1].view(np.int32), b[1].view(np.int32))
+    assert c.G.stream_status() & 16 == 0
+
+
+def test_bf16_kappa_c_above_group_count():
+    # C = 777 gives 28 groups of 32 < kappa_c = 128: every centroid becomes a candidate
+    _cuda()
+    _tc()
+    c = get_case("random_edges")
+    R = c.q.shape[0]
+    out = []
+    for prec in (0, 1):
+        ids = torch.empty((R, 128), dtype=torch.int32, device="cuda")
+        sc = torch.empty((R, 128), dtype=torch.float32, device="cuda")
+        c.G.top_centroids(c.params(prec, kc=128), c.dq, ids, sc)
+        torch.cuda.synchronize()
+        out.append(ids.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
