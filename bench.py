@@ -290,31 +290,32 @@ def run_ours(a):
     name, (launches, ms) = dom
     per_launch_ms = ms / max(1, launches)
     clocks = clk.summary()
-    if name == "gather":
-        roof = {"kernel": "k_gather", "bound": "hbm", "achieved": traffic["gather_bytes"] / (per_launch_ms * 1e-3) / 1e9,
-                "peak": hbm_peak, "unit": "GB/s"}
-    elif name == "refine":
-        roof = {"kernel": "k_refine", "bound": "hbm", "achieved": traffic["refine_bytes"] / (per_launch_ms * 1e-3) / 1e9,
-                "peak": hbm_peak, "unit": "GB/s"}
-    elif name == "select_kd":
-        roof = {"kernel": "k_sel_*", "bound": "hbm", "achieved": traffic["select_bytes"] / (per_launch_ms * 1e-3) / 1e9,
+    R = a.batch * 32
+    C = ix["centroids"].shape[0]
+    gemm_flops = 2.0 * R * C * 128
+    hbm_kernels = {"gather": ("k_gather", traffic["gather_bytes"]),
+                   "refine": ("k_refine", traffic["refine_bytes"]),
+                   "refine_tc": ("k_refine_tc", traffic["refine_bytes"]),
+                   "select_kd": ("k_sel_*", traffic["select_bytes"])}
+    if name in hbm_kernels:
+        kname, nbytes = hbm_kernels[name]
+        roof = {"kernel": kname, "bound": "hbm", "achieved": nbytes / (per_launch_ms * 1e-3) / 1e9,
                 "peak": hbm_peak, "unit": "GB/s"}
     elif name == "topc_f32_scan":
-        R = a.batch * 32
-        C = ix["centroids"].shape[0]
-        fl = 2.0 * R * C * 128
         sm = clocks.get("sm_mhz") or 1900.0
         peak_alu = 148 * 128 * 2 * sm * 1e6 / 1e12
-        roof = {"kernel": "k_topc_f32_scan", "bound": "alu", "achieved": fl / (per_launch_ms * 1e-3) / 1e12,
+        roof = {"kernel": "k_topc_f32_scan", "bound": "alu", "achieved": gemm_flops / (per_launch_ms * 1e-3) / 1e12,
                 "peak": peak_alu, "unit": "TFLOP/s"}
         peak_src = "derived: 148 SMs x 128 FP32 lanes x 2 x median SM clock"
-    else:
-        R = a.batch * 32
-        C = ix["centroids"].shape[0]
-        fl = 2.0 * R * C * 128
+    elif name == "topc_tc1":
         pk_t = peaks.get("bf16_tflops", 1800.0)
-        roof = {"kernel": name, "bound": "tensor", "achieved": fl / (per_launch_ms * 1e-3) / 1e12,
-                "peak": pk_t, "unit": "TFLOP/s"}
+        roof = {"kernel": "k_topc_tc1", "bound": "tensor",
+                "achieved": gemm_flops / (per_launch_ms * 1e-3) / 1e12, "peak": pk_t, "unit": "TFLOP/s"}
+    else:
+        # the two-pass tensor-core scan runs the product twice (group maxima, then the filter)
+        pk_t = peaks.get("bf16_tflops", 1800.0)
+        roof = {"kernel": "k_topc_tc (2 passes)", "bound": "tensor",
+                "achieved": 2 * gemm_flops / (per_launch_ms * 1e-3) / 1e12, "peak": pk_t, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["peak_source"] = peak_src
     roof["traffic"] = None
@@ -360,7 +361,7 @@ def run_ours(a):
 
 def _count_launches(prof):
     # kernels per launcher call: select_kd launches 8 kernels, topc_merge 2, others 1
-    per = {"select_kd": 8, "topc_merge": 2}
+    per = {"select_kd": 8, "topc_merge": 2, "topc_tc": 3}
     return sum(v[0] * per.get(k, 1) for k, v in prof.items())
 
 

@@ -204,6 +204,48 @@ tachiom_status tachiom_refine_noalloc(tachiom_index *index, const tachiom_search
                                       const int32_t *h_k, int32_t nq, const int32_t *d_cand_ids,
                                       int32_t *d_out_ids, float *d_out_scores, void *stream);
 
+/* ---- continuous-batching request loop ----
+ * A server owns n_slots CUDA streams. Requests (one query each: host fp32
+ * [ntok x 128], its own k) are submitted from any host thread; a scheduler
+ * thread forms batches from the queue in arrival order whenever a slot is
+ * free and launches them, so requests that arrive while other batches run are
+ * admitted as slots free up and their work overlaps on the device. A batch is
+ * launched when it is full, when its oldest request has waited max_wait_us,
+ * or at once when nothing else runs; it is held back while the scratch that
+ * in-flight batches may use would exceed scratch_budget_bytes (0: no limit).
+ * A request's result is the same bits alone and in any mix.              */
+typedef struct {
+  int32_t n_slots;              /* batches in flight at once, 1..64 */
+  int32_t max_batch_queries;    /* queries per batch */
+  int32_t max_batch_rows;       /* query tokens per batch, >= 32 */
+  int32_t max_wait_us;          /* longest a queued request waits for a fuller batch */
+  int64_t scratch_budget_bytes; /* device scratch all in-flight batches may use; 0 = unlimited */
+} tachiom_server_config;
+
+typedef struct {
+  int64_t completed;   /* requests finished */
+  int64_t batches;     /* batches launched and finished */
+  double mean_batch;   /* queries per batch */
+  double p50_ms, p95_ms, p99_ms; /* latency: submission to results on the host */
+  double qps;          /* completed / (last completion - first submission) */
+} tachiom_server_stats;
+
+typedef struct tachiom_server tachiom_server;
+
+tachiom_status tachiom_server_create(tachiom_index *index, const tachiom_search_params *params,
+                                     const tachiom_server_config *cfg, tachiom_server **out);
+/* Queue one query; *id receives its request id. The query is copied. */
+tachiom_status tachiom_server_submit(tachiom_server *server, const float *h_query, int32_t ntok,
+                                     int32_t k, uint64_t *id);
+/* Wait up to timeout_ms (< 0: forever) for a request; copy its k ids and
+ * scores to host buffers (may be NULL) and its latency in ms, then forget it.
+ * TACHIOM_ERR_TIMEOUT if it has not finished in time (it stays queued). */
+tachiom_status tachiom_server_wait(tachiom_server *server, uint64_t id, int32_t timeout_ms,
+                                   int32_t *h_ids, float *h_scores, double *latency_ms);
+tachiom_status tachiom_server_read_stats(tachiom_server *server, tachiom_server_stats *out);
+/* Finish every queued and running request, then release the server. */
+tachiom_status tachiom_server_destroy(tachiom_server *server);
+
 /* Synchronise `stream`, then return and clear the TACHIOM_FLAG_* bits raised
  * by work on that stream. Blocking.                                         */
 tachiom_status tachiom_stream_status(tachiom_index *index, void *stream, uint32_t *h_flags);
@@ -240,6 +282,15 @@ int tachiom_tc_available(void);
  * TACHIOM_ERR_INVALID when the device has no tensor-core path.              */
 tachiom_status tachiom_debug_tc_scores(tachiom_index *index, const float *d_rows, int32_t nrows,
                                        float *d_out, void *stream);
+
+/* Diagnostics of step (c): the refined score S of every candidate slot,
+ * d_cand_ids int32 [nq x kappa_d] (slots < 0 give -inf), to d_scores fp32
+ * [nq x kappa_d], before any top-k. With TACHIOM_PREC_BF16 on a tensor-core
+ * device these are the approximate scores the FP32 repair starts from; the
+ * tests use them to check its error bound. Asynchronous.                   */
+tachiom_status tachiom_debug_refine_scores(tachiom_index *index, const tachiom_search_params *params,
+                                           const float *d_queries, const int32_t *h_ntok, int32_t nq,
+                                           const int32_t *d_cand_ids, float *d_scores, void *stream);
 
 /* Library version string. */
 const char *tachiom_version(void);

@@ -301,10 +301,10 @@ static double refine_doc(const oracle_index *ix, const float *q, int ntok, int32
 
 int oracle_refine(const oracle_index *ix, const float *q, int ntok, const int32_t *docs, int64_t n,
                   double *out_s) {
-  for (int64_t u = 0; u < n; u++) {
+  for (int64_t u = 0; u < n; u++)
     if (docs[u] < 0 || docs[u] >= ix->D) return 1;
-    out_s[u] = refine_doc(ix, q, ntok, docs[u]);
-  }
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t u = 0; u < n; u++) out_s[u] = refine_doc(ix, q, ntok, docs[u]);
   return 0;
 }
 

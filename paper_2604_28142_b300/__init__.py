@@ -12,6 +12,7 @@ from .binding import (  # noqa: F401
     FLAG_TOPC_RESCUED,
     TachiomError,
     Index,
+    Server,
     SearchParams,
     lib,
     lib_path,

@@ -68,6 +68,16 @@ def tc_available() -> bool:
     return bool(lib().tachiom_tc_available())
 
 
+class ServerConfig(ct.Structure):
+    _fields_ = [("n_slots", ct.c_int32), ("max_batch_queries", ct.c_int32), ("max_batch_rows", ct.c_int32),
+                ("max_wait_us", ct.c_int32), ("scratch_budget_bytes", ct.c_int64)]
+
+
+class ServerStats(ct.Structure):
+    _fields_ = [("completed", ct.c_int64), ("batches", ct.c_int64), ("mean_batch", ct.c_double),
+                ("p50_ms", ct.c_double), ("p95_ms", ct.c_double), ("p99_ms", ct.c_double), ("qps", ct.c_double)]
+
+
 def lib_path() -> str:
     return os.environ.get("TACHIOM_LIB", os.path.join(_HERE, "libtachiom.so"))
 
@@ -99,8 +109,15 @@ def lib():
         "tachiom_stream_status": ([P, P, U32p], ct.c_int),
         "tachiom_debug_tc_scores": ([P, P, I32, P, P], ct.c_int),
         "tachiom_tc_available": ([], ct.c_int),
+        "tachiom_debug_refine_scores": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P], ct.c_int),
         "tachiom_profile_enable": ([ct.c_int], ct.c_int),
         "tachiom_profile_read": ([P, ct.POINTER(ProfileEntry), I32, ct.POINTER(ct.c_int32)], ct.c_int),
+        "tachiom_server_create": ([P, ct.POINTER(SearchParams), ct.POINTER(ServerConfig), ct.POINTER(ct.c_void_p)],
+                                  ct.c_int),
+        "tachiom_server_submit": ([P, P, I32, I32, ct.POINTER(ct.c_uint64)], ct.c_int),
+        "tachiom_server_wait": ([P, ct.c_uint64, I32, P, P, ct.POINTER(ct.c_double)], ct.c_int),
+        "tachiom_server_read_stats": ([P, ct.POINTER(ServerStats)], ct.c_int),
+        "tachiom_server_destroy": ([P], ct.c_int),
         "tachiom_last_error": ([], ct.c_char_p),
         "tachiom_version": ([], ct.c_char_p),
     }
@@ -228,7 +245,54 @@ class Index:
     def debug_tc_scores(self, rows, out, stream=None):
         _check(lib().tachiom_debug_tc_scores(self.h, _dp(rows), int(rows.shape[0]), _dp(out), _stream(stream)))
 
+    def debug_refine_scores(self, params: SearchParams, queries, ntok, cand_ids, out, stream=None):
+        ntok = np.ascontiguousarray(ntok, dtype=np.int32)
+        _check(lib().tachiom_debug_refine_scores(self.h, ct.byref(params), _dp(queries), _hp(ntok),
+                                                 int(ntok.shape[0]), _dp(cand_ids), _dp(out), _stream(stream)))
+
     def stream_status(self, stream=None) -> int:
         f = ct.c_uint32()
         _check(lib().tachiom_stream_status(self.h, _stream(stream), ct.byref(f)))
         return f.value
+
+
+class Server:
+    """Continuous-batching request loop (tachiom_server_*) over a loaded Index."""
+
+    def __init__(self, index: Index, params: SearchParams, n_slots: int = 3, max_batch_queries: int = 64,
+                 max_batch_rows: int = 2048, max_wait_us: int = 200, scratch_budget_bytes: int = 0):
+        self.index = index  # keeps the index alive
+        cfg = ServerConfig(n_slots, max_batch_queries, max_batch_rows, max_wait_us, scratch_budget_bytes)
+        h = ct.c_void_p()
+        _check(lib().tachiom_server_create(index.h, ct.byref(params), ct.byref(cfg), ct.byref(h)))
+        self.h = h
+
+    def submit(self, query: np.ndarray, k: int) -> int:
+        q = np.ascontiguousarray(query, dtype=np.float32)
+        rid = ct.c_uint64()
+        _check(lib().tachiom_server_submit(self.h, _hp(q), int(q.shape[0]), int(k), ct.byref(rid)))
+        return rid.value
+
+    def wait(self, rid: int, k: int, timeout_ms: int = -1):
+        ids = np.empty(k, np.int32)
+        sc = np.empty(k, np.float32)
+        lat = ct.c_double()
+        _check(lib().tachiom_server_wait(self.h, ct.c_uint64(rid), int(timeout_ms), _hp(ids), _hp(sc),
+                                         ct.byref(lat)))
+        return ids, sc, lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().tachiom_server_read_stats(self.h, ct.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tachiom_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

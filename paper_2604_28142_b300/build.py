@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtachiom.so")
-SOURCES = ["index.cu", "search.cu", "k_topc.cu", "k_topc_tc.cu", "k_gather.cu", "k_refine.cu", "profile.cu", "refine_noalloc.cu"]
+SOURCES = ["index.cu", "search.cu", "k_topc.cu", "k_topc_tc.cu", "k_gather.cu", "k_refine.cu", "profile.cu", "refine_noalloc.cu", "k_refine_tc.cu", "server.cu", "k_topc_tc1.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -21,7 +21,7 @@ def _nvcc() -> str:
 
 def build(force: bool = False, verbose: bool = False, jobs: int = 8) -> str:
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    hdrs = [os.path.join(CSRC, "tachiom_internal.cuh"),
+    hdrs = [os.path.join(CSRC, "tachiom_internal.cuh"), os.path.join(CSRC, "tc_common.cuh"),
             os.path.join(os.path.dirname(HERE), "include", "tachiom.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

@@ -171,6 +171,11 @@ extern "C" tachiom_status tachiom_index_load(const tachiom_index_desc *desc, int
     }
   for (int64_t j = 0; j < C; j++) loff[j + 1] += loff[j];
   ix->n_list = loff[C];
+  if (ix->n_list >= (1LL << 31)) {
+    delete ix;
+    cudaSetDevice(prev);
+    return fail(TACHIOM_ERR_CAPACITY, "more than 2^31 (doc, centroid) list entries");
+  }
   std::vector<int32_t> ldoc((size_t)ix->n_list);
   {
     std::vector<int64_t> fill(loff.begin(), loff.end() - 1);

@@ -24,6 +24,16 @@
 namespace tachiom {
 
 constexpr int G_THREADS = 1024;
+constexpr int G_SEGCAP = 1536;  // (query token, retrieved centroid) segments described at once
+
+// Per (token, centroid) segment of a list inside the CTA's document range:
+// start (absolute position in list_doc), exclusive prefix of the lengths within
+// its token, and the order-preserving key of <q_i, c_j>.
+struct GSeg {
+  int32_t start;
+  int32_t pref;
+  uint32_t key;
+};
 
 __global__ void __launch_bounds__(G_THREADS, 1)
 k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
@@ -35,11 +45,11 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
   uint32_t *best = gsm;                                   // [RD] max key of the current token
   float *S = reinterpret_cast<float *>(gsm + RD);         // [RD] running S~
   uint32_t *h = gsm + 2 * RD;                             // [NBINS1]
-  __shared__ int64_t seg_base[MAX_KC];
-  __shared__ uint32_t seg_key[MAX_KC];
-  __shared__ int seg_pref[MAX_KC + 1];
+  GSeg *seg = reinterpret_cast<GSeg *>(gsm + 2 * RD + NBINS1);  // [G_SEGCAP]
+  __shared__ int tok_total[MAX_NTOK];
 
   const int r = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = (int64_t)r * RD;
   const int nd = (int)min((int64_t)RD, D - r0);
   for (int x = tid; x < RD; x += G_THREADS) {
@@ -48,61 +58,85 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
   }
   for (int b = tid; b < NBINS1; b += G_THREADS) h[b] = 0u;
   const int row_b = qoff[q], row_e = qoff[q + 1];
-  __syncthreads();
+  const int per_group = max(1, G_SEGCAP / kc);  // tokens whose segments fit at once
 
-  for (int i = row_b; i < row_e; i++) {
-    if (tid < kc) {
-      int32_t j = top_ids[(int64_t)i * kc + tid];
-      int len = 0;
-      if (j >= C) {
+  for (int i0 = row_b; i0 < row_e; i0 += per_group) {
+    const int ng = min(per_group, row_e - i0);
+    __syncthreads();  // previous group's segments are no longer read
+    // describe every segment of the group in parallel (independent loads)
+    for (int e = tid; e < ng * kc; e += G_THREADS) {
+      const int ti = e / kc;
+      int32_t jj = top_ids[(int64_t)(i0 + ti) * kc + (e % kc)];
+      if (jj >= C) {
         atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
-        j = -1;
+        jj = -1;
       }
-      if (j >= 0) {
-        int lo = list_roff[(int64_t)j * nr1 + r], hi = list_roff[(int64_t)j * nr1 + r + 1];
-        seg_base[tid] = list_off[j] + lo;
-        seg_key[tid] = fkey(top_s[(int64_t)i * kc + tid]);
-        len = hi - lo;
+      GSeg g;
+      g.start = 0;
+      g.pref = 0;  // length until the scan below
+      g.key = 0u;
+      if (jj >= 0) {
+        const int lo = list_roff[(int64_t)jj * nr1 + r], hi = list_roff[(int64_t)jj * nr1 + r + 1];
+        g.start = (int32_t)(list_off[jj] + lo);
+        g.pref = hi - lo;
+        g.key = fkey(top_s[(int64_t)(i0 + ti) * kc + (e % kc)]);
       }
-      seg_pref[tid + 1] = len;
+      seg[e] = g;
     }
     __syncthreads();
-    if (tid == 0) {
-      seg_pref[0] = 0;
-      for (int u = 0; u < kc; u++) seg_pref[u + 1] += seg_pref[u];
+    // exclusive prefix of the lengths within each token: one warp per token
+    for (int ti = warp; ti < ng; ti += G_THREADS / 32) {
+      GSeg *sg = seg + ti * kc;
+      int carry = 0;
+      for (int u0 = 0; u0 < kc; u0 += 32) {
+        const int u = u0 + lane;
+        const int len = u < kc ? sg[u].pref : 0;
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (u < kc) sg[u].pref = carry + incl - len;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (lane == 0) tok_total[ti] = carry;
     }
     __syncthreads();
-    const int total = seg_pref[kc];
-    // pass 1: per-document max over the retrieved centroids (step 3)
-    for (int e = tid; e < total; e += G_THREADS) {
-      int lo = 0, hi = kc;  // find seg with pref[seg] <= e < pref[seg+1]
-      while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (seg_pref[mid] <= e) lo = mid; else hi = mid;
+    for (int ti = 0; ti < ng; ti++) {
+      const GSeg *sg = seg + ti * kc;
+      const int total = tok_total[ti];
+      // pass 1: per-document max over the retrieved centroids (step 3)
+      for (int e = tid; e < total; e += G_THREADS) {
+        int lo = 0, hi = kc;  // the segment with pref <= e < next pref
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (sg[mid].pref <= e) lo = mid; else hi = mid;
+        }
+        const int32_t d = list_doc[sg[lo].start + (e - sg[lo].pref)];
+        atomicMax(&best[d - r0], sg[lo].key);
       }
-      int32_t d = list_doc[seg_base[lo] + (e - seg_pref[lo])];
-      atomicMax(&best[d - r0], seg_key[lo]);
+      __syncthreads();
+      // pass 2: fold the max into S~ once per reached document (step 4)
+      for (int e = tid; e < total; e += G_THREADS) {
+        int lo = 0, hi = kc;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (sg[mid].pref <= e) lo = mid; else hi = mid;
+        }
+        const int32_t d = list_doc[sg[lo].start + (e - sg[lo].pref)];
+        const uint32_t v = atomicExch(&best[d - r0], 0u);
+        if (v) {
+          const float sv = funkey(v), cur = S[d - r0];
+          S[d - r0] = (cur == -INFINITY) ? sv : cur + sv;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // pass 2: fold the max into S~ once per reached document (step 4)
-    for (int e = tid; e < total; e += G_THREADS) {
-      int lo = 0, hi = kc;
-      while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (seg_pref[mid] <= e) lo = mid; else hi = mid;
-      }
-      int32_t d = list_doc[seg_base[lo] + (e - seg_pref[lo])];
-      uint32_t v = atomicExch(&best[d - r0], 0u);
-      if (v) {
-        float s = funkey(v), cur = S[d - r0];
-        S[d - r0] = (cur == -INFINITY) ? s : cur + s;
-      }
-    }
-    __syncthreads();
   }
   float *out = dense + (int64_t)q * D + r0;
   for (int x = tid; x < nd; x += G_THREADS) {
-    float v = S[x];
+    const float v = S[x];
     out[x] = v;
     if (v != -INFINITY) atomicAdd(&h[fkey(v) >> 20], 1u);
   }
@@ -118,12 +152,11 @@ tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, 
   if (nq <= 0) return TACHIOM_OK;
   TPROF("gather", s);
   TCUDA(cudaMemsetAsync(hist, 0, (size_t)nq * NBINS1 * 4, s));
-  size_t smem = (size_t)ix.range_docs * 8 + NBINS1 * 4;
+  const size_t smem = (size_t)ix.range_docs * 8 + NBINS1 * 4 + (size_t)G_SEGCAP * sizeof(GSeg);
   TCUDA(cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(ix.n_ranges, nq);
-  k_gather<<<grid, G_THREADS, smem, s>>>(meta_qoff, top_ids, top_s, kc, ix.list_off, ix.list_doc,
-                                         ix.list_roff, ix.n_ranges + 1, ix.D, ix.range_docs, ix.C, dense, hist,
-                                         flags);
+  k_gather<<<grid, G_THREADS, smem, s>>>(meta_qoff, top_ids, top_s, kc, ix.list_off, ix.list_doc, ix.list_roff,
+                                         ix.n_ranges + 1, ix.D, ix.range_docs, ix.C, dense, hist, flags);
   TLAUNCH();
   return TACHIOM_OK;
 }
@@ -141,9 +174,11 @@ constexpr int SEL_THREADS = 256;
 __device__ __forceinline__ int level_shift(int L) { return L == 1 ? 20 : (L == 2 ? 8 : 0); }
 __device__ __forceinline__ int level_bins(int L) { return L == 3 ? 256 : 4096; }
 
-__global__ void k_sel_find(const uint32_t *__restrict__ hist, uint32_t *__restrict__ state, int kd, int L,
+__global__ void k_sel_find(const uint32_t *__restrict__ hist, uint32_t *__restrict__ state,
+                           const int32_t *__restrict__ meta, int nq, int kd_max, int L,
                            uint32_t *__restrict__ flags) {
   const int q = blockIdx.x;
+  const int kd = min(kd_max, meta[4 * nq + 2 + q]);
   uint32_t *st = state + (int64_t)q * 8;
   if (threadIdx.x != 0) return;
   if (L == 1) {
@@ -243,8 +278,9 @@ k_sel_collect(const float *__restrict__ dense, int64_t D, uint32_t *__restrict__
 // ordered pass for a cut inside a long run of equal keys: the lowest doc ids win
 __global__ void __launch_bounds__(1024)
 k_sel_ties(const float *__restrict__ dense, int64_t D, uint32_t *__restrict__ state,
-           uint64_t *__restrict__ selbuf, int kd) {
+           uint64_t *__restrict__ selbuf, const int32_t *__restrict__ meta, int nq, int kd_max) {
   const int q = blockIdx.x;
+  const int kd = min(kd_max, meta[4 * nq + 2 + q]);
   uint32_t *st = state + (int64_t)q * 8;
   if (!st[S_TIES]) return;
   __shared__ int s_taken;
@@ -280,10 +316,11 @@ k_sel_ties(const float *__restrict__ dense, int64_t D, uint32_t *__restrict__ st
 }
 
 __global__ void __launch_bounds__(1024)
-k_sel_sort(uint32_t *__restrict__ state, uint64_t *__restrict__ selbuf, int kd, int32_t *__restrict__ cand,
-           float *__restrict__ cand_s, int32_t *__restrict__ ncand) {
+k_sel_sort(uint32_t *__restrict__ state, uint64_t *__restrict__ selbuf, const int32_t *__restrict__ meta, int nq,
+           int kd, int32_t *__restrict__ cand, float *__restrict__ cand_s, int32_t *__restrict__ ncand) {
   extern __shared__ __align__(16) uint64_t ssm[];
   const int q = blockIdx.x;
+  const int kdq = min(kd, meta[4 * nq + 2 + q]);  // this query's cut; the row stride stays kd
   const uint32_t *st = state + (int64_t)q * 8;
   const int n = (int)umin(st[S_CNT], (uint32_t)SEL_CAP);
   const int np = next_pow2(max(n, 2));
@@ -291,7 +328,7 @@ k_sel_sort(uint32_t *__restrict__ state, uint64_t *__restrict__ selbuf, int kd, 
   for (int i = threadIdx.x; i < np; i += blockDim.x) ssm[i] = i < n ? buf[i] : 0ull;
   __syncthreads();
   block_sort_desc(ssm, np);
-  const int m = min(n, kd);
+  const int m = min(n, kdq);
   for (int i = threadIdx.x; i < kd; i += blockDim.x) {
     uint64_t v = i < m ? ssm[i] : 0ull;
     cand[(int64_t)q * kd + i] = v ? comp_id(v) : -1;
@@ -300,29 +337,30 @@ k_sel_sort(uint32_t *__restrict__ state, uint64_t *__restrict__ selbuf, int kd, 
   if (threadIdx.x == 0) ncand[q] = m;
 }
 
-tachiom_status launch_select_kd(const Index &ix, int nq, int kd, const float *dense, const uint32_t *hist,
+tachiom_status launch_select_kd(const Index &ix, const int32_t *meta, int nq, int kd, const float *dense,
+                                const uint32_t *hist,
                                 uint32_t *hist2, uint32_t *state, uint64_t *selbuf, int32_t *cand,
                                 float *cand_s, int32_t *ncand, uint32_t *flags, cudaStream_t s) {
   if (nq <= 0) return TACHIOM_OK;
   TPROF("select_kd", s);
   const int64_t D = ix.D;
   dim3 grid((unsigned)((D + SEL_CHUNK - 1) / SEL_CHUNK), nq);
-  k_sel_find<<<nq, 32, 0, s>>>(hist, state, kd, 1, flags);
+  k_sel_find<<<nq, 32, 0, s>>>(hist, state, meta, nq, kd, 1, flags);
   TLAUNCH();
   for (int L = 2; L <= 3; L++) {
     TCUDA(cudaMemsetAsync(hist2, 0, (size_t)nq * NBINS1 * 4, s));
     k_sel_hist<<<grid, SEL_THREADS, 0, s>>>(dense, D, state, hist2, L);
     TLAUNCH();
-    k_sel_find<<<nq, 32, 0, s>>>(hist2, state, kd, L, flags);
+    k_sel_find<<<nq, 32, 0, s>>>(hist2, state, meta, nq, kd, L, flags);
     TLAUNCH();
   }
   k_sel_collect<<<grid, SEL_THREADS, 0, s>>>(dense, D, state, selbuf, flags);
   TLAUNCH();
-  k_sel_ties<<<nq, 1024, 0, s>>>(dense, D, state, selbuf, kd);
+  k_sel_ties<<<nq, 1024, 0, s>>>(dense, D, state, selbuf, meta, nq, kd);
   TLAUNCH();
   size_t smem = (size_t)SEL_CAP * 8;
   TCUDA(cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_sel_sort<<<nq, 1024, smem, s>>>(state, selbuf, kd, cand, cand_s, ncand);
+  k_sel_sort<<<nq, 1024, smem, s>>>(state, selbuf, meta, nq, kd, cand, cand_s, ncand);
   TLAUNCH();
   return TACHIOM_OK;
 }

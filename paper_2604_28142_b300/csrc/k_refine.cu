@@ -52,6 +52,13 @@ k_refine(const float *__restrict__ queries, const int32_t *__restrict__ meta, in
   const int ntok = meta[3 * nq + 2 + q];
   const int i0 = grp * G;
   if (i0 >= ntok) return;
+  {
+    // nothing to do in this slice (e.g. the tail of a short rescoring window): skip the tables
+    const int sb = blockIdx.x * R_DOCS_PER_CTA, se = min(kd, sb + R_DOCS_PER_CTA);
+    int any = 0;
+    for (int i = sb + (int)threadIdx.x; i < se && !any; i += R_THREADS) any = cand[(int64_t)q * kd + i] >= 0;
+    if (!__syncthreads_or(any)) return;
+  }
   const int ng = min(G, ntok - i0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 

@@ -12,10 +12,10 @@
 //
 // Selection without per-row buffers, in two passes over the same products:
 //   pass 1  every group of 32 consecutive centroids reports, per query row, its
-//           maximum score (one redux.sync per column);
-//   tau     tau_r = the kappa_c-th largest group maximum of row r. Those kappa_c
-//           maxima are kappa_c distinct scores, so tau_r <= the row's
-//           kappa_c-th best approximate score;
+//           two largest scores (redux.sync per column);
+//   tau     tau_r = a lower bound on the row's kappa_c-th largest of those
+//           2 x G scores, which are scores of distinct centroids, so tau_r <=
+//           the row's kappa_c-th best approximate score (k_topc_tau);
 //   pass 2  every score >= tau_r - margin is appended to the row's list.
 // With margin = 2 * delta, delta a bound on |BF16 score - FP32 score|, the
 // list holds every centroid of the row's exact FP32 top-kappa_c; the merge
@@ -32,7 +32,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "tachiom_internal.cuh"
+#include "tc_common.cuh"
 
 namespace tachiom {
 
@@ -51,7 +51,6 @@ constexpr int THREADS = 320;       // 10 warps
 constexpr int EPI_WARPS = 8;
 constexpr int TMEM_COLS = 512;
 constexpr int CAPG = 4096;         // candidates per row after pass 2
-constexpr uint64_t TIMEOUT_NS = 2000000000ull;
 
 struct Ctl {
   uint64_t full[STAGES];
@@ -62,117 +61,11 @@ struct Ctl {
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
-  uint32_t thr[BN];  // pass 2: fkey(tau - margin) per row of the CTA
+  float thrf[BN];    // pass 2: tau - margin per row of the CTA (+inf for rows past R)
 };
 constexpr int SMEM_BYTES = TILE_BYTES + (int)sizeof(Ctl) + 1024;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: false when the CTA is aborting or the time limit passed
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort, uint32_t *flags) {
-  uint64_t t0 = 0;
-  for (uint32_t i = 0;; i++) {
-    if (mbar_test(b, parity)) return true;
-    if ((i & 63) == 0) {
-      if (*abort) return false;
-      uint64_t t = gtimer();
-      if (i == 0) t0 = t;
-      else if (t - t0 > TIMEOUT_NS) {
-        *abort = 1;
-        atomicOr(flags, TACHIOM_FLAG_TIMEOUT);
-        return false;
-      }
-    }
-  }
-}
-// wait with a bound and no abort check (drain at exit)
-__device__ __forceinline__ void mbar_drain(uint64_t *b, uint32_t parity) {
-  uint64_t t0 = gtimer();
-  while (!mbar_test(b, parity))
-    if (gtimer() - t0 > TIMEOUT_NS) break;
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // 128-byte swizzle
-  return d;
-}
-
-// instruction descriptor: kind::f16, A = B = BF16, D = F32, K-major both, M = 128, N = 256
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accum));
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-#define TC_LD32(taddr, v)                                                                                    \
-  asm volatile(                                                                                              \
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"      \
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                             \
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),      \
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), \
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),           \
-        "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),           \
-        "=r"(v[30]), "=r"(v[31])                                                                             \
-      : "r"(taddr))
-
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ uint32_t redux_max(uint32_t x) {
-  uint32_t r;
-  asm volatile("redux.sync.max.u32 %0, %1, 0xffffffff;" : "=r"(r) : "r"(x));
-  return r;
-}
-
-// MODE 1: group maxima -> gmax[rb][tile*4 + quarter][256]
+// MODE 1: two largest per group -> gmax[rb][tile*4 + quarter][2][256]
 // MODE 2: append scores >= thr to cand[row][CAPG], cnt[row]
 // MODE 3: raw scores to (float *)cand [R x C] (diagnostics and tests)
 template <int MODE>
@@ -209,10 +102,10 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   }
   if (MODE == 2) {
     for (int n = threadIdx.x; n < BN; n += THREADS) {
-      int row = rb * BN + n;
-      uint32_t t = (row < R) ? tau[row] : 0xFFFFFFFFu;
+      const int row = rb * BN + n;
+      const uint32_t t = (row < R) ? tau[row] : 0u;
       // tau == 0: fewer than kappa_c groups, keep everything
-      ctl->thr[n] = (row >= R) ? 0xFFFFFFFFu : (t == 0 ? 0u : fkey(funkey(t) - margin));
+      ctl->thrf[n] = (row >= R) ? INFINITY : (t == 0 ? -INFINITY : funkey(t) - margin);
     }
   }
   if (warp == 1) {
@@ -263,7 +156,8 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         for (int kk = 0; kk < 8; kk++) {
           const uint32_t off = (uint32_t)((kk >> 2) * A_HALF + (kk & 3) * 32);
           const uint32_t boff = (uint32_t)((kk >> 2) * B_HALF + (kk & 3) * 32);
-          mma_bf16(tmem + (uint32_t)(buf * BN), sdesc(a_base + off), sdesc(b_base + boff), kk > 0 ? 1u : 0u);
+          mma_bf16(tmem + (uint32_t)(buf * BN), sdesc(a_base + off), sdesc(b_base + boff), idesc_bf16(BM, BN),
+                   kk > 0 ? 1u : 0u);
         }
         mma_commit(&ctl->empty[s]);
         mma_commit(&ctl->tfull[buf]);
@@ -279,55 +173,68 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int half = e >> 2;            // column half: query rows [half*128, +128)
     for (int it = 0; it < nt; it++) {
       const int buf = it & 1;
-      if (!mbar_wait(&ctl->tfull[buf], (it >> 1) & 1, abort, flags)) break;
-      fence_after();
-      uint32_t v[4][32];
-      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + half * 128);
-      TC_LD32(ta + 0, v[0]);
-      TC_LD32(ta + 32, v[1]);
-      TC_LD32(ta + 64, v[2]);
-      TC_LD32(ta + 96, v[3]);
-      tmem_ld_wait();
-      fence_before();
+      // one lane waits, the whole warp follows its verdict (the TMEM loads below are warp-aligned)
+      int ok = 0;
+      if (lane == 0) ok = mbar_wait(&ctl->tfull[buf], (it >> 1) & 1, abort, flags) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
       __syncwarp();
-      if (lane == 0) mbar_arrive(&ctl->tempty[buf]);
+      fence_after();
+      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + half * 128);
       const int tile = t0 + it;
       const int64_t j = (int64_t)tile * BM + quarter * 32 + lane;  // this thread's centroid
       const bool jv = j < C;
-      if (MODE == 1) {
-        uint32_t *dst = gmax + ((int64_t)rb * G + tile * 4 + quarter) * BN + half * 128;
-#pragma unroll
-        for (int ch = 0; ch < 4; ch++) {
-          uint32_t mine = 0;
-#pragma unroll
-          for (int c = 0; c < 32; c++) {
-            uint32_t k = jv ? fkey(__uint_as_float(v[ch][c])) : 0u;
-            uint32_t m = redux_max(k);
-            if (c == lane) mine = m;
-          }
-          dst[ch * 32 + lane] = mine;
+#pragma unroll 1
+      for (int pr = 0; pr < 2; pr++) {
+        uint32_t v[2][32];
+        TC_LD32(ta + pr * 64, v[0]);
+        TC_LD32(ta + pr * 64 + 32, v[1]);
+        tmem_ld_wait();
+        if (pr == 1) {
+          // every column of this buffer has been read: hand it back to the MMA warp
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&ctl->tempty[buf]);
         }
-      } else if (MODE == 3) {
-        // diagnostic: raw scores [R x C]
 #pragma unroll
-        for (int ch = 0; ch < 4; ch++) {
+        for (int cc = 0; cc < 2; cc++) {
+          const int ch = pr * 2 + cc;
+          if (MODE == 1) {
+            // the two largest scores of the warp's 32 centroids, per query row
+            uint32_t *dst = gmax + (((int64_t)rb * G + tile * 4 + quarter) * 2) * BN + half * 128;
+            float m1l = -INFINITY, m2l = -INFINITY;
 #pragma unroll
-          for (int c = 0; c < 32; c++) {
-            const int row = rb * BN + half * 128 + ch * 32 + c;
-            if (jv && row < R) reinterpret_cast<float *>(cand)[(int64_t)row * C + j] = __uint_as_float(v[ch][c]);
-          }
-        }
-      } else {
+            for (int c = 0; c < 32; c++) {
+              const float x = jv ? __uint_as_float(v[cc][c]) : -INFINITY;
+              const float m1 = redux_fmax(x);
+              const unsigned eq = __ballot_sync(0xffffffffu, x == m1);
+              const float m2 = (__popc(eq) > 1) ? m1 : redux_fmax(x == m1 ? -INFINITY : x);
+              m1l = (c == lane) ? m1 : m1l;
+              m2l = (c == lane) ? m2 : m2l;
+            }
+            dst[ch * 32 + lane] = (m1l == -INFINITY) ? 0u : fkey(m1l);
+            dst[BN + ch * 32 + lane] = (m2l == -INFINITY) ? 0u : fkey(m2l);
+          } else if (MODE == 3) {
+            // diagnostic: raw scores [R x C]
 #pragma unroll
-        for (int ch = 0; ch < 4; ch++) {
+            for (int c = 0; c < 32; c++) {
+              const int row = rb * BN + half * 128 + ch * 32 + c;
+              if (jv && row < R) reinterpret_cast<float *>(cand)[(int64_t)row * C + j] = __uint_as_float(v[cc][c]);
+            }
+          } else {
+            // the warp's max per column decides (uniformly) whether any lane has a candidate
 #pragma unroll
-          for (int c = 0; c < 32; c++) {
-            const int n = half * 128 + ch * 32 + c;
-            const float sc = __uint_as_float(v[ch][c]);
-            if (jv && rb * BN + n < R && fkey(sc) >= ctl->thr[n]) {
-              const int row = rb * BN + n;
-              const int pos = atomicAdd(&cnt[row], 1);
-              if (pos < CAPG) cand[(int64_t)row * CAPG + pos] = comp_key(sc, (int32_t)j);
+            for (int c = 0; c < 32; c++) {
+              const int n = half * 128 + ch * 32 + c;
+              const float sc = jv ? __uint_as_float(v[cc][c]) : -INFINITY;
+              const float lim = ctl->thrf[n];
+              if (redux_fmax(sc) >= lim) {
+                if (sc >= lim) {
+                  const int row = rb * BN + n;
+                  const int pos = atomicAdd(&cnt[row], 1);
+                  if (pos < CAPG) cand[(int64_t)row * CAPG + pos] = comp_key(sc, (int32_t)j);
+                }
+              }
             }
           }
         }
@@ -343,31 +250,60 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   }
 }
 
-// tau_r = kappa_c-th largest group maximum of row r over one part of the groups;
-// the parts combine by max (each part's value is itself a valid lower bound).
-__global__ void __launch_bounds__(128)
-k_topc_tau(const uint32_t *__restrict__ gmax, int G, int gpart, int R, int kc, uint32_t *__restrict__ tau) {
-  extern __shared__ uint32_t top[];  // [kc][128]
-  const int rb = blockIdx.x >> 1, n = (blockIdx.x & 1) * 128 + threadIdx.x;
-  const int row = rb * BN + n;
-  const int tid = threadIdx.x;
-  for (int i = 0; i < kc; i++) top[i * 128 + tid] = 0u;
-  const int g0 = blockIdx.y * gpart, g1 = min(G, g0 + gpart);
-  const uint32_t *src = gmax + (int64_t)rb * G * BN + n;
-  uint32_t last = 0u;
-  for (int g = g0; g < g1; g++) {
-    const uint32_t x = src[(int64_t)g * BN];
-    if (x > last) {
-      int i = kc - 1;
-      while (i > 0 && top[(i - 1) * 128 + tid] < x) {
-        top[i * 128 + tid] = top[(i - 1) * 128 + tid];
-        i--;
-      }
-      top[i * 128 + tid] = x;
-      last = top[(kc - 1) * 128 + tid];
+// tau_r: a lower bound on the row's kappa_c-th largest score, from the two
+// largest scores of every group (2 x G actual scores of distinct centroids):
+// a saturating 8-bit histogram per row over [-cmax, cmax] (TAU_BINS bins; a
+// score above the range counts in the top bin), then the lower edge of the
+// highest bin at which the count from the top reaches kappa_c. At least
+// kappa_c scores lie at or above that edge, so it cannot exceed the
+// kappa_c-th largest score; the work per value does not depend on the order
+// in which the values arrive. A block owns 32 rows; its 4 warps histogram one
+// quarter of the groups each, lane = row.
+constexpr int TAU_WARPS = 4;
+constexpr int TAU_BINS = 1024;
+__global__ void __launch_bounds__(TAU_WARPS * 32)
+k_topc_tau(const uint32_t *__restrict__ gmax, int G, int R, int kc, float cmax, uint32_t *__restrict__ tau) {
+  extern __shared__ unsigned char hsm[];  // [TAU_WARPS][TAU_BINS][32] saturating counts
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rb = blockIdx.x >> 3, slab = blockIdx.x & 7;
+  const int n = slab * 32 + lane;
+  for (int i = threadIdx.x; i < TAU_WARPS * TAU_BINS * 32 / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t *>(hsm)[i] = 0u;
+  __syncthreads();
+  unsigned char *h = hsm + (size_t)warp * TAU_BINS * 32 + lane;
+  const float scale = TAU_BINS / (2.f * cmax);
+  const int per = (G + TAU_WARPS - 1) / TAU_WARPS;
+  const int g0 = warp * per, g1 = min(G, g0 + per);
+  const uint32_t *src = gmax + (int64_t)rb * G * 2 * BN + n;
+  for (int g = g0; g < g1; g += 4) {
+    uint32_t x[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) x[u] = (g + (u >> 1) < g1) ? src[((int64_t)(g + (u >> 1)) * 2 + (u & 1)) * BN] : 0u;
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      if (!x[u]) continue;
+      const float sc = funkey(x[u]);
+      const int b = max(0, min(TAU_BINS - 1, (int)floorf((sc + cmax) * scale)));
+      unsigned char *p = h + b * 32;
+      const unsigned char c = *p;
+      if (c != 255) *p = c + 1;
     }
   }
-  if (row < R && last) atomicMax(&tau[row], last);
+  __syncthreads();
+  if (warp == 0) {
+    int cum = 0, b = TAU_BINS - 1;
+    for (; b >= 0; b--) {
+      int c = 0;
+#pragma unroll
+      for (int w = 0; w < TAU_WARPS; w++) c += hsm[((size_t)w * TAU_BINS + b) * 32 + lane];
+      cum += c;
+      if (cum >= kc) break;
+    }
+    const int row = rb * BN + n;
+    // bin b's lower edge; fewer than kappa_c scores in all: no bound (keep everything)
+    const float edge = (b > 0) ? (b / scale - cmax) : -INFINITY;
+    if (row < R) tau[row] = (b >= 0 && edge > -INFINITY) ? fkey(edge) : 0u;
+  }
 }
 
 // ---- host side ---------------------------------------------------------------------------
@@ -407,6 +343,10 @@ tachiom_status encode_map(CUtensorMap *map, const void *base, int64_t rows, int 
 
 }  // namespace tc
 
+tachiom_status encode_bf16_map(CUtensorMap *map, const void *base, int64_t rows, int box_rows) {
+  return tc::encode_map(map, base, rows, box_rows);
+}
+
 int topc_tc_supported() {
   static int cached = -1;
   if (cached >= 0) return cached;
@@ -424,7 +364,7 @@ int topc_tc_capg() { return tc::CAPG; }
 size_t topc_tc_gmax_elems(int64_t C, int rows) {
   const int64_t ntiles = (C + tc::BM - 1) / tc::BM;
   const int64_t rbs = (rows + tc::BN - 1) / tc::BN;
-  return (size_t)(rbs * ntiles * 4 * tc::BN);
+  return (size_t)(rbs * ntiles * 4 * 2 * tc::BN);
 }
 
 tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, float margin,
@@ -452,11 +392,9 @@ tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nr
   k_topc_tc<1><<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, gmax, nullptr, 0.f, nullptr,
                                                   nullptr, flags);
   TLAUNCH();
-  TCUDA(cudaMemsetAsync(tau, 0, (size_t)nrows * 4, s));
-  const int parts = std::max(1, std::min(8, G / std::max(1, 64 * kc)));
-  const int gpart = (G + parts - 1) / parts;
-  TCUDA(cudaFuncSetAttribute(k_topc_tau, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_KC * 128 * 4));
-  k_topc_tau<<<dim3(rbs * 2, parts), 128, (size_t)kc * 128 * 4, s>>>(gmax, G, gpart, nrows, kc, tau);
+  const size_t tsm = (size_t)TAU_WARPS * TAU_BINS * 32;
+  TCUDA(cudaFuncSetAttribute(k_topc_tau, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+  k_topc_tau<<<rbs * 8, TAU_WARPS * 32, tsm, s>>>(gmax, G, nrows, kc, 1.0001f * ix.cnorm_max + 1e-6f, tau);
   TLAUNCH();
   TCUDA(cudaMemsetAsync(cnt, 0, (size_t)nrows * 4, s));
   k_topc_tc<2><<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, nullptr, tau, margin, cnt,

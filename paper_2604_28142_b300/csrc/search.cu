@@ -45,6 +45,14 @@ tachiom_status ws_get(Index *ix, cudaStream_t stream, Workspace **out) {
   return TACHIOM_OK;
 }
 
+void ws_release(Index *ix, cudaStream_t stream) {
+  std::lock_guard<std::mutex> g(ix->mu);
+  auto it = ix->ws.find(stream);
+  if (it == ix->ws.end()) return;
+  ws_destroy(it->second);
+  ix->ws.erase(it);
+}
+
 struct Need {
   int64_t nq = 0, rows = 0, kc = 0, kd = 0, split_entries = 0, dense = 0, gmax = 0;
 };
@@ -82,7 +90,7 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
     w->cap_q = w->cap_rows = 0;                      \
     return st;                                       \
   }
-  AL(w->d_meta, (4 * nq + 2) * 4);
+  AL(w->d_meta, (5 * nq + 2) * 4);
   AL(w->d_rows_f32, rows * DIM * 4);
   AL(w->d_rows_bf16, rows * DIM * 2);
   AL(w->d_split, se * 8);
@@ -100,6 +108,7 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   AL(w->d_cand_s, nq * kd * 4);
   AL(w->d_ncand, nq * 4);
   AL(w->d_part, nq * groups * kd * 4);
+  AL(w->d_win, nq * kd * 4);
   AL(w->d_out_ids, nq * kd * 4);
   AL(w->d_out_s, nq * kd * 4);
 #undef AL
@@ -212,8 +221,10 @@ static int resolve_kd(const tachiom_search_params *p, int max_k) {
 }
 
 // upload qoff | koff | k | ntok through pinned staging
-static tachiom_status upload_meta(Workspace *w, const int32_t *h_ntok, const int32_t *h_k, int nq) {
-  tachiom_status st = host_reserve(w, 4 * (int64_t)nq + 2);
+// qoff [nq+1] | koff [nq+1] | k [nq] | ntok [nq] | kappa_d of each query [nq]
+static tachiom_status upload_meta(Workspace *w, const tachiom_search_params *p, const int32_t *h_ntok,
+                                  const int32_t *h_k, int nq) {
+  tachiom_status st = host_reserve(w, 5 * (int64_t)nq + 2);
   if (st) return st;
   TCUDA(cudaEventSynchronize(w->meta_done));
   int32_t *m = w->h_meta;
@@ -225,8 +236,9 @@ static tachiom_status upload_meta(Workspace *w, const int32_t *h_ntok, const int
     m[nq + 2 + i] = m[nq + 1 + i] + k;
     m[2 * nq + 2 + i] = k;
     m[3 * nq + 2 + i] = h_ntok[i];
+    m[4 * nq + 2 + i] = resolve_kd(p, k);  // per query, so a result never depends on its batch
   }
-  TCUDA(cudaMemcpyAsync(w->d_meta, m, (size_t)(4 * nq + 2) * 4, cudaMemcpyHostToDevice, w->stream));
+  TCUDA(cudaMemcpyAsync(w->d_meta, m, (size_t)(5 * nq + 2) * 4, cudaMemcpyHostToDevice, w->stream));
   TCUDA(cudaEventRecord(w->meta_done, w->stream));
   return TACHIOM_OK;
 }
@@ -247,7 +259,9 @@ static float bf16_delta(const Index &ix) {
 
 // scratch sizes of step (a) for a batch
 static void need_topc(const Index &ix, const tachiom_search_params *p, int rows, const Plan &plan, Need *n) {
-  if (use_tc(p)) {
+  if (use_tc(p) && p->kappa_c <= topc_tc1_max_kc()) {
+    n->split_entries = (int64_t)rows * topc_tc1_splits(ix, rows) * topc_tc1_capout();
+  } else if (use_tc(p)) {
     n->split_entries = (int64_t)rows * topc_tc_capg();
     n->gmax = (int64_t)topc_tc_gmax_elems(ix.C, rows);
   } else {
@@ -260,7 +274,19 @@ static tachiom_status run_topc(Index *ix, Workspace *w, const tachiom_search_par
                                int nrows, const Plan &plan) {
   const int kc = p->kappa_c;
   tachiom_status st;
+  if (use_tc(p) && kc <= topc_tc1_max_kc()) {
+    // one pass, per-row running top-kappa_c in the epilogue
+    if ((st = launch_quantize_bf16(rows, w->d_rows_bf16, (int64_t)nrows * DIM, w->stream))) return st;
+    const float margin = 2.f * bf16_delta(*ix);
+    const int splits = topc_tc1_splits(*ix, nrows);
+    if ((st = launch_topc_tc1(*ix, w->d_rows_bf16, nrows, kc, margin, w->d_split, w->d_split_cnt, w->d_flags,
+                              w->stream)))
+      return st;
+    return launch_topc_merge(*ix, rows, nrows, kc, splits, topc_tc1_capout(), w->d_split, w->d_split_cnt, margin, 1,
+                             w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
+  }
   if (use_tc(p)) {
+    // kappa_c above the single-pass limit: two passes (group maxima, then a filter)
     if ((st = launch_quantize_bf16(rows, w->d_rows_bf16, (int64_t)nrows * DIM, w->stream))) return st;
     const float margin = 2.f * bf16_delta(*ix);
     if ((st = launch_topc_tc(*ix, w->d_rows_bf16, nrows, kc, margin, w->d_gmax, w->d_tau, w->d_split_cnt,
@@ -274,6 +300,32 @@ static tachiom_status run_topc(Index *ix, Workspace *w, const tachiom_search_par
     return st;
   return launch_topc_merge(*ix, rows, nrows, kc, plan.splits, plan.capout, w->d_split, w->d_split_cnt, 0.f, 0,
                            w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
+}
+
+// Bound on |tensor-core centroid term - FP32 centroid term| for one (query token,
+// document token): the query split q_hi + q_lo leaves 2^-18 |q_k| per component,
+// the bf16 table is exact when the centroids are stored in bf16 (a rounded
+// copy otherwise: 2^-9); the bound used is 16x those for the accumulation.
+static float refine_tc_delta(const Index &ix) {
+  const float rel = ix.cdtype == TACHIOM_DTYPE_BF16 ? ldexpf(1.f, -14) : ldexpf(1.f, -5);
+  return rel * ix.cnorm_max;
+}
+
+// steps (c)-(d): FP32 refine, or the tensor-core refine plus the FP32 repair of the
+// top-k window, into the caller's outputs
+static tachiom_status run_refine(Index *ix, Workspace *w, const tachiom_search_params *p, const float *queries,
+                                 int nq, const int32_t *cand, int kd, int32_t *out_ids, float *out_s,
+                                 cudaStream_t stream) {
+  tachiom_status st;
+  if (use_tc(p)) {
+    if ((st = launch_refine_tc(*ix, queries, w->d_meta, nq, cand, kd, w->d_part, w->d_flags, stream))) return st;
+    if ((st = launch_refine_window(*ix, w->d_meta, nq, cand, kd, w->d_part, refine_tc_delta(*ix), w->d_win,
+                                   stream)))
+      return st;
+    cand = w->d_win;
+  }
+  if ((st = launch_refine(*ix, queries, w->d_meta, nq, cand, kd, w->d_part, w->d_flags, stream))) return st;
+  return launch_final_topk(*ix, w->d_meta, nq, cand, kd, w->d_part, out_ids, out_s, stream);
 }
 
 struct DeviceGuard {
@@ -314,17 +366,15 @@ static tachiom_status search_device(Index *ix, const tachiom_search_params *p, c
   need_topc(*ix, p, b.rows, plan, &n);
   n.dense = (int64_t)nq * ix->D;
   if ((st = ws_reserve(ix, w, n))) return st;
-  if ((st = upload_meta(w, h_ntok, h_k, nq))) return st;
+  if ((st = upload_meta(w, p, h_ntok, h_k, nq))) return st;
   if ((st = run_topc(ix, w, p, d_queries, b.rows, plan))) return st;
   if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, p->kappa_c, w->d_dense, w->d_hist,
                           w->d_flags, stream)))
     return st;
-  if ((st = launch_select_kd(*ix, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
+  if ((st = launch_select_kd(*ix, w->d_meta, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
                              w->d_cand, w->d_cand_s, w->d_ncand, w->d_flags, stream)))
     return st;
-  if ((st = launch_refine(*ix, d_queries, w->d_meta, nq, w->d_cand, kd, w->d_part, w->d_flags, stream)))
-    return st;
-  return launch_final_topk(*ix, w->d_meta, nq, w->d_cand, kd, w->d_part, d_out_ids, d_out_scores, stream);
+  return run_refine(ix, w, p, d_queries, nq, w->d_cand, kd, d_out_ids, d_out_scores, stream);
 }
 
 }  // namespace tachiom
@@ -464,12 +514,12 @@ extern "C" tachiom_status tachiom_gather(tachiom_index *index, const tachiom_sea
   n.kd = kd;
   n.dense = (int64_t)nq * ix->D;
   if ((st = ws_reserve(ix, w, n))) return st;
-  if ((st = upload_meta(w, h_ntok, nullptr, nq))) return st;
+  if ((st = upload_meta(w, params, h_ntok, nullptr, nq))) return st;
   if ((st = launch_score_pairs(*ix, d_queries, b.rows, d_top_ids, params->kappa_c, w->d_top_s, s))) return st;
   if ((st = launch_gather(*ix, w->d_meta, nq, d_top_ids, w->d_top_s, params->kappa_c, w->d_dense, w->d_hist,
                           w->d_flags, s)))
     return st;
-  return launch_select_kd(*ix, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
+  return launch_select_kd(*ix, w->d_meta, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
                           d_cand_ids, d_cand_scores, d_ncand, w->d_flags, s);
 }
 
@@ -498,9 +548,8 @@ extern "C" tachiom_status tachiom_refine(tachiom_index *index, const tachiom_sea
   n.kc = params->kappa_c;
   n.kd = kd;
   if ((st = ws_reserve(ix, w, n))) return st;
-  if ((st = upload_meta(w, h_ntok, h_k, nq))) return st;
-  if ((st = launch_refine(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, w->d_part, w->d_flags, s))) return st;
-  return launch_final_topk(*ix, w->d_meta, nq, d_cand_ids, kd, w->d_part, d_out_ids, d_out_scores, s);
+  if ((st = upload_meta(w, params, h_ntok, h_k, nq))) return st;
+  return run_refine(ix, w, params, d_queries, nq, d_cand_ids, kd, d_out_ids, d_out_scores, s);
 }
 
 extern "C" tachiom_status tachiom_stream_status(tachiom_index *index, void *stream, uint32_t *h_flags) {
@@ -537,4 +586,36 @@ extern "C" tachiom_status tachiom_debug_tc_scores(tachiom_index *index, const fl
   if ((st = ws_reserve(ix, w, n))) return st;
   if ((st = launch_quantize_bf16(d_rows, w->d_rows_bf16, (int64_t)nrows * DIM, s))) return st;
   return launch_topc_tc_raw(*ix, w->d_rows_bf16, nrows, d_out, w->d_flags, s);
+}
+
+extern "C" tachiom_status tachiom_debug_refine_scores(tachiom_index *index, const tachiom_search_params *params,
+                                                     const float *d_queries, const int32_t *h_ntok, int32_t nq,
+                                                     const int32_t *d_cand_ids, float *d_scores, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
+  DeviceGuard g(ix->device);
+  tachiom_status st;
+  if ((st = check_params(params))) return st;
+  if (params->kappa_d < 1) return fail(TACHIOM_ERR_INVALID, "kappa_d must be given");
+  Batch b;
+  if ((st = check_batch(h_ntok, nullptr, nq, 0, &b))) return st;
+  if (nq == 0) return TACHIOM_OK;
+  if (!d_queries || !d_cand_ids || !d_scores) return fail(TACHIOM_ERR_INVALID, "NULL device buffer");
+  const int kd = params->kappa_d;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w;
+  if ((st = ws_get(ix, s, &w))) return st;
+  Need n;
+  n.nq = nq;
+  n.rows = b.rows;
+  n.kc = params->kappa_c;
+  n.kd = kd;
+  if ((st = ws_reserve(ix, w, n))) return st;
+  if ((st = upload_meta(w, params, h_ntok, nullptr, nq))) return st;
+  if (use_tc(params)) {
+    if ((st = launch_refine_tc(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, w->d_part, w->d_flags, s))) return st;
+  } else {
+    if ((st = launch_refine(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, w->d_part, w->d_flags, s))) return st;
+  }
+  return launch_refine_sum(*ix, w->d_meta, nq, d_cand_ids, kd, w->d_part, d_scores, s);
 }

@@ -153,6 +153,7 @@ struct Workspace {
   float *d_cand_s = nullptr;           // [B x kd]
   int32_t *d_ncand = nullptr;          // [B]
   float *d_part = nullptr;             // [B x groups x kd] refine partial sums
+  int32_t *d_win = nullptr;            // [B x kd] FP32 rescoring window of the tensor-core refine
   int32_t *d_out_ids = nullptr;        // staging for search_host
   float *d_out_s = nullptr;
   uint32_t *d_flags = nullptr;         // status word
@@ -170,6 +171,7 @@ struct Workspace {
 // lifecycle helpers (search.cu)
 tachiom_status ws_get(Index *ix, cudaStream_t stream, Workspace **out);
 void ws_destroy(Workspace *w);
+void ws_release(Index *ix, cudaStream_t stream);  // free a stream's scratch (the stream is idle)
 
 // ---- per-launcher timing (tachiom_profile_enable) -----------------------------------
 class ProfScope {
@@ -203,6 +205,11 @@ int topc_tc_supported();
 tachiom_status launch_topc_tc_raw(const Index &ix, const __nv_bfloat16 *rows, int nrows, float *out,
                                   uint32_t *flags, cudaStream_t s);
 int topc_tc_capg();
+tachiom_status launch_topc_tc1(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, float margin,
+                               uint64_t *split_out, int32_t *split_cnt, uint32_t *flags, cudaStream_t s);
+int topc_tc1_capout();
+int topc_tc1_max_kc();
+int topc_tc1_splits(const Index &ix, int nrows);
 size_t topc_tc_gmax_elems(int64_t C, int rows);
 tachiom_status launch_score_pairs(const Index &ix, const float *rows, int nrows, const int32_t *ids,
                                   int kc, float *scores, cudaStream_t s);
@@ -210,7 +217,7 @@ tachiom_status launch_score_pairs(const Index &ix, const float *rows, int nrows,
 tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, const int32_t *top_ids,
                              const float *top_s, int kc, float *dense, uint32_t *hist,
                              uint32_t *flags, cudaStream_t s);
-tachiom_status launch_select_kd(const Index &ix, int nq, int kd, const float *dense,
+tachiom_status launch_select_kd(const Index &ix, const int32_t *meta, int nq, int kd, const float *dense,
                                 const uint32_t *hist, uint32_t *hist2, uint32_t *state,
                                 uint64_t *selbuf, int32_t *cand, float *cand_s, int32_t *ncand,
                                 uint32_t *flags, cudaStream_t s);
@@ -222,5 +229,11 @@ tachiom_status launch_final_topk(const Index &ix, const int32_t *meta, int nq, c
                                  int kd, const float *part, int32_t *out_ids, float *out_s,
                                  cudaStream_t s);
 int refine_groups(int M);
+tachiom_status launch_refine_tc(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s);
+tachiom_status launch_refine_sum(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
+                                 const float *part, float *out, cudaStream_t s);
+tachiom_status launch_refine_window(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
+                                    const float *part, float delta_per_token, int32_t *win, cudaStream_t s);
 
 }  // namespace tachiom

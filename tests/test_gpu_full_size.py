@@ -1,0 +1,52 @@
+"""Full-size parity: the 1M-document passage-ranking workload (~70M tokens,
+C = 262,144 bf16 centroids) in the launch configuration the benchmark times
+(batches of 64 queries x 32 tokens, kappa_c = 40, kappa_d = 1000, k = 10), checked
+against the FP64 oracle on a sample of queries it can compute one by one.
+Needs a GPU; the index is generated on the device and cached on local disk.
+"""
+import numpy as np
+import pytest
+
+import synth
+from compare import check_ranking, overlap
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def full():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2604_28142_b300 as T
+    from oracle import Oracle
+    ix = synth.load_or_make("msmarco-1M", device="cuda")
+    cfg = synth.CONFIGS["msmarco-1M"]
+    q = synth.make_queries(cfg, n_queries=64, seed=cfg.query_seed + 17, ntok_min=32, ntok_max=32)
+    return T, ix, q, T.Index(ix, 0), Oracle(ix)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_batch_sampled_against_oracle(full, prec):
+    T, ix, q, G, O = full
+    if prec == 1 and not T.tc_available():
+        pytest.skip("no tensor-core path")
+    k, kc, kd = 10, 40, 1000
+    nq = len(q["ntok"])
+    dq = torch.from_numpy(q["queries"]).cuda()
+    oi = torch.empty(nq * k, dtype=torch.int32, device="cuda")
+    os_ = torch.empty(nq * k, dtype=torch.float32, device="cuda")
+    G.search(T.SearchParams(kappa_c=kc, kappa_d=kd, precision=prec), dq, q["ntok"], np.full(nq, k, np.int32), oi, os_)
+    torch.cuda.synchronize()
+    assert G.stream_status() & ~2 == 0
+    gi, gs = oi.cpu().numpy(), os_.cpu().numpy()
+    sample = [0, 17, 40, 63]
+    rows = np.concatenate([np.arange(u * 32, (u + 1) * 32) for u in sample])
+    res = O.search(q["queries"][rows], q["ntok"][sample], k, kc, kd)
+    ov = []
+    for j, u in enumerate(sample):
+        sl = slice(u * k, (u + 1) * k)
+        check_ranking(gi[sl], gs[sl], res["ids"][j * k:(j + 1) * k], res["scores"][j * k:(j + 1) * k], 1e-5, 1e-4,
+                      what=f"query {u}")
+        ov.append(overlap(gi[sl], res["ids"][j * k:(j + 1) * k]))
+    assert np.mean(ov) >= 0.99

@@ -337,3 +337,37 @@ def test_bf16_kappa_c_above_group_count():
         torch.cuda.synchronize()
         out.append(ids.cpu().numpy())
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("name", ["small", "small32", "random_edges"])
+def test_refine_tc_within_error_bound(name):
+    # approximate refined scores (tensor-core centroid term) are within the Delta
+    # the FP32 repair of the top-k window relies on; the FP32 kernel is within 1e-5
+    _cuda()
+    _tc()
+    c = get_case(name)
+    res = c.O.search(c.q, c.ntok, c.k, c.kc, c.kd, stages=True)
+    cand = np.ascontiguousarray(res["cand_ids"])
+    dc = torch.from_numpy(cand).cuda()
+    out = {}
+    for prec in (0, 1):
+        o = torch.empty((c.nq, c.kd), dtype=torch.float32, device="cuda")
+        c.G.debug_refine_scores(c.params(prec), c.dq, c.ntok, dc, o)
+        torch.cuda.synchronize()
+        out[prec] = o.cpu().numpy().astype(np.float64)
+    Cw = _widened(c.ix)
+    cmax = np.linalg.norm(Cw, axis=1).max()
+    rel = 2.0 ** -14 if c.ix["centroid_dtype"] == "bf16" else 2.0 ** -5
+    worst = 0.0
+    for u in range(c.nq):
+        cd = cand[u]
+        valid = cd >= 0
+        exact = c.O.refine(c.q[c.qoff[u]:c.qoff[u + 1]], cd[valid])
+        ntok = int(c.ntok[u])
+        delta = ntok * rel * cmax + 4 * 2.0 ** -20 * (np.abs(exact).max() + 1)
+        e1 = np.abs(out[1][u][valid] - exact)
+        e0 = np.abs(out[0][u][valid] - exact)
+        assert e1.max() <= delta, (u, e1.max(), delta)
+        assert np.all(e0 <= 1e-5 * np.maximum(1, np.abs(exact)))
+        worst = max(worst, e1.max() / delta)
+    assert worst > 0
