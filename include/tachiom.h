@@ -127,7 +127,8 @@ typedef struct {
   int32_t kappa_d;    /* candidates refined per query, 1..4096; 0 means max(1000, 4 max_k) capped
                          at 4096 */
   int32_t precision;  /* TACHIOM_PREC_* for step (a) */
-  int32_t plan_id;    /* -1: the library picks launch shapes; >= 0: a fixed plan (autotuner) */
+  int32_t plan_id;    /* -1: the library's choice of kernels; >= 0: a plan from tachiom_autotune
+                         (bits 0-1 step (a) kernel, 2-3 step (c) kernel, 4- FP32 scan slices) */
 } tachiom_search_params;
 
 /* The whole path, steps (a)-(d), for a batch of nq queries.
@@ -245,6 +246,30 @@ tachiom_status tachiom_server_wait(tachiom_server *server, uint64_t id, int32_t 
 tachiom_status tachiom_server_read_stats(tachiom_server *server, tachiom_server_stats *out);
 /* Finish every queued and running request, then release the server. */
 tachiom_status tachiom_server_destroy(tachiom_server *server);
+
+/* ---- CUDA graphs and the autotuner ----
+ * tachiom_graph_create captures the whole search for one batch shape (nq
+ * queries with these token counts and k) into a CUDA graph, after one
+ * uncaptured run that sizes its scratch; tachiom_graph_launch copies the
+ * device queries in, replays the graph on `stream` and copies the results out
+ * (same layouts as tachiom_search). Launches of one graph must not overlap.
+ * Blocking create; asynchronous launch.                                     */
+typedef struct tachiom_graph tachiom_graph;
+tachiom_status tachiom_graph_create(tachiom_index *index, const tachiom_search_params *params,
+                                    const int32_t *h_ntok, const int32_t *h_k, int32_t nq,
+                                    tachiom_graph **out);
+tachiom_status tachiom_graph_launch(tachiom_graph *graph, const float *d_queries, int32_t *d_out_ids,
+                                    float *d_out_scores, void *stream);
+tachiom_status tachiom_graph_destroy(tachiom_graph *graph);
+
+/* Time every kernel choice for this batch (step (a): single-pass or two-pass
+ * tensor-core scan, or FP32 scan slices; step (c): tensor-core refine with the
+ * FP32 window, or FP32 refine; every choice returns the same results) and
+ * return the fastest as a plan id for tachiom_search_params.plan_id, with its
+ * median time in ms. Blocking.                                              */
+tachiom_status tachiom_autotune(tachiom_index *index, const tachiom_search_params *params,
+                                const float *d_queries, const int32_t *h_ntok, const int32_t *h_k,
+                                int32_t nq, int32_t *best_plan, float *best_ms, void *stream);
 
 /* Synchronise `stream`, then return and clear the TACHIOM_FLAG_* bits raised
  * by work on that stream. Blocking.                                         */

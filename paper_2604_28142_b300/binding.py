@@ -118,6 +118,11 @@ def lib():
         "tachiom_server_wait": ([P, ct.c_uint64, I32, P, P, ct.POINTER(ct.c_double)], ct.c_int),
         "tachiom_server_read_stats": ([P, ct.POINTER(ServerStats)], ct.c_int),
         "tachiom_server_destroy": ([P], ct.c_int),
+        "tachiom_graph_create": ([P, ct.POINTER(SearchParams), P, P, I32, ct.POINTER(ct.c_void_p)], ct.c_int),
+        "tachiom_graph_launch": ([P, P, P, P, P], ct.c_int),
+        "tachiom_graph_destroy": ([P], ct.c_int),
+        "tachiom_autotune": ([P, ct.POINTER(SearchParams), P, P, P, I32, ct.POINTER(ct.c_int32),
+                              ct.POINTER(ct.c_float), P], ct.c_int),
         "tachiom_last_error": ([], ct.c_char_p),
         "tachiom_version": ([], ct.c_char_p),
     }
@@ -250,6 +255,19 @@ class Index:
         _check(lib().tachiom_debug_refine_scores(self.h, ct.byref(params), _dp(queries), _hp(ntok),
                                                  int(ntok.shape[0]), _dp(cand_ids), _dp(out), _stream(stream)))
 
+    def autotune(self, params: SearchParams, queries, ntok, k, stream=None):
+        """(best plan id, its median ms) for this batch (tachiom_autotune)."""
+        ntok = np.ascontiguousarray(ntok, dtype=np.int32)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        plan = ct.c_int32()
+        ms = ct.c_float()
+        _check(lib().tachiom_autotune(self.h, ct.byref(params), _dp(queries), _hp(ntok), _hp(k), int(ntok.shape[0]),
+                                      ct.byref(plan), ct.byref(ms), _stream(stream)))
+        return plan.value, ms.value
+
+    def graph(self, params: SearchParams, ntok, k) -> "Graph":
+        return Graph(self, params, ntok, k)
+
     def stream_status(self, stream=None) -> int:
         f = ct.c_uint32()
         _check(lib().tachiom_stream_status(self.h, _stream(stream), ct.byref(f)))
@@ -289,6 +307,33 @@ class Server:
     def close(self):
         if getattr(self, "h", None):
             lib().tachiom_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """A captured search of one batch shape (tachiom_graph_*)."""
+
+    def __init__(self, index: Index, params: SearchParams, ntok, k):
+        self.index = index
+        ntok = np.ascontiguousarray(ntok, dtype=np.int32)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        h = ct.c_void_p()
+        _check(lib().tachiom_graph_create(index.h, ct.byref(params), _hp(ntok), _hp(k), int(ntok.shape[0]),
+                                          ct.byref(h)))
+        self.h = h
+
+    def launch(self, queries, out_ids, out_scores, stream=None):
+        _check(lib().tachiom_graph_launch(self.h, _dp(queries), _dp(out_ids), _dp(out_scores), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tachiom_graph_destroy(self.h)
             self.h = None
 
     def __del__(self):

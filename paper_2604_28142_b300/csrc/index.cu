@@ -52,12 +52,20 @@ __global__ void k_round_bf16(const float *__restrict__ in, __nv_bfloat16 *__rest
     out[i] = __float2bfloat16_rn(in[i]);
 }
 
-__global__ void k_row_norm_max(const float *__restrict__ c, int64_t C, unsigned *__restrict__ out) {
+// max_j ||c_j|| and max_j ||bf16(c_j) - c_j|| (slightly rounded up)
+__global__ void k_row_norm_max(const float *__restrict__ c, const __nv_bfloat16 *__restrict__ cb, int64_t C,
+                               unsigned *__restrict__ out) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < C;
        j += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < DIM; k++) s = fmaf(c[j * DIM + k], c[j * DIM + k], s);
-    atomicMax(out, __float_as_uint(sqrtf(s)));  // non-negative floats order as uints
+    float s = 0.f, e = 0.f;
+    for (int k = 0; k < DIM; k++) {
+      const float x = c[j * DIM + k], d = __bfloat162float(cb[j * DIM + k]) - x;
+      s = fmaf(x, x, s);
+      e = fmaf(d, d, e);
+    }
+    // non-negative floats order as uints
+    atomicMax(out, __float_as_uint(sqrtf(s) * (1.f + ldexpf(1.f, -12))));
+    atomicMax(out + 1, __float_as_uint(sqrtf(e) * (1.f + ldexpf(1.f, -12))));
   }
 }
 
@@ -227,20 +235,24 @@ extern "C" tachiom_status tachiom_index_load(const tachiom_index_desc *desc, int
   }
   {
     unsigned *dmax = nullptr;
-    TRY(dalloc(ix, &dmax, 1));
-    cudaMemset(dmax, 0, 4);
-    k_row_norm_max<<<(unsigned)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096), 256>>>(ix->cent_f32, C, dmax);
-    unsigned hmax = 0;
-    cudaError_t e = cudaMemcpy(&hmax, dmax, 4, cudaMemcpyDeviceToHost);
+    TRY(dalloc(ix, &dmax, 2));
+    cudaMemset(dmax, 0, 8);
+    k_row_norm_max<<<(unsigned)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096), 256>>>(ix->cent_f32, ix->cent_bf16,
+                                                                                          C, dmax);
+    unsigned hm[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(hm, dmax, 8, cudaMemcpyDeviceToHost);
+    const unsigned hmax = hm[0];
     cudaFree(dmax);
-    ix->device_bytes -= 4;
+    ix->device_bytes -= 8;
     if (e != cudaSuccess) {
       st = fail(TACHIOM_ERR_CUDA, "centroid norm pass failed: %s", cudaGetErrorString(e));
       goto fail_;
     }
-    float f;
+    float f, g;
     memcpy(&f, &hmax, 4);
+    memcpy(&g, &hm[1], 4);
     ix->cnorm_max = f;
+    ix->cerr_max = g;
   }
   if (desc->centroid_type) TRY(upload(ix, &ix->cent_type, desc->centroid_type, (size_t)C));
   TRY(upload(ix, &ix->doc_off, desc->doc_offsets, (size_t)D + 1));

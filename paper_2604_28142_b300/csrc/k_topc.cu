@@ -19,17 +19,58 @@
 
 namespace tachiom {
 
-__global__ void k_quantize_bf16(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = __float2bfloat16_rn(in[i]);
+// Rows to BF16 (round to nearest) and, per row, the half-width of the window the
+// BF16 scores must be repaired in. With e = bf16(q) - q and c_hat the BF16 copy of
+// c (exact for a BF16-stored table):
+//   |<bf16(q), c_hat> - <q, c>| <= |<e, c>| + |<bf16(q), c_hat - c>| + accumulation
+//                                <= ||e|| cmax + ||bf16(q)|| (cerr + 2^-15 cmax)
+// (Cauchy-Schwarz; cmax = max ||c_j||, cerr = max ||c_hat_j - c_j||; the last term
+// bounds the FP32 accumulation of 128 products). margin = 2 * that bound.
+__global__ void k_quantize_rows(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, int nrows,
+                                float cmax, float cerr, float *__restrict__ margins) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nrows) return;
+  const float4 x = reinterpret_cast<const float4 *>(in + (int64_t)warp * DIM)[lane];
+  const float xs[4] = {x.x, x.y, x.z, x.w};
+  float e2 = 0.f, h2 = 0.f;
+  __nv_bfloat16 hb[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    hb[u] = __float2bfloat16_rn(xs[u]);
+    const float h = __bfloat162float(hb[u]);
+    e2 = fmaf(h - xs[u], h - xs[u], e2);
+    h2 = fmaf(h, h, h2);
+  }
+  reinterpret_cast<uint2 *>(out + (int64_t)warp * DIM)[lane] =
+      make_uint2(*reinterpret_cast<uint16_t *>(&hb[0]) | ((uint32_t)*reinterpret_cast<uint16_t *>(&hb[1]) << 16),
+                 *reinterpret_cast<uint16_t *>(&hb[2]) | ((uint32_t)*reinterpret_cast<uint16_t *>(&hb[3]) << 16));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+  }
+  if (lane == 0 && margins) {
+    // the factor 1 + 2^-10 covers the FP32 rounding of these norms
+    const float d = (sqrtf(e2) * cmax + sqrtf(h2) * (cerr + ldexpf(cmax, -15))) * (1.f + ldexpf(1.f, -10)) + 1e-7f;
+    margins[warp] = 2.f * d;
+  }
 }
 
 tachiom_status launch_quantize_bf16(const float *rows, __nv_bfloat16 *out, int64_t n, cudaStream_t s) {
+  // n = rows x 128; no margins
   if (n <= 0) return TACHIOM_OK;
   TPROF("quantize_bf16", s);
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-  k_quantize_bf16<<<blocks, 256, 0, s>>>(rows, out, n);
+  const int nrows = (int)(n / DIM);
+  k_quantize_rows<<<(nrows + 7) / 8, 256, 0, s>>>(rows, out, nrows, 0.f, 0.f, nullptr);
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
+tachiom_status launch_quantize_rows(const Index &ix, const float *rows, __nv_bfloat16 *out, int nrows,
+                                    float *margins, cudaStream_t s) {
+  if (nrows <= 0) return TACHIOM_OK;
+  TPROF("quantize_bf16", s);
+  k_quantize_rows<<<(nrows + 7) / 8, 256, 0, s>>>(rows, out, nrows, ix.cnorm_max, ix.cerr_max, margins);
   TLAUNCH();
   return TACHIOM_OK;
 }
@@ -224,7 +265,7 @@ constexpr int M_MAX = 16384;  // entries one row's merge sorts
 __global__ void __launch_bounds__(M_THREADS)
 k_topc_merge(const float *__restrict__ rows, int nrows, const float *__restrict__ cent, int64_t C,
              int kc, int splits, int capout, const uint64_t *__restrict__ split_in,
-             const int32_t *__restrict__ split_cnt, float margin, int rescore,
+             const int32_t *__restrict__ split_cnt, const float *__restrict__ margins, int rescore,
              int32_t *__restrict__ top_ids, float *__restrict__ top_s, uint32_t *__restrict__ flags,
              int32_t *__restrict__ lossy_rows) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -269,6 +310,7 @@ k_topc_merge(const float *__restrict__ rows, int nrows, const float *__restrict_
     // window: every entry whose approximate score is >= (approx kappa_c-th) - margin
     __shared__ int s_w;
     if (tid == 0) {
+      const float margin = margins ? margins[r] : 0.f;
       float t = (n >= kc) ? comp_score(a[kc - 1]) : -INFINITY;
       int w = 0;
       while (w < n && comp_score(a[w]) >= t - margin) w++;
@@ -327,7 +369,7 @@ k_topc_rescue(const float *__restrict__ rows, int nrows, const float *__restrict
 
 tachiom_status launch_topc_merge(const Index &ix, const float *rows, int nrows, int kc, int splits,
                                  int capout, const uint64_t *split, const int32_t *split_cnt,
-                                 float margin, int rescore, int32_t *top_ids, float *top_s,
+                                 const float *margins, int rescore, int32_t *top_ids, float *top_s,
                                  uint32_t *flags, cudaStream_t s) {
   if (nrows <= 0) return TACHIOM_OK;
   if (splits > 1024) return fail(TACHIOM_ERR_INVALID, "too many splits");
@@ -339,7 +381,7 @@ tachiom_status launch_topc_merge(const Index &ix, const float *rows, int nrows, 
   size_t smem = (size_t)M_MAX * 8;
   TCUDA(cudaFuncSetAttribute(k_topc_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_topc_merge<<<nrows, M_THREADS, smem, s>>>(rows, nrows, ix.cent_f32, ix.C, kc, splits, capout, split,
-                                              split_cnt, margin, rescore, top_ids, top_s, flags, lossy);
+                                              split_cnt, margins, rescore, top_ids, top_s, flags, lossy);
   TLAUNCH();
   k_topc_rescue<<<nrows, M_THREADS, 0, s>>>(rows, nrows, ix.cent_f32, ix.C, kc, lossy, top_ids, top_s);
   TLAUNCH();

@@ -72,7 +72,8 @@ template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
 k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t C, int R,
           int ntiles, int tiles_per_split, int G, uint32_t *__restrict__ gmax, const uint32_t *__restrict__ tau,
-          float margin, int32_t *__restrict__ cnt, uint64_t *__restrict__ cand, uint32_t *__restrict__ flags) {
+          const float *__restrict__ margins, int32_t *__restrict__ cnt, uint64_t *__restrict__ cand,
+          uint32_t *__restrict__ flags) {
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
   unsigned char *tsm = (unsigned char *)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *Bs = tsm;                  // [2 halves][256 rows][128 B]
@@ -105,7 +106,7 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const int row = rb * BN + n;
       const uint32_t t = (row < R) ? tau[row] : 0u;
       // tau == 0: fewer than kappa_c groups, keep everything
-      ctl->thrf[n] = (row >= R) ? INFINITY : (t == 0 ? -INFINITY : funkey(t) - margin);
+      ctl->thrf[n] = (row >= R) ? INFINITY : (t == 0 ? -INFINITY : funkey(t) - margins[row]);
     }
   }
   if (warp == 1) {
@@ -367,7 +368,7 @@ size_t topc_tc_gmax_elems(int64_t C, int rows) {
   return (size_t)(rbs * ntiles * 4 * 2 * tc::BN);
 }
 
-tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, float margin,
+tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, const float *margins,
                               uint32_t *gmax, uint32_t *tau, int32_t *cnt, uint64_t *cand, uint32_t *flags,
                               cudaStream_t s) {
   using namespace tc;
@@ -389,7 +390,7 @@ tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nr
   dim3 grid(splits, rbs);
   TCUDA(cudaFuncSetAttribute(k_topc_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   TCUDA(cudaFuncSetAttribute(k_topc_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  k_topc_tc<1><<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, gmax, nullptr, 0.f, nullptr,
+  k_topc_tc<1><<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, gmax, nullptr, nullptr, nullptr,
                                                   nullptr, flags);
   TLAUNCH();
   const size_t tsm = (size_t)TAU_WARPS * TAU_BINS * 32;
@@ -397,7 +398,7 @@ tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nr
   k_topc_tau<<<rbs * 8, TAU_WARPS * 32, tsm, s>>>(gmax, G, nrows, kc, 1.0001f * ix.cnorm_max + 1e-6f, tau);
   TLAUNCH();
   TCUDA(cudaMemsetAsync(cnt, 0, (size_t)nrows * 4, s));
-  k_topc_tc<2><<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, nullptr, tau, margin, cnt,
+  k_topc_tc<2><<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, nullptr, tau, margins, cnt,
                                                   cand, flags);
   TLAUNCH();
   return TACHIOM_OK;
@@ -419,7 +420,7 @@ tachiom_status launch_topc_tc_raw(const Index &ix, const __nv_bfloat16 *rows, in
   splits = (ntiles + per - 1) / per;
   TCUDA(cudaFuncSetAttribute(k_topc_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   k_topc_tc<3><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, ntiles * 4,
-                                                               nullptr, nullptr, 0.f, nullptr,
+                                                               nullptr, nullptr, nullptr, nullptr,
                                                                reinterpret_cast<uint64_t *>(out), flags);
   TLAUNCH();
   return TACHIOM_OK;

@@ -15,7 +15,8 @@
 // private 96-entry buffer in shared memory. A score s is kept when
 // s >= thr - margin; a full buffer is compacted by a quickselect of its
 // kappa_c-th entry, which raises thr, and keeps every entry >= thr - margin.
-// margin = 2 * delta, delta a bound on |BF16 score - FP32 score|, so the
+// margin = 2 * delta_row, delta_row a bound on |BF16 score - FP32 score| for the
+// row (from its own rounding error, k_quantize_rows), so the
 // survivors of all slices contain the row's exact FP32 top-kappa_c and the
 // merge (k_topc_merge) rescoring that window in FP32 returns it exactly. A
 // row whose kept set cannot fit is marked and recomputed in FP32.
@@ -106,7 +107,7 @@ __device__ __noinline__ int compact(uint64_t *buf, int n, int kc, float margin, 
 
 __global__ void __launch_bounds__(THREADS, 1)
 k_topc_tc1(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmC, int64_t C, int R,
-           int ntiles, int tiles_per_split, int kc, float margin, uint64_t *__restrict__ split_out,
+           int ntiles, int tiles_per_split, int kc, const float *__restrict__ margins, uint64_t *__restrict__ split_out,
            int32_t *__restrict__ split_cnt, uint32_t *__restrict__ flags) {
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
   unsigned char *tsm = (unsigned char *)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
@@ -198,6 +199,7 @@ k_topc_tc1(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUte
     const int rloc = quarter * 32 + lane;             // TMEM lane = row within the CTA
     const int row = rb * BM + rloc;
     const bool rv = row < R;
+    const float margin = rv ? margins[row] : 0.f;
     uint64_t *mybuf = cbuf + rloc;                    // entry i at mybuf[i * BM]
     int cnt = 0;
     float thr = -INFINITY;
@@ -275,7 +277,7 @@ int topc_tc1_splits(const Index &ix, int nrows) {
 
 tachiom_status encode_bf16_map(CUtensorMap *map, const void *base, int64_t rows, int box_rows);
 
-tachiom_status launch_topc_tc1(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, float margin,
+tachiom_status launch_topc_tc1(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, const float *margins,
                                uint64_t *split_out, int32_t *split_cnt, uint32_t *flags, cudaStream_t s) {
   using namespace tc1;
   if (nrows <= 0) return TACHIOM_OK;
@@ -290,7 +292,7 @@ tachiom_status launch_topc_tc1(const Index &ix, const __nv_bfloat16 *rows, int n
   const int splits = topc_tc1_splits(ix, nrows);
   const int per = (ntiles + splits - 1) / splits;
   TCUDA(cudaFuncSetAttribute(k_topc_tc1, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  k_topc_tc1<<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mQ, mC, ix.C, nrows, ntiles, per, kc, margin, split_out,
+  k_topc_tc1<<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mQ, mC, ix.C, nrows, ntiles, per, kc, margins, split_out,
                                                             split_cnt, flags);
   TLAUNCH();
   return TACHIOM_OK;

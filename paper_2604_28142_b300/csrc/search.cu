@@ -100,6 +100,7 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   AL(w->d_dense, dn * 4);
   AL(w->d_gmax, gm * 4);
   AL(w->d_tau, rows * 4);
+  AL(w->d_margin, rows * 4);
   AL(w->d_hist, nq * NBINS1 * 4);
   AL(w->d_hist2, nq * NBINS1 * 4);
   AL(w->d_selstate, nq * 8 * 4);
@@ -163,9 +164,10 @@ static Plan make_plan(const Index &ix, int rows, int kc, int precision, int plan
   splits = (int)std::min<int64_t>(splits, max_splits);
   p.capout = kc + 64;
   splits = std::min(splits, std::max(1, 16384 / p.capout));
-  if (plan_id >= 0) {
-    // plan_id encodes an explicit slice count (autotuner)
-    splits = std::max(1, std::min(plan_id, (int)std::min<int64_t>(max_splits, 16384 / p.capout)));
+  const int forced = plan_id >= 0 ? (plan_id >> 4) : 0;
+  if (forced > 0) {
+    // an explicit slice count of the FP32 scan (autotuner)
+    splits = std::max(1, std::min(forced, (int)std::min<int64_t>(max_splits, 16384 / p.capout)));
   }
   p.splits = splits;
   (void)precision;
@@ -247,21 +249,34 @@ static bool use_tc(const tachiom_search_params *p) {
   return p->precision == TACHIOM_PREC_BF16 && topc_tc_supported();
 }
 
-// Bound on |BF16 product score - FP32 score| for a unit-norm query row:
-// rounding the query to BF16 moves each product by at most 2^-9 |q_k c_k|
-// (relative), so the sum moves by at most 2^-9 ||q|| ||c_j||; FP32-stored
-// centroids are rounded too (another 2^-9). The bound used doubles that and
-// adds an absolute term for the accumulation.
-static float bf16_delta(const Index &ix) {
-  const float rel = ix.cdtype == TACHIOM_DTYPE_BF16 ? ldexpf(1.f, -8) : ldexpf(1.f, -7);
-  return rel * ix.cnorm_max + 1e-5f;
+// plan_id >= 0 overrides the library's choices (all choices give the same results):
+//   bits 0-1  step (a) kernel: 0 default, 1 single-pass tensor-core scan, 2 two-pass
+//             tensor-core scan, 3 FP32 CUDA-core scan
+//   bits 2-3  step (c) kernel: 0 default, 1 tensor-core refine + FP32 window, 2 FP32 refine
+//   bits 4-   slices of the FP32 scan (0: default)
+enum { SCAN_DEFAULT = 0, SCAN_TC1 = 1, SCAN_TC2 = 2, SCAN_F32 = 3 };
+enum { REFINE_DEFAULT = 0, REFINE_TC = 1, REFINE_F32 = 2 };
+
+static int scan_kind(const tachiom_search_params *p) {
+  const int forced = p->plan_id >= 0 ? (p->plan_id & 3) : SCAN_DEFAULT;
+  if (!use_tc(p)) return SCAN_F32;
+  if (forced == SCAN_F32) return SCAN_F32;
+  if (forced == SCAN_TC2) return SCAN_TC2;
+  return p->kappa_c <= topc_tc1_max_kc() ? SCAN_TC1 : SCAN_TC2;
+}
+
+static int refine_kind(const tachiom_search_params *p) {
+  const int forced = p->plan_id >= 0 ? ((p->plan_id >> 2) & 3) : REFINE_DEFAULT;
+  if (!use_tc(p)) return REFINE_F32;
+  return forced == REFINE_F32 ? REFINE_F32 : REFINE_TC;
 }
 
 // scratch sizes of step (a) for a batch
 static void need_topc(const Index &ix, const tachiom_search_params *p, int rows, const Plan &plan, Need *n) {
-  if (use_tc(p) && p->kappa_c <= topc_tc1_max_kc()) {
+  const int kind = scan_kind(p);
+  if (kind == SCAN_TC1) {
     n->split_entries = (int64_t)rows * topc_tc1_splits(ix, rows) * topc_tc1_capout();
-  } else if (use_tc(p)) {
+  } else if (kind == SCAN_TC2) {
     n->split_entries = (int64_t)rows * topc_tc_capg();
     n->gmax = (int64_t)topc_tc_gmax_elems(ix.C, rows);
   } else {
@@ -274,31 +289,30 @@ static tachiom_status run_topc(Index *ix, Workspace *w, const tachiom_search_par
                                int nrows, const Plan &plan) {
   const int kc = p->kappa_c;
   tachiom_status st;
-  if (use_tc(p) && kc <= topc_tc1_max_kc()) {
+  const int kind = scan_kind(p);
+  if (kind == SCAN_TC1) {
     // one pass, per-row running top-kappa_c in the epilogue
-    if ((st = launch_quantize_bf16(rows, w->d_rows_bf16, (int64_t)nrows * DIM, w->stream))) return st;
-    const float margin = 2.f * bf16_delta(*ix);
+    if ((st = launch_quantize_rows(*ix, rows, w->d_rows_bf16, nrows, w->d_margin, w->stream))) return st;
     const int splits = topc_tc1_splits(*ix, nrows);
-    if ((st = launch_topc_tc1(*ix, w->d_rows_bf16, nrows, kc, margin, w->d_split, w->d_split_cnt, w->d_flags,
+    if ((st = launch_topc_tc1(*ix, w->d_rows_bf16, nrows, kc, w->d_margin, w->d_split, w->d_split_cnt, w->d_flags,
                               w->stream)))
       return st;
-    return launch_topc_merge(*ix, rows, nrows, kc, splits, topc_tc1_capout(), w->d_split, w->d_split_cnt, margin, 1,
+    return launch_topc_merge(*ix, rows, nrows, kc, splits, topc_tc1_capout(), w->d_split, w->d_split_cnt, w->d_margin, 1,
                              w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
   }
-  if (use_tc(p)) {
-    // kappa_c above the single-pass limit: two passes (group maxima, then a filter)
-    if ((st = launch_quantize_bf16(rows, w->d_rows_bf16, (int64_t)nrows * DIM, w->stream))) return st;
-    const float margin = 2.f * bf16_delta(*ix);
-    if ((st = launch_topc_tc(*ix, w->d_rows_bf16, nrows, kc, margin, w->d_gmax, w->d_tau, w->d_split_cnt,
+  if (kind == SCAN_TC2) {
+    // two passes (group maxima, then a filter): kappa_c above the single-pass limit
+    if ((st = launch_quantize_rows(*ix, rows, w->d_rows_bf16, nrows, w->d_margin, w->stream))) return st;
+    if ((st = launch_topc_tc(*ix, w->d_rows_bf16, nrows, kc, w->d_margin, w->d_gmax, w->d_tau, w->d_split_cnt,
                              w->d_split, w->d_flags, w->stream)))
       return st;
-    return launch_topc_merge(*ix, rows, nrows, kc, 1, topc_tc_capg(), w->d_split, w->d_split_cnt, margin, 1,
+    return launch_topc_merge(*ix, rows, nrows, kc, 1, topc_tc_capg(), w->d_split, w->d_split_cnt, w->d_margin, 1,
                              w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
   }
   if ((st = launch_topc_f32(*ix, rows, nrows, kc, plan.splits, plan.capout, w->d_split, w->d_split_cnt,
                             w->d_flags, w->stream)))
     return st;
-  return launch_topc_merge(*ix, rows, nrows, kc, plan.splits, plan.capout, w->d_split, w->d_split_cnt, 0.f, 0,
+  return launch_topc_merge(*ix, rows, nrows, kc, plan.splits, plan.capout, w->d_split, w->d_split_cnt, nullptr, 0,
                            w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
 }
 
@@ -317,7 +331,7 @@ static tachiom_status run_refine(Index *ix, Workspace *w, const tachiom_search_p
                                  int nq, const int32_t *cand, int kd, int32_t *out_ids, float *out_s,
                                  cudaStream_t stream) {
   tachiom_status st;
-  if (use_tc(p)) {
+  if (refine_kind(p) == REFINE_TC) {
     if ((st = launch_refine_tc(*ix, queries, w->d_meta, nq, cand, kd, w->d_part, w->d_flags, stream))) return st;
     if ((st = launch_refine_window(*ix, w->d_meta, nq, cand, kd, w->d_part, refine_tc_delta(*ix), w->d_win,
                                    stream)))
@@ -618,4 +632,178 @@ extern "C" tachiom_status tachiom_debug_refine_scores(tachiom_index *index, cons
     if ((st = launch_refine(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, w->d_part, w->d_flags, s))) return st;
   }
   return launch_refine_sum(*ix, w->d_meta, nq, d_cand_ids, kd, w->d_part, d_scores, s);
+}
+
+// ---- CUDA graphs of a fixed batch shape --------------------------------------------------
+namespace tachiom {
+struct Graph {
+  Index *ix = nullptr;
+  cudaStream_t stream = nullptr;  // capture stream; its workspace holds the graph's scratch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  float *d_in = nullptr;
+  int32_t *d_ids = nullptr;
+  float *d_s = nullptr;
+  int64_t rows = 0, total_k = 0;
+};
+
+static void graph_free(Graph *g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->d_in) cudaFree(g->d_in);
+  if (g->d_ids) cudaFree(g->d_ids);
+  if (g->d_s) cudaFree(g->d_s);
+  if (g->stream) {
+    ws_release(g->ix, g->stream);
+    cudaStreamDestroy(g->stream);
+  }
+  delete g;
+}
+}  // namespace tachiom
+
+extern "C" tachiom_status tachiom_graph_create(tachiom_index *index, const tachiom_search_params *params,
+                                               const int32_t *h_ntok, const int32_t *h_k, int32_t nq,
+                                               tachiom_graph **out) {
+  Index *ix = as_index(index);
+  if (!ix || !out) return fail(TACHIOM_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  tachiom_status st;
+  if ((st = check_params(params))) return st;
+  Batch b;
+  if ((st = check_batch(h_ntok, h_k, nq, 0, &b))) return st;
+  if (nq < 1 || !h_k) return fail(TACHIOM_ERR_INVALID, "a graph needs at least one query and its k");
+  DeviceGuard dg(ix->device);
+  Graph *g = new Graph();
+  g->ix = ix;
+  g->rows = b.rows;
+  g->total_k = b.total_k;
+  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&g->d_in, (size_t)b.rows * DIM * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_ids, (size_t)b.total_k * 4) != cudaSuccess ||
+      cudaMalloc(&g->d_s, (size_t)b.total_k * 4) != cudaSuccess) {
+    cudaGetLastError();
+    graph_free(g);
+    return fail(TACHIOM_ERR_OOM, "graph buffers");
+  }
+  cudaMemsetAsync(g->d_in, 0, (size_t)b.rows * DIM * 4, g->stream);
+  // first run outside the capture: scratch grows, kernel attributes are set
+  if ((st = search_device(ix, params, g->d_in, h_ntok, h_k, nq, g->d_ids, g->d_s, g->stream, nullptr))) {
+    graph_free(g);
+    return st;
+  }
+  if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+    graph_free(g);
+    return fail(TACHIOM_ERR_CUDA, "graph warm-up failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    graph_free(g);
+    return fail(TACHIOM_ERR_CUDA, "cudaStreamBeginCapture failed");
+  }
+  st = search_device(ix, params, g->d_in, h_ntok, h_k, nq, g->d_ids, g->d_s, g->stream, nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+  g->graph = graph;
+  if (st || e != cudaSuccess) {
+    cudaGetLastError();
+    graph_free(g);
+    return st ? st : fail(TACHIOM_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e));
+  }
+  if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    graph_free(g);
+    return fail(TACHIOM_ERR_CUDA, "cudaGraphInstantiate failed");
+  }
+  *out = reinterpret_cast<tachiom_graph *>(g);
+  return TACHIOM_OK;
+}
+
+extern "C" tachiom_status tachiom_graph_launch(tachiom_graph *graph, const float *d_queries, int32_t *d_out_ids,
+                                               float *d_out_scores, void *stream) {
+  Graph *g = reinterpret_cast<Graph *>(graph);
+  if (!g || !d_queries || !d_out_ids || !d_out_scores) return fail(TACHIOM_ERR_INVALID, "NULL argument");
+  DeviceGuard dg(g->ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  TCUDA(cudaMemcpyAsync(g->d_in, d_queries, (size_t)g->rows * DIM * 4, cudaMemcpyDeviceToDevice, s));
+  TCUDA(cudaGraphLaunch(g->exec, s));
+  TCUDA(cudaMemcpyAsync(d_out_ids, g->d_ids, (size_t)g->total_k * 4, cudaMemcpyDeviceToDevice, s));
+  TCUDA(cudaMemcpyAsync(d_out_scores, g->d_s, (size_t)g->total_k * 4, cudaMemcpyDeviceToDevice, s));
+  return TACHIOM_OK;
+}
+
+extern "C" tachiom_status tachiom_graph_destroy(tachiom_graph *graph) {
+  graph_free(reinterpret_cast<Graph *>(graph));
+  return TACHIOM_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------------------------
+extern "C" tachiom_status tachiom_autotune(tachiom_index *index, const tachiom_search_params *params,
+                                           const float *d_queries, const int32_t *h_ntok, const int32_t *h_k,
+                                           int32_t nq, int32_t *best_plan, float *best_ms, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix || !params || !best_plan) return fail(TACHIOM_ERR_INVALID, "NULL argument");
+  tachiom_status st;
+  if ((st = check_params(params))) return st;
+  Batch b;
+  if ((st = check_batch(h_ntok, h_k, nq, 0, &b))) return st;
+  if (nq < 1 || !d_queries || !h_k) return fail(TACHIOM_ERR_INVALID, "autotuning needs a batch");
+  DeviceGuard dg(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t *d_ids = nullptr;
+  float *d_s = nullptr;
+  if (cudaMalloc(&d_ids, (size_t)b.total_k * 4) != cudaSuccess || cudaMalloc(&d_s, (size_t)b.total_k * 4) != cudaSuccess) {
+    cudaGetLastError();
+    if (d_ids) cudaFree(d_ids);
+    return fail(TACHIOM_ERR_OOM, "autotune buffers");
+  }
+  // candidate plans: step (a) kernel x step (c) kernel (x FP32 scan slices on the FP32 path)
+  std::vector<int32_t> plans;
+  const int tc = use_tc(params) ? 1 : 0;
+  if (tc) {
+    for (int sk : {SCAN_TC1, SCAN_TC2})
+      for (int rk : {REFINE_TC, REFINE_F32}) {
+        if (sk == SCAN_TC1 && params->kappa_c > topc_tc1_max_kc()) continue;
+        plans.push_back(sk | (rk << 2));
+      }
+  } else {
+    const int sms = sm_count(ix->device);
+    const int row_tiles = (b.rows + 31) / 32;
+    const int base = std::max(1, (2 * sms + row_tiles - 1) / row_tiles);
+    for (int m : {1, 2, 4}) plans.push_back(SCAN_F32 | (REFINE_F32 << 2) | ((base * m / 2 > 0 ? base * m / 2 : 1) << 4));
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int32_t bestp = -1;
+  for (int32_t pl : plans) {
+    tachiom_search_params p = *params;
+    p.plan_id = pl;
+    // one untimed run (scratch, attributes), then the median of three timed runs
+    if ((st = search_device(ix, &p, d_queries, h_ntok, h_k, nq, d_ids, d_s, s, nullptr))) break;
+    float t[3];
+    for (int r = 0; r < 3; r++) {
+      cudaEventRecord(e0, s);
+      if ((st = search_device(ix, &p, d_queries, h_ntok, h_k, nq, d_ids, d_s, s, nullptr))) break;
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t[r], e0, e1);
+    }
+    if (st) break;
+    std::sort(t, t + 3);
+    if (t[1] < best) {
+      best = t[1];
+      bestp = pl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(d_ids);
+  cudaFree(d_s);
+  if (st) return st;
+  *best_plan = bestp;
+  if (best_ms) *best_ms = best;
+  return TACHIOM_OK;
 }

@@ -107,6 +107,7 @@ struct Index {
   float *cent_f32 = nullptr;            // [C x 128] FP32 values of the stored centroids
   __nv_bfloat16 *cent_bf16 = nullptr;   // [C x 128] BF16 operand of the tensor-core path
   float cnorm_max = 0.f;                // max_j ||c_j|| (error bound of the BF16 path)
+  float cerr_max = 0.f;                 // max_j ||bf16(c_j) - c_j|| (0 for a BF16-stored table)
   int32_t *cent_type = nullptr;         // [C] or null
   int64_t *doc_off = nullptr;           // [D+1]
   int32_t *tok_cid = nullptr;           // [T]
@@ -140,6 +141,7 @@ struct Workspace {
   uint64_t *d_split = nullptr;         // [rows x splits x capout] candidates of step (a)
   uint32_t *d_gmax = nullptr;          // tensor-core path: group maxima of pass 1
   uint32_t *d_tau = nullptr;           // tensor-core path: per-row lower bound of the cut
+  float *d_margin = nullptr;           // tensor-core path: per-row repair window (twice the error bound)
   int64_t cap_gmax = 0;
   int32_t *d_split_cnt = nullptr;      // [rows x splits]
   int32_t *d_top_ids = nullptr;        // [rows x kc]
@@ -196,16 +198,18 @@ tachiom_status launch_topc_f32(const Index &ix, const float *rows, int nrows, in
                                cudaStream_t s);
 tachiom_status launch_topc_merge(const Index &ix, const float *rows, int nrows, int kc, int splits,
                                  int capout, const uint64_t *split, const int32_t *split_cnt,
-                                 float margin, int rescore, int32_t *top_ids, float *top_s,
+                                 const float *margins, int rescore, int32_t *top_ids, float *top_s,
                                  uint32_t *flags, cudaStream_t s);
-tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, float margin,
+tachiom_status launch_quantize_rows(const Index &ix, const float *rows, __nv_bfloat16 *out, int nrows,
+                                    float *margins, cudaStream_t s);
+tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, const float *margins,
                               uint32_t *gmax, uint32_t *tau, int32_t *cnt, uint64_t *cand, uint32_t *flags,
                               cudaStream_t s);
 int topc_tc_supported();
 tachiom_status launch_topc_tc_raw(const Index &ix, const __nv_bfloat16 *rows, int nrows, float *out,
                                   uint32_t *flags, cudaStream_t s);
 int topc_tc_capg();
-tachiom_status launch_topc_tc1(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, float margin,
+tachiom_status launch_topc_tc1(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, const float *margins,
                                uint64_t *split_out, int32_t *split_cnt, uint32_t *flags, cudaStream_t s);
 int topc_tc1_capout();
 int topc_tc1_max_kc();

@@ -38,7 +38,8 @@ def test_full_size_batch_sampled_against_oracle(full, prec):
     os_ = torch.empty(nq * k, dtype=torch.float32, device="cuda")
     G.search(T.SearchParams(kappa_c=kc, kappa_d=kd, precision=prec), dq, q["ntok"], np.full(nq, k, np.int32), oi, os_)
     torch.cuda.synchronize()
-    assert G.stream_status() & ~2 == 0
+    flags = G.stream_status()
+    assert flags & ~3 == 0, flags  # an exact FP32 fallback or the ordered tie pass may run
     gi, gs = oi.cpu().numpy(), os_.cpu().numpy()
     sample = [0, 17, 40, 63]
     rows = np.concatenate([np.arange(u * 32, (u + 1) * 32) for u in sample])

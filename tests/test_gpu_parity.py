@@ -184,7 +184,7 @@ def test_search_end_to_end_fp32(name):
         check_ranking(gi[sl], gs[sl], res["ids"][sl], res["scores"][sl], RTOL_FP32, GAP, what=f"query {u}")
         ov.append(overlap(gi[sl], res["ids"][sl], 10))
     assert np.mean(ov) >= 0.99, ov
-    assert c.G.stream_status() & ~0b10 == 0
+    assert c.G.stream_status() & ~0b11 == 0
 
 
 @pytest.mark.parametrize("name", ["tiny", "random_edges"])
@@ -290,6 +290,15 @@ def test_tc_scores_within_error_bound(name):
     assert err.max() <= delta, (err.max(), delta)
     # and the bound is not vacuous: the scores do carry BF16 rounding error
     assert err.max() > 0
+    # the per-row bound the repair window uses: ||e|| cmax + ||q_hat|| (cerr + 2^-15 cmax),
+    # e = bf16(q) - q, cerr = max ||bf16(c) - c|| (Cauchy-Schwarz)
+    qh = torch.from_numpy(c.q[:R]).to(torch.bfloat16).to(torch.float64).numpy()
+    e = qh - c.q[:R].astype(np.float64)
+    cb = torch.from_numpy(Cw.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    cerr = np.linalg.norm(cb - Cw, axis=1).max()
+    drow = np.linalg.norm(e, axis=1) * cmax + np.linalg.norm(qh, axis=1) * (cerr + 2.0 ** -15 * cmax)
+    assert np.all(err.max(axis=1) <= drow), (err.max(axis=1) / drow).max()
+    assert (err.max(axis=1) / drow).max() > 0.05  # and it is not loose by orders of magnitude
     assert c.G.stream_status() == 0
 
 
