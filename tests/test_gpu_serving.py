@@ -79,6 +79,7 @@ def test_admission_by_scratch_budget(env):
     T, G, ix = env
     params = T.SearchParams(kappa_c=20, kappa_d=500, precision=0)
     reqs, _ = _requests(24, 11)
+    reqs = [(q, min(k, 100)) for q, k in reqs]  # k <= kappa_d
     # room for about one batch of 8 queries at a time
     D = ix["doc_offsets"].shape[0] - 1
     budget = 8 * D * 4 + 8 * 32 * (20 * 8 + 4096 * 8) + 8 * 500 * 64 + 8 * 16384 * 8 + 1
