@@ -25,6 +25,7 @@ namespace tachiom {
 
 constexpr int G_THREADS = 1024;
 constexpr int G_SEGCAP = 1536;  // (query token, retrieved centroid) segments described at once
+constexpr int G_REG = 4;        // list entries per thread and token kept in registers
 
 // Per (token, centroid) segment of a list inside the CTA's document range:
 // start (absolute position in list_doc), exclusive prefix of the lengths within
@@ -103,12 +104,40 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
       if (lane == 0) tok_total[ti] = carry;
     }
     __syncthreads();
+    // Tokens in order; each thread keeps the list entries it handles for the current
+    // token in registers (both passes use them) and loads the next token's entries
+    // before the second pass, so their latency overlaps the current token's work.
+    int32_t dc[G_REG], dn[G_REG];
+    uint32_t kcur[G_REG], knx[G_REG];
+    auto fetch = [&](int ti, int32_t (&d)[G_REG], uint32_t (&k)[G_REG]) {
+      const GSeg *sg = seg + ti * kc;
+      const int total = tok_total[ti];
+#pragma unroll
+      for (int u = 0; u < G_REG; u++) {
+        const int e = tid + u * G_THREADS;
+        d[u] = -1;
+        k[u] = 0u;
+        if (e < total) {
+          int lo = 0, hi = kc;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sg[mid].pref <= e) lo = mid; else hi = mid;
+          }
+          d[u] = list_doc[sg[lo].start + (e - sg[lo].pref)] - (int32_t)r0;
+          k[u] = sg[lo].key;
+        }
+      }
+    };
+    if (ng > 0) fetch(0, dc, kcur);
     for (int ti = 0; ti < ng; ti++) {
       const GSeg *sg = seg + ti * kc;
       const int total = tok_total[ti];
       // pass 1: per-document max over the retrieved centroids (step 3)
-      for (int e = tid; e < total; e += G_THREADS) {
-        int lo = 0, hi = kc;  // the segment with pref <= e < next pref
+#pragma unroll
+      for (int u = 0; u < G_REG; u++)
+        if (dc[u] >= 0) atomicMax(&best[dc[u]], kcur[u]);
+      for (int e = tid + G_REG * G_THREADS; e < total; e += G_THREADS) {
+        int lo = 0, hi = kc;
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
           if (sg[mid].pref <= e) lo = mid; else hi = mid;
@@ -117,8 +146,19 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
         atomicMax(&best[d - r0], sg[lo].key);
       }
       __syncthreads();
+      if (ti + 1 < ng) fetch(ti + 1, dn, knx);
       // pass 2: fold the max into S~ once per reached document (step 4)
-      for (int e = tid; e < total; e += G_THREADS) {
+#pragma unroll
+      for (int u = 0; u < G_REG; u++) {
+        if (dc[u] >= 0) {
+          const uint32_t v = atomicExch(&best[dc[u]], 0u);
+          if (v) {
+            const float sv = funkey(v), cur = S[dc[u]];
+            S[dc[u]] = (cur == -INFINITY) ? sv : cur + sv;
+          }
+        }
+      }
+      for (int e = tid + G_REG * G_THREADS; e < total; e += G_THREADS) {
         int lo = 0, hi = kc;
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
@@ -132,6 +172,11 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
         }
       }
       __syncthreads();
+#pragma unroll
+      for (int u = 0; u < G_REG; u++) {
+        dc[u] = dn[u];
+        kcur[u] = knx[u];
+      }
     }
   }
   float *out = dense + (int64_t)q * D + r0;

@@ -388,6 +388,15 @@ tachiom_status launch_topc_merge(const Index &ix, const float *rows, int nrows, 
   return TACHIOM_OK;
 }
 
+tachiom_status launch_topc_rescue(const Index &ix, const float *rows, int nrows, int kc, const int32_t *lossy_rows,
+                                  int32_t *top_ids, float *top_s, cudaStream_t s) {
+  if (nrows <= 0) return TACHIOM_OK;
+  TPROF("topc_rescue", s);
+  k_topc_rescue<<<nrows, M_THREADS, 0, s>>>(rows, nrows, ix.cent_f32, ix.C, kc, lossy_rows, top_ids, top_s);
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
 // FP32 scores of given (row, centroid id) pairs; ids < 0 give -inf.
 __global__ void k_score_pairs(const float *__restrict__ rows, int nrows, const float *__restrict__ cent,
                               int64_t C, const int32_t *__restrict__ ids, int kc, float *__restrict__ out) {

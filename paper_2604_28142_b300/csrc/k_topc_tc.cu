@@ -10,18 +10,18 @@
 // issues TMA, warp 1 owns TMEM and issues the MMAs, warps 2..9 are the
 // epilogue (warp w reads TMEM lanes 32*(w%4).., column half (w-2)/4).
 //
-// Selection without per-row buffers, in two passes over the same products:
-//   pass 1  every group of 32 consecutive centroids reports, per query row, its
-//           two largest scores (redux.sync per column);
-//   tau     tau_r = a lower bound on the row's kappa_c-th largest of those
-//           2 x G scores, which are scores of distinct centroids, so tau_r <=
-//           the row's kappa_c-th best approximate score (k_topc_tau);
-//   pass 2  every score >= tau_r - margin is appended to the row's list.
-// With margin = 2 * delta, delta a bound on |BF16 score - FP32 score|, the
-// list holds every centroid of the row's exact FP32 top-kappa_c; the merge
-// kernel rescores the window in FP32 and keeps the exact top-kappa_c, so the
-// result equals the FP32 path's. A row whose list overflows is recomputed in
-// FP32 (k_topc_rescue).
+// Selection without any per-row state in the GEMM:
+//   pass    every group of 32 consecutive centroids reports, per query row, its
+//           maximum approximate score (one redux.sync per column) -> gmax;
+//   select  tau'_r = a lower bound on the row's kappa_c-th largest group maximum
+//           (saturating histogram); every group whose maximum is >= tau'_r -
+//           margin_r is kept. A centroid of the row's exact FP32 top-kappa_c has
+//           an approximate score >= (approximate kappa_c-th best) - 2 delta_r
+//           >= tau'_r - margin_r (margin_r = 2 delta_r), so its group is kept:
+//           about kappa_c groups per row survive;
+//   rescore the centroids of the kept groups are scored exactly in FP32 (the
+//           same fmaf chain as the FP32 path) and the exact top-kappa_c is kept.
+// A row whose kept groups do not fit is recomputed by a full FP32 scan.
 //
 // Every wait on an mbarrier is bounded by %globaltimer; a wait that runs out
 // raises TACHIOM_FLAG_TIMEOUT, every role leaves its loop, in-flight copies
@@ -50,7 +50,6 @@ constexpr int TILE_BYTES = B_BYTES + STAGES * A_STAGE;  // 192 KB
 constexpr int THREADS = 320;       // 10 warps
 constexpr int EPI_WARPS = 8;
 constexpr int TMEM_COLS = 512;
-constexpr int CAPG = 4096;         // candidates per row after pass 2
 
 struct Ctl {
   uint64_t full[STAGES];
@@ -61,18 +60,15 @@ struct Ctl {
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
-  float thrf[BN];    // pass 2: tau - margin per row of the CTA (+inf for rows past R)
 };
 constexpr int SMEM_BYTES = TILE_BYTES + (int)sizeof(Ctl) + 1024;
 
-// MODE 1: two largest per group -> gmax[rb][tile*4 + quarter][2][256]
-// MODE 2: append scores >= thr to cand[row][CAPG], cnt[row]
+// MODE 1: maximum per group of 32 centroids -> (float) gmax[rb][tile * 4 + quarter][256]
 // MODE 3: raw scores to (float *)cand [R x C] (diagnostics and tests)
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
 k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t C, int R,
-          int ntiles, int tiles_per_split, int G, uint32_t *__restrict__ gmax, const uint32_t *__restrict__ tau,
-          const float *__restrict__ margins, int32_t *__restrict__ cnt, uint64_t *__restrict__ cand,
+          int ntiles, int tiles_per_split, int G, uint32_t *__restrict__ gmax, uint64_t *__restrict__ cand,
           uint32_t *__restrict__ flags) {
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
   unsigned char *tsm = (unsigned char *)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
@@ -100,14 +96,6 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     mbar_init(&ctl->drain, 1);
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (MODE == 2) {
-    for (int n = threadIdx.x; n < BN; n += THREADS) {
-      const int row = rb * BN + n;
-      const uint32_t t = (row < R) ? tau[row] : 0u;
-      // tau == 0: fewer than kappa_c groups, keep everything
-      ctl->thrf[n] = (row >= R) ? INFINITY : (t == 0 ? -INFINITY : funkey(t) - margins[row]);
-    }
   }
   if (warp == 1) {
     __syncwarp();
@@ -201,41 +189,21 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         for (int cc = 0; cc < 2; cc++) {
           const int ch = pr * 2 + cc;
           if (MODE == 1) {
-            // the two largest scores of the warp's 32 centroids, per query row
-            uint32_t *dst = gmax + (((int64_t)rb * G + tile * 4 + quarter) * 2) * BN + half * 128;
-            float m1l = -INFINITY, m2l = -INFINITY;
+            // maximum score of the warp's 32 centroids, per query row (-inf: no valid centroid)
+            float *dst = reinterpret_cast<float *>(gmax) + ((int64_t)rb * G + tile * 4 + quarter) * BN + half * 128;
+            float mine = -INFINITY;
 #pragma unroll
             for (int c = 0; c < 32; c++) {
-              const float x = jv ? __uint_as_float(v[cc][c]) : -INFINITY;
-              const float m1 = redux_fmax(x);
-              const unsigned eq = __ballot_sync(0xffffffffu, x == m1);
-              const float m2 = (__popc(eq) > 1) ? m1 : redux_fmax(x == m1 ? -INFINITY : x);
-              m1l = (c == lane) ? m1 : m1l;
-              m2l = (c == lane) ? m2 : m2l;
+              const float m = redux_fmax(jv ? __uint_as_float(v[cc][c]) : -INFINITY);
+              mine = (c == lane) ? m : mine;
             }
-            dst[ch * 32 + lane] = (m1l == -INFINITY) ? 0u : fkey(m1l);
-            dst[BN + ch * 32 + lane] = (m2l == -INFINITY) ? 0u : fkey(m2l);
+            dst[ch * 32 + lane] = mine;
           } else if (MODE == 3) {
             // diagnostic: raw scores [R x C]
 #pragma unroll
             for (int c = 0; c < 32; c++) {
               const int row = rb * BN + half * 128 + ch * 32 + c;
               if (jv && row < R) reinterpret_cast<float *>(cand)[(int64_t)row * C + j] = __uint_as_float(v[cc][c]);
-            }
-          } else {
-            // the warp's max per column decides (uniformly) whether any lane has a candidate
-#pragma unroll
-            for (int c = 0; c < 32; c++) {
-              const int n = half * 128 + ch * 32 + c;
-              const float sc = jv ? __uint_as_float(v[cc][c]) : -INFINITY;
-              const float lim = ctl->thrf[n];
-              if (redux_fmax(sc) >= lim) {
-                if (sc >= lim) {
-                  const int row = rb * BN + n;
-                  const int pos = atomicAdd(&cnt[row], 1);
-                  if (pos < CAPG) cand[(int64_t)row * CAPG + pos] = comp_key(sc, (int32_t)j);
-                }
-              }
             }
           }
         }
@@ -251,59 +219,148 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   }
 }
 
-// tau_r: a lower bound on the row's kappa_c-th largest score, from the two
-// largest scores of every group (2 x G actual scores of distinct centroids):
-// a saturating 8-bit histogram per row over [-cmax, cmax] (TAU_BINS bins; a
-// score above the range counts in the top bin), then the lower edge of the
-// highest bin at which the count from the top reaches kappa_c. At least
-// kappa_c scores lie at or above that edge, so it cannot exceed the
-// kappa_c-th largest score; the work per value does not depend on the order
-// in which the values arrive. A block owns 32 rows; its 4 warps histogram one
-// quarter of the groups each, lane = row.
-constexpr int TAU_WARPS = 4;
-constexpr int TAU_BINS = 1024;
-__global__ void __launch_bounds__(TAU_WARPS * 32)
-k_topc_tau(const uint32_t *__restrict__ gmax, int G, int R, int kc, float cmax, uint32_t *__restrict__ tau) {
-  extern __shared__ unsigned char hsm[];  // [TAU_WARPS][TAU_BINS][32] saturating counts
+constexpr int SEL_BINS = 1024;
+constexpr int SEL_WARPS = 4;
+constexpr int GCAP = 256;  // groups a row may keep (8192 centroids)
+
+// One block = 32 query rows of a row block (lane = row); its 4 warps histogram a
+// quarter of the groups each (saturating 8-bit counts over [-cmax, cmax]); warp 0
+// finds tau' = the lower edge of the highest bin at which the count from the top
+// reaches kappa_c (at least kappa_c group maxima lie at or above it, so tau' is at
+// most the kappa_c-th largest); then every group with max >= tau' - margin_r is
+// listed for the row.
+__global__ void __launch_bounds__(SEL_WARPS * 32)
+k_group_select(const float *__restrict__ gmax, int G, int R, int kc, float cmax, const float *__restrict__ margins,
+               int32_t *__restrict__ glist, int32_t *__restrict__ gcount) {
+  extern __shared__ unsigned char hsm[];  // [SEL_WARPS][32 rows][SEL_BINS + 4]
+  __shared__ float s_lim[32];
+  __shared__ int s_cnt[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rb = blockIdx.x >> 3, slab = blockIdx.x & 7;
   const int n = slab * 32 + lane;
-  for (int i = threadIdx.x; i < TAU_WARPS * TAU_BINS * 32 / 4; i += blockDim.x)
-    reinterpret_cast<uint32_t *>(hsm)[i] = 0u;
+  const int row = rb * BN + n;
+  constexpr int HS = SEL_BINS + 4;  // row stride: lanes fall in different banks
+  for (int i = threadIdx.x; i < SEL_WARPS * 32 * HS / 4; i += blockDim.x) reinterpret_cast<uint32_t *>(hsm)[i] = 0u;
+  if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0;
   __syncthreads();
-  unsigned char *h = hsm + (size_t)warp * TAU_BINS * 32 + lane;
-  const float scale = TAU_BINS / (2.f * cmax);
-  const int per = (G + TAU_WARPS - 1) / TAU_WARPS;
+  unsigned char *h = hsm + ((size_t)warp * 32 + lane) * HS;
+  const float scale = SEL_BINS / (2.f * cmax);
+  const int per = (G + SEL_WARPS - 1) / SEL_WARPS;
   const int g0 = warp * per, g1 = min(G, g0 + per);
-  const uint32_t *src = gmax + (int64_t)rb * G * 2 * BN + n;
-  for (int g = g0; g < g1; g += 4) {
-    uint32_t x[8];
+  const float *src = gmax + (int64_t)rb * G * BN + n;
+  for (int g = g0; g < g1; g += 8) {
+    float x[8];
 #pragma unroll
-    for (int u = 0; u < 8; u++) x[u] = (g + (u >> 1) < g1) ? src[((int64_t)(g + (u >> 1)) * 2 + (u & 1)) * BN] : 0u;
+    for (int u = 0; u < 8; u++) x[u] = (g + u < g1) ? src[(int64_t)(g + u) * BN] : -INFINITY;
 #pragma unroll
     for (int u = 0; u < 8; u++) {
-      if (!x[u]) continue;
-      const float sc = funkey(x[u]);
-      const int b = max(0, min(TAU_BINS - 1, (int)floorf((sc + cmax) * scale)));
-      unsigned char *p = h + b * 32;
-      const unsigned char c = *p;
-      if (c != 255) *p = c + 1;
+      if (x[u] == -INFINITY) continue;
+      const int b = max(0, min(SEL_BINS - 1, (int)floorf((x[u] + cmax) * scale)));
+      const unsigned char c = h[b];
+      if (c != 255) h[b] = c + 1;
     }
   }
   __syncthreads();
   if (warp == 0) {
-    int cum = 0, b = TAU_BINS - 1;
+    int cum = 0, b = SEL_BINS - 1;
     for (; b >= 0; b--) {
       int c = 0;
 #pragma unroll
-      for (int w = 0; w < TAU_WARPS; w++) c += hsm[((size_t)w * TAU_BINS + b) * 32 + lane];
+      for (int w = 0; w < SEL_WARPS; w++) c += hsm[((size_t)w * 32 + lane) * HS + b];
       cum += c;
       if (cum >= kc) break;
     }
-    const int row = rb * BN + n;
-    // bin b's lower edge; fewer than kappa_c scores in all: no bound (keep everything)
-    const float edge = (b > 0) ? (b / scale - cmax) : -INFINITY;
-    if (row < R) tau[row] = (b >= 0 && edge > -INFINITY) ? fkey(edge) : 0u;
+    const float edge = (b > 0) ? (b / scale - cmax) : -INFINITY;  // b <= 0: no useful bound
+    s_lim[lane] = (row < R) ? edge - margins[row] : INFINITY;
+  }
+  __syncthreads();
+  const float lim = s_lim[lane];
+  int32_t *out = glist + (int64_t)row * GCAP;
+  for (int g = g0; g < g1; g += 8) {
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) x[u] = (g + u < g1) ? src[(int64_t)(g + u) * BN] : -INFINITY;
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      if (x[u] != -INFINITY && x[u] >= lim) {
+        const int pos = atomicAdd(&s_cnt[lane], 1);
+        if (pos < GCAP) out[pos] = g + u;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && row < R) gcount[row] = s_cnt[lane];
+}
+
+// exact FP32 score: fmaf chain over k = 0..127 (the FP32 path's arithmetic)
+template <bool BF16C>
+__device__ __forceinline__ float dot_exact(const float *__restrict__ q, const float *__restrict__ cf,
+                                           const __nv_bfloat16 *__restrict__ cb, int64_t j) {
+  float acc = 0.f;
+  if (BF16C) {
+    const uint4 *row = reinterpret_cast<const uint4 *>(cb + j * DIM);
+#pragma unroll 4
+    for (int k8 = 0; k8 < DIM / 8; k8++) {
+      const uint4 u = row[k8];
+      const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int h = 0; h < 4; h++) {
+        acc = fmaf(q[k8 * 8 + 2 * h], __uint_as_float(w[h] << 16), acc);
+        acc = fmaf(q[k8 * 8 + 2 * h + 1], __uint_as_float(w[h] & 0xffff0000u), acc);
+      }
+    }
+  } else {
+    const float4 *row = reinterpret_cast<const float4 *>(cf + j * DIM);
+#pragma unroll 4
+    for (int k4 = 0; k4 < DIM / 4; k4++) {
+      const float4 c = row[k4];
+      acc = fmaf(q[k4 * 4 + 0], c.x, acc);
+      acc = fmaf(q[k4 * 4 + 1], c.y, acc);
+      acc = fmaf(q[k4 * 4 + 2], c.z, acc);
+      acc = fmaf(q[k4 * 4 + 3], c.w, acc);
+    }
+  }
+  return acc;
+}
+
+// One block per query row: the centroids of the kept groups scored exactly in
+// FP32, sorted by (score desc, id asc); the first kappa_c are the answer. A row
+// whose groups overflowed the list is marked for the full FP32 scan.
+template <bool BF16C>
+__global__ void __launch_bounds__(256)
+k_group_rescore(const float *__restrict__ rows, int R, const float *__restrict__ cent_f32,
+                const __nv_bfloat16 *__restrict__ cent_bf16, int64_t C, int kc, const int32_t *__restrict__ glist,
+                const int32_t *__restrict__ gcount, int32_t *__restrict__ top_ids, float *__restrict__ top_s,
+                int32_t *__restrict__ lossy_rows, uint32_t *__restrict__ flags) {
+  extern __shared__ __align__(16) uint64_t rsm[];  // [GCAP * 32] keys
+  __shared__ float q[DIM];
+  const int r = blockIdx.x;
+  if (r >= R) return;
+  const int ngr = gcount[r];
+  const bool lossy = ngr > GCAP;
+  const int n = min(ngr, GCAP) * 32;
+  const int np = next_pow2(max(n, 2));
+  for (int k = threadIdx.x; k < DIM; k += blockDim.x) q[k] = rows[(int64_t)r * DIM + k];
+  __syncthreads();
+  const int32_t *gl = glist + (int64_t)r * GCAP;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    uint64_t key = 0ull;
+    if (i < n) {
+      const int64_t j = (int64_t)gl[i >> 5] * 32 + (i & 31);
+      if (j < C) key = comp_key(dot_exact<BF16C>(q, cent_f32, cent_bf16, j), (int32_t)j);
+    }
+    rsm[i] = key;
+  }
+  __syncthreads();
+  block_sort_desc(rsm, np);
+  for (int i = threadIdx.x; i < kc; i += blockDim.x) {
+    const uint64_t v = i < n ? rsm[i] : 0ull;
+    top_ids[(int64_t)r * kc + i] = v ? comp_id(v) : -1;
+    top_s[(int64_t)r * kc + i] = v ? comp_score(v) : -INFINITY;
+  }
+  if (threadIdx.x == 0) {
+    lossy_rows[r] = lossy ? 1 : 0;
+    if (lossy) atomicOr(flags, TACHIOM_FLAG_TOPC_RESCUED);
   }
 }
 
@@ -360,24 +417,26 @@ int topc_tc_supported() {
   return cached;
 }
 
-int topc_tc_capg() { return tc::CAPG; }
+
 
 size_t topc_tc_gmax_elems(int64_t C, int rows) {
   const int64_t ntiles = (C + tc::BM - 1) / tc::BM;
   const int64_t rbs = (rows + tc::BN - 1) / tc::BN;
-  return (size_t)(rbs * ntiles * 4 * 2 * tc::BN);
+  return (size_t)(rbs * ntiles * 4 * tc::BN);
 }
 
-tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, const float *margins,
-                              uint32_t *gmax, uint32_t *tau, int32_t *cnt, uint64_t *cand, uint32_t *flags,
-                              cudaStream_t s) {
+size_t topc_tc_glist_elems(int rows) { return (size_t)rows * tc::GCAP; }
+
+tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, const float *rows, int nrows, int kc,
+                              const float *margins, uint32_t *gmax, int32_t *glist, int32_t *gcount,
+                              int32_t *lossy_rows, int32_t *top_ids, float *top_s, uint32_t *flags, cudaStream_t s) {
   using namespace tc;
   if (nrows <= 0) return TACHIOM_OK;
   TPROF("topc_tc", s);
   CUtensorMap mA, mB;
   tachiom_status st;
   if ((st = encode_map(&mA, ix.cent_bf16, ix.C, BM))) return st;
-  if ((st = encode_map(&mB, rows, nrows, BN))) return st;
+  if ((st = encode_map(&mB, rows_bf16, nrows, BN))) return st;
   const int ntiles = (int)((ix.C + BM - 1) / BM);
   const int rbs = (nrows + BN - 1) / BN;
   int sms = 148;
@@ -387,19 +446,25 @@ tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nr
   const int per = (ntiles + splits - 1) / splits;
   splits = (ntiles + per - 1) / per;
   const int G = ntiles * 4;
-  dim3 grid(splits, rbs);
   TCUDA(cudaFuncSetAttribute(k_topc_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  TCUDA(cudaFuncSetAttribute(k_topc_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  k_topc_tc<1><<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, gmax, nullptr, nullptr, nullptr,
-                                                  nullptr, flags);
+  k_topc_tc<1><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, gmax, nullptr,
+                                                               flags);
   TLAUNCH();
-  const size_t tsm = (size_t)TAU_WARPS * TAU_BINS * 32;
-  TCUDA(cudaFuncSetAttribute(k_topc_tau, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-  k_topc_tau<<<rbs * 8, TAU_WARPS * 32, tsm, s>>>(gmax, G, nrows, kc, 1.0001f * ix.cnorm_max + 1e-6f, tau);
+  const size_t hsm = (size_t)SEL_WARPS * 32 * (SEL_BINS + 4);
+  TCUDA(cudaFuncSetAttribute(k_group_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+  k_group_select<<<rbs * 8, SEL_WARPS * 32, hsm, s>>>(reinterpret_cast<const float *>(gmax), G, nrows, kc,
+                                                      1.0001f * ix.cnorm_max + 1e-6f, margins, glist, gcount);
   TLAUNCH();
-  TCUDA(cudaMemsetAsync(cnt, 0, (size_t)nrows * 4, s));
-  k_topc_tc<2><<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, nullptr, tau, margins, cnt,
-                                                  cand, flags);
+  const size_t rsm = (size_t)GCAP * 32 * 8;
+  if (ix.cdtype == TACHIOM_DTYPE_BF16) {
+    TCUDA(cudaFuncSetAttribute(k_group_rescore<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    k_group_rescore<true><<<nrows, 256, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc, glist, gcount,
+                                                  top_ids, top_s, lossy_rows, flags);
+  } else {
+    TCUDA(cudaFuncSetAttribute(k_group_rescore<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    k_group_rescore<false><<<nrows, 256, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc, glist, gcount,
+                                                   top_ids, top_s, lossy_rows, flags);
+  }
   TLAUNCH();
   return TACHIOM_OK;
 }
@@ -420,8 +485,7 @@ tachiom_status launch_topc_tc_raw(const Index &ix, const __nv_bfloat16 *rows, in
   splits = (ntiles + per - 1) / per;
   TCUDA(cudaFuncSetAttribute(k_topc_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   k_topc_tc<3><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, ntiles * 4,
-                                                               nullptr, nullptr, nullptr, nullptr,
-                                                               reinterpret_cast<uint64_t *>(out), flags);
+                                                               nullptr, reinterpret_cast<uint64_t *>(out), flags);
   TLAUNCH();
   return TACHIOM_OK;
 }

@@ -101,6 +101,9 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   AL(w->d_gmax, gm * 4);
   AL(w->d_tau, rows * 4);
   AL(w->d_margin, rows * 4);
+  AL(w->d_glist, (int64_t)topc_tc_glist_elems((int)rows) * 4);
+  AL(w->d_gcount, rows * 4);
+  AL(w->d_lossy, rows * 4);
   AL(w->d_hist, nq * NBINS1 * 4);
   AL(w->d_hist2, nq * NBINS1 * 4);
   AL(w->d_selstate, nq * 8 * 4);
@@ -250,8 +253,9 @@ static bool use_tc(const tachiom_search_params *p) {
 }
 
 // plan_id >= 0 overrides the library's choices (all choices give the same results):
-//   bits 0-1  step (a) kernel: 0 default, 1 single-pass tensor-core scan, 2 two-pass
-//             tensor-core scan, 3 FP32 CUDA-core scan
+//   bits 0-1  step (a) kernel: 0 default (2), 1 single-pass tensor-core scan with per-row
+//             selection in the epilogue, 2 tensor-core group maxima + exact rescoring of the
+//             kept groups, 3 FP32 CUDA-core scan
 //   bits 2-3  step (c) kernel: 0 default, 1 tensor-core refine + FP32 window, 2 FP32 refine
 //   bits 4-   slices of the FP32 scan (0: default)
 enum { SCAN_DEFAULT = 0, SCAN_TC1 = 1, SCAN_TC2 = 2, SCAN_F32 = 3 };
@@ -261,8 +265,8 @@ static int scan_kind(const tachiom_search_params *p) {
   const int forced = p->plan_id >= 0 ? (p->plan_id & 3) : SCAN_DEFAULT;
   if (!use_tc(p)) return SCAN_F32;
   if (forced == SCAN_F32) return SCAN_F32;
-  if (forced == SCAN_TC2) return SCAN_TC2;
-  return p->kappa_c <= topc_tc1_max_kc() ? SCAN_TC1 : SCAN_TC2;
+  if (forced == SCAN_TC1 && p->kappa_c <= topc_tc1_max_kc()) return SCAN_TC1;
+  return SCAN_TC2;
 }
 
 static int refine_kind(const tachiom_search_params *p) {
@@ -277,7 +281,7 @@ static void need_topc(const Index &ix, const tachiom_search_params *p, int rows,
   if (kind == SCAN_TC1) {
     n->split_entries = (int64_t)rows * topc_tc1_splits(ix, rows) * topc_tc1_capout();
   } else if (kind == SCAN_TC2) {
-    n->split_entries = (int64_t)rows * topc_tc_capg();
+    n->split_entries = rows;
     n->gmax = (int64_t)topc_tc_gmax_elems(ix.C, rows);
   } else {
     n->split_entries = (int64_t)rows * plan.splits * plan.capout;
@@ -301,13 +305,12 @@ static tachiom_status run_topc(Index *ix, Workspace *w, const tachiom_search_par
                              w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
   }
   if (kind == SCAN_TC2) {
-    // two passes (group maxima, then a filter): kappa_c above the single-pass limit
+    // group maxima from the tensor cores, then the exact FP32 top-kappa_c of the kept groups
     if ((st = launch_quantize_rows(*ix, rows, w->d_rows_bf16, nrows, w->d_margin, w->stream))) return st;
-    if ((st = launch_topc_tc(*ix, w->d_rows_bf16, nrows, kc, w->d_margin, w->d_gmax, w->d_tau, w->d_split_cnt,
-                             w->d_split, w->d_flags, w->stream)))
+    if ((st = launch_topc_tc(*ix, w->d_rows_bf16, rows, nrows, kc, w->d_margin, w->d_gmax, w->d_glist, w->d_gcount,
+                             w->d_lossy, w->d_top_ids, w->d_top_s, w->d_flags, w->stream)))
       return st;
-    return launch_topc_merge(*ix, rows, nrows, kc, 1, topc_tc_capg(), w->d_split, w->d_split_cnt, w->d_margin, 1,
-                             w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
+    return launch_topc_rescue(*ix, rows, nrows, kc, w->d_lossy, w->d_top_ids, w->d_top_s, w->stream);
   }
   if ((st = launch_topc_f32(*ix, rows, nrows, kc, plan.splits, plan.capout, w->d_split, w->d_split_cnt,
                             w->d_flags, w->stream)))

@@ -142,6 +142,9 @@ struct Workspace {
   uint32_t *d_gmax = nullptr;          // tensor-core path: group maxima of pass 1
   uint32_t *d_tau = nullptr;           // tensor-core path: per-row lower bound of the cut
   float *d_margin = nullptr;           // tensor-core path: per-row repair window (twice the error bound)
+  int32_t *d_glist = nullptr;          // tensor-core path: kept centroid groups per row
+  int32_t *d_gcount = nullptr;         // tensor-core path: number of kept groups per row
+  int32_t *d_lossy = nullptr;          // rows recomputed by the full FP32 scan
   int64_t cap_gmax = 0;
   int32_t *d_split_cnt = nullptr;      // [rows x splits]
   int32_t *d_top_ids = nullptr;        // [rows x kc]
@@ -202,13 +205,15 @@ tachiom_status launch_topc_merge(const Index &ix, const float *rows, int nrows, 
                                  uint32_t *flags, cudaStream_t s);
 tachiom_status launch_quantize_rows(const Index &ix, const float *rows, __nv_bfloat16 *out, int nrows,
                                     float *margins, cudaStream_t s);
-tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, const float *margins,
-                              uint32_t *gmax, uint32_t *tau, int32_t *cnt, uint64_t *cand, uint32_t *flags,
-                              cudaStream_t s);
+tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, const float *rows, int nrows, int kc,
+                              const float *margins, uint32_t *gmax, int32_t *glist, int32_t *gcount,
+                              int32_t *lossy_rows, int32_t *top_ids, float *top_s, uint32_t *flags, cudaStream_t s);
+tachiom_status launch_topc_rescue(const Index &ix, const float *rows, int nrows, int kc, const int32_t *lossy_rows,
+                                  int32_t *top_ids, float *top_s, cudaStream_t s);
+size_t topc_tc_glist_elems(int rows);
 int topc_tc_supported();
 tachiom_status launch_topc_tc_raw(const Index &ix, const __nv_bfloat16 *rows, int nrows, float *out,
                                   uint32_t *flags, cudaStream_t s);
-int topc_tc_capg();
 tachiom_status launch_topc_tc1(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, const float *margins,
                                uint64_t *split_out, int32_t *split_cnt, uint32_t *flags, cudaStream_t s);
 int topc_tc1_capout();

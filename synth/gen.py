@@ -334,7 +334,7 @@ def make_index(cfg: SynthConfig, device="cpu", log=None) -> dict:
         torch.as_tensor(kappa, device=device))
     # residuals against the stored centroids; norms kept in fp16
     rnorm = torch.empty(T, dtype=torch.float16, device=device)
-    Rn = torch.empty(T, DIM, dtype=xdt, device=device)
+    Rn = X  # the normalised residuals overwrite the token vectors chunk by chunk
     for s in range(0, T, ch):
         e = min(T, s + ch)
         r = X[s:e].to(torch.float32) - cwide[assign[s:e]]
