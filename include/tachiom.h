@@ -309,13 +309,16 @@ tachiom_status tachiom_debug_tc_scores(tachiom_index *index, const float *d_rows
                                        float *d_out, void *stream);
 
 /* Diagnostics of step (c): the refined score S of every candidate slot,
- * d_cand_ids int32 [nq x kappa_d] (slots < 0 give -inf), to d_scores fp32
- * [nq x kappa_d], before any top-k. With TACHIOM_PREC_BF16 on a tensor-core
- * device these are the approximate scores the FP32 repair starts from; the
- * tests use them to check its error bound. Asynchronous.                   */
+ * d_cand_ids int32 [nq x kappa_d] (slots < 0 are left untouched), to d_scores
+ * fp32 [nq x kappa_d], before any top-k. With TACHIOM_PREC_BF16 on a
+ * tensor-core device these are the approximate scores of the decode-and-MMA
+ * pass, and d_bounds (fp32 [nq x kappa_d], may be NULL) receives each
+ * document's rigorous bound on |approximate - FP32 score| that the FP32
+ * repair relies on; the tests check both against the oracle. Asynchronous. */
 tachiom_status tachiom_debug_refine_scores(tachiom_index *index, const tachiom_search_params *params,
                                            const float *d_queries, const int32_t *h_ntok, int32_t nq,
-                                           const int32_t *d_cand_ids, float *d_scores, void *stream);
+                                           const int32_t *d_cand_ids, float *d_scores, float *d_bounds,
+                                           void *stream);
 
 /* Library version string. */
 const char *tachiom_version(void);

@@ -109,7 +109,7 @@ def lib():
         "tachiom_stream_status": ([P, P, U32p], ct.c_int),
         "tachiom_debug_tc_scores": ([P, P, I32, P, P], ct.c_int),
         "tachiom_tc_available": ([], ct.c_int),
-        "tachiom_debug_refine_scores": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P], ct.c_int),
+        "tachiom_debug_refine_scores": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P, P], ct.c_int),
         "tachiom_profile_enable": ([ct.c_int], ct.c_int),
         "tachiom_profile_read": ([P, ct.POINTER(ProfileEntry), I32, ct.POINTER(ct.c_int32)], ct.c_int),
         "tachiom_server_create": ([P, ct.POINTER(SearchParams), ct.POINTER(ServerConfig), ct.POINTER(ct.c_void_p)],
@@ -250,10 +250,11 @@ class Index:
     def debug_tc_scores(self, rows, out, stream=None):
         _check(lib().tachiom_debug_tc_scores(self.h, _dp(rows), int(rows.shape[0]), _dp(out), _stream(stream)))
 
-    def debug_refine_scores(self, params: SearchParams, queries, ntok, cand_ids, out, stream=None):
+    def debug_refine_scores(self, params: SearchParams, queries, ntok, cand_ids, out, bounds=None, stream=None):
         ntok = np.ascontiguousarray(ntok, dtype=np.int32)
         _check(lib().tachiom_debug_refine_scores(self.h, ct.byref(params), _dp(queries), _hp(ntok),
-                                                 int(ntok.shape[0]), _dp(cand_ids), _dp(out), _stream(stream)))
+                                                 int(ntok.shape[0]), _dp(cand_ids), _dp(out), _dp(bounds),
+                                                 _stream(stream)))
 
     def autotune(self, params: SearchParams, queries, ntok, k, stream=None):
         """(best plan id, its median ms) for this batch (tachiom_autotune)."""

@@ -1,0 +1,376 @@
+// Step (c), reduced-precision pass: decode, then tensor cores.
+//
+// S(q,d) = sum_i max_{t in d} <q_i, x_t>,  x_t = c_a(t) + rho_t r^_t
+//
+// is the same number as the ADC form of Sec. 2.2 (Refine): the lookup
+// sum_m T[m][code_{t,m}][i] is <q_i, r^_t> split by subspace. On the B300 the
+// dense form is cheaper: a warp rebuilds x_t for 16 document tokens (the bf16
+// centroid row, gathered with cp.async one chunk ahead, plus rho_t times the
+// token's codewords, read from a bf16 copy of the codebooks in shared memory
+// with 16-byte code loads), rounds it to bf16, and one mma.sync chain
+// (m16n8k16, 16 tokens x 8 query tokens per n-tile, all 32 query tokens of the
+// query) scores the tile. The CTA keeps every query token, so codes and rows
+// are read once per query.
+//
+// The result is approximate; it only chooses the documents the FP32 kernel
+// (k_refine, lookup tables) rescores. Rigorous bound, per document d:
+//   |<bf16(q_i), bf16(x_t)> - <q_i, x_t>| <= ||e_qi|| ||x_t|| + ||bf16(q_i)|| ||e_xt||
+//                                           + 2^-17 ||bf16(q_i)|| ||bf16(x_t)||
+// with e_q = bf16(q) - q, e_x = bf16(x~) - x (x~ built from the bf16 codewords;
+// the codeword rounding enters e_x through a per-codeword error table). Taking
+// the max over t and summing over i gives Delta_d >= |S_approx(d) - S(d)|.
+#include <cuda_fp16.h>
+
+#include "tachiom_internal.cuh"
+
+namespace tachiom {
+
+constexpr int RD_THREADS = 256;
+constexpr int RD_WARPS = RD_THREADS / 32;
+constexpr int RD_DOCS_PER_CTA = 128;
+constexpr int RD_ROW = 272;              // 256-byte bf16 row + 16 bytes padding (conflict-free ldmatrix)
+constexpr int RD_TILE = 16 * RD_ROW;     // one 16-token tile
+
+__device__ __forceinline__ uint32_t rd_pack(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void rd_mma(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+struct DecPos {
+  int slot;
+  int64_t tb, te, c0;
+};
+
+__device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int step, const int32_t *cand_q,
+                                         const int64_t *doc_off, int64_t D, float *sa_row, float *da_row,
+                                         uint32_t *flags, int lane) {
+  if (p.c0 + 16 < p.te) {
+    p.c0 += 16;
+    return true;
+  }
+  for (p.slot += step; p.slot < s_end; p.slot += step) {
+    const int32_t d = cand_q[p.slot];
+    if (d < 0) continue;
+    if (d >= D) {
+      if (lane == 0) {
+        atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
+        sa_row[p.slot] = -INFINITY;
+        da_row[p.slot] = 0.f;
+      }
+      continue;
+    }
+    p.tb = doc_off[d];
+    p.te = doc_off[d + 1];
+    if (p.te == p.tb) {
+      if (lane == 0) {
+        sa_row[p.slot] = 0.f;
+        da_row[p.slot] = 0.f;
+      }
+      continue;
+    }
+    p.c0 = p.tb;
+    return true;
+  }
+  return false;
+}
+
+// sa[q][slot] = approximate S, da[q][slot] = its bound Delta_d
+template <int M>
+__global__ void __launch_bounds__(RD_THREADS, 1)
+k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta, int nq,
+             const int32_t *__restrict__ cand, int kd, const int64_t *__restrict__ doc_off,
+             const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
+             const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
+             const __nv_bfloat16 *__restrict__ cent_bf16, float cerr, float *__restrict__ sa,
+             float *__restrict__ da, int64_t D, uint32_t *__restrict__ flags) {
+  constexpr int DS = 128 / M;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __nv_bfloat16 *cbk = reinterpret_cast<__nv_bfloat16 *>(dsm);            // [M][256][DS] bf16 codewords
+  float *cerr2 = reinterpret_cast<float *>(dsm + M * 256 * DS * 2);        // [M][256] ||bf16(w) - w||^2
+  float *qn = cerr2 + M * 256;                                             // [32] ||e_q||, [32] ||q_hat||
+  unsigned char *tiles = reinterpret_cast<unsigned char *>(qn + 64);       // [warps][3 tiles]
+
+  const int q = blockIdx.y;
+  const int ntok = meta[3 * nq + 2 + q];
+  const int s_begin = blockIdx.x * RD_DOCS_PER_CTA;
+  const int s_end = min(kd, s_begin + RD_DOCS_PER_CTA);
+  const int32_t *cand_q = cand + (int64_t)q * kd;
+  {
+    int any = 0;
+    for (int i = s_begin + (int)threadIdx.x; i < s_end && !any; i += RD_THREADS) any = cand_q[i] >= 0;
+    if (!__syncthreads_or(any)) return;
+  }
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gq = lane >> 2, tig = lane & 3;
+  // codebooks to bf16, with the squared rounding error of each codeword
+  for (int mj = tid; mj < M * 256; mj += RD_THREADS) {
+    float e2 = 0.f;
+#pragma unroll
+    for (int u = 0; u < DS; u++) {
+      const float w = codebooks[(int64_t)mj * DS + u];
+      const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+      cbk[mj * DS + u] = wb;
+      const float d = __bfloat162float(wb) - w;
+      e2 = fmaf(d, d, e2);
+    }
+    cerr2[mj] = e2;
+  }
+  // query tokens: B fragments (bf16) and the norms of the rounding error
+  const float *qrow = queries + (int64_t)meta[q] * DIM;
+  if (warp < 4) {
+    // warp w: query tokens 8w..8w+7, lane pairs reduce the norms
+    for (int t = 0; t < 8; t++) {
+      const int i = warp * 8 + t;
+      float e2 = 0.f, h2 = 0.f;
+      if (i < ntok) {
+        for (int k = lane; k < DIM; k += 32) {
+          const float x = qrow[(int64_t)i * DIM + k];
+          const float h = __bfloat162float(__float2bfloat16_rn(x));
+          e2 = fmaf(h - x, h - x, e2);
+          h2 = fmaf(h, h, h2);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+      }
+      if (lane == 0) {
+        qn[i] = sqrtf(e2) * (1.f + ldexpf(1.f, -10));
+        qn[32 + i] = sqrtf(h2) * (1.f + ldexpf(1.f, -10));
+      }
+    }
+  }
+  uint32_t bq[4][8][2];
+#pragma unroll
+  for (int nt = 0; nt < 4; nt++) {
+    const int n = nt * 8 + gq;
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int k = s * 16 + h * 8 + tig * 2;
+        const float x0 = n < ntok ? qrow[(int64_t)n * DIM + k] : 0.f;
+        const float x1 = n < ntok ? qrow[(int64_t)n * DIM + k + 1] : 0.f;
+        bq[nt][s][h] = rd_pack(x0, x1);
+      }
+    }
+  }
+  __syncthreads();
+
+  unsigned char *wt = tiles + warp * 3 * RD_TILE;       // 2 centroid stages + 1 decoded tile
+  const uint32_t wt_s = (uint32_t)__cvta_generic_to_shared(wt);
+  const uint32_t lm_off = (uint32_t)((((lane >> 3) & 1) * 8 + (lane & 7)) * RD_ROW + ((lane >> 4) * 8) * 2);
+  float *sa_row = sa + (int64_t)q * kd;
+  float *da_row = da + (int64_t)q * kd;
+  // decode layout: lane -> row lane >> 1, dims (lane & 1) * 64 .. +64
+  const int drow = lane >> 1, dhalf = lane & 1;
+
+  auto issue = [&](const DecPos &p, int b, uint4 (&cw)[2], float &rh) {
+    const int64_t tl = p.c0 + (lane & 15);
+    const int32_t cid_l = (tl < p.te) ? tok_cid[tl] : 0;
+    const uint32_t dst0 = wt_s + (uint32_t)(b * RD_TILE);
+#pragma unroll
+    for (int it = 0; it < 8; it++) {
+      const int qq = it * 32 + lane;
+      const int row = qq >> 4, pc = qq & 15;
+      const int32_t cr = __shfl_sync(0xffffffffu, cid_l, row);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst0 + (uint32_t)(row * RD_ROW + pc * 16)),
+                   "l"(cent_bf16 + (int64_t)cr * DIM + pc * 8)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // this lane decodes row drow, half dhalf: codes of its subspaces, and the norm
+    const int64_t t = p.c0 + drow;
+    cw[0] = cw[1] = make_uint4(0u, 0u, 0u, 0u);
+    rh = 0.f;
+    if (t < p.te) {
+      if constexpr (M == 32) {
+        cw[0] = *reinterpret_cast<const uint4 *>(codes + t * M + dhalf * 16);
+      } else if constexpr (M == 16) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(codes + t * M + dhalf * 8);
+        cw[0] = make_uint4(v.x, v.y, 0u, 0u);
+      } else {
+        const uint32_t v = *reinterpret_cast<const uint32_t *>(codes + t * M + dhalf * 4);
+        cw[0] = make_uint4(v, 0u, 0u, 0u);
+      }
+      rh = __half2float(__ushort_as_half(rnorm[t]));
+    }
+  };
+
+  DecPos cur;
+  cur.slot = s_begin + warp - RD_WARPS;
+  cur.tb = cur.te = cur.c0 = 0;
+  bool has = dec_next(cur, s_end, RD_WARPS, cand_q, doc_off, D, sa_row, da_row, flags, lane);
+  uint4 cw_c[2], cw_n[2];
+  float rh_c = 0.f, rh_n = 0.f;
+  int b = 0;
+  if (has) issue(cur, b, cw_c, rh_c);
+  float mx[4][2];
+#pragma unroll
+  for (int nt = 0; nt < 4; nt++) mx[nt][0] = mx[nt][1] = -INFINITY;
+  float xmax = 0.f, exmax = 0.f;  // per document: max ||x_t|| and max ||e_xt|| (lane-local, reduced at the end)
+  while (has) {
+    DecPos nxt = cur;
+    const bool hn = dec_next(nxt, s_end, RD_WARPS, cand_q, doc_off, D, sa_row, da_row, flags, lane);
+    if (hn) {
+      issue(nxt, b ^ 1, cw_n, rh_n);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncwarp();
+    // decode: x~ = c + rho * w (bf16 codewords), rounded to bf16 into the decoded tile.
+    // This lane: row drow, dims [dhalf * 64, +64) = subspaces [dhalf * M / 2, +M / 2).
+    {
+      const unsigned char *crow = wt + b * RD_TILE + drow * RD_ROW + dhalf * 128;
+      unsigned char *xrow = wt + 2 * RD_TILE + drow * RD_ROW + dhalf * 128;
+      const uint8_t *cb8 = reinterpret_cast<const uint8_t *>(cw_c);  // codes of this lane's subspaces
+      const bool live = cur.c0 + drow < cur.te;
+      float x2 = 0.f, ex2 = 0.f, cwe2 = 0.f;
+#pragma unroll
+      for (int mm = 0; mm < M / 2; mm++) cwe2 += cerr2[(dhalf * (M / 2) + mm) * 256 + cb8[mm]];
+#pragma unroll
+      for (int v = 0; v < 8; v++) {  // 8 dims per step
+        const uint4 cu = *reinterpret_cast<const uint4 *>(crow + v * 16);
+        const uint32_t cwd[4] = {cu.x, cu.y, cu.z, cu.w};
+        uint32_t ob[4];
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+          float xs[2];
+#pragma unroll
+          for (int e = 0; e < 2; e++) {
+            const int kl = v * 8 + 2 * h + e;  // dim within this lane's half
+            const int mm = kl / DS;
+            const int m = dhalf * (M / 2) + mm;
+            const float w = __bfloat162float(cbk[(m * 256 + cb8[mm]) * DS + (kl % DS)]);
+            const float c = e == 0 ? __uint_as_float(cwd[h] << 16) : __uint_as_float(cwd[h] & 0xffff0000u);
+            xs[e] = fmaf(rh_c, w, c);
+          }
+          const __nv_bfloat162 xb = __floats2bfloat162_rn(xs[0], xs[1]);
+          const float2 xf = __bfloat1622float2(xb);
+          x2 = fmaf(xf.x, xf.x, fmaf(xf.y, xf.y, x2));
+          ex2 = fmaf(xf.x - xs[0], xf.x - xs[0], fmaf(xf.y - xs[1], xf.y - xs[1], ex2));
+          ob[h] = *reinterpret_cast<const uint32_t *>(&xb);
+        }
+        *reinterpret_cast<uint4 *>(xrow + v * 16) = make_uint4(ob[0], ob[1], ob[2], ob[3]);
+      }
+      // the two halves of the row: ||x^||, ||e_x|| (bf16 rounding of x~, plus rho times the
+      // codeword rounding, plus the FP32 rounding of x~ itself)
+      x2 += __shfl_xor_sync(0xffffffffu, x2, 1);
+      ex2 += __shfl_xor_sync(0xffffffffu, ex2, 1);
+      cwe2 += __shfl_xor_sync(0xffffffffu, cwe2, 1);
+      if (live) {
+        const float slack = 1.f + ldexpf(1.f, -10);
+        const float xn = sqrtf(x2) * slack;
+        xmax = fmaxf(xmax, xn);
+        exmax = fmaxf(exmax, (sqrtf(ex2) + rh_c * sqrtf(cwe2)) * slack + ldexpf(xn, -22));
+      }
+    }
+    __syncwarp();
+    float acc[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; nt++) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+    const uint32_t lm = wt_s + 2 * RD_TILE + lm_off;
+#pragma unroll
+    for (int s = 0; s < 8; s++) {
+      uint32_t a[4];
+      asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                   : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                   : "r"(lm + s * 32)
+                   : "memory");
+#pragma unroll
+      for (int nt = 0; nt < 4; nt++) rd_mma(acc[nt], a, bq[nt][s][0], bq[nt][s][1]);
+    }
+    // running max per query token over this thread's tokens (rows gq, gq + 8)
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      if (cur.c0 + gq + h * 8 >= cur.te) continue;
+#pragma unroll
+      for (int nt = 0; nt < 4; nt++) {
+        mx[nt][0] = fmaxf(mx[nt][0], acc[nt][h * 2 + 0]);
+        mx[nt][1] = fmaxf(mx[nt][1], acc[nt][h * 2 + 1]);
+      }
+    }
+    if (!hn || nxt.slot != cur.slot) {
+      // document complete: max over the lanes sharing tig, sum over query tokens, the bound
+      float xm = xmax, em = exmax;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+        em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
+      }
+      float sum = 0.f, dl = 0.f;
+#pragma unroll
+      for (int nt = 0; nt < 4; nt++) {
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+          float v = mx[nt][e];
+          v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
+          v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 8));
+          v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 16));
+          const int i = nt * 8 + tig * 2 + e;
+          if (i < ntok) {
+            sum += v;
+            // |<q^, x^> - <q, x>| <= ||e_q|| ||x|| + ||q^|| ||x^ - x||, ||x|| <= ||x^|| + ||x^ - x||
+            dl += qn[i] * (xm + em + cerr) + qn[32 + i] * (em + cerr) + ldexpf(qn[32 + i] * xm, -17);
+          }
+          mx[nt][e] = -INFINITY;
+        }
+      }
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+      dl += __shfl_xor_sync(0xffffffffu, dl, 1);
+      dl += __shfl_xor_sync(0xffffffffu, dl, 2);
+      if (lane == 0) {
+        sa_row[cur.slot] = sum;
+        da_row[cur.slot] = dl * (1.f + ldexpf(1.f, -10)) + ldexpf(fabsf(sum) + 1.f, -20) * 8.f;
+      }
+      xmax = exmax = 0.f;
+    }
+    __syncwarp();
+    cur = nxt;
+    has = hn;
+    b ^= 1;
+    cw_c[0] = cw_n[0];
+    cw_c[1] = cw_n[1];
+    rh_c = rh_n;
+  }
+}
+
+template <int M>
+static tachiom_status launch_refine_dec_m(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                          const int32_t *cand, int kd, float *sa, float *da, uint32_t *flags,
+                                          cudaStream_t s) {
+  constexpr int DS = 128 / M;
+  const size_t smem = (size_t)M * 256 * DS * 2 + (size_t)M * 256 * 4 + 64 * 4 + (size_t)RD_WARPS * 3 * RD_TILE;
+  dim3 grid((kd + RD_DOCS_PER_CTA - 1) / RD_DOCS_PER_CTA, nq);
+  TCUDA(cudaFuncSetAttribute(k_refine_dec<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_refine_dec<M><<<grid, RD_THREADS, smem, s>>>(queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes,
+                                                  ix.rnorm, ix.codebooks, ix.cent_bf16, ix.cerr_max, sa, da, ix.D,
+                                                  flags);
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
+tachiom_status launch_refine_dec(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                 const int32_t *cand, int kd, float *sa, float *da, uint32_t *flags, cudaStream_t s) {
+  if (nq <= 0) return TACHIOM_OK;
+  TPROF("refine_dec", s);
+  switch (ix.M) {
+    case 8: return launch_refine_dec_m<8>(ix, queries, meta, nq, cand, kd, sa, da, flags, s);
+    case 16: return launch_refine_dec_m<16>(ix, queries, meta, nq, cand, kd, sa, da, flags, s);
+    case 32: return launch_refine_dec_m<32>(ix, queries, meta, nq, cand, kd, sa, da, flags, s);
+  }
+  return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
+}
+
+}  // namespace tachiom

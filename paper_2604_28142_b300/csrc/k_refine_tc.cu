@@ -396,4 +396,55 @@ tachiom_status launch_refine_sum(const Index &ix, const int32_t *meta, int nq, c
   return TACHIOM_OK;
 }
 
+// Per query: the documents whose approximate S (sa) is within 2 max(Delta) of the
+// approximate k-th, for the FP32 kernel to rescore (decode-and-MMA pass; each
+// document carries its own bound da).
+__global__ void __launch_bounds__(1024)
+k_refine_window_b(const int32_t *__restrict__ meta, int nq, const int32_t *__restrict__ cand, int kd,
+                  const float *__restrict__ sa, const float *__restrict__ da, int32_t *__restrict__ win) {
+  extern __shared__ __align__(16) uint64_t wsm2[];
+  __shared__ float s_lim;
+  __shared__ unsigned s_dmax;
+  const int q = blockIdx.x;
+  const int k = meta[2 * nq + 2 + q];
+  const int np = next_pow2(max(kd, 2));
+  if (threadIdx.x == 0) s_dmax = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    uint64_t v = 0ull;
+    if (i < kd) {
+      const int32_t d = cand[(int64_t)q * kd + i];
+      const float s = sa[(int64_t)q * kd + i];
+      if (d >= 0 && s != -INFINITY) {
+        v = comp_key(s, d);
+        atomicMax(&s_dmax, __float_as_uint(da[(int64_t)q * kd + i]));  // non-negative: uint order
+      }
+    }
+    wsm2[i] = v;
+  }
+  __syncthreads();
+  block_sort_desc(wsm2, np);
+  if (threadIdx.x == 0) {
+    const uint64_t kth = wsm2[min(k, np) - 1];
+    s_lim = kth ? comp_score(kth) - 2.f * __uint_as_float(s_dmax) : -INFINITY;
+  }
+  __syncthreads();
+  const float lim = s_lim;
+  for (int i = threadIdx.x; i < kd; i += blockDim.x) {
+    const uint64_t v = i < np ? wsm2[i] : 0ull;
+    win[(int64_t)q * kd + i] = (v && comp_score(v) >= lim) ? comp_id(v) : -1;
+  }
+}
+
+tachiom_status launch_refine_window_b(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
+                                      const float *sa, const float *da, int32_t *win, cudaStream_t s) {
+  if (nq <= 0) return TACHIOM_OK;
+  TPROF("refine_window", s);
+  const size_t smem = (size_t)next_pow2(std::max(kd, 2)) * 8;
+  TCUDA(cudaFuncSetAttribute(k_refine_window_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_refine_window_b<<<nq, 1024, smem, s>>>(meta, nq, cand, kd, sa, da, win);
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
 }  // namespace tachiom

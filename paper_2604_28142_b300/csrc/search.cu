@@ -256,10 +256,11 @@ static bool use_tc(const tachiom_search_params *p) {
 //   bits 0-1  step (a) kernel: 0 default (2), 1 single-pass tensor-core scan with per-row
 //             selection in the epilogue, 2 tensor-core group maxima + exact rescoring of the
 //             kept groups, 3 FP32 CUDA-core scan
-//   bits 2-3  step (c) kernel: 0 default, 1 tensor-core refine + FP32 window, 2 FP32 refine
+//   bits 2-3  step (c) kernel: 0 default (3), 1 tensor-core centroid term + lookup tables, then the
+//             FP32 window, 2 FP32 refine only, 3 decode + tensor cores, then the FP32 window
 //   bits 4-   slices of the FP32 scan (0: default)
 enum { SCAN_DEFAULT = 0, SCAN_TC1 = 1, SCAN_TC2 = 2, SCAN_F32 = 3 };
-enum { REFINE_DEFAULT = 0, REFINE_TC = 1, REFINE_F32 = 2 };
+enum { REFINE_DEFAULT = 0, REFINE_TC = 1, REFINE_F32 = 2, REFINE_DEC = 3 };
 
 static int scan_kind(const tachiom_search_params *p) {
   const int forced = p->plan_id >= 0 ? (p->plan_id & 3) : SCAN_DEFAULT;
@@ -272,7 +273,8 @@ static int scan_kind(const tachiom_search_params *p) {
 static int refine_kind(const tachiom_search_params *p) {
   const int forced = p->plan_id >= 0 ? ((p->plan_id >> 2) & 3) : REFINE_DEFAULT;
   if (!use_tc(p)) return REFINE_F32;
-  return forced == REFINE_F32 ? REFINE_F32 : REFINE_TC;
+  if (forced == REFINE_F32 || forced == REFINE_TC) return forced;
+  return REFINE_DEC;
 }
 
 // scratch sizes of step (a) for a batch
@@ -334,7 +336,13 @@ static tachiom_status run_refine(Index *ix, Workspace *w, const tachiom_search_p
                                  int nq, const int32_t *cand, int kd, int32_t *out_ids, float *out_s,
                                  cudaStream_t stream) {
   tachiom_status st;
-  if (refine_kind(p) == REFINE_TC) {
+  const int rk = refine_kind(p);
+  if (rk == REFINE_DEC) {
+    float *sa = w->d_part, *da = w->d_part + (int64_t)nq * kd;  // consumed before the FP32 pass reuses d_part
+    if ((st = launch_refine_dec(*ix, queries, w->d_meta, nq, cand, kd, sa, da, w->d_flags, stream))) return st;
+    if ((st = launch_refine_window_b(*ix, w->d_meta, nq, cand, kd, sa, da, w->d_win, stream))) return st;
+    cand = w->d_win;
+  } else if (rk == REFINE_TC) {
     if ((st = launch_refine_tc(*ix, queries, w->d_meta, nq, cand, kd, w->d_part, w->d_flags, stream))) return st;
     if ((st = launch_refine_window(*ix, w->d_meta, nq, cand, kd, w->d_part, refine_tc_delta(*ix), w->d_win,
                                    stream)))
@@ -607,7 +615,8 @@ extern "C" tachiom_status tachiom_debug_tc_scores(tachiom_index *index, const fl
 
 extern "C" tachiom_status tachiom_debug_refine_scores(tachiom_index *index, const tachiom_search_params *params,
                                                      const float *d_queries, const int32_t *h_ntok, int32_t nq,
-                                                     const int32_t *d_cand_ids, float *d_scores, void *stream) {
+                                                     const int32_t *d_cand_ids, float *d_scores, float *d_bounds,
+                                                     void *stream) {
   Index *ix = as_index(index);
   if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
   DeviceGuard g(ix->device);
@@ -629,7 +638,11 @@ extern "C" tachiom_status tachiom_debug_refine_scores(tachiom_index *index, cons
   n.kd = kd;
   if ((st = ws_reserve(ix, w, n))) return st;
   if ((st = upload_meta(w, params, h_ntok, nullptr, nq))) return st;
-  if (use_tc(params)) {
+  if (use_tc(params) && refine_kind(params) == REFINE_DEC) {
+    // approximate S and its per-document bound
+    float *bounds = d_bounds ? d_bounds : w->d_part;
+    return launch_refine_dec(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, d_scores, bounds, w->d_flags, s);
+  } else if (use_tc(params)) {
     if ((st = launch_refine_tc(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, w->d_part, w->d_flags, s))) return st;
   } else {
     if ((st = launch_refine(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, w->d_part, w->d_flags, s))) return st;
@@ -765,7 +778,7 @@ extern "C" tachiom_status tachiom_autotune(tachiom_index *index, const tachiom_s
   const int tc = use_tc(params) ? 1 : 0;
   if (tc) {
     for (int sk : {SCAN_TC1, SCAN_TC2})
-      for (int rk : {REFINE_TC, REFINE_F32}) {
+      for (int rk : {REFINE_DEC, REFINE_TC, REFINE_F32}) {
         if (sk == SCAN_TC1 && params->kappa_c > topc_tc1_max_kc()) continue;
         plans.push_back(sk | (rk << 2));
       }

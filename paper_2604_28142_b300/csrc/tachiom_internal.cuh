@@ -240,6 +240,10 @@ tachiom_status launch_final_topk(const Index &ix, const int32_t *meta, int nq, c
 int refine_groups(int M);
 tachiom_status launch_refine_tc(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                 const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s);
+tachiom_status launch_refine_dec(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                 const int32_t *cand, int kd, float *sa, float *da, uint32_t *flags, cudaStream_t s);
+tachiom_status launch_refine_window_b(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
+                                      const float *sa, const float *da, int32_t *win, cudaStream_t s);
 tachiom_status launch_refine_sum(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
                                  const float *part, float *out, cudaStream_t s);
 tachiom_status launch_refine_window(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,

@@ -350,7 +350,7 @@ def test_bf16_kappa_c_above_group_count():
 
 @pytest.mark.parametrize("name", ["small", "small32", "random_edges"])
 def test_refine_tc_within_error_bound(name):
-    # approximate refined scores (tensor-core centroid term) are within the Delta
+    # approximate refined scores (decode + tensor cores) are within the per-document bound
     # the FP32 repair of the top-k window relies on; the FP32 kernel is within 1e-5
     _cuda()
     _tc()
@@ -359,24 +359,25 @@ def test_refine_tc_within_error_bound(name):
     cand = np.ascontiguousarray(res["cand_ids"])
     dc = torch.from_numpy(cand).cuda()
     out = {}
+    bnd = torch.full((c.nq, c.kd), -1.0, dtype=torch.float32, device="cuda")
     for prec in (0, 1):
-        o = torch.empty((c.nq, c.kd), dtype=torch.float32, device="cuda")
-        c.G.debug_refine_scores(c.params(prec), c.dq, c.ntok, dc, o)
+        o = torch.full((c.nq, c.kd), np.nan, dtype=torch.float32, device="cuda")
+        c.G.debug_refine_scores(c.params(prec), c.dq, c.ntok, dc, o, bnd if prec == 1 else None)
         torch.cuda.synchronize()
         out[prec] = o.cpu().numpy().astype(np.float64)
-    Cw = _widened(c.ix)
-    cmax = np.linalg.norm(Cw, axis=1).max()
-    rel = 2.0 ** -14 if c.ix["centroid_dtype"] == "bf16" else 2.0 ** -5
+    bounds = bnd.cpu().numpy().astype(np.float64)
     worst = 0.0
     for u in range(c.nq):
         cd = cand[u]
         valid = cd >= 0
         exact = c.O.refine(c.q[c.qoff[u]:c.qoff[u + 1]], cd[valid])
-        ntok = int(c.ntok[u])
-        delta = ntok * rel * cmax + 4 * 2.0 ** -20 * (np.abs(exact).max() + 1)
         e1 = np.abs(out[1][u][valid] - exact)
         e0 = np.abs(out[0][u][valid] - exact)
-        assert e1.max() <= delta, (u, e1.max(), delta)
+        b = bounds[u][valid]
+        assert np.all(b >= 0)
+        assert np.all(e1 <= b), (u, (e1 - b).max())
         assert np.all(e0 <= 1e-5 * np.maximum(1, np.abs(exact)))
-        worst = max(worst, e1.max() / delta)
-    assert worst > 0
+        worst = max(worst, (e1 / np.maximum(b, 1e-30)).max())
+    # the approximation really is approximate, and the bound is not loose by orders of magnitude
+    assert 0.0 < worst
+    assert worst > 1e-3
