@@ -320,6 +320,12 @@ tachiom_status tachiom_debug_refine_scores(tachiom_index *index, const tachiom_s
                                            const int32_t *d_cand_ids, float *d_scores, float *d_bounds,
                                            void *stream);
 
+/* Diagnostics of the tensor-core step (a): runs it on nrows device rows on the
+ * legacy default stream and copies, per row, the number of 32-centroid groups
+ * kept for exact rescoring to h_groups int32 [nrows] (host). Blocking.     */
+tachiom_status tachiom_debug_topc_groups(tachiom_index *index, const tachiom_search_params *params,
+                                         const float *d_rows, int32_t nrows, int32_t *h_groups);
+
 /* Library version string. */
 const char *tachiom_version(void);
 

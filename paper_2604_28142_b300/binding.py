@@ -109,6 +109,7 @@ def lib():
         "tachiom_stream_status": ([P, P, U32p], ct.c_int),
         "tachiom_debug_tc_scores": ([P, P, I32, P, P], ct.c_int),
         "tachiom_tc_available": ([], ct.c_int),
+        "tachiom_debug_topc_groups": ([P, ct.POINTER(SearchParams), P, I32, P], ct.c_int),
         "tachiom_debug_refine_scores": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P, P], ct.c_int),
         "tachiom_profile_enable": ([ct.c_int], ct.c_int),
         "tachiom_profile_read": ([P, ct.POINTER(ProfileEntry), I32, ct.POINTER(ct.c_int32)], ct.c_int),
@@ -268,6 +269,11 @@ class Index:
 
     def graph(self, params: SearchParams, ntok, k) -> "Graph":
         return Graph(self, params, ntok, k)
+
+    def debug_topc_groups(self, params: SearchParams, rows) -> np.ndarray:
+        out = np.empty(int(rows.shape[0]), np.int32)
+        _check(lib().tachiom_debug_topc_groups(self.h, ct.byref(params), _dp(rows), int(rows.shape[0]), _hp(out)))
+        return out
 
     def stream_status(self, stream=None) -> int:
         f = ct.c_uint32()

@@ -6,19 +6,29 @@
 // sum_m T[m][code_{t,m}][i] is <q_i, r^_t> split by subspace. On the B300 the
 // dense form is cheaper: a warp rebuilds x_t for 16 document tokens (the bf16
 // centroid row, gathered with cp.async one chunk ahead, plus rho_t times the
-// token's codewords, read from a bf16 copy of the codebooks in shared memory
-// with 16-byte code loads), rounds it to bf16, and one mma.sync chain
+// token's codewords, read from an fp16 copy of the codebooks in shared memory
+// with 16-byte code loads), rounds it to fp16, and one mma.sync chain
 // (m16n8k16, 16 tokens x 8 query tokens per n-tile, all 32 query tokens of the
 // query) scores the tile. The CTA keeps every query token, so codes and rows
-// are read once per query.
+// are read once per query. fp16 rather than bf16 operands: the same tensor
+// rate, a unit roundoff of 2^-11 instead of 2^-8, so the bound below, and with
+// it the window the FP32 kernel has to rescore, is about 8x narrower. The
+// values here (unit-scale embeddings) are far inside the fp16 range; a value
+// that overflows it gives an infinite bound, which sends the document to the
+// FP32 kernel.
 //
 // The result is approximate; it only chooses the documents the FP32 kernel
 // (k_refine, lookup tables) rescores. Rigorous bound, per document d:
-//   |<bf16(q_i), bf16(x_t)> - <q_i, x_t>| <= ||e_qi|| ||x_t|| + ||bf16(q_i)|| ||e_xt||
-//                                           + 2^-17 ||bf16(q_i)|| ||bf16(x_t)||
-// with e_q = bf16(q) - q, e_x = bf16(x~) - x (x~ built from the bf16 codewords;
+//   |<h(q_i), h(x_t)> - <q_i, x_t>| <= ||e_qi|| ||x_t|| + ||h(q_i)|| ||e_xt||
+//                                     + 2^-17 ||h(q_i)|| ||h(x_t)||
+// with h() the rounding to fp16, e_q = h(q) - q, e_x = h(x~) - x (x~ built from the fp16 codewords;
 // the codeword rounding enters e_x through a per-codeword error table). Taking
 // the max over t and summing over i gives Delta_d >= |S_approx(d) - S(d)|.
+// The documents are then compared with the FP32 kernel's scores, whose own
+// rounding (a chain of at most 150 FP32 operations per query token, over the
+// terms of <q, c> and rho <q, w>, with ||c|| <= cnorm and ||rho w|| <= ||x|| +
+// cnorm) is below 2^-16 ||q_i|| (||x_t|| + 2 cnorm) per query token; Delta_d
+// carries that term too.
 #include <cuda_fp16.h>
 
 #include "tachiom_internal.cuh"
@@ -28,17 +38,17 @@ namespace tachiom {
 constexpr int RD_THREADS = 256;
 constexpr int RD_WARPS = RD_THREADS / 32;
 constexpr int RD_DOCS_PER_CTA = 128;
-constexpr int RD_ROW = 272;              // 256-byte bf16 row + 16 bytes padding (conflict-free ldmatrix)
+constexpr int RD_ROW = 272;              // 128 2-byte values + 16 bytes padding (conflict-free ldmatrix)
 constexpr int RD_TILE = 16 * RD_ROW;     // one 16-token tile
 
 __device__ __forceinline__ uint32_t rd_pack(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  __half2 v = __floats2half2_rn(lo, hi);
   return *reinterpret_cast<uint32_t *>(&v);
 }
 
 __device__ __forceinline__ void rd_mma(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
@@ -89,13 +99,13 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
              const int32_t *__restrict__ cand, int kd, const int64_t *__restrict__ doc_off,
              const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
              const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
-             const __nv_bfloat16 *__restrict__ cent_bf16, float cerr, float *__restrict__ sa,
+             const __nv_bfloat16 *__restrict__ cent_bf16, float cerr, float cnorm, float *__restrict__ sa,
              float *__restrict__ da, int64_t D, uint32_t *__restrict__ flags) {
   constexpr int DS = 128 / M;
   extern __shared__ __align__(16) unsigned char dsm[];
-  __nv_bfloat16 *cbk = reinterpret_cast<__nv_bfloat16 *>(dsm);            // [M][256][DS] bf16 codewords
-  float *cerr2 = reinterpret_cast<float *>(dsm + M * 256 * DS * 2);        // [M][256] ||bf16(w) - w||^2
-  float *qn = cerr2 + M * 256;                                             // [32] ||e_q||, [32] ||q_hat||
+  __half *cbk = reinterpret_cast<__half *>(dsm);                           // [M][256][DS] fp16 codewords
+  float *cerr2 = reinterpret_cast<float *>(dsm + M * 256 * DS * 2);        // [M][256] ||h(w) - w||^2
+  float *qn = cerr2 + M * 256;                                             // [32] ||e_q||, [32] ||h(q)||
   unsigned char *tiles = reinterpret_cast<unsigned char *>(qn + 64);       // [warps][3 tiles]
 
   const int q = blockIdx.y;
@@ -110,20 +120,20 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gq = lane >> 2, tig = lane & 3;
-  // codebooks to bf16, with the squared rounding error of each codeword
+  // codebooks to fp16, with the squared rounding error of each codeword
   for (int mj = tid; mj < M * 256; mj += RD_THREADS) {
     float e2 = 0.f;
 #pragma unroll
     for (int u = 0; u < DS; u++) {
       const float w = codebooks[(int64_t)mj * DS + u];
-      const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+      const __half wb = __float2half_rn(w);
       cbk[mj * DS + u] = wb;
-      const float d = __bfloat162float(wb) - w;
+      const float d = __half2float(wb) - w;
       e2 = fmaf(d, d, e2);
     }
     cerr2[mj] = e2;
   }
-  // query tokens: B fragments (bf16) and the norms of the rounding error
+  // query tokens: B fragments (fp16) and the norms of the rounding error
   const float *qrow = queries + (int64_t)meta[q] * DIM;
   if (warp < 4) {
     // warp w: query tokens 8w..8w+7, lane pairs reduce the norms
@@ -133,7 +143,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
       if (i < ntok) {
         for (int k = lane; k < DIM; k += 32) {
           const float x = qrow[(int64_t)i * DIM + k];
-          const float h = __bfloat162float(__float2bfloat16_rn(x));
+          const float h = __half2float(__float2half_rn(x));
           e2 = fmaf(h - x, h - x, e2);
           h2 = fmaf(h, h, h2);
         }
@@ -228,7 +238,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncwarp();
-    // decode: x~ = c + rho * w (bf16 codewords), rounded to bf16 into the decoded tile.
+    // decode: x~ = c + rho * w (fp16 codewords), rounded to fp16 into the decoded tile.
     // This lane: row drow, dims [dhalf * 64, +64) = subspaces [dhalf * M / 2, +M / 2).
     {
       const unsigned char *crow = wt + b * RD_TILE + drow * RD_ROW + dhalf * 128;
@@ -251,19 +261,19 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
             const int kl = v * 8 + 2 * h + e;  // dim within this lane's half
             const int mm = kl / DS;
             const int m = dhalf * (M / 2) + mm;
-            const float w = __bfloat162float(cbk[(m * 256 + cb8[mm]) * DS + (kl % DS)]);
+            const float w = __half2float(cbk[(m * 256 + cb8[mm]) * DS + (kl % DS)]);
             const float c = e == 0 ? __uint_as_float(cwd[h] << 16) : __uint_as_float(cwd[h] & 0xffff0000u);
             xs[e] = fmaf(rh_c, w, c);
           }
-          const __nv_bfloat162 xb = __floats2bfloat162_rn(xs[0], xs[1]);
-          const float2 xf = __bfloat1622float2(xb);
+          const __half2 xb = __floats2half2_rn(xs[0], xs[1]);
+          const float2 xf = __half22float2(xb);
           x2 = fmaf(xf.x, xf.x, fmaf(xf.y, xf.y, x2));
           ex2 = fmaf(xf.x - xs[0], xf.x - xs[0], fmaf(xf.y - xs[1], xf.y - xs[1], ex2));
           ob[h] = *reinterpret_cast<const uint32_t *>(&xb);
         }
         *reinterpret_cast<uint4 *>(xrow + v * 16) = make_uint4(ob[0], ob[1], ob[2], ob[3]);
       }
-      // the two halves of the row: ||x^||, ||e_x|| (bf16 rounding of x~, plus rho times the
+      // the two halves of the row: ||x^||, ||e_x|| (fp16 rounding of x~, plus rho times the
       // codeword rounding, plus the FP32 rounding of x~ itself)
       x2 += __shfl_xor_sync(0xffffffffu, x2, 1);
       ex2 += __shfl_xor_sync(0xffffffffu, ex2, 1);
@@ -321,7 +331,8 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
           if (i < ntok) {
             sum += v;
             // |<q^, x^> - <q, x>| <= ||e_q|| ||x|| + ||q^|| ||x^ - x||, ||x|| <= ||x^|| + ||x^ - x||
-            dl += qn[i] * (xm + em + cerr) + qn[32 + i] * (em + cerr) + ldexpf(qn[32 + i] * xm, -17);
+            dl += qn[i] * (xm + em + cerr) + qn[32 + i] * (em + cerr) + ldexpf(qn[32 + i] * xm, -17) +
+                  ldexpf((qn[i] + qn[32 + i]) * (xm + em + 2.f * cnorm), -16);
           }
           mx[nt][e] = -INFINITY;
         }
@@ -355,7 +366,8 @@ static tachiom_status launch_refine_dec_m(const Index &ix, const float *queries,
   dim3 grid((kd + RD_DOCS_PER_CTA - 1) / RD_DOCS_PER_CTA, nq);
   TCUDA(cudaFuncSetAttribute(k_refine_dec<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_refine_dec<M><<<grid, RD_THREADS, smem, s>>>(queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes,
-                                                  ix.rnorm, ix.codebooks, ix.cent_bf16, ix.cerr_max, sa, da, ix.D,
+                                                  ix.rnorm, ix.codebooks, ix.cent_bf16, ix.cerr_max,
+                                                  ix.cnorm_max + ix.cerr_max, sa, da, ix.D,
                                                   flags);
   TLAUNCH();
   return TACHIOM_OK;

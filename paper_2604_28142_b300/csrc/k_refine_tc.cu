@@ -396,39 +396,57 @@ tachiom_status launch_refine_sum(const Index &ix, const int32_t *meta, int nq, c
   return TACHIOM_OK;
 }
 
-// Per query: the documents whose approximate S (sa) is within 2 max(Delta) of the
-// approximate k-th, for the FP32 kernel to rescore (decode-and-MMA pass; each
-// document carries its own bound da).
+// Per query: the documents that can still be in the exact top-k after the
+// decode-and-MMA pass, each with its own bound da: sa - da <= S <= sa + da. The
+// k-th largest lower bound L is at most the exact k-th score, so a document
+// with sa + da < L is strictly below it and never reaches the top-k; the others
+// (sorted by upper bound, first) go to the FP32 kernel. A document whose bound
+// is not finite is always kept. The bounds are widened by 2^-22 (|sa| + da) to
+// cover the rounding of the two sums.
+__device__ __forceinline__ void window_bounds(float s, float e, float *lo, float *up) {
+  if (isfinite(s) && e <= 3.0e38f) {
+    const float w = ldexpf(fabsf(s) + e, -22);
+    *lo = (s - e) - w;
+    *up = (s + e) + w;
+  } else {
+    *lo = -INFINITY;
+    *up = INFINITY;
+  }
+}
+
 __global__ void __launch_bounds__(1024)
 k_refine_window_b(const int32_t *__restrict__ meta, int nq, const int32_t *__restrict__ cand, int kd,
                   const float *__restrict__ sa, const float *__restrict__ da, int32_t *__restrict__ win) {
   extern __shared__ __align__(16) uint64_t wsm2[];
   __shared__ float s_lim;
-  __shared__ unsigned s_dmax;
   const int q = blockIdx.x;
   const int k = meta[2 * nq + 2 + q];
   const int np = next_pow2(max(kd, 2));
-  if (threadIdx.x == 0) s_dmax = 0u;
-  __syncthreads();
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    uint64_t v = 0ull;
-    if (i < kd) {
-      const int32_t d = cand[(int64_t)q * kd + i];
-      const float s = sa[(int64_t)q * kd + i];
-      if (d >= 0 && s != -INFINITY) {
-        v = comp_key(s, d);
-        atomicMax(&s_dmax, __float_as_uint(da[(int64_t)q * kd + i]));  // non-negative: uint order
+  for (int pass = 0; pass < 2; pass++) {
+    // pass 0: keys of the lower bounds (for L); pass 1: keys of the upper bounds
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+      uint64_t v = 0ull;
+      if (i < kd) {
+        const int32_t d = cand[(int64_t)q * kd + i];
+        const float s = sa[(int64_t)q * kd + i];
+        if (d >= 0 && s != -INFINITY) {
+          float lo, up;
+          window_bounds(s, da[(int64_t)q * kd + i], &lo, &up);
+          v = comp_key(pass == 0 ? lo : up, d);
+        }
       }
+      wsm2[i] = v;
     }
-    wsm2[i] = v;
+    __syncthreads();
+    block_sort_desc(wsm2, np);
+    if (pass == 0) {
+      if (threadIdx.x == 0) {
+        const uint64_t kth = wsm2[min(k, np) - 1];
+        s_lim = kth ? comp_score(kth) : -INFINITY;
+      }
+      __syncthreads();
+    }
   }
-  __syncthreads();
-  block_sort_desc(wsm2, np);
-  if (threadIdx.x == 0) {
-    const uint64_t kth = wsm2[min(k, np) - 1];
-    s_lim = kth ? comp_score(kth) - 2.f * __uint_as_float(s_dmax) : -INFINITY;
-  }
-  __syncthreads();
   const float lim = s_lim;
   for (int i = threadIdx.x; i < kd; i += blockDim.x) {
     const uint64_t v = i < np ? wsm2[i] : 0ull;

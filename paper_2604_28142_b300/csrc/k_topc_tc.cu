@@ -14,8 +14,8 @@
 //   pass    every group of 32 consecutive centroids reports, per query row, its
 //           maximum approximate score (one redux.sync per column) -> gmax;
 //   select  tau'_r = a lower bound on the row's kappa_c-th largest group maximum
-//           (saturating histogram); every group whose maximum is >= tau'_r -
-//           margin_r is kept. A centroid of the row's exact FP32 top-kappa_c has
+//           (two histogram levels, the second inside the bin the first finds);
+//           every group whose maximum is >= tau'_r - margin_r is kept. A centroid of the row's exact FP32 top-kappa_c has
 //           an approximate score >= (approximate kappa_c-th best) - 2 delta_r
 //           >= tau'_r - margin_r (margin_r = 2 delta_r), so its group is kept:
 //           about kappa_c groups per row survive;
@@ -219,62 +219,100 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   }
 }
 
-constexpr int SEL_BINS = 1024;
-constexpr int SEL_WARPS = 4;
-constexpr int GCAP = 256;  // groups a row may keep (8192 centroids)
+constexpr int SEL_BINS = 512;   // bins per histogram level
+constexpr int SEL_PARTS = 16;   // slices of the groups, one block each
+constexpr int GCAP = 256;       // groups a row may keep (8192 centroids)
 
-// One block = 32 query rows of a row block (lane = row); its 4 warps histogram a
-// quarter of the groups each (saturating 8-bit counts over [-cmax, cmax]); warp 0
-// finds tau' = the lower edge of the highest bin at which the count from the top
-// reaches kappa_c (at least kappa_c group maxima lie at or above it, so tau' is at
-// most the kappa_c-th largest); then every group with max >= tau' - margin_r is
-// listed for the row.
-__global__ void __launch_bounds__(SEL_WARPS * 32)
-k_group_select(const float *__restrict__ gmax, int G, int R, int kc, float cmax, const float *__restrict__ margins,
-               int32_t *__restrict__ glist, int32_t *__restrict__ gcount) {
-  extern __shared__ unsigned char hsm[];  // [SEL_WARPS][32 rows][SEL_BINS + 4]
-  __shared__ float s_lim[32];
-  __shared__ int s_cnt[32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Histogram of the group maxima of 32 rows (lane = row) over one slice of the
+// groups. Level 1 bins [-cmax, cmax]; level 2 bins the row's level-1 bin
+// [lo_r, lo_r + w1) again. Counts are added to hist[row][SEL_BINS].
+__global__ void __launch_bounds__(32)
+k_gsel_hist(const float *__restrict__ gmax, int G, int R, float cmax, int level, const float *__restrict__ lo,
+            uint32_t *__restrict__ hist) {
+  __shared__ uint16_t h[32][SEL_BINS + 2];
+  const int lane = threadIdx.x;
   const int rb = blockIdx.x >> 3, slab = blockIdx.x & 7;
   const int n = slab * 32 + lane;
   const int row = rb * BN + n;
-  constexpr int HS = SEL_BINS + 4;  // row stride: lanes fall in different banks
-  for (int i = threadIdx.x; i < SEL_WARPS * 32 * HS / 4; i += blockDim.x) reinterpret_cast<uint32_t *>(hsm)[i] = 0u;
-  if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0;
-  __syncthreads();
-  unsigned char *h = hsm + ((size_t)warp * 32 + lane) * HS;
-  const float scale = SEL_BINS / (2.f * cmax);
-  const int per = (G + SEL_WARPS - 1) / SEL_WARPS;
-  const int g0 = warp * per, g1 = min(G, g0 + per);
+  for (int b = 0; b < SEL_BINS; b++) h[lane][b] = 0;
+  const float w1 = 2.f * cmax / SEL_BINS;
+  const float base = (level == 1) ? -cmax : (row < R ? lo[row] : 0.f);
+  const float scale = (level == 1) ? 1.f / w1 : SEL_BINS / w1;
+  const bool skip = row >= R || (level == 2 && lo[row] == -INFINITY);
+  const int per = (G + SEL_PARTS - 1) / SEL_PARTS;
+  const int g0 = blockIdx.y * per, g1 = min(G, g0 + per);
   const float *src = gmax + (int64_t)rb * G * BN + n;
-  for (int g = g0; g < g1; g += 8) {
-    float x[8];
+  if (!skip) {
+    for (int g = g0; g < g1; g += 8) {
+      float x[8];
 #pragma unroll
-    for (int u = 0; u < 8; u++) x[u] = (g + u < g1) ? src[(int64_t)(g + u) * BN] : -INFINITY;
+      for (int u = 0; u < 8; u++) x[u] = (g + u < g1) ? src[(int64_t)(g + u) * BN] : -INFINITY;
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-      if (x[u] == -INFINITY) continue;
-      const int b = max(0, min(SEL_BINS - 1, (int)floorf((x[u] + cmax) * scale)));
-      const unsigned char c = h[b];
-      if (c != 255) h[b] = c + 1;
+      for (int u = 0; u < 8; u++) {
+        if (x[u] == -INFINITY) continue;
+        const float f = (x[u] - base) * scale;
+        if (level == 2 && (f < 0.f || f >= (float)SEL_BINS)) continue;  // outside the row's level-1 bin
+        const int b = max(0, min(SEL_BINS - 1, (int)floorf(f)));
+        h[lane][b]++;
+      }
     }
   }
-  __syncthreads();
-  if (warp == 0) {
-    int cum = 0, b = SEL_BINS - 1;
+  __syncwarp();
+  if (skip) return;
+  uint32_t *hq = hist + (int64_t)row * SEL_BINS;
+  for (int b = 0; b < SEL_BINS; b++)
+    if (h[lane][b]) atomicAdd(&hq[b], (uint32_t)h[lane][b]);
+}
+
+// Per row: the bin holding the kappa_c-th largest group maximum. Level 1 writes
+// the bin's lower edge to lo[row] and the count strictly above it to above[row]
+// (lo = -inf when fewer than kappa_c groups exist); level 2 narrows to a sub-bin
+// and writes lim[row] = its lower edge - margin_r, a value no larger than the
+// kappa_c-th largest group maximum minus the margin.
+__global__ void k_gsel_tau(const uint32_t *__restrict__ hist, int R, int kc, float cmax, int level,
+                           float *__restrict__ lo, uint32_t *__restrict__ above, const float *__restrict__ margins,
+                           float *__restrict__ lim) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= R) return;
+  const uint32_t *hq = hist + (int64_t)row * SEL_BINS;
+  const float w1 = 2.f * cmax / SEL_BINS;
+  if (level == 1) {
+    uint32_t cum = 0;
+    int b = SEL_BINS - 1;
     for (; b >= 0; b--) {
-      int c = 0;
-#pragma unroll
-      for (int w = 0; w < SEL_WARPS; w++) c += hsm[((size_t)w * 32 + lane) * HS + b];
-      cum += c;
-      if (cum >= kc) break;
+      if (cum + hq[b] >= (uint32_t)kc) break;
+      cum += hq[b];
     }
-    const float edge = (b > 0) ? (b / scale - cmax) : -INFINITY;  // b <= 0: no useful bound
-    s_lim[lane] = (row < R) ? edge - margins[row] : INFINITY;
+    lo[row] = (b >= 0) ? -cmax + b * w1 : -INFINITY;
+    above[row] = cum;
+    if (b < 0) lim[row] = -INFINITY;
+  } else {
+    if (lo[row] == -INFINITY) return;
+    uint32_t cum = above[row];
+    int b = SEL_BINS - 1;
+    for (; b >= 0; b--) {
+      if (cum + hq[b] >= (uint32_t)kc) break;
+      cum += hq[b];
+    }
+    const float w2 = w1 / SEL_BINS;
+    // the bin edges are computed in FP32: step down by one more sub-bin for safety
+    lim[row] = (b >= 0) ? lo[row] + b * w2 - w2 - margins[row] : -INFINITY;
   }
-  __syncthreads();
-  const float lim = s_lim[lane];
+}
+
+// Every group whose maximum is >= lim[row] goes to the row's list.
+__global__ void __launch_bounds__(32)
+k_gsel_collect(const float *__restrict__ gmax, int G, int R, const float *__restrict__ lim,
+               int32_t *__restrict__ glist, int32_t *__restrict__ gcount) {
+  const int lane = threadIdx.x;
+  const int rb = blockIdx.x >> 3, slab = blockIdx.x & 7;
+  const int n = slab * 32 + lane;
+  const int row = rb * BN + n;
+  if (row >= R) return;
+  const float l = lim[row];
+  const int per = (G + SEL_PARTS - 1) / SEL_PARTS;
+  const int g0 = blockIdx.y * per, g1 = min(G, g0 + per);
+  const float *src = gmax + (int64_t)rb * G * BN + n;
   int32_t *out = glist + (int64_t)row * GCAP;
   for (int g = g0; g < g1; g += 8) {
     float x[8];
@@ -282,14 +320,12 @@ k_group_select(const float *__restrict__ gmax, int G, int R, int kc, float cmax,
     for (int u = 0; u < 8; u++) x[u] = (g + u < g1) ? src[(int64_t)(g + u) * BN] : -INFINITY;
 #pragma unroll
     for (int u = 0; u < 8; u++) {
-      if (x[u] != -INFINITY && x[u] >= lim) {
-        const int pos = atomicAdd(&s_cnt[lane], 1);
+      if (x[u] != -INFINITY && x[u] >= l) {
+        const int pos = atomicAdd(&gcount[row], 1);
         if (pos < GCAP) out[pos] = g + u;
       }
     }
   }
-  __syncthreads();
-  if (warp == 0 && row < R) gcount[row] = s_cnt[lane];
 }
 
 // exact FP32 score: fmaf chain over k = 0..127 (the FP32 path's arithmetic)
@@ -324,41 +360,55 @@ __device__ __forceinline__ float dot_exact(const float *__restrict__ q, const fl
 }
 
 // One block per query row: the centroids of the kept groups scored exactly in
-// FP32, sorted by (score desc, id asc); the first kappa_c are the answer. A row
-// whose groups overflowed the list is marked for the full FP32 scan.
+// FP32. Only scores >= lim[row] are kept: kappa_c groups have a BF16 maximum
+// >= lim + 2 margin, so kappa_c distinct centroids score >= lim + margin
+// exactly and the kappa_c-th exact score (ties included) is above lim. The
+// kept keys are sorted by (score desc, id asc); the first kappa_c are the
+// answer. A row whose groups overflowed the list, or whose kept scores
+// overflowed the buffer, is marked for the full FP32 scan.
+constexpr int FCAP = 4096;  // kept exact scores per row
+
 template <bool BF16C>
 __global__ void __launch_bounds__(256)
 k_group_rescore(const float *__restrict__ rows, int R, const float *__restrict__ cent_f32,
                 const __nv_bfloat16 *__restrict__ cent_bf16, int64_t C, int kc, const int32_t *__restrict__ glist,
-                const int32_t *__restrict__ gcount, int32_t *__restrict__ top_ids, float *__restrict__ top_s,
-                int32_t *__restrict__ lossy_rows, uint32_t *__restrict__ flags) {
-  extern __shared__ __align__(16) uint64_t rsm[];  // [GCAP * 32] keys
+                const int32_t *__restrict__ gcount, const float *__restrict__ lim, int32_t *__restrict__ top_ids,
+                float *__restrict__ top_s, int32_t *__restrict__ lossy_rows, uint32_t *__restrict__ flags) {
+  extern __shared__ __align__(16) uint64_t rsm[];  // [FCAP] keys
   __shared__ float q[DIM];
+  __shared__ int s_cnt;
   const int r = blockIdx.x;
   if (r >= R) return;
   const int ngr = gcount[r];
-  const bool lossy = ngr > GCAP;
   const int n = min(ngr, GCAP) * 32;
-  const int np = next_pow2(max(n, 2));
+  const float l = lim[r];
   for (int k = threadIdx.x; k < DIM; k += blockDim.x) q[k] = rows[(int64_t)r * DIM + k];
+  if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   const int32_t *gl = glist + (int64_t)r * GCAP;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    uint64_t key = 0ull;
-    if (i < n) {
-      const int64_t j = (int64_t)gl[i >> 5] * 32 + (i & 31);
-      if (j < C) key = comp_key(dot_exact<BF16C>(q, cent_f32, cent_bf16, j), (int32_t)j);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t j = (int64_t)gl[i >> 5] * 32 + (i & 31);
+    if (j >= C) continue;
+    const float sc = dot_exact<BF16C>(q, cent_f32, cent_bf16, j);
+    if (!(sc < l)) {
+      const int pos = atomicAdd(&s_cnt, 1);
+      if (pos < FCAP) rsm[pos] = comp_key(sc, (int32_t)j);
     }
-    rsm[i] = key;
   }
+  __syncthreads();
+  const int cnt = s_cnt;
+  const int m = min(cnt, FCAP);
+  const int np = next_pow2(max(m, 2));
+  for (int i = m + threadIdx.x; i < np; i += blockDim.x) rsm[i] = 0ull;
   __syncthreads();
   block_sort_desc(rsm, np);
   for (int i = threadIdx.x; i < kc; i += blockDim.x) {
-    const uint64_t v = i < n ? rsm[i] : 0ull;
+    const uint64_t v = i < m ? rsm[i] : 0ull;
     top_ids[(int64_t)r * kc + i] = v ? comp_id(v) : -1;
     top_s[(int64_t)r * kc + i] = v ? comp_score(v) : -INFINITY;
   }
   if (threadIdx.x == 0) {
+    const bool lossy = ngr > GCAP || cnt > FCAP;
     lossy_rows[r] = lossy ? 1 : 0;
     if (lossy) atomicOr(flags, TACHIOM_FLAG_TOPC_RESCUED);
   }
@@ -425,7 +475,7 @@ size_t topc_tc_gmax_elems(int64_t C, int rows) {
   return (size_t)(rbs * ntiles * 4 * tc::BN);
 }
 
-size_t topc_tc_glist_elems(int rows) { return (size_t)rows * tc::GCAP; }
+size_t topc_tc_glist_elems(int rows) { return (size_t)rows * (tc::GCAP + tc::SEL_BINS + 3); }
 
 tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, const float *rows, int nrows, int kc,
                               const float *margins, uint32_t *gmax, int32_t *glist, int32_t *gcount,
@@ -450,20 +500,36 @@ tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, c
   k_topc_tc<1><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, gmax, nullptr,
                                                                flags);
   TLAUNCH();
-  const size_t hsm = (size_t)SEL_WARPS * 32 * (SEL_BINS + 4);
-  TCUDA(cudaFuncSetAttribute(k_group_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-  k_group_select<<<rbs * 8, SEL_WARPS * 32, hsm, s>>>(reinterpret_cast<const float *>(gmax), G, nrows, kc,
-                                                      1.0001f * ix.cnorm_max + 1e-6f, margins, glist, gcount);
-  TLAUNCH();
-  const size_t rsm = (size_t)GCAP * 32 * 8;
+  {
+    // selection workspace inside glist's tail: hist [rows x SEL_BINS] u32, lo, above, lim [rows]
+    uint32_t *hist = reinterpret_cast<uint32_t *>(glist + (int64_t)nrows * GCAP);
+    float *lo = reinterpret_cast<float *>(hist + (int64_t)nrows * SEL_BINS);
+    uint32_t *above = reinterpret_cast<uint32_t *>(lo + nrows);
+    float *lim = reinterpret_cast<float *>(above + nrows);
+    const float cm = 1.0001f * ix.cnorm_max + 1e-6f;
+    const dim3 sg(rbs * 8, SEL_PARTS);
+    for (int level = 1; level <= 2; level++) {
+      TCUDA(cudaMemsetAsync(hist, 0, (size_t)nrows * SEL_BINS * 4, s));
+      k_gsel_hist<<<sg, 32, 0, s>>>(reinterpret_cast<const float *>(gmax), G, nrows, cm, level, lo, hist);
+      TLAUNCH();
+      k_gsel_tau<<<(nrows + 127) / 128, 128, 0, s>>>(hist, nrows, kc, cm, level, lo, above, margins, lim);
+      TLAUNCH();
+    }
+    TCUDA(cudaMemsetAsync(gcount, 0, (size_t)nrows * 4, s));
+    k_gsel_collect<<<sg, 32, 0, s>>>(reinterpret_cast<const float *>(gmax), G, nrows, lim, glist, gcount);
+    TLAUNCH();
+  }
+  const float *lim = reinterpret_cast<const float *>(glist + (int64_t)nrows * GCAP) +
+                     (int64_t)nrows * SEL_BINS + 2 * (int64_t)nrows;
+  const size_t rsm = (size_t)FCAP * 8;
   if (ix.cdtype == TACHIOM_DTYPE_BF16) {
     TCUDA(cudaFuncSetAttribute(k_group_rescore<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
     k_group_rescore<true><<<nrows, 256, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc, glist, gcount,
-                                                  top_ids, top_s, lossy_rows, flags);
+                                                  lim, top_ids, top_s, lossy_rows, flags);
   } else {
     TCUDA(cudaFuncSetAttribute(k_group_rescore<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
     k_group_rescore<false><<<nrows, 256, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc, glist, gcount,
-                                                   top_ids, top_s, lossy_rows, flags);
+                                                   lim, top_ids, top_s, lossy_rows, flags);
   }
   TLAUNCH();
   return TACHIOM_OK;

@@ -823,3 +823,30 @@ extern "C" tachiom_status tachiom_autotune(tachiom_index *index, const tachiom_s
   if (best_ms) *best_ms = best;
   return TACHIOM_OK;
 }
+
+extern "C" tachiom_status tachiom_debug_topc_groups(tachiom_index *index, const tachiom_search_params *params,
+                                                   const float *d_rows, int32_t nrows, int32_t *h_groups) {
+  Index *ix = as_index(index);
+  if (!ix || !params || !h_groups) return fail(TACHIOM_ERR_INVALID, "NULL argument");
+  tachiom_status st;
+  if ((st = check_params(params))) return st;
+  if (scan_kind(params) != SCAN_TC2) return fail(TACHIOM_ERR_INVALID, "not the group-selection path");
+  if (nrows <= 0) return TACHIOM_OK;
+  DeviceGuard g(ix->device);
+  int32_t *ids = nullptr;
+  float *sc = nullptr;
+  if (cudaMalloc(&ids, (size_t)nrows * params->kappa_c * 4) != cudaSuccess ||
+      cudaMalloc(&sc, (size_t)nrows * params->kappa_c * 4) != cudaSuccess) {
+    cudaGetLastError();
+    if (ids) cudaFree(ids);
+    return fail(TACHIOM_ERR_OOM, "debug buffers");
+  }
+  st = tachiom_top_centroids(index, params, d_rows, nrows, ids, sc, nullptr);
+  Workspace *w = nullptr;
+  if (!st) st = ws_get(ix, nullptr, &w);
+  if (!st && cudaMemcpy(h_groups, w->d_gcount, (size_t)nrows * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = fail(TACHIOM_ERR_CUDA, "copy failed");
+  cudaFree(ids);
+  cudaFree(sc);
+  return st;
+}
