@@ -1,18 +1,23 @@
 // Step (b): inverted-list gather and centroid-only late interaction
 // (Sec. 2.2, Gather steps 2-4), then the kappa_d truncation.
 //
-// k_gather: one CTA per (query, range of R documents). For each query token i
-// in ascending order it walks, for every j in Top_i, the slice of L_j that
-// falls in its range (lists are doc-sorted and a per-(list, range) offset
-// table locates the slice) and keeps
-//     s~_i(d) = max_{j in Top_i : d in L_j} <q_i, c_j>
-// in a shared-memory word per document (atomicMax on an order-preserving
-// key); a second walk of the same slices hands each reached document's max
-// to exactly one thread (atomicExch), which adds it to S~(q, d). Tokens are
-// folded in ascending i, so S~ is summed in a fixed order and the candidate
-// scores are bit-identical run to run. The range's S~ values go to a dense
-// per-query array (-inf = not reached), and a 4096-bin histogram of their
-// keys goes to the query's histogram for the selection.
+// k_gather: one CTA per (query, range of R documents). Each Top_i arrives
+// sorted by (score desc, id asc), so the best retrieved centroid of token i
+// for document d is the one of smallest rank u in Top_i. For each query token
+// i in ascending order the CTA walks, for every j in Top_i, the slice of L_j
+// that falls in its range (lists are doc-sorted and a per-(list, range) offset
+// table locates the slice) and raises a shared-memory word per document to
+//     code = (i + 1) << 8 | (255 - u)          (atomicMax)
+// so the word holds the latest token that reached d and, within it, the best
+// rank. The thread whose atomicMax replaces an earlier token's code is the
+// only one that sees it, and it folds that token's maximum
+//     s~_i'(d) = <q_i', c_{Top_i'[u']}>
+// into S~(q, d); a barrier separates the tokens, and the codes left after the
+// last token are folded at the end. Every document's S~ is therefore summed
+// in ascending i, and the candidate scores are bit-identical run to run. The
+// range's S~ values go to a dense per-query array (-inf = not reached), and a
+// 4096-bin histogram of their keys goes to the query's histogram for the
+// selection.
 //
 // Selection of the kappa_d best (S~ desc, doc asc): the histogram locates the
 // bin that holds the kappa_d-th key; up to two more histogram levels narrow
@@ -29,12 +34,20 @@ constexpr int G_REG = 4;        // list entries per thread and token kept in reg
 
 // Per (token, centroid) segment of a list inside the CTA's document range:
 // start (absolute position in list_doc), exclusive prefix of the lengths within
-// its token, and the order-preserving key of <q_i, c_j>.
+// its token, and the code (i + 1) << 8 | (255 - rank).
 struct GSeg {
   int32_t start;
   int32_t pref;
   uint32_t key;
 };
+
+// S~(d) += the score a code stands for (the first token sets it)
+__device__ __forceinline__ void gather_fold(float *S, int x, uint32_t code, const float *__restrict__ tsq, int kc) {
+  const int tok = (int)(code >> 8) - 1, u = 255 - (int)(code & 255u);
+  const float sv = __ldg(tsq + (int64_t)tok * kc + u);
+  const float cur = S[x];
+  S[x] = (cur == -INFINITY) ? sv : cur + sv;
+}
 
 __global__ void __launch_bounds__(G_THREADS, 1)
 k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
@@ -43,7 +56,7 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
          int64_t D, int RD, int64_t C, float *__restrict__ dense, uint32_t *__restrict__ hist,
          uint32_t *__restrict__ flags) {
   extern __shared__ __align__(16) uint32_t gsm[];
-  uint32_t *best = gsm;                                   // [RD] max key of the current token
+  uint32_t *best = gsm;                                   // [RD] code of the latest token (0: none)
   float *S = reinterpret_cast<float *>(gsm + RD);         // [RD] running S~
   uint32_t *h = gsm + 2 * RD;                             // [NBINS1]
   GSeg *seg = reinterpret_cast<GSeg *>(gsm + 2 * RD + NBINS1);  // [G_SEGCAP]
@@ -59,6 +72,7 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
   }
   for (int b = tid; b < NBINS1; b += G_THREADS) h[b] = 0u;
   const int row_b = qoff[q], row_e = qoff[q + 1];
+  const float *tsq = top_s + (int64_t)row_b * kc;  // Top_i scores of this query's tokens
   const int per_group = max(1, G_SEGCAP / kc);  // tokens whose segments fit at once
 
   for (int i0 = row_b; i0 < row_e; i0 += per_group) {
@@ -80,7 +94,7 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
         const int lo = list_roff[(int64_t)jj * nr1 + r], hi = list_roff[(int64_t)jj * nr1 + r + 1];
         g.start = (int32_t)(list_off[jj] + lo);
         g.pref = hi - lo;
-        g.key = fkey(top_s[(int64_t)(i0 + ti) * kc + (e % kc)]);
+        g.key = ((uint32_t)(i0 + ti - row_b + 1) << 8) | (uint32_t)(255 - e % kc);
       }
       seg[e] = g;
     }
@@ -104,14 +118,14 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
       if (lane == 0) tok_total[ti] = carry;
     }
     __syncthreads();
-    // Tokens in order; each thread keeps the list entries it handles for the current
-    // token in registers (both passes use them) and loads the next token's entries
-    // before the second pass, so their latency overlaps the current token's work.
-    int32_t dc[G_REG], dn[G_REG];
-    uint32_t kcur[G_REG], knx[G_REG];
+    // Tokens in order, one barrier each; each thread keeps the list entries it
+    // handles for a token in registers, loaded two tokens ahead so that their
+    // latency overlaps the current token's work.
+    int32_t d0[G_REG], d1[G_REG], d2[G_REG];
+    uint32_t k0[G_REG], k1[G_REG], k2[G_REG];
     auto fetch = [&](int ti, int32_t (&d)[G_REG], uint32_t (&k)[G_REG]) {
       const GSeg *sg = seg + ti * kc;
-      const int total = tok_total[ti];
+      const int total = ti < ng ? tok_total[ti] : 0;
 #pragma unroll
       for (int u = 0; u < G_REG; u++) {
         const int e = tid + u * G_THREADS;
@@ -128,56 +142,42 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
         }
       }
     };
-    if (ng > 0) fetch(0, dc, kcur);
+    auto visit = [&](int x, uint32_t code) {
+      const uint32_t old = atomicMax(&best[x], code);
+      if (old != 0u && (old >> 8) != (code >> 8)) gather_fold(S, x, old, tsq, kc);
+    };
+    fetch(0, d0, k0);
+    fetch(1, d1, k1);
     for (int ti = 0; ti < ng; ti++) {
-      const GSeg *sg = seg + ti * kc;
-      const int total = tok_total[ti];
-      // pass 1: per-document max over the retrieved centroids (step 3)
+      fetch(ti + 2, d2, k2);
 #pragma unroll
       for (int u = 0; u < G_REG; u++)
-        if (dc[u] >= 0) atomicMax(&best[dc[u]], kcur[u]);
+        if (d0[u] >= 0) visit(d0[u], k0[u]);
+      const GSeg *sg = seg + ti * kc;
+      const int total = tok_total[ti];
       for (int e = tid + G_REG * G_THREADS; e < total; e += G_THREADS) {
         int lo = 0, hi = kc;
         while (hi - lo > 1) {
           const int mid = (lo + hi) >> 1;
           if (sg[mid].pref <= e) lo = mid; else hi = mid;
         }
-        const int32_t d = list_doc[sg[lo].start + (e - sg[lo].pref)];
-        atomicMax(&best[d - r0], sg[lo].key);
-      }
-      __syncthreads();
-      if (ti + 1 < ng) fetch(ti + 1, dn, knx);
-      // pass 2: fold the max into S~ once per reached document (step 4)
-#pragma unroll
-      for (int u = 0; u < G_REG; u++) {
-        if (dc[u] >= 0) {
-          const uint32_t v = atomicExch(&best[dc[u]], 0u);
-          if (v) {
-            const float sv = funkey(v), cur = S[dc[u]];
-            S[dc[u]] = (cur == -INFINITY) ? sv : cur + sv;
-          }
-        }
-      }
-      for (int e = tid + G_REG * G_THREADS; e < total; e += G_THREADS) {
-        int lo = 0, hi = kc;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (sg[mid].pref <= e) lo = mid; else hi = mid;
-        }
-        const int32_t d = list_doc[sg[lo].start + (e - sg[lo].pref)];
-        const uint32_t v = atomicExch(&best[d - r0], 0u);
-        if (v) {
-          const float sv = funkey(v), cur = S[d - r0];
-          S[d - r0] = (cur == -INFINITY) ? sv : cur + sv;
-        }
+        visit(list_doc[sg[lo].start + (e - sg[lo].pref)] - (int32_t)r0, sg[lo].key);
       }
       __syncthreads();
 #pragma unroll
       for (int u = 0; u < G_REG; u++) {
-        dc[u] = dn[u];
-        kcur[u] = knx[u];
+        d0[u] = d1[u];
+        k0[u] = k1[u];
+        d1[u] = d2[u];
+        k1[u] = k2[u];
       }
     }
+  }
+  // the codes of the last token that reached each document
+  __syncthreads();
+  for (int x = tid; x < nd; x += G_THREADS) {
+    const uint32_t c = best[x];
+    if (c) gather_fold(S, x, c, tsq, kc);
   }
   float *out = dense + (int64_t)q * D + r0;
   for (int x = tid; x < nd; x += G_THREADS) {

@@ -35,15 +35,22 @@
 
 namespace tachiom {
 
-constexpr int RD_THREADS = 256;
-constexpr int RD_WARPS = RD_THREADS / 32;
-constexpr int RD_DOCS_PER_CTA = 128;
+constexpr int RD_DOCS_PER_CTA = 64;
 constexpr int RD_ROW = 272;              // 128 2-byte values + 16 bytes padding (conflict-free ldmatrix)
 constexpr int RD_TILE = 16 * RD_ROW;     // one 16-token tile
+constexpr int RD_SMEM_MAX = 227 * 1024;
 
-__device__ __forceinline__ uint32_t rd_pack(float lo, float hi) {
-  __half2 v = __floats2half2_rn(lo, hi);
-  return *reinterpret_cast<uint32_t *>(&v);
+// shared memory: fp16 codebooks, codeword error table, query norms, the fp16
+// query tile [32][RD_ROW], then per warp two tiles (centroid rows land by
+// cp.async and are decoded in place)
+template <int M>
+constexpr int rd_fixed_bytes() {
+  return M * 256 * (128 / M) * 2 + M * 256 * 4 + 64 * 4 + 32 * RD_ROW;
+}
+template <int M>
+constexpr int rd_warps() {
+  return (RD_SMEM_MAX - rd_fixed_bytes<M>()) / (2 * RD_TILE) > 16 ? 16
+                                                                 : (RD_SMEM_MAX - rd_fixed_bytes<M>()) / (2 * RD_TILE);
 }
 
 __device__ __forceinline__ void rd_mma(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
@@ -54,26 +61,40 @@ __device__ __forceinline__ void rd_mma(float *d, const uint32_t *a, uint32_t b0,
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void rd_ldm4(uint32_t *r, uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr)
+               : "memory");
+}
+
 struct DecPos {
   int slot;
   int64_t tb, te, c0;
 };
 
-__device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int step, const int32_t *cand_q,
+// next 16-token chunk of the warp's document, or the next document of the CTA's
+// slice (taken from a shared counter, so the warps stay balanced)
+__device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int *s_next, const int32_t *cand_q,
                                          const int64_t *doc_off, int64_t D, float *sa_row, float *da_row,
                                          uint32_t *flags, int lane) {
   if (p.c0 + 16 < p.te) {
     p.c0 += 16;
     return true;
   }
-  for (p.slot += step; p.slot < s_end; p.slot += step) {
-    const int32_t d = cand_q[p.slot];
+  for (;;) {
+    int slot = 0;
+    if (lane == 0) slot = atomicAdd(s_next, 1);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot >= s_end) return false;
+    p.slot = slot;
+    const int32_t d = cand_q[slot];
     if (d < 0) continue;
     if (d >= D) {
       if (lane == 0) {
         atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
-        sa_row[p.slot] = -INFINITY;
-        da_row[p.slot] = 0.f;
+        sa_row[slot] = -INFINITY;
+        da_row[slot] = 0.f;
       }
       continue;
     }
@@ -81,20 +102,19 @@ __device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int step, const i
     p.te = doc_off[d + 1];
     if (p.te == p.tb) {
       if (lane == 0) {
-        sa_row[p.slot] = 0.f;
-        da_row[p.slot] = 0.f;
+        sa_row[slot] = 0.f;
+        da_row[slot] = 0.f;
       }
       continue;
     }
     p.c0 = p.tb;
     return true;
   }
-  return false;
 }
 
 // sa[q][slot] = approximate S, da[q][slot] = its bound Delta_d
-template <int M>
-__global__ void __launch_bounds__(RD_THREADS, 1)
+template <int M, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1)
 k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta, int nq,
              const int32_t *__restrict__ cand, int kd, const int64_t *__restrict__ doc_off,
              const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
@@ -102,11 +122,14 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
              const __nv_bfloat16 *__restrict__ cent_bf16, float cerr, float cnorm, float *__restrict__ sa,
              float *__restrict__ da, int64_t D, uint32_t *__restrict__ flags) {
   constexpr int DS = 128 / M;
+  constexpr int NT = WARPS * 32;
   extern __shared__ __align__(16) unsigned char dsm[];
   __half *cbk = reinterpret_cast<__half *>(dsm);                           // [M][256][DS] fp16 codewords
   float *cerr2 = reinterpret_cast<float *>(dsm + M * 256 * DS * 2);        // [M][256] ||h(w) - w||^2
   float *qn = cerr2 + M * 256;                                             // [32] ||e_q||, [32] ||h(q)||
-  unsigned char *tiles = reinterpret_cast<unsigned char *>(qn + 64);       // [warps][3 tiles]
+  unsigned char *qsm = reinterpret_cast<unsigned char *>(qn + 64);         // [32][RD_ROW] fp16 query tokens
+  unsigned char *tiles = qsm + 32 * RD_ROW;                                // [WARPS][2 tiles]
+  __shared__ int s_next;
 
   const int q = blockIdx.y;
   const int ntok = meta[3 * nq + 2 + q];
@@ -115,13 +138,13 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   const int32_t *cand_q = cand + (int64_t)q * kd;
   {
     int any = 0;
-    for (int i = s_begin + (int)threadIdx.x; i < s_end && !any; i += RD_THREADS) any = cand_q[i] >= 0;
+    for (int i = s_begin + (int)threadIdx.x; i < s_end && !any; i += NT) any = cand_q[i] >= 0;
     if (!__syncthreads_or(any)) return;
   }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int gq = lane >> 2, tig = lane & 3;
+  const int gq = lane >> 2;
   // codebooks to fp16, with the squared rounding error of each codeword
-  for (int mj = tid; mj < M * 256; mj += RD_THREADS) {
+  for (int mj = tid; mj < M * 256; mj += NT) {
     float e2 = 0.f;
 #pragma unroll
     for (int u = 0; u < DS; u++) {
@@ -133,58 +156,49 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     }
     cerr2[mj] = e2;
   }
-  // query tokens: B fragments (fp16) and the norms of the rounding error
+  // query tokens: the fp16 tile (B operand, zero rows past ntok) and the norms of the rounding error
   const float *qrow = queries + (int64_t)meta[q] * DIM;
-  if (warp < 4) {
-    // warp w: query tokens 8w..8w+7, lane pairs reduce the norms
-    for (int t = 0; t < 8; t++) {
-      const int i = warp * 8 + t;
-      float e2 = 0.f, h2 = 0.f;
-      if (i < ntok) {
-        for (int k = lane; k < DIM; k += 32) {
-          const float x = qrow[(int64_t)i * DIM + k];
-          const float h = __half2float(__float2half_rn(x));
-          e2 = fmaf(h - x, h - x, e2);
-          h2 = fmaf(h, h, h2);
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-        h2 += __shfl_xor_sync(0xffffffffu, h2, o);
-      }
-      if (lane == 0) {
-        qn[i] = sqrtf(e2) * (1.f + ldexpf(1.f, -10));
-        qn[32 + i] = sqrtf(h2) * (1.f + ldexpf(1.f, -10));
+  for (int x = tid; x < 32 * DIM / 2; x += NT) {
+    const int i = x / (DIM / 2), k = (x % (DIM / 2)) * 2;
+    const float x0 = i < ntok ? qrow[(int64_t)i * DIM + k] : 0.f;
+    const float x1 = i < ntok ? qrow[(int64_t)i * DIM + k + 1] : 0.f;
+    *reinterpret_cast<__half2 *>(qsm + i * RD_ROW + k * 2) = __floats2half2_rn(x0, x1);
+  }
+  for (int i = warp; i < 32; i += WARPS) {
+    float e2 = 0.f, h2 = 0.f;
+    if (i < ntok) {
+      for (int k = lane; k < DIM; k += 32) {
+        const float x = qrow[(int64_t)i * DIM + k];
+        const float h = __half2float(__float2half_rn(x));
+        e2 = fmaf(h - x, h - x, e2);
+        h2 = fmaf(h, h, h2);
       }
     }
-  }
-  uint32_t bq[4][8][2];
 #pragma unroll
-  for (int nt = 0; nt < 4; nt++) {
-    const int n = nt * 8 + gq;
-#pragma unroll
-    for (int s = 0; s < 8; s++) {
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        const int k = s * 16 + h * 8 + tig * 2;
-        const float x0 = n < ntok ? qrow[(int64_t)n * DIM + k] : 0.f;
-        const float x1 = n < ntok ? qrow[(int64_t)n * DIM + k + 1] : 0.f;
-        bq[nt][s][h] = rd_pack(x0, x1);
-      }
+    for (int o = 16; o > 0; o >>= 1) {
+      e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+      h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+    }
+    if (lane == 0) {
+      qn[i] = sqrtf(e2) * (1.f + ldexpf(1.f, -10));
+      qn[32 + i] = sqrtf(h2) * (1.f + ldexpf(1.f, -10));
     }
   }
+  if (tid == 0) s_next = s_begin;
   __syncthreads();
 
-  unsigned char *wt = tiles + warp * 3 * RD_TILE;       // 2 centroid stages + 1 decoded tile
+  unsigned char *wt = tiles + warp * 2 * RD_TILE;
   const uint32_t wt_s = (uint32_t)__cvta_generic_to_shared(wt);
-  const uint32_t lm_off = (uint32_t)((((lane >> 3) & 1) * 8 + (lane & 7)) * RD_ROW + ((lane >> 4) * 8) * 2);
+  const uint32_t qs_s = (uint32_t)__cvta_generic_to_shared(qsm);
+  // ldmatrix row addresses: A (document tokens x dims) and B (query tokens x dims, two n-tiles per x4)
+  const uint32_t la_off = (uint32_t)((((lane >> 3) & 1) * 8 + (lane & 7)) * RD_ROW + ((lane >> 4) * 8) * 2);
+  const uint32_t lb_off = (uint32_t)((((lane >> 4) * 8) + (lane & 7)) * RD_ROW + ((lane >> 3) & 1) * 16);
   float *sa_row = sa + (int64_t)q * kd;
   float *da_row = da + (int64_t)q * kd;
   // decode layout: lane -> row lane >> 1, dims (lane & 1) * 64 .. +64
   const int drow = lane >> 1, dhalf = lane & 1;
 
-  auto issue = [&](const DecPos &p, int b, uint4 (&cw)[2], float &rh) {
+  auto issue = [&](const DecPos &p, int b, uint4 &cw, float &rh) {
     const int64_t tl = p.c0 + (lane & 15);
     const int32_t cid_l = (tl < p.te) ? tok_cid[tl] : 0;
     const uint32_t dst0 = wt_s + (uint32_t)(b * RD_TILE);
@@ -200,27 +214,27 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     asm volatile("cp.async.commit_group;" ::: "memory");
     // this lane decodes row drow, half dhalf: codes of its subspaces, and the norm
     const int64_t t = p.c0 + drow;
-    cw[0] = cw[1] = make_uint4(0u, 0u, 0u, 0u);
+    cw = make_uint4(0u, 0u, 0u, 0u);
     rh = 0.f;
     if (t < p.te) {
       if constexpr (M == 32) {
-        cw[0] = *reinterpret_cast<const uint4 *>(codes + t * M + dhalf * 16);
+        cw = *reinterpret_cast<const uint4 *>(codes + t * M + dhalf * 16);
       } else if constexpr (M == 16) {
         const uint2 v = *reinterpret_cast<const uint2 *>(codes + t * M + dhalf * 8);
-        cw[0] = make_uint4(v.x, v.y, 0u, 0u);
+        cw = make_uint4(v.x, v.y, 0u, 0u);
       } else {
         const uint32_t v = *reinterpret_cast<const uint32_t *>(codes + t * M + dhalf * 4);
-        cw[0] = make_uint4(v, 0u, 0u, 0u);
+        cw = make_uint4(v, 0u, 0u, 0u);
       }
       rh = __half2float(__ushort_as_half(rnorm[t]));
     }
   };
 
   DecPos cur;
-  cur.slot = s_begin + warp - RD_WARPS;
+  cur.slot = 0;
   cur.tb = cur.te = cur.c0 = 0;
-  bool has = dec_next(cur, s_end, RD_WARPS, cand_q, doc_off, D, sa_row, da_row, flags, lane);
-  uint4 cw_c[2], cw_n[2];
+  bool has = dec_next(cur, s_end, &s_next, cand_q, doc_off, D, sa_row, da_row, flags, lane);
+  uint4 cw_c, cw_n;
   float rh_c = 0.f, rh_n = 0.f;
   int b = 0;
   if (has) issue(cur, b, cw_c, rh_c);
@@ -230,7 +244,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   float xmax = 0.f, exmax = 0.f;  // per document: max ||x_t|| and max ||e_xt|| (lane-local, reduced at the end)
   while (has) {
     DecPos nxt = cur;
-    const bool hn = dec_next(nxt, s_end, RD_WARPS, cand_q, doc_off, D, sa_row, da_row, flags, lane);
+    const bool hn = dec_next(nxt, s_end, &s_next, cand_q, doc_off, D, sa_row, da_row, flags, lane);
     if (hn) {
       issue(nxt, b ^ 1, cw_n, rh_n);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -238,37 +252,42 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncwarp();
-    // decode: x~ = c + rho * w (fp16 codewords), rounded to fp16 into the decoded tile.
+    // decode in place: x~ = c + rho * w (fp16 codewords), rounded to fp16.
     // This lane: row drow, dims [dhalf * 64, +64) = subspaces [dhalf * M / 2, +M / 2).
     {
-      const unsigned char *crow = wt + b * RD_TILE + drow * RD_ROW + dhalf * 128;
-      unsigned char *xrow = wt + 2 * RD_TILE + drow * RD_ROW + dhalf * 128;
-      const uint8_t *cb8 = reinterpret_cast<const uint8_t *>(cw_c);  // codes of this lane's subspaces
+      unsigned char *xrow = wt + b * RD_TILE + drow * RD_ROW + dhalf * 128;
+      const uint8_t *cb8 = reinterpret_cast<const uint8_t *>(&cw_c);  // codes of this lane's subspaces
       const bool live = cur.c0 + drow < cur.te;
       float x2 = 0.f, ex2 = 0.f, cwe2 = 0.f;
 #pragma unroll
       for (int mm = 0; mm < M / 2; mm++) cwe2 += cerr2[(dhalf * (M / 2) + mm) * 256 + cb8[mm]];
 #pragma unroll
       for (int v = 0; v < 8; v++) {  // 8 dims per step
-        const uint4 cu = *reinterpret_cast<const uint4 *>(crow + v * 16);
+        const uint4 cu = *reinterpret_cast<const uint4 *>(xrow + v * 16);
         const uint32_t cwd[4] = {cu.x, cu.y, cu.z, cu.w};
+        uint32_t wv[4];
+        if constexpr (DS >= 8) {
+          const int mm = (v * 8) / DS;
+          const int m = dhalf * (M / 2) + mm;
+          const uint4 t = *reinterpret_cast<const uint4 *>(cbk + (m * 256 + cb8[mm]) * DS + (v * 8) % DS);
+          wv[0] = t.x; wv[1] = t.y; wv[2] = t.z; wv[3] = t.w;
+        } else {
+          const int mm = 2 * v;
+          const int m = dhalf * (M / 2) + mm;
+          const uint2 t0 = *reinterpret_cast<const uint2 *>(cbk + (m * 256 + cb8[mm]) * DS);
+          const uint2 t1 = *reinterpret_cast<const uint2 *>(cbk + ((m + 1) * 256 + cb8[mm + 1]) * DS);
+          wv[0] = t0.x; wv[1] = t0.y; wv[2] = t1.x; wv[3] = t1.y;
+        }
         uint32_t ob[4];
 #pragma unroll
         for (int h = 0; h < 4; h++) {
-          float xs[2];
-#pragma unroll
-          for (int e = 0; e < 2; e++) {
-            const int kl = v * 8 + 2 * h + e;  // dim within this lane's half
-            const int mm = kl / DS;
-            const int m = dhalf * (M / 2) + mm;
-            const float w = __half2float(cbk[(m * 256 + cb8[mm]) * DS + (kl % DS)]);
-            const float c = e == 0 ? __uint_as_float(cwd[h] << 16) : __uint_as_float(cwd[h] & 0xffff0000u);
-            xs[e] = fmaf(rh_c, w, c);
-          }
-          const __half2 xb = __floats2half2_rn(xs[0], xs[1]);
+          const float2 w = __half22float2(*reinterpret_cast<const __half2 *>(&wv[h]));
+          const float c0 = __uint_as_float(cwd[h] << 16), c1 = __uint_as_float(cwd[h] & 0xffff0000u);
+          const float xs0 = fmaf(rh_c, w.x, c0), xs1 = fmaf(rh_c, w.y, c1);
+          const __half2 xb = __floats2half2_rn(xs0, xs1);
           const float2 xf = __half22float2(xb);
           x2 = fmaf(xf.x, xf.x, fmaf(xf.y, xf.y, x2));
-          ex2 = fmaf(xf.x - xs[0], xf.x - xs[0], fmaf(xf.y - xs[1], xf.y - xs[1], ex2));
+          ex2 = fmaf(xf.x - xs0, xf.x - xs0, fmaf(xf.y - xs1, xf.y - xs1, ex2));
           ob[h] = *reinterpret_cast<const uint32_t *>(&xb);
         }
         *reinterpret_cast<uint4 *>(xrow + v * 16) = make_uint4(ob[0], ob[1], ob[2], ob[3]);
@@ -289,16 +308,18 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     float acc[4][4];
 #pragma unroll
     for (int nt = 0; nt < 4; nt++) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-    const uint32_t lm = wt_s + 2 * RD_TILE + lm_off;
+    const uint32_t la = wt_s + (uint32_t)(b * RD_TILE) + la_off;
 #pragma unroll
     for (int s = 0; s < 8; s++) {
       uint32_t a[4];
-      asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                   : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
-                   : "r"(lm + s * 32)
-                   : "memory");
+      rd_ldm4(a, la + s * 32);
 #pragma unroll
-      for (int nt = 0; nt < 4; nt++) rd_mma(acc[nt], a, bq[nt][s][0], bq[nt][s][1]);
+      for (int np = 0; np < 2; np++) {
+        uint32_t bb[4];
+        rd_ldm4(bb, qs_s + lb_off + (uint32_t)(np * 16 * RD_ROW + s * 32));
+        rd_mma(acc[2 * np], a, bb[0], bb[1]);
+        rd_mma(acc[2 * np + 1], a, bb[2], bb[3]);
+      }
     }
     // running max per query token over this thread's tokens (rows gq, gq + 8)
 #pragma unroll
@@ -312,6 +333,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     }
     if (!hn || nxt.slot != cur.slot) {
       // document complete: max over the lanes sharing tig, sum over query tokens, the bound
+      const int tig = lane & 3;
       float xm = xmax, em = exmax;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -351,8 +373,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     cur = nxt;
     has = hn;
     b ^= 1;
-    cw_c[0] = cw_n[0];
-    cw_c[1] = cw_n[1];
+    cw_c = cw_n;
     rh_c = rh_n;
   }
 }
@@ -361,14 +382,14 @@ template <int M>
 static tachiom_status launch_refine_dec_m(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                           const int32_t *cand, int kd, float *sa, float *da, uint32_t *flags,
                                           cudaStream_t s) {
-  constexpr int DS = 128 / M;
-  const size_t smem = (size_t)M * 256 * DS * 2 + (size_t)M * 256 * 4 + 64 * 4 + (size_t)RD_WARPS * 3 * RD_TILE;
+  constexpr int W = rd_warps<M>();
+  static_assert(W >= 4, "decode refine: shared memory for fewer than 4 warps");
+  const size_t smem = (size_t)rd_fixed_bytes<M>() + (size_t)W * 2 * RD_TILE;
   dim3 grid((kd + RD_DOCS_PER_CTA - 1) / RD_DOCS_PER_CTA, nq);
-  TCUDA(cudaFuncSetAttribute(k_refine_dec<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_refine_dec<M><<<grid, RD_THREADS, smem, s>>>(queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes,
-                                                  ix.rnorm, ix.codebooks, ix.cent_bf16, ix.cerr_max,
-                                                  ix.cnorm_max + ix.cerr_max, sa, da, ix.D,
-                                                  flags);
+  TCUDA(cudaFuncSetAttribute(k_refine_dec<M, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_refine_dec<M, W><<<grid, W * 32, smem, s>>>(queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes,
+                                                 ix.rnorm, ix.codebooks, ix.cent_bf16, ix.cerr_max,
+                                                 ix.cnorm_max + ix.cerr_max, sa, da, ix.D, flags);
   TLAUNCH();
   return TACHIOM_OK;
 }

@@ -397,22 +397,44 @@ tachiom_status launch_topc_rescue(const Index &ix, const float *rows, int nrows,
   return TACHIOM_OK;
 }
 
-// FP32 scores of given (row, centroid id) pairs; ids < 0 give -inf.
-__global__ void k_score_pairs(const float *__restrict__ rows, int nrows, const float *__restrict__ cent,
-                              int64_t C, const int32_t *__restrict__ ids, int kc, float *__restrict__ out) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= (int64_t)nrows * kc) return;
-  int r = (int)(i / kc);
-  int32_t j = ids[i];
-  out[i] = (j >= 0 && j < C) ? dot_f32(rows + (int64_t)r * DIM, cent + (int64_t)j * DIM) : -INFINITY;
+// FP32 scores of given (row, centroid id) pairs (ids < 0 or >= C give -inf; ids >= C
+// raise TACHIOM_FLAG_BAD_INPUT),
+// each row's pairs then sorted by (score desc, id asc) as step (a) delivers them.
+// One warp per row, kappa_c <= 128.
+__global__ void __launch_bounds__(128)
+k_score_pairs(const float *__restrict__ rows, int nrows, const float *__restrict__ cent, int64_t C,
+              const int32_t *__restrict__ ids, int kc, int32_t *__restrict__ out_ids, float *__restrict__ out,
+              uint32_t *__restrict__ flags) {
+  __shared__ uint64_t keys[4][MAX_KC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * 4 + warp;
+  if (r >= nrows) return;
+  const int np = next_pow2(max(kc, 2));
+  for (int u = lane; u < np; u += 32) {
+    uint64_t key = 0ull;
+    if (u < kc) {
+      const int32_t j = ids[(int64_t)r * kc + u];
+      const bool ok = j >= 0 && j < C;
+      if (j >= C) atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
+      key = comp_key(ok ? dot_f32(rows + (int64_t)r * DIM, cent + (int64_t)j * DIM) : -INFINITY, ok ? j : -1);
+    }
+    keys[warp][u] = key;
+  }
+  __syncwarp();
+  warp_sort_desc(keys[warp], np);
+  for (int u = lane; u < kc; u += 32) {
+    const uint64_t v = keys[warp][u];
+    out_ids[(int64_t)r * kc + u] = comp_id(v);
+    out[(int64_t)r * kc + u] = comp_score(v);
+  }
 }
 
 tachiom_status launch_score_pairs(const Index &ix, const float *rows, int nrows, const int32_t *ids,
-                                  int kc, float *scores, cudaStream_t s) {
-  int64_t n = (int64_t)nrows * kc;
-  if (n <= 0) return TACHIOM_OK;
+                                  int kc, int32_t *out_ids, float *scores, uint32_t *flags, cudaStream_t s) {
+  if ((int64_t)nrows * kc <= 0) return TACHIOM_OK;
   TPROF("score_pairs", s);
-  k_score_pairs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rows, nrows, ix.cent_f32, ix.C, ids, kc, scores);
+  k_score_pairs<<<(unsigned)((nrows + 3) / 4), 128, 0, s>>>(rows, nrows, ix.cent_f32, ix.C, ids, kc, out_ids,
+                                                            scores, flags);
   TLAUNCH();
   return TACHIOM_OK;
 }

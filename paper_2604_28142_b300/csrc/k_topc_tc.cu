@@ -10,15 +10,21 @@
 // issues TMA, warp 1 owns TMEM and issues the MMAs, warps 2..9 are the
 // epilogue (warp w reads TMEM lanes 32*(w%4).., column half (w-2)/4).
 //
-// Selection without any per-row state in the GEMM:
+// Selection:
 //   pass    every group of 32 consecutive centroids reports, per query row, its
-//           maximum approximate score (one redux.sync per column) -> gmax;
-//   select  tau'_r = a lower bound on the row's kappa_c-th largest group maximum
-//           (two histogram levels, the second inside the bin the first finds);
-//           every group whose maximum is >= tau'_r - margin_r is kept. A centroid of the row's exact FP32 top-kappa_c has
-//           an approximate score >= (approximate kappa_c-th best) - 2 delta_r
-//           >= tau'_r - margin_r (margin_r = 2 delta_r), so its group is kept:
-//           about kappa_c groups per row survive;
+//           maximum approximate score (one redux.sync per column) -> gmax; each
+//           epilogue lane also keeps, for each of its query rows, the TOPM
+//           largest group maxima it has seen (a stream = one CTA's TMEM lane
+//           quarter; tiles go to CTAs in a strided order, so the streams see
+//           interleaved parts of the centroid table);
+//   select  tau'_r = the kappa_c-th largest value in the union of the row's
+//           streams, a lower bound on its kappa_c-th largest group maximum
+//           (the union holds maxima of distinct groups); every group whose
+//           maximum is >= tau'_r - margin_r is kept. A centroid of the row's
+//           exact FP32 top-kappa_c has an approximate score >= (approximate
+//           kappa_c-th best) - 2 delta_r >= tau'_r - margin_r (margin_r =
+//           2 delta_r), so its group is kept: about kappa_c groups per row
+//           survive;
 //   rescore the centroids of the kept groups are scored exactly in FP32 (the
 //           same fmaf chain as the FP32 path) and the exact top-kappa_c is kept.
 // A row whose kept groups do not fit is recomputed by a full FP32 scan.
@@ -50,6 +56,7 @@ constexpr int TILE_BYTES = B_BYTES + STAGES * A_STAGE;  // 192 KB
 constexpr int THREADS = 320;       // 10 warps
 constexpr int EPI_WARPS = 8;
 constexpr int TMEM_COLS = 512;
+constexpr int TOPM = 8;            // group maxima kept per (query row, stream)
 
 struct Ctl {
   uint64_t full[STAGES];
@@ -63,12 +70,14 @@ struct Ctl {
 };
 constexpr int SMEM_BYTES = TILE_BYTES + (int)sizeof(Ctl) + 1024;
 
-// MODE 1: maximum per group of 32 centroids -> (float) gmax[rb][tile * 4 + quarter][256]
+// CTA (x, rb) takes the tiles x, x + splits, x + 2 splits, ... against query rows [rb * 256, +256).
+// MODE 1: maximum per group of 32 centroids -> (float) gmax[rb][tile * 4 + quarter][256], and per
+//         query row the TOPM largest of its stream -> tops[row][x * 4 + quarter][TOPM] (descending)
 // MODE 3: raw scores to (float *)cand [R x C] (diagnostics and tests)
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
 k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t C, int R,
-          int ntiles, int tiles_per_split, int G, uint32_t *__restrict__ gmax, uint64_t *__restrict__ cand,
+          int ntiles, int G, uint32_t *__restrict__ gmax, float *__restrict__ tops, uint64_t *__restrict__ cand,
           uint32_t *__restrict__ flags) {
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
   unsigned char *tsm = (unsigned char *)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
@@ -78,9 +87,9 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rb = blockIdx.y;
-  const int t0 = blockIdx.x * tiles_per_split;
-  const int t1 = min(ntiles, t0 + tiles_per_split);
-  const int nt = max(0, t1 - t0);
+  const int splits = gridDim.x;
+  const int nt = max(0, (ntiles - (int)blockIdx.x + splits - 1) / splits);
+  auto tile_of = [&](int it) { return (int)blockIdx.x + it * splits; };
   volatile int *abort = &ctl->abort;
 
   if (threadIdx.x == 0) {
@@ -122,8 +131,8 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (it >= STAGES && !mbar_wait(&ctl->empty[s], ((it / STAGES) & 1) ^ 1, abort, flags)) break;
         unsigned char *a = As + s * A_STAGE;
         mbar_expect_tx(&ctl->full[s], A_STAGE);
-        tma_load_2d(a, &tmA, 0, (t0 + it) * BM, &ctl->full[s]);
-        tma_load_2d(a + A_HALF, &tmA, KH, (t0 + it) * BM, &ctl->full[s]);
+        tma_load_2d(a, &tmA, 0, tile_of(it) * BM, &ctl->full[s]);
+        tma_load_2d(a + A_HALF, &tmA, KH, tile_of(it) * BM, &ctl->full[s]);
         issued = it + 1;
       }
       // drain: every copy this warp issued has landed before the CTA may exit
@@ -160,6 +169,23 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int e = warp - 2;
     const int quarter = warp & 3;       // TMEM lane quarter this warp may access
     const int half = e >> 2;            // column half: query rows [half*128, +128)
+    // running TOPM largest group maxima of this lane's rows half*128 + ch*32 + lane (descending)
+    float tm[2][2][TOPM];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int b = 0; b < 2; b++)
+#pragma unroll
+        for (int k = 0; k < TOPM; k++) tm[a][b][k] = -INFINITY;
+    auto insert = [](float (&t)[TOPM], float x) {
+      x = (x == x) ? x : -INFINITY;
+#pragma unroll
+      for (int k = 0; k < TOPM; k++) {
+        const float hi = fmaxf(t[k], x);
+        x = fminf(t[k], x);
+        t[k] = hi;
+      }
+    };
     for (int it = 0; it < nt; it++) {
       const int buf = it & 1;
       // one lane waits, the whole warp follows its verdict (the TMEM loads below are warp-aligned)
@@ -170,7 +196,7 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       __syncwarp();
       fence_after();
       const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + half * 128);
-      const int tile = t0 + it;
+      const int tile = tile_of(it);
       const int64_t j = (int64_t)tile * BM + quarter * 32 + lane;  // this thread's centroid
       const bool jv = j < C;
 #pragma unroll 1
@@ -198,6 +224,7 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
               mine = (c == lane) ? m : mine;
             }
             dst[ch * 32 + lane] = mine;
+            if (pr == 0) insert(tm[0][cc], mine); else insert(tm[1][cc], mine);
           } else if (MODE == 3) {
             // diagnostic: raw scores [R x C]
 #pragma unroll
@@ -206,6 +233,18 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
               if (jv && row < R) reinterpret_cast<float *>(cand)[(int64_t)row * C + j] = __uint_as_float(v[cc][c]);
             }
           }
+        }
+      }
+    }
+    if (MODE == 1) {
+#pragma unroll
+      for (int ch = 0; ch < 4; ch++) {
+        const int row = rb * BN + half * 128 + ch * 32 + lane;
+        if (row < R) {
+          float4 *d = reinterpret_cast<float4 *>(tops + ((int64_t)row * splits * 4 + blockIdx.x * 4 + quarter) * TOPM);
+          const float *t = tm[ch >> 1][ch & 1];
+#pragma unroll
+          for (int k = 0; k < TOPM / 4; k++) d[k] = make_float4(t[4 * k], t[4 * k + 1], t[4 * k + 2], t[4 * k + 3]);
         }
       }
     }
@@ -219,108 +258,72 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   }
 }
 
-constexpr int SEL_BINS = 512;   // bins per histogram level
-constexpr int SEL_PARTS = 16;   // slices of the groups, one block each
 constexpr int GCAP = 256;       // groups a row may keep (8192 centroids)
+constexpr int LIM_THREADS = 128;
+constexpr int LIM_VPT = 37;     // values per thread: up to 148 CTAs x 4 streams x TOPM per row
 
-// Histogram of the group maxima of 32 rows (lane = row) over one slice of the
-// groups. Level 1 bins [-cmax, cmax]; level 2 bins the row's level-1 bin
-// [lo_r, lo_r + w1) again. Counts are added to hist[row][SEL_BINS].
-__global__ void __launch_bounds__(32)
-k_gsel_hist(const float *__restrict__ gmax, int G, int R, float cmax, int level, const float *__restrict__ lo,
-            uint32_t *__restrict__ hist) {
-  __shared__ uint16_t h[32][SEL_BINS + 2];
-  const int lane = threadIdx.x;
-  const int rb = blockIdx.x >> 3, slab = blockIdx.x & 7;
-  const int n = slab * 32 + lane;
-  const int row = rb * BN + n;
-  for (int b = 0; b < SEL_BINS; b++) h[lane][b] = 0;
-  const float w1 = 2.f * cmax / SEL_BINS;
-  const float base = (level == 1) ? -cmax : (row < R ? lo[row] : 0.f);
-  const float scale = (level == 1) ? 1.f / w1 : SEL_BINS / w1;
-  const bool skip = row >= R || (level == 2 && lo[row] == -INFINITY);
-  const int per = (G + SEL_PARTS - 1) / SEL_PARTS;
-  const int g0 = blockIdx.y * per, g1 = min(G, g0 + per);
-  const float *src = gmax + (int64_t)rb * G * BN + n;
-  if (!skip) {
-    for (int g = g0; g < g1; g += 8) {
-      float x[8];
-#pragma unroll
-      for (int u = 0; u < 8; u++) x[u] = (g + u < g1) ? src[(int64_t)(g + u) * BN] : -INFINITY;
-#pragma unroll
-      for (int u = 0; u < 8; u++) {
-        if (x[u] == -INFINITY) continue;
-        const float f = (x[u] - base) * scale;
-        if (level == 2 && (f < 0.f || f >= (float)SEL_BINS)) continue;  // outside the row's level-1 bin
-        const int b = max(0, min(SEL_BINS - 1, (int)floorf(f)));
-        h[lane][b]++;
-      }
-    }
-  }
-  __syncwarp();
-  if (skip) return;
-  uint32_t *hq = hist + (int64_t)row * SEL_BINS;
-  for (int b = 0; b < SEL_BINS; b++)
-    if (h[lane][b]) atomicAdd(&hq[b], (uint32_t)h[lane][b]);
-}
-
-// Per row: the bin holding the kappa_c-th largest group maximum. Level 1 writes
-// the bin's lower edge to lo[row] and the count strictly above it to above[row]
-// (lo = -inf when fewer than kappa_c groups exist); level 2 narrows to a sub-bin
-// and writes lim[row] = its lower edge - margin_r, a value no larger than the
-// kappa_c-th largest group maximum minus the margin.
-__global__ void k_gsel_tau(const uint32_t *__restrict__ hist, int R, int kc, float cmax, int level,
-                           float *__restrict__ lo, uint32_t *__restrict__ above, const float *__restrict__ margins,
-                           float *__restrict__ lim) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+// Per row: tau' = the kappa_c-th largest value of the union of its streams'
+// TOPM lists (bitwise search for the largest key with at least kappa_c keys
+// >= it), lim[row] = tau' - margin_r; -inf when the union has fewer than
+// kappa_c finite values.
+__global__ void __launch_bounds__(LIM_THREADS)
+k_gsel_lim(const float *__restrict__ tops, int R, int nvals, int kc, const float *__restrict__ margins,
+           float *__restrict__ lim) {
+  __shared__ int cnt[3];
+  const int row = blockIdx.x;
   if (row >= R) return;
-  const uint32_t *hq = hist + (int64_t)row * SEL_BINS;
-  const float w1 = 2.f * cmax / SEL_BINS;
-  if (level == 1) {
-    uint32_t cum = 0;
-    int b = SEL_BINS - 1;
-    for (; b >= 0; b--) {
-      if (cum + hq[b] >= (uint32_t)kc) break;
-      cum += hq[b];
-    }
-    lo[row] = (b >= 0) ? -cmax + b * w1 : -INFINITY;
-    above[row] = cum;
-    if (b < 0) lim[row] = -INFINITY;
-  } else {
-    if (lo[row] == -INFINITY) return;
-    uint32_t cum = above[row];
-    int b = SEL_BINS - 1;
-    for (; b >= 0; b--) {
-      if (cum + hq[b] >= (uint32_t)kc) break;
-      cum += hq[b];
-    }
-    const float w2 = w1 / SEL_BINS;
-    // the bin edges are computed in FP32: step down by one more sub-bin for safety
-    lim[row] = (b >= 0) ? lo[row] + b * w2 - w2 - margins[row] : -INFINITY;
+  const float *src = tops + (int64_t)row * nvals;
+  uint32_t key[LIM_VPT];
+#pragma unroll
+  for (int u = 0; u < LIM_VPT; u++) {
+    const int i = threadIdx.x + u * LIM_THREADS;
+    key[u] = i < nvals ? fkey(src[i]) : 0u;
+  }
+  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t T = 0u;
+  for (int bit = 31, it = 0; bit >= 0; bit--, it++) {
+    // buffer it % 3 is counted now; buffer (it + 1) % 3 was last read two iterations ago
+    if (threadIdx.x == 0) cnt[(it + 1) % 3] = 0;
+    const uint32_t cand = T | (1u << bit);
+    int c = 0;
+#pragma unroll
+    for (int u = 0; u < LIM_VPT; u++) c += key[u] >= cand ? 1 : 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&cnt[it % 3], c);
+    __syncthreads();
+    if (cnt[it % 3] >= kc) T = cand;
+  }
+  if (threadIdx.x == 0) {
+    const float v = funkey(T);
+    lim[row] = (nvals >= kc && T > fkey(-INFINITY) && v == v) ? v - margins[row] : -INFINITY;
   }
 }
 
-// Every group whose maximum is >= lim[row] goes to the row's list.
-__global__ void __launch_bounds__(32)
+// Every group whose maximum is >= lim[row] goes to the row's list. Block =
+// 8 warps on the same 32 rows (lane = row), each warp a strided share of
+// one slice of the groups.
+constexpr int COL_PARTS = 16;
+__global__ void __launch_bounds__(256)
 k_gsel_collect(const float *__restrict__ gmax, int G, int R, const float *__restrict__ lim,
                int32_t *__restrict__ glist, int32_t *__restrict__ gcount) {
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rb = blockIdx.x >> 3, slab = blockIdx.x & 7;
   const int n = slab * 32 + lane;
   const int row = rb * BN + n;
-  if (row >= R) return;
-  const float l = lim[row];
-  const int per = (G + SEL_PARTS - 1) / SEL_PARTS;
+  const bool live = row < R;
+  const float l = live ? lim[row] : INFINITY;
+  const int per = (G + COL_PARTS - 1) / COL_PARTS;
   const int g0 = blockIdx.y * per, g1 = min(G, g0 + per);
   const float *src = gmax + (int64_t)rb * G * BN + n;
   int32_t *out = glist + (int64_t)row * GCAP;
-  for (int g = g0; g < g1; g += 8) {
+  for (int g = g0 + warp * 8; g < g1; g += 64) {
     float x[8];
 #pragma unroll
     for (int u = 0; u < 8; u++) x[u] = (g + u < g1) ? src[(int64_t)(g + u) * BN] : -INFINITY;
 #pragma unroll
     for (int u = 0; u < 8; u++) {
-      if (x[u] != -INFINITY && x[u] >= l) {
+      if (live && x[u] != -INFINITY && x[u] >= l) {
         const int pos = atomicAdd(&gcount[row], 1);
         if (pos < GCAP) out[pos] = g + u;
       }
@@ -328,82 +331,104 @@ k_gsel_collect(const float *__restrict__ gmax, int G, int R, const float *__rest
   }
 }
 
-// exact FP32 score: fmaf chain over k = 0..127 (the FP32 path's arithmetic)
-template <bool BF16C>
-__device__ __forceinline__ float dot_exact(const float *__restrict__ q, const float *__restrict__ cf,
-                                           const __nv_bfloat16 *__restrict__ cb, int64_t j) {
-  float acc = 0.f;
-  if (BF16C) {
-    const uint4 *row = reinterpret_cast<const uint4 *>(cb + j * DIM);
-#pragma unroll 4
-    for (int k8 = 0; k8 < DIM / 8; k8++) {
-      const uint4 u = row[k8];
-      const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-      for (int h = 0; h < 4; h++) {
-        acc = fmaf(q[k8 * 8 + 2 * h], __uint_as_float(w[h] << 16), acc);
-        acc = fmaf(q[k8 * 8 + 2 * h + 1], __uint_as_float(w[h] & 0xffff0000u), acc);
-      }
-    }
-  } else {
-    const float4 *row = reinterpret_cast<const float4 *>(cf + j * DIM);
-#pragma unroll 4
-    for (int k4 = 0; k4 < DIM / 4; k4++) {
-      const float4 c = row[k4];
-      acc = fmaf(q[k4 * 4 + 0], c.x, acc);
-      acc = fmaf(q[k4 * 4 + 1], c.y, acc);
-      acc = fmaf(q[k4 * 4 + 2], c.z, acc);
-      acc = fmaf(q[k4 * 4 + 3], c.w, acc);
-    }
-  }
-  return acc;
-}
-
 // One block per query row: the centroids of the kept groups scored exactly in
-// FP32. Only scores >= lim[row] are kept: kappa_c groups have a BF16 maximum
-// >= lim + 2 margin, so kappa_c distinct centroids score >= lim + margin
-// exactly and the kappa_c-th exact score (ties included) is above lim. The
-// kept keys are sorted by (score desc, id asc); the first kappa_c are the
-// answer. A row whose groups overflowed the list, or whose kept scores
-// overflowed the buffer, is marked for the full FP32 scan.
-constexpr int FCAP = 4096;  // kept exact scores per row
+// FP32 (a warp stages a group's 32 centroid rows in shared memory with
+// coalesced loads; lane l scores centroid l with the FP32 path's arithmetic,
+// the fmaf chain over k = 0..127). Only scores >= lim[row] are kept: kappa_c
+// groups have a BF16 maximum >= lim + 2 margin, so kappa_c distinct centroids
+// score >= lim + margin exactly and the kappa_c-th exact score (ties
+// included) is above lim. The kept keys are sorted by (score desc, id asc);
+// the first kappa_c are the answer. A row whose groups overflowed the list,
+// or whose kept scores overflowed the buffer, is marked for the full FP32 scan.
+constexpr int FCAP = 2048;       // kept exact scores per row
+constexpr int RS_WARPS = 8;
 
 template <bool BF16C>
-__global__ void __launch_bounds__(256)
+constexpr int rs_row_bytes() { return BF16C ? DIM * 2 + 16 : DIM * 4 + 16; }
+template <bool BF16C>
+constexpr size_t rs_smem() { return (size_t)FCAP * 8 + (size_t)RS_WARPS * 32 * rs_row_bytes<BF16C>(); }
+
+template <bool BF16C>
+__global__ void __launch_bounds__(RS_WARPS * 32)
 k_group_rescore(const float *__restrict__ rows, int R, const float *__restrict__ cent_f32,
                 const __nv_bfloat16 *__restrict__ cent_bf16, int64_t C, int kc, const int32_t *__restrict__ glist,
                 const int32_t *__restrict__ gcount, const float *__restrict__ lim, int32_t *__restrict__ top_ids,
                 float *__restrict__ top_s, int32_t *__restrict__ lossy_rows, uint32_t *__restrict__ flags) {
-  extern __shared__ __align__(16) uint64_t rsm[];  // [FCAP] keys
+  constexpr int RB = rs_row_bytes<BF16C>();
+  constexpr int CH = BF16C ? DIM * 2 / 16 : DIM * 4 / 16;  // 16-byte chunks per centroid row
+  extern __shared__ __align__(16) unsigned char rsm_raw[];
+  uint64_t *keys = reinterpret_cast<uint64_t *>(rsm_raw);  // [FCAP]
   __shared__ float q[DIM];
   __shared__ int s_cnt;
   const int r = blockIdx.x;
   if (r >= R) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char *st = rsm_raw + FCAP * 8 + warp * 32 * RB;
   const int ngr = gcount[r];
-  const int n = min(ngr, GCAP) * 32;
+  const int ng = min(ngr, GCAP);
   const float l = lim[r];
   for (int k = threadIdx.x; k < DIM; k += blockDim.x) q[k] = rows[(int64_t)r * DIM + k];
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   const int32_t *gl = glist + (int64_t)r * GCAP;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int64_t j = (int64_t)gl[i >> 5] * 32 + (i & 31);
-    if (j >= C) continue;
-    const float sc = dot_exact<BF16C>(q, cent_f32, cent_bf16, j);
-    if (!(sc < l)) {
-      const int pos = atomicAdd(&s_cnt, 1);
-      if (pos < FCAP) rsm[pos] = comp_key(sc, (int32_t)j);
+  for (int g = warp; g < ng; g += RS_WARPS) {
+    const int64_t j0 = (int64_t)gl[g] * 32;
+    uint4 v[CH];
+#pragma unroll
+    for (int u = 0; u < CH; u++) {
+      const int c = u * 32 + lane, row = c / CH, pc = c % CH;
+      v[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (j0 + row < C)
+        v[u] = BF16C ? reinterpret_cast<const uint4 *>(cent_bf16 + (j0 + row) * DIM)[pc]
+                     : reinterpret_cast<const uint4 *>(cent_f32 + (j0 + row) * DIM)[pc];
     }
+#pragma unroll
+    for (int u = 0; u < CH; u++) {
+      const int c = u * 32 + lane, row = c / CH, pc = c % CH;
+      *reinterpret_cast<uint4 *>(st + row * RB + pc * 16) = v[u];
+    }
+    __syncwarp();
+    const int64_t j = j0 + lane;
+    if (j < C) {
+      float acc = 0.f;
+      const uint4 *cr = reinterpret_cast<const uint4 *>(st + lane * RB);
+      if (BF16C) {
+#pragma unroll
+        for (int k8 = 0; k8 < DIM / 8; k8++) {
+          const uint4 u = cr[k8];
+          const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+          for (int h = 0; h < 4; h++) {
+            acc = fmaf(q[k8 * 8 + 2 * h], __uint_as_float(w[h] << 16), acc);
+            acc = fmaf(q[k8 * 8 + 2 * h + 1], __uint_as_float(w[h] & 0xffff0000u), acc);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k4 = 0; k4 < DIM / 4; k4++) {
+          const uint4 u = cr[k4];
+          acc = fmaf(q[k4 * 4 + 0], __uint_as_float(u.x), acc);
+          acc = fmaf(q[k4 * 4 + 1], __uint_as_float(u.y), acc);
+          acc = fmaf(q[k4 * 4 + 2], __uint_as_float(u.z), acc);
+          acc = fmaf(q[k4 * 4 + 3], __uint_as_float(u.w), acc);
+        }
+      }
+      if (!(acc < l)) {
+        const int pos = atomicAdd(&s_cnt, 1);
+        if (pos < FCAP) keys[pos] = comp_key(acc, (int32_t)j);
+      }
+    }
+    __syncwarp();
   }
   __syncthreads();
   const int cnt = s_cnt;
   const int m = min(cnt, FCAP);
   const int np = next_pow2(max(m, 2));
-  for (int i = m + threadIdx.x; i < np; i += blockDim.x) rsm[i] = 0ull;
+  for (int i = m + threadIdx.x; i < np; i += blockDim.x) keys[i] = 0ull;
   __syncthreads();
-  block_sort_desc(rsm, np);
+  block_sort_desc(keys, np);
   for (int i = threadIdx.x; i < kc; i += blockDim.x) {
-    const uint64_t v = i < m ? rsm[i] : 0ull;
+    const uint64_t v = i < m ? keys[i] : 0ull;
     top_ids[(int64_t)r * kc + i] = v ? comp_id(v) : -1;
     top_s[(int64_t)r * kc + i] = v ? comp_score(v) : -INFINITY;
   }
@@ -469,13 +494,36 @@ int topc_tc_supported() {
 
 
 
-size_t topc_tc_gmax_elems(int64_t C, int rows) {
-  const int64_t ntiles = (C + tc::BM - 1) / tc::BM;
-  const int64_t rbs = (rows + tc::BN - 1) / tc::BN;
-  return (size_t)(rbs * ntiles * 4 * tc::BN);
+static int tc_sms(int device) {
+  int sms = 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 148;
+  }
+  return sms;
 }
 
-size_t topc_tc_glist_elems(int rows) { return (size_t)rows * (tc::GCAP + tc::SEL_BINS + 3); }
+// CTAs along the centroid axis: enough to fill the SMs, at least enough streams
+// for a row's union to hold kappa_c values, at most what k_gsel_lim holds
+static int tc_splits(int ntiles, int rbs, int kc, int sms) {
+  using namespace tc;
+  int sp = std::max(1, sms / rbs);
+  sp = std::max(sp, (kc + 4 * TOPM - 1) / (4 * TOPM));
+  sp = std::min(sp, LIM_VPT * LIM_THREADS / (4 * TOPM));
+  return std::max(1, std::min(sp, ntiles));
+}
+
+// gmax [rbs][groups][256] followed by tops [rows][streams][TOPM]
+size_t topc_tc_gmax_elems(const Index &ix, int rows) {
+  using namespace tc;
+  const int ntiles = (int)((ix.C + BM - 1) / BM);
+  const int rbs = (rows + BN - 1) / BN;
+  const int splits = tc_splits(ntiles, rbs, MAX_KC, tc_sms(ix.device));
+  return (size_t)rbs * ntiles * 4 * BN + (size_t)rows * splits * 4 * TOPM;
+}
+
+// glist [rows][GCAP] followed by lim [rows]
+size_t topc_tc_glist_elems(int rows) { return (size_t)rows * (tc::GCAP + 1); }
 
 tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, const float *rows, int nrows, int kc,
                               const float *margins, uint32_t *gmax, int32_t *glist, int32_t *gcount,
@@ -489,47 +537,30 @@ tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, c
   if ((st = encode_map(&mB, rows_bf16, nrows, BN))) return st;
   const int ntiles = (int)((ix.C + BM - 1) / BM);
   const int rbs = (nrows + BN - 1) / BN;
-  int sms = 148;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
-  int splits = std::max(1, sms / rbs);
-  splits = std::min(splits, ntiles);
-  const int per = (ntiles + splits - 1) / splits;
-  splits = (ntiles + per - 1) / per;
+  const int splits = tc_splits(ntiles, rbs, kc, tc_sms(ix.device));
   const int G = ntiles * 4;
+  float *tops = reinterpret_cast<float *>(gmax) + (int64_t)rbs * G * BN;
+  float *lim = reinterpret_cast<float *>(glist + (int64_t)nrows * GCAP);
   TCUDA(cudaFuncSetAttribute(k_topc_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  k_topc_tc<1><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, G, gmax, nullptr,
+  k_topc_tc<1><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, G, gmax, tops, nullptr,
                                                                flags);
   TLAUNCH();
-  {
-    // selection workspace inside glist's tail: hist [rows x SEL_BINS] u32, lo, above, lim [rows]
-    uint32_t *hist = reinterpret_cast<uint32_t *>(glist + (int64_t)nrows * GCAP);
-    float *lo = reinterpret_cast<float *>(hist + (int64_t)nrows * SEL_BINS);
-    uint32_t *above = reinterpret_cast<uint32_t *>(lo + nrows);
-    float *lim = reinterpret_cast<float *>(above + nrows);
-    const float cm = 1.0001f * ix.cnorm_max + 1e-6f;
-    const dim3 sg(rbs * 8, SEL_PARTS);
-    for (int level = 1; level <= 2; level++) {
-      TCUDA(cudaMemsetAsync(hist, 0, (size_t)nrows * SEL_BINS * 4, s));
-      k_gsel_hist<<<sg, 32, 0, s>>>(reinterpret_cast<const float *>(gmax), G, nrows, cm, level, lo, hist);
-      TLAUNCH();
-      k_gsel_tau<<<(nrows + 127) / 128, 128, 0, s>>>(hist, nrows, kc, cm, level, lo, above, margins, lim);
-      TLAUNCH();
-    }
-    TCUDA(cudaMemsetAsync(gcount, 0, (size_t)nrows * 4, s));
-    k_gsel_collect<<<sg, 32, 0, s>>>(reinterpret_cast<const float *>(gmax), G, nrows, lim, glist, gcount);
-    TLAUNCH();
-  }
-  const float *lim = reinterpret_cast<const float *>(glist + (int64_t)nrows * GCAP) +
-                     (int64_t)nrows * SEL_BINS + 2 * (int64_t)nrows;
-  const size_t rsm = (size_t)FCAP * 8;
+  k_gsel_lim<<<nrows, LIM_THREADS, 0, s>>>(tops, nrows, splits * 4 * TOPM, kc, margins, lim);
+  TLAUNCH();
+  TCUDA(cudaMemsetAsync(gcount, 0, (size_t)nrows * 4, s));
+  k_gsel_collect<<<dim3(rbs * 8, COL_PARTS), 256, 0, s>>>(reinterpret_cast<const float *>(gmax), G, nrows, lim,
+                                                          glist, gcount);
+  TLAUNCH();
   if (ix.cdtype == TACHIOM_DTYPE_BF16) {
+    const size_t rsm = rs_smem<true>();
     TCUDA(cudaFuncSetAttribute(k_group_rescore<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-    k_group_rescore<true><<<nrows, 256, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc, glist, gcount,
-                                                  lim, top_ids, top_s, lossy_rows, flags);
+    k_group_rescore<true><<<nrows, RS_WARPS * 32, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc,
+                                                            glist, gcount, lim, top_ids, top_s, lossy_rows, flags);
   } else {
+    const size_t rsm = rs_smem<false>();
     TCUDA(cudaFuncSetAttribute(k_group_rescore<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-    k_group_rescore<false><<<nrows, 256, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc, glist, gcount,
-                                                   lim, top_ids, top_s, lossy_rows, flags);
+    k_group_rescore<false><<<nrows, RS_WARPS * 32, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc,
+                                                             glist, gcount, lim, top_ids, top_s, lossy_rows, flags);
   }
   TLAUNCH();
   return TACHIOM_OK;
@@ -546,11 +577,9 @@ tachiom_status launch_topc_tc_raw(const Index &ix, const __nv_bfloat16 *rows, in
   if ((st = encode_map(&mB, rows, nrows, BN))) return st;
   const int ntiles = (int)((ix.C + BM - 1) / BM);
   const int rbs = (nrows + BN - 1) / BN;
-  int splits = std::min(ntiles, 148);
-  const int per = (ntiles + splits - 1) / splits;
-  splits = (ntiles + per - 1) / per;
+  const int splits = std::min(ntiles, 148);
   TCUDA(cudaFuncSetAttribute(k_topc_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  k_topc_tc<3><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, per, ntiles * 4,
+  k_topc_tc<3><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, ntiles * 4, nullptr,
                                                                nullptr, reinterpret_cast<uint64_t *>(out), flags);
   TLAUNCH();
   return TACHIOM_OK;

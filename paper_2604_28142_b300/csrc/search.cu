@@ -284,7 +284,7 @@ static void need_topc(const Index &ix, const tachiom_search_params *p, int rows,
     n->split_entries = (int64_t)rows * topc_tc1_splits(ix, rows) * topc_tc1_capout();
   } else if (kind == SCAN_TC2) {
     n->split_entries = rows;
-    n->gmax = (int64_t)topc_tc_gmax_elems(ix.C, rows);
+    n->gmax = (int64_t)topc_tc_gmax_elems(ix, rows);
   } else {
     n->split_entries = (int64_t)rows * plan.splits * plan.capout;
   }
@@ -540,8 +540,10 @@ extern "C" tachiom_status tachiom_gather(tachiom_index *index, const tachiom_sea
   n.dense = (int64_t)nq * ix->D;
   if ((st = ws_reserve(ix, w, n))) return st;
   if ((st = upload_meta(w, params, h_ntok, nullptr, nq))) return st;
-  if ((st = launch_score_pairs(*ix, d_queries, b.rows, d_top_ids, params->kappa_c, w->d_top_s, s))) return st;
-  if ((st = launch_gather(*ix, w->d_meta, nq, d_top_ids, w->d_top_s, params->kappa_c, w->d_dense, w->d_hist,
+  if ((st = launch_score_pairs(*ix, d_queries, b.rows, d_top_ids, params->kappa_c, w->d_top_ids, w->d_top_s,
+                                w->d_flags, s)))
+    return st;
+  if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, params->kappa_c, w->d_dense, w->d_hist,
                           w->d_flags, s)))
     return st;
   return launch_select_kd(*ix, w->d_meta, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,

@@ -219,9 +219,9 @@ tachiom_status launch_topc_tc1(const Index &ix, const __nv_bfloat16 *rows, int n
 int topc_tc1_capout();
 int topc_tc1_max_kc();
 int topc_tc1_splits(const Index &ix, int nrows);
-size_t topc_tc_gmax_elems(int64_t C, int rows);
+size_t topc_tc_gmax_elems(const Index &ix, int rows);
 tachiom_status launch_score_pairs(const Index &ix, const float *rows, int nrows, const int32_t *ids,
-                                  int kc, float *scores, cudaStream_t s);
+                                  int kc, int32_t *out_ids, float *scores, uint32_t *flags, cudaStream_t s);
 // step (b)
 tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, const int32_t *top_ids,
                              const float *top_s, int kc, float *dense, uint32_t *hist,
