@@ -106,6 +106,25 @@ def dist_env():
     return rank, world, local
 
 
+def rank_query_seed(cfg, rank):
+    """Each replica draws its own query stream."""
+    return cfg.query_seed + 7919 * rank
+
+
+def combine_over_ranks(elapsed, units, world, device="cpu"):
+    """(max elapsed over the ranks, units summed over the ranks): the whole job's
+    throughput is units / elapsed. Plain values with one rank."""
+    if world <= 1:
+        return float(elapsed), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def load_workload(name, device, rank, world, log):
     """Index (cached on local disk) + the query stream."""
     import torch
@@ -173,7 +192,7 @@ def algorithmic_traffic(T_idx, ix, params, dq, ntok, k, kc, kd, torch):
     cbytes = 2 if ix["centroid_dtype"] == "bf16" else 4
     refine_bytes = ntoks * (4 + M + 2 + 128 * cbytes)
     return {"list_entries": entries, "gather_bytes": gather_bytes, "refine_tokens": ntoks,
-            "refine_bytes": refine_bytes, "select_bytes": nq * D * 4}
+            "refine_bytes": refine_bytes, "select_bytes": nq * D * 4, "_cand": cid}
 
 
 def run_ours(a):
@@ -197,7 +216,7 @@ def run_ours(a):
         prec = T.PREC_BF16 if a.precision == "bf16" else T.PREC_FP32
     params = T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=prec)
     nb = a.warmup + a.steps
-    q = synth.make_queries(cfg, n_queries=nb * a.batch, seed=cfg.query_seed + 7919 * rank, ntok_min=32,
+    q = synth.make_queries(cfg, n_queries=nb * a.batch, seed=rank_query_seed(cfg, rank), ntok_min=32,
                            ntok_max=32)
     qs, ntok = q["queries"], q["ntok"]
     qoff = np.concatenate([[0], np.cumsum(ntok)])
@@ -239,13 +258,8 @@ def run_ours(a):
     prof = T.profile_read()
     T.profile_enable(False)
     step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
-    tot_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms, queries_total = combine_over_ranks(float(step_ms.sum()), a.steps * a.batch, world, "cuda")
     flags = G.stream_status()
-    queries_total = a.steps * a.batch * world
     qps = queries_total / (tot_ms / 1e3)
     # ---- end to end through the host-buffer entry point ----
     e2e = None
@@ -257,11 +271,7 @@ def run_ours(a):
         t1 = time.perf_counter()
         for s in range(a.steps):
             G.search_host(params, hq[s], batches[a.warmup + s][1], kk)
-        e2e_s = time.perf_counter() - t1
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s, _ = combine_over_ranks(time.perf_counter() - t1, 0, world, "cuda")
         h2d = int(hq[0].nbytes) + (4 * a.batch + 2) * 4
         d2h = a.batch * a.k * 8
         e2e = {"value": queries_total / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
@@ -283,6 +293,22 @@ def run_ours(a):
         kg = G.debug_topc_groups(params, batches[b0][0])
         traffic["kept_groups_per_row"] = {"mean": float(kg.mean()), "p99": float(np.percentile(kg, 99)),
                                           "max": int(kg.max())}
+        # documents the decode-and-MMA refine leaves to the FP32 kernel (same rule as the window kernel)
+        cand = traffic["_cand"]
+        sa = torch.empty(cand.shape, dtype=torch.float32, device="cuda")
+        da = torch.empty(cand.shape, dtype=torch.float32, device="cuda")
+        G.debug_refine_scores(params, batches[b0][0], batches[b0][1], cand, sa, da)
+        torch.cuda.synchronize()
+        cn, san, dan = cand.cpu().numpy(), sa.cpu().numpy(), da.cpu().numpy()
+        wins = []
+        for u in range(cn.shape[0]):
+            ok = (cn[u] >= 0) & np.isfinite(san[u])
+            lo, up = (san[u] - dan[u])[ok], (san[u] + dan[u])[ok]
+            L = np.sort(lo)[-a.k] if lo.size >= a.k else -np.inf
+            wins.append(int((up >= L).sum()))
+        traffic["refine_window_docs"] = {"mean": float(np.mean(wins)), "max": int(np.max(wins)),
+                                         "mean_bound": float(dan[cn >= 0].mean())}
+    traffic.pop("_cand", None)
     import json as _j
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -365,8 +391,9 @@ def run_ours(a):
 
 
 def _count_launches(prof):
-    # kernels per launcher call: select_kd launches 8 kernels, topc_merge 2, others 1
-    per = {"select_kd": 8, "topc_merge": 2, "topc_tc": 3}
+    # kernels per launcher call: select_kd launches 8 kernels, topc_tc 4 (GEMM, lim, collect,
+    # rescoring), topc_merge 2, the others 1
+    per = {"select_kd": 8, "topc_merge": 2, "topc_tc": 4}
     return sum(v[0] * per.get(k, 1) for k, v in prof.items())
 
 

@@ -120,7 +120,9 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
     __syncthreads();
     // Tokens in order, one barrier each; each thread keeps the list entries it
     // handles for a token in registers, loaded two tokens ahead so that their
-    // latency overlaps the current token's work.
+    // latency overlaps the current token's work. The three register sets keep
+    // fixed roles in a 3-way unrolled loop: a register copy would wait for the
+    // load still in flight.
     int32_t d0[G_REG], d1[G_REG], d2[G_REG];
     uint32_t k0[G_REG], k1[G_REG], k2[G_REG];
     auto fetch = [&](int ti, int32_t (&d)[G_REG], uint32_t (&k)[G_REG]) {
@@ -146,13 +148,13 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
       const uint32_t old = atomicMax(&best[x], code);
       if (old != 0u && (old >> 8) != (code >> 8)) gather_fold(S, x, old, tsq, kc);
     };
-    fetch(0, d0, k0);
-    fetch(1, d1, k1);
-    for (int ti = 0; ti < ng; ti++) {
-      fetch(ti + 2, d2, k2);
+    // token ti: fetch ti + 2 into (dn, kn), then fold the entries in (dc, kc_)
+    auto step = [&](int ti, const int32_t (&dc)[G_REG], const uint32_t (&kcur)[G_REG], int32_t (&dn)[G_REG],
+                    uint32_t (&kn)[G_REG]) {
+      fetch(ti + 2, dn, kn);
 #pragma unroll
       for (int u = 0; u < G_REG; u++)
-        if (d0[u] >= 0) visit(d0[u], k0[u]);
+        if (dc[u] >= 0) visit(dc[u], kcur[u]);
       const GSeg *sg = seg + ti * kc;
       const int total = tok_total[ti];
       for (int e = tid + G_REG * G_THREADS; e < total; e += G_THREADS) {
@@ -164,13 +166,13 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
         visit(list_doc[sg[lo].start + (e - sg[lo].pref)] - (int32_t)r0, sg[lo].key);
       }
       __syncthreads();
-#pragma unroll
-      for (int u = 0; u < G_REG; u++) {
-        d0[u] = d1[u];
-        k0[u] = k1[u];
-        d1[u] = d2[u];
-        k1[u] = k2[u];
-      }
+    };
+    fetch(0, d0, k0);
+    fetch(1, d1, k1);
+    for (int ti = 0; ti < ng; ti += 3) {
+      step(ti, d0, k0, d2, k2);
+      if (ti + 1 < ng) step(ti + 1, d1, k1, d0, k0);
+      if (ti + 2 < ng) step(ti + 2, d2, k2, d1, k1);
     }
   }
   // the codes of the last token that reached each document
@@ -219,40 +221,67 @@ constexpr int SEL_THREADS = 256;
 __device__ __forceinline__ int level_shift(int L) { return L == 1 ? 20 : (L == 2 ? 8 : 0); }
 __device__ __forceinline__ int level_bins(int L) { return L == 3 ? 256 : 4096; }
 
-__global__ void k_sel_find(const uint32_t *__restrict__ hist, uint32_t *__restrict__ state,
-                           const int32_t *__restrict__ meta, int nq, int kd_max, int L,
-                           uint32_t *__restrict__ flags) {
+// One block per query: the bin holding the cut (the need-th key from the top
+// among the keys that share the prefix found so far). Thread t sums bins
+// [nb - (t+1) w, nb - t w) (w = nb / 256), a block scan from the top finds the
+// thread whose chunk holds the cut, and that thread walks its chunk.
+constexpr int FIND_THREADS = 256;
+__global__ void __launch_bounds__(FIND_THREADS)
+k_sel_find(const uint32_t *__restrict__ hist, uint32_t *__restrict__ state, const int32_t *__restrict__ meta, int nq,
+           int kd_max, int L, uint32_t *__restrict__ flags) {
+  __shared__ uint32_t wsum[FIND_THREADS / 32];
   const int q = blockIdx.x;
   const int kd = min(kd_max, meta[4 * nq + 2 + q]);
   uint32_t *st = state + (int64_t)q * 8;
-  if (threadIdx.x != 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (L == 1) {
-    st[S_PREFIX] = 0; st[S_LEVEL] = 1; st[S_ABOVE] = 0; st[S_DONE] = 0; st[S_KMIN] = 1;
-    st[S_CNT] = 0; st[S_TIES] = 0;
+    if (tid == 0) {
+      st[S_PREFIX] = 0; st[S_LEVEL] = 1; st[S_ABOVE] = 0; st[S_DONE] = 0; st[S_KMIN] = 1;
+      st[S_CNT] = 0; st[S_TIES] = 0;
+    }
   } else if (st[S_DONE]) {
     return;
   }
   const uint32_t *hq = hist + (int64_t)q * NBINS1;
   const int nb = level_bins(L);
-  uint32_t above = st[S_ABOVE];
-  uint32_t need = (uint32_t)kd > above ? (uint32_t)kd - above : 0;
-  uint32_t cum = 0;
-  int b = nb - 1;
-  for (; b >= 0; b--) {
-    if (cum + hq[b] >= need) break;
-    cum += hq[b];
+  const int w = nb / FIND_THREADS;
+  const int top = nb - tid * w;  // this thread's chunk is [top - w, top)
+  uint32_t mine = 0;
+  for (int b = top - 1; b >= top - w; b--) mine += hq[b];
+  // inclusive scan of the chunk sums, from the top bin down (thread order)
+  uint32_t inc = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
   }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int u = 0; u < warp; u++) before += wsum[u];
+  const uint32_t excl = before + inc - mine;  // keys in bins above this chunk
+  const uint32_t total = before + inc;        // ... and including it (for the last thread: all keys)
+  const uint32_t above = st[S_ABOVE];
+  const uint32_t need = (uint32_t)kd > above ? (uint32_t)kd - above : 0;
   const int sh = level_shift(L);
-  uint32_t prefix = st[S_PREFIX];
-  if (b < 0) {
+  const uint32_t prefix = st[S_PREFIX];
+  __syncthreads();  // every thread has read the state before one rewrites it
+  if (tid == FIND_THREADS - 1 && total < need) {
     // fewer keys than needed in the whole range: take everything in it
-    uint32_t lo_key = (L == 1) ? 1u : (prefix << (sh + (L == 2 ? 12 : 8)));
+    const uint32_t lo_key = (L == 1) ? 1u : (prefix << (sh + (L == 2 ? 12 : 8)));
     st[S_KMIN] = lo_key == 0 ? 1u : lo_key;
     st[S_DONE] = 1;
     return;
   }
-  // the cut lies in bin b
-  uint32_t newprefix = (L == 1) ? (uint32_t)b : ((prefix << (L == 2 ? 12 : 8)) | (uint32_t)b);
+  if (!(excl < need && need <= total)) return;
+  // the cut lies in this chunk: walk it from the top
+  uint32_t cum = excl;
+  int b = top - 1;
+  for (; b > top - w; b--) {
+    if (cum + hq[b] >= need) break;
+    cum += hq[b];
+  }
+  const uint32_t newprefix = (L == 1) ? (uint32_t)b : ((prefix << (L == 2 ? 12 : 8)) | (uint32_t)b);
   uint32_t kmin = newprefix << sh;
   if (kmin == 0) kmin = 1;
   st[S_PREFIX] = newprefix;
@@ -267,6 +296,33 @@ __global__ void k_sel_find(const uint32_t *__restrict__ hist, uint32_t *__restri
     st[S_TIES] = 1;
     atomicOr(flags, TACHIOM_FLAG_SELECT_TIES);
   }
+}
+
+// The dense row q, chunk [b0, e0): f(x, v) for every reached document, with
+// 16-byte loads (4 in flight per thread) on the aligned middle of the chunk.
+template <typename F>
+__device__ __forceinline__ void sel_scan(const float *__restrict__ dq, int64_t row_base, int64_t b0, int64_t e0,
+                                         F f) {
+  const int64_t xa = min(e0, b0 + ((4 - ((row_base + b0) & 3)) & 3));
+  const int64_t xe = xa + ((e0 - xa) & ~(int64_t)15);
+  for (int64_t x = b0 + threadIdx.x; x < xa; x += blockDim.x) f(x, dq[x]);
+  const float4 *v4 = reinterpret_cast<const float4 *>(dq + xa);
+  const int64_t n4 = (xe - xa) >> 2;
+  for (int64_t i = threadIdx.x; i < n4; i += 4 * (int64_t)blockDim.x) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      v[u] = (i + u * blockDim.x < n4) ? v4[i + u * blockDim.x] : make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int64_t x = xa + 4 * (i + u * blockDim.x);
+      f(x, v[u].x);
+      f(x + 1, v[u].y);
+      f(x + 2, v[u].z);
+      f(x + 3, v[u].w);
+    }
+  }
+  for (int64_t x = xe + threadIdx.x; x < e0; x += blockDim.x) f(x, dq[x]);
 }
 
 __global__ void __launch_bounds__(SEL_THREADS)
@@ -285,12 +341,11 @@ k_sel_hist(const float *__restrict__ dense, int64_t D, const uint32_t *__restric
   const int64_t b0 = (int64_t)blockIdx.x * SEL_CHUNK;
   const int64_t e0 = min(D, b0 + SEL_CHUNK);
   const float *dq = dense + (int64_t)q * D;
-  for (int64_t x = b0 + threadIdx.x; x < e0; x += SEL_THREADS) {
-    float v = dq[x];
-    if (v == -INFINITY) continue;
-    uint32_t k = fkey(v);
+  sel_scan(dq, (int64_t)q * D, b0, e0, [&](int64_t, float v) {
+    if (v == -INFINITY) return;
+    const uint32_t k = fkey(v);
     if ((k >> psh) == prefix) atomicAdd(&h[(k >> sh) & (nb - 1)], 1u);
-  }
+  });
   __syncthreads();
   uint32_t *hq = hist + (int64_t)q * NBINS1;
   for (int b = threadIdx.x; b < nb; b += SEL_THREADS)
@@ -308,16 +363,15 @@ k_sel_collect(const float *__restrict__ dense, int64_t D, uint32_t *__restrict__
   const int64_t e0 = min(D, b0 + SEL_CHUNK);
   const float *dq = dense + (int64_t)q * D;
   uint64_t *buf = selbuf + (int64_t)q * SEL_CAP;
-  for (int64_t x = b0 + threadIdx.x; x < e0; x += SEL_THREADS) {
-    float v = dq[x];
-    if (v == -INFINITY) continue;
-    uint32_t k = fkey(v);
+  sel_scan(dq, (int64_t)q * D, b0, e0, [&](int64_t x, float v) {
+    if (v == -INFINITY) return;
+    const uint32_t k = fkey(v);
     if (ties ? (k > kmin) : (k >= kmin)) {
-      uint32_t pos = atomicAdd(&st[S_CNT], 1u);
+      const uint32_t pos = atomicAdd(&st[S_CNT], 1u);
       if (pos < (uint32_t)SEL_CAP) buf[pos] = comp_key(v, (int32_t)x);
       else atomicOr(flags, TACHIOM_FLAG_CAPACITY);
     }
-  }
+  });
 }
 
 // ordered pass for a cut inside a long run of equal keys: the lowest doc ids win
@@ -360,26 +414,104 @@ k_sel_ties(const float *__restrict__ dense, int64_t D, uint32_t *__restrict__ st
   if (threadIdx.x == 0) st[S_CNT] = (uint32_t)(base + min(s_taken, need));
 }
 
-__global__ void __launch_bounds__(1024)
+// Per query: the collected keys (n <= SEL_CAP, all at or above the cut) in
+// shared memory; the first min(n, kappa_d) by (S~ desc, doc asc) are written.
+// Small buffers are sorted whole. A large one first finds the kappa_d-th
+// largest key T by a radix select over the 64-bit keys (8 passes of 8 bits; the
+// keys are unique, the doc id being part of the key), keeps the kappa_d keys
+// >= T and sorts only those.
+constexpr int SORT_THREADS = 1024;
+constexpr int SORT_SMALL = 2048;
+__global__ void __launch_bounds__(SORT_THREADS)
 k_sel_sort(uint32_t *__restrict__ state, uint64_t *__restrict__ selbuf, const int32_t *__restrict__ meta, int nq,
            int kd, int32_t *__restrict__ cand, float *__restrict__ cand_s, int32_t *__restrict__ ncand) {
-  extern __shared__ __align__(16) uint64_t ssm[];
+  extern __shared__ __align__(16) uint64_t ssm[];  // [SEL_CAP] keys, then [next_pow2(kappa_d)] kept keys
+  __shared__ uint32_t hist[256];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint32_t s_need;
+  __shared__ int s_cnt;
   const int q = blockIdx.x;
   const int kdq = min(kd, meta[4 * nq + 2 + q]);  // this query's cut; the row stride stays kd
   const uint32_t *st = state + (int64_t)q * 8;
   const int n = (int)umin(st[S_CNT], (uint32_t)SEL_CAP);
-  const int np = next_pow2(max(n, 2));
   const uint64_t *buf = selbuf + (int64_t)q * SEL_CAP;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) ssm[i] = i < n ? buf[i] : 0ull;
-  __syncthreads();
-  block_sort_desc(ssm, np);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = min(n, kdq);
-  for (int i = threadIdx.x; i < kd; i += blockDim.x) {
-    uint64_t v = i < m ? ssm[i] : 0ull;
+  uint64_t *keys = ssm;
+  if (n <= SORT_SMALL || n <= kdq) {
+    const int np = next_pow2(max(n, 2));
+    for (int i = tid; i < np; i += SORT_THREADS) keys[i] = i < n ? buf[i] : 0ull;
+    __syncthreads();
+    block_sort_desc(keys, np);
+  } else {
+    for (int i = tid; i < n; i += SORT_THREADS) keys[i] = buf[i];
+    uint64_t prefix = 0ull;
+    uint32_t need = (uint32_t)kdq;
+    for (int pass = 0; pass < 8; pass++) {
+      const int shift = 56 - 8 * pass;
+      const uint64_t hi = pass == 0 ? 0ull : (~0ull << (shift + 8));
+      if (tid < 256) hist[tid] = 0u;
+      __syncthreads();
+      for (int b0 = 0; b0 < n; b0 += SORT_THREADS) {
+        const int i = b0 + tid;
+        int dg = -1;
+        if (i < n) {
+          const uint64_t k = keys[i];
+          if ((k & hi) == prefix) dg = (int)((k >> shift) & 255u);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
+        if (dg >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[dg], (uint32_t)__popc(peers));
+      }
+      __syncthreads();
+      if (warp == 0) {
+        // lane l: digits [248 - 8l, 256 - 8l), from the top
+        uint32_t c = 0;
+        for (int d = 255 - 8 * lane; d > 247 - 8 * lane; d--) c += hist[d];
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        const uint32_t excl = inc - c;
+        if (excl < need && need <= inc) {
+          uint32_t cum = excl;
+          int d = 255 - 8 * lane;
+          for (; d > 248 - 8 * lane; d--) {
+            if (cum + hist[d] >= need) break;
+            cum += hist[d];
+          }
+          s_prefix = prefix | ((uint64_t)d << shift);
+          s_need = need - cum;
+        }
+      }
+      __syncthreads();
+      prefix = s_prefix;
+      need = s_need;
+    }
+    // prefix is now the kappa_d-th largest key: keep the kappa_d keys >= it, sort them
+    uint64_t *kept = ssm + SEL_CAP;
+    const int np = next_pow2(max(kdq, 2));
+    if (tid == 0) s_cnt = 0;
+    for (int i = kdq + tid; i < np; i += SORT_THREADS) kept[i] = 0ull;
+    __syncthreads();
+    for (int i = tid; i < n; i += SORT_THREADS) {
+      const uint64_t k = keys[i];
+      if (k >= prefix) {
+        const int pos = atomicAdd(&s_cnt, 1);
+        if (pos < kdq) kept[pos] = k;
+      }
+    }
+    __syncthreads();
+    block_sort_desc(kept, np);
+    keys = kept;
+  }
+  for (int i = tid; i < kd; i += SORT_THREADS) {
+    const uint64_t v = i < m ? keys[i] : 0ull;
     cand[(int64_t)q * kd + i] = v ? comp_id(v) : -1;
     cand_s[(int64_t)q * kd + i] = v ? comp_score(v) : -INFINITY;
   }
-  if (threadIdx.x == 0) ncand[q] = m;
+  if (tid == 0) ncand[q] = m;
 }
 
 tachiom_status launch_select_kd(const Index &ix, const int32_t *meta, int nq, int kd, const float *dense,
@@ -390,22 +522,22 @@ tachiom_status launch_select_kd(const Index &ix, const int32_t *meta, int nq, in
   TPROF("select_kd", s);
   const int64_t D = ix.D;
   dim3 grid((unsigned)((D + SEL_CHUNK - 1) / SEL_CHUNK), nq);
-  k_sel_find<<<nq, 32, 0, s>>>(hist, state, meta, nq, kd, 1, flags);
+  k_sel_find<<<nq, FIND_THREADS, 0, s>>>(hist, state, meta, nq, kd, 1, flags);
   TLAUNCH();
   for (int L = 2; L <= 3; L++) {
     TCUDA(cudaMemsetAsync(hist2, 0, (size_t)nq * NBINS1 * 4, s));
     k_sel_hist<<<grid, SEL_THREADS, 0, s>>>(dense, D, state, hist2, L);
     TLAUNCH();
-    k_sel_find<<<nq, 32, 0, s>>>(hist2, state, meta, nq, kd, L, flags);
+    k_sel_find<<<nq, FIND_THREADS, 0, s>>>(hist2, state, meta, nq, kd, L, flags);
     TLAUNCH();
   }
   k_sel_collect<<<grid, SEL_THREADS, 0, s>>>(dense, D, state, selbuf, flags);
   TLAUNCH();
   k_sel_ties<<<nq, 1024, 0, s>>>(dense, D, state, selbuf, meta, nq, kd);
   TLAUNCH();
-  size_t smem = (size_t)SEL_CAP * 8;
+  const size_t smem = (size_t)SEL_CAP * 8 + (size_t)next_pow2(std::max(kd, 2)) * 8;
   TCUDA(cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_sel_sort<<<nq, 1024, smem, s>>>(state, selbuf, meta, nq, kd, cand, cand_s, ncand);
+  k_sel_sort<<<nq, SORT_THREADS, smem, s>>>(state, selbuf, meta, nq, kd, cand, cand_s, ncand);
   TLAUNCH();
   return TACHIOM_OK;
 }

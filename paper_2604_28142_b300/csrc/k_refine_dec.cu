@@ -195,8 +195,9 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   const uint32_t lb_off = (uint32_t)((((lane >> 4) * 8) + (lane & 7)) * RD_ROW + ((lane >> 3) & 1) * 16);
   float *sa_row = sa + (int64_t)q * kd;
   float *da_row = da + (int64_t)q * kd;
-  // decode layout: lane -> row lane >> 1, dims (lane & 1) * 64 .. +64
-  const int drow = lane >> 1, dhalf = lane & 1;
+  // decode layout: lane -> row lane & 15, dims (lane >> 4) * 64 .. +64 (the 8 lanes of a
+  // 16-byte shared-memory phase then read 8 different rows: no bank conflicts)
+  const int drow = lane & 15, dhalf = lane >> 4;
 
   auto issue = [&](const DecPos &p, int b, uint4 &cw, float &rh) {
     const int64_t tl = p.c0 + (lane & 15);
@@ -230,34 +231,29 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     }
   };
 
-  DecPos cur;
-  cur.slot = 0;
-  cur.tb = cur.te = cur.c0 = 0;
-  bool has = dec_next(cur, s_end, &s_next, cand_q, doc_off, D, sa_row, da_row, flags, lane);
-  uint4 cw_c, cw_n;
-  float rh_c = 0.f, rh_n = 0.f;
-  int b = 0;
-  if (has) issue(cur, b, cw_c, rh_c);
+  // chunk pipeline: the chunk of (pa, stage 0, cwa, rha) is processed while the next
+  // one's copies and loads land in (pb, stage 1, cwb, rhb), then the roles swap; the
+  // loop is unrolled twice so no register holding a load in flight is copied
+  DecPos pa, pb;
+  pa.slot = pb.slot = 0;
+  pa.tb = pa.te = pa.c0 = 0;
+  uint4 cwa = make_uint4(0u, 0u, 0u, 0u), cwb = make_uint4(0u, 0u, 0u, 0u);
+  float rha = 0.f, rhb = 0.f;
   float mx[4][2];
 #pragma unroll
   for (int nt = 0; nt < 4; nt++) mx[nt][0] = mx[nt][1] = -INFINITY;
   float xmax = 0.f, exmax = 0.f;  // per document: max ||x_t|| and max ||e_xt|| (lane-local, reduced at the end)
-  while (has) {
-    DecPos nxt = cur;
-    const bool hn = dec_next(nxt, s_end, &s_next, cand_q, doc_off, D, sa_row, da_row, flags, lane);
-    if (hn) {
-      issue(nxt, b ^ 1, cw_n, rh_n);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
+
+  // process the chunk P in stage B with codes CW and norm RH; HN: a next chunk exists, NSLOT its slot
+  auto process = [&](const DecPos &P, const int B, const uint4 &CW, const float RH, const bool HN,
+                     const int NSLOT) {
     __syncwarp();
     // decode in place: x~ = c + rho * w (fp16 codewords), rounded to fp16.
     // This lane: row drow, dims [dhalf * 64, +64) = subspaces [dhalf * M / 2, +M / 2).
     {
-      unsigned char *xrow = wt + b * RD_TILE + drow * RD_ROW + dhalf * 128;
-      const uint8_t *cb8 = reinterpret_cast<const uint8_t *>(&cw_c);  // codes of this lane's subspaces
-      const bool live = cur.c0 + drow < cur.te;
+      unsigned char *xrow = wt + B * RD_TILE + drow * RD_ROW + dhalf * 128;
+      const uint8_t *cb8 = reinterpret_cast<const uint8_t *>(&CW);  // codes of this lane's subspaces
+      const bool live = P.c0 + drow < P.te;
       float x2 = 0.f, ex2 = 0.f, cwe2 = 0.f;
 #pragma unroll
       for (int mm = 0; mm < M / 2; mm++) cwe2 += cerr2[(dhalf * (M / 2) + mm) * 256 + cb8[mm]];
@@ -283,7 +279,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
         for (int h = 0; h < 4; h++) {
           const float2 w = __half22float2(*reinterpret_cast<const __half2 *>(&wv[h]));
           const float c0 = __uint_as_float(cwd[h] << 16), c1 = __uint_as_float(cwd[h] & 0xffff0000u);
-          const float xs0 = fmaf(rh_c, w.x, c0), xs1 = fmaf(rh_c, w.y, c1);
+          const float xs0 = fmaf(RH, w.x, c0), xs1 = fmaf(RH, w.y, c1);
           const __half2 xb = __floats2half2_rn(xs0, xs1);
           const float2 xf = __half22float2(xb);
           x2 = fmaf(xf.x, xf.x, fmaf(xf.y, xf.y, x2));
@@ -294,21 +290,21 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
       }
       // the two halves of the row: ||x^||, ||e_x|| (fp16 rounding of x~, plus rho times the
       // codeword rounding, plus the FP32 rounding of x~ itself)
-      x2 += __shfl_xor_sync(0xffffffffu, x2, 1);
-      ex2 += __shfl_xor_sync(0xffffffffu, ex2, 1);
-      cwe2 += __shfl_xor_sync(0xffffffffu, cwe2, 1);
+      x2 += __shfl_xor_sync(0xffffffffu, x2, 16);
+      ex2 += __shfl_xor_sync(0xffffffffu, ex2, 16);
+      cwe2 += __shfl_xor_sync(0xffffffffu, cwe2, 16);
       if (live) {
         const float slack = 1.f + ldexpf(1.f, -10);
         const float xn = sqrtf(x2) * slack;
         xmax = fmaxf(xmax, xn);
-        exmax = fmaxf(exmax, (sqrtf(ex2) + rh_c * sqrtf(cwe2)) * slack + ldexpf(xn, -22));
+        exmax = fmaxf(exmax, (sqrtf(ex2) + RH * sqrtf(cwe2)) * slack + ldexpf(xn, -22));
       }
     }
     __syncwarp();
     float acc[4][4];
 #pragma unroll
     for (int nt = 0; nt < 4; nt++) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-    const uint32_t la = wt_s + (uint32_t)(b * RD_TILE) + la_off;
+    const uint32_t la = wt_s + (uint32_t)(B * RD_TILE) + la_off;
 #pragma unroll
     for (int s = 0; s < 8; s++) {
       uint32_t a[4];
@@ -324,14 +320,14 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     // running max per query token over this thread's tokens (rows gq, gq + 8)
 #pragma unroll
     for (int h = 0; h < 2; h++) {
-      if (cur.c0 + gq + h * 8 >= cur.te) continue;
+      if (P.c0 + gq + h * 8 >= P.te) continue;
 #pragma unroll
       for (int nt = 0; nt < 4; nt++) {
         mx[nt][0] = fmaxf(mx[nt][0], acc[nt][h * 2 + 0]);
         mx[nt][1] = fmaxf(mx[nt][1], acc[nt][h * 2 + 1]);
       }
     }
-    if (!hn || nxt.slot != cur.slot) {
+    if (!HN || NSLOT != P.slot) {
       // document complete: max over the lanes sharing tig, sum over query tokens, the bound
       const int tig = lane & 3;
       float xm = xmax, em = exmax;
@@ -364,17 +360,37 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
       dl += __shfl_xor_sync(0xffffffffu, dl, 1);
       dl += __shfl_xor_sync(0xffffffffu, dl, 2);
       if (lane == 0) {
-        sa_row[cur.slot] = sum;
-        da_row[cur.slot] = dl * (1.f + ldexpf(1.f, -10)) + ldexpf(fabsf(sum) + 1.f, -20) * 8.f;
+        sa_row[P.slot] = sum;
+        da_row[P.slot] = dl * (1.f + ldexpf(1.f, -10)) + ldexpf(fabsf(sum) + 1.f, -20) * 8.f;
       }
       xmax = exmax = 0.f;
     }
+  };
+
+  bool has = dec_next(pa, s_end, &s_next, cand_q, doc_off, D, sa_row, da_row, flags, lane);
+  if (has) issue(pa, 0, cwa, rha);
+  while (has) {
+    pb = pa;
+    bool hn = dec_next(pb, s_end, &s_next, cand_q, doc_off, D, sa_row, da_row, flags, lane);
+    if (hn) {
+      issue(pb, 1, cwb, rhb);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    process(pa, 0, cwa, rha, hn, pb.slot);
     __syncwarp();
-    cur = nxt;
-    has = hn;
-    b ^= 1;
-    cw_c = cw_n;
-    rh_c = rh_n;
+    if (!hn) break;
+    pa = pb;
+    has = dec_next(pa, s_end, &s_next, cand_q, doc_off, D, sa_row, da_row, flags, lane);
+    if (has) {
+      issue(pa, 0, cwa, rha);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    process(pb, 1, cwb, rhb, has, pa.slot);
+    __syncwarp();
   }
 }
 
