@@ -24,6 +24,8 @@
 // it when that bin is wide; every key at or above the cut is collected and
 // sorted exactly. A cut inside a run of equal keys wider than the buffer
 // takes the ordered tie pass (lowest doc ids first).
+#include <algorithm>
+
 #include "tachiom_internal.cuh"
 
 namespace tachiom {
@@ -49,20 +51,23 @@ __device__ __forceinline__ void gather_fold(float *S, int x, uint32_t code, cons
   S[x] = (cur == -INFINITY) ? sv : cur + sv;
 }
 
+// The (range, query) pairs k_gather_sort could not hold, one after another per CTA.
 __global__ void __launch_bounds__(G_THREADS, 1)
-k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
-         const float *__restrict__ top_s, int kc, const int64_t *__restrict__ list_off,
-         const int32_t *__restrict__ list_doc, const int32_t *__restrict__ list_roff, int nr1,
-         int64_t D, int RD, int64_t C, float *__restrict__ dense, uint32_t *__restrict__ hist,
-         uint32_t *__restrict__ flags) {
+k_gather_tok(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
+             const float *__restrict__ top_s, int kc, const int64_t *__restrict__ list_off,
+             const int32_t *__restrict__ list_doc, const int32_t *__restrict__ list_roff, int nr1,
+             int64_t D, int RD, int64_t C, float *__restrict__ dense, uint32_t *__restrict__ hist,
+             uint32_t *__restrict__ flags, const int2 *__restrict__ items, const int *__restrict__ nitems) {
   extern __shared__ __align__(16) uint32_t gsm[];
   uint32_t *best = gsm;                                   // [RD] code of the latest token (0: none)
   float *S = reinterpret_cast<float *>(gsm + RD);         // [RD] running S~
   uint32_t *h = gsm + 2 * RD;                             // [NBINS1]
   GSeg *seg = reinterpret_cast<GSeg *>(gsm + 2 * RD + NBINS1);  // [G_SEGCAP]
   __shared__ int tok_total[MAX_NTOK];
-
-  const int r = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
+  const int n_items = *nitems;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+  __syncthreads();  // the previous item's shared state is no longer read
+  const int r = items[item].x, q = items[item].y, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = (int64_t)r * RD;
   const int nd = (int)min((int64_t)RD, D - r0);
@@ -130,8 +135,10 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
       const int total = ti < ng ? tok_total[ti] : 0;
 #pragma unroll
       for (int u = 0; u < G_REG; u++) {
+        // the load is issued unconditionally (position 0 for a missing entry, whose code
+        // is 0): a select on its result would wait for it here instead of two tokens later
         const int e = tid + u * G_THREADS;
-        d[u] = -1;
+        int64_t pos = 0;
         k[u] = 0u;
         if (e < total) {
           int lo = 0, hi = kc;
@@ -139,22 +146,24 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
             const int mid = (lo + hi) >> 1;
             if (sg[mid].pref <= e) lo = mid; else hi = mid;
           }
-          d[u] = list_doc[sg[lo].start + (e - sg[lo].pref)] - (int32_t)r0;
+          pos = sg[lo].start + (e - sg[lo].pref);
           k[u] = sg[lo].key;
         }
+        d[u] = __ldg(list_doc + pos);
       }
     };
     auto visit = [&](int x, uint32_t code) {
       const uint32_t old = atomicMax(&best[x], code);
       if (old != 0u && (old >> 8) != (code >> 8)) gather_fold(S, x, old, tsq, kc);
     };
-    // token ti: fetch ti + 2 into (dn, kn), then fold the entries in (dc, kc_)
+    // token ti: fetch ti + 2 into (dn, kn), then fold the entries in (dc, kcur); dc holds
+    // absolute doc ids, kcur = 0 marks no entry
     auto step = [&](int ti, const int32_t (&dc)[G_REG], const uint32_t (&kcur)[G_REG], int32_t (&dn)[G_REG],
                     uint32_t (&kn)[G_REG]) {
       fetch(ti + 2, dn, kn);
 #pragma unroll
       for (int u = 0; u < G_REG; u++)
-        if (dc[u] >= 0) visit(dc[u], kcur[u]);
+        if (kcur[u]) visit(dc[u] - (int32_t)r0, kcur[u]);
       const GSeg *sg = seg + ti * kc;
       const int total = tok_total[ti];
       for (int e = tid + G_REG * G_THREADS; e < total; e += G_THREADS) {
@@ -191,19 +200,249 @@ k_gather(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
   uint32_t *hq = hist + (int64_t)q * NBINS1;
   for (int b = tid; b < NBINS1; b += G_THREADS)
     if (h[b]) atomicAdd(&hq[b], h[b]);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// k_gather_sort: one CTA per (range of R documents, query). Every (token i,
+// rank u) slice of L_{Top_i[u]} inside the range is described at once, and
+// each of its entries becomes a 32-bit key
+//     (d - r0) << 12 | i << 7 | u
+// loaded with all loads in flight. A counting sort by document (16-bit counts
+// in shared memory, a block-wide scan, a scatter) puts each document's keys
+// into one run, and each key then finds its place in its (short) run by
+// counting the run's smaller keys, so a run is ordered by token, then rank.
+// One pass over the range's documents writes S~: for a reached document, the
+// first key of each token holds the token's best (lowest) rank - Top_i is
+// sorted by score desc, so that is the token's maximum - and the scores are
+// added in ascending i, the order (and so the FP32 sums) of the token-serial
+// form.
+// A range with more entries than the key buffers hold is left to k_gather_tok.
+constexpr int GS_THREADS = 1024;
+constexpr int GS_ECAP_MAX = 16384;
+
+__host__ __device__ inline size_t gs_fixed(int kc, int RD) {
+  return (size_t)MAX_NTOK * kc * sizeof(GSeg)   // slice descriptors
+         + (size_t)MAX_NTOK * kc * 4             // Top_i scores
+         + (size_t)NBINS1 * 4                    // histogram
+         + (size_t)((RD + 1) / 2) * 4;           // packed 16-bit per-document counts / cursors
+}
+inline int gs_ecap(int kc, int RD) {
+  const size_t avail = 227 * 1024 - 1024 - gs_fixed(kc, RD);
+  return (int)std::min<size_t>(GS_ECAP_MAX, avail / 8) & ~1023;
+}
+
+__device__ __forceinline__ uint32_t gs_get16(const uint32_t *w, int x) { return (w[x >> 1] >> ((x & 1) << 4)) & 0xffffu; }
+
+__global__ void __launch_bounds__(GS_THREADS, 1)
+k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_ids,
+              const float *__restrict__ top_s, int kc, const int64_t *__restrict__ list_off,
+              const int32_t *__restrict__ list_doc, const int32_t *__restrict__ list_roff, int nr1,
+              int64_t D, int RD, int64_t C, int ecap, float *__restrict__ dense, uint32_t *__restrict__ hist,
+              uint32_t *__restrict__ flags, int2 *__restrict__ ovf, int *__restrict__ novf) {
+  extern __shared__ __align__(16) unsigned char gsr[];
+  GSeg *seg = reinterpret_cast<GSeg *>(gsr);                                                 // [32 * kc]
+  float *sc = reinterpret_cast<float *>(gsr + (size_t)MAX_NTOK * kc * sizeof(GSeg));        // [32 * kc]
+  uint32_t *h = reinterpret_cast<uint32_t *>(sc + MAX_NTOK * kc);                           // [NBINS1]
+  uint32_t *cnt = h + NBINS1;                                                                // [RD / 2]
+  uint32_t *kin = cnt + (RD + 1) / 2;                                                        // [ecap]
+  uint32_t *kout = kin + ecap;                                                               // [ecap]
+  __shared__ uint32_t wsum[GS_THREADS / 32];
+  const int r = blockIdx.x, q = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t r0 = (int64_t)r * RD;
+  const int nd = (int)min((int64_t)RD, D - r0);
+  const int row_b = qoff[q], ntok = qoff[q + 1] - row_b;
+  const int nseg = ntok * kc;
+  // slice descriptors (length in .pref until the scan), the scores, empty counts and histogram
+  for (int e = tid; e < nseg; e += GS_THREADS) {
+    int32_t jj = top_ids[(int64_t)row_b * kc + e];
+    if (jj >= C) {
+      atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
+      jj = -1;
+    }
+    GSeg g;
+    g.start = 0;
+    g.pref = 0;
+    g.key = (uint32_t)((e / kc) << 7 | (e % kc));
+    if (jj >= 0) {
+      const int lo = list_roff[(int64_t)jj * nr1 + r], hi = list_roff[(int64_t)jj * nr1 + r + 1];
+      g.start = (int32_t)(list_off[jj] + lo);
+      g.pref = hi - lo;
+    }
+    seg[e] = g;
+    sc[e] = top_s[(int64_t)row_b * kc + e];
+  }
+  for (int b = tid; b < NBINS1; b += GS_THREADS) h[b] = 0u;
+  for (int x = tid; x < (RD + 1) / 2; x += GS_THREADS) cnt[x] = 0u;
+  __syncthreads();
+  // exclusive prefix of the slice lengths: thread t owns descriptors [t * per, (t + 1) * per)
+  uint32_t total;
+  {
+    const int per = (nseg + GS_THREADS - 1) / GS_THREADS;
+    const int s0 = min(nseg, tid * per), s1 = min(nseg, s0 + per);
+    uint32_t mine = 0;
+    for (int e = s0; e < s1; e++) mine += (uint32_t)seg[e].pref;
+    uint32_t inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t base = 0;
+    total = 0;
+    for (int w = 0; w < GS_THREADS / 32; w++) {
+      if (w < warp) base += wsum[w];
+      total += wsum[w];
+    }
+    base += inc - mine;
+    for (int e = s0; e < s1; e++) {
+      const int len = seg[e].pref;
+      seg[e].pref = (int32_t)base;
+      base += (uint32_t)len;
+    }
+  }
+  if (total > (uint32_t)ecap) {
+    // too many entries for the key buffers: the token-serial kernel takes this range
+    if (tid == 0) {
+      const int k = atomicAdd(novf, 1);
+      ovf[k] = make_int2(r, q);
+    }
+    return;
+  }
+  __syncthreads();
+  // the keys (four entries per thread in flight) and the per-document counts
+  const int n = (int)total;
+  for (int e0 = 0; e0 < n; e0 += 4 * GS_THREADS) {
+    int64_t pos[4];
+    uint32_t code[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int e = e0 + u * GS_THREADS + tid;
+      pos[u] = 0;
+      code[u] = 0u;
+      if (e < n) {
+        int lo = 0, hi = nseg;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if ((uint32_t)seg[mid].pref <= (uint32_t)e) lo = mid; else hi = mid;
+        }
+        pos[u] = seg[lo].start + (e - seg[lo].pref);
+        code[u] = seg[lo].key;
+      }
+    }
+    int32_t dv[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) dv[u] = __ldg(list_doc + pos[u]);
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int e = e0 + u * GS_THREADS + tid;
+      if (e < n) {
+        const uint32_t x = (uint32_t)(dv[u] - (int32_t)r0);
+        kin[e] = (x << 12) | code[u];
+        atomicAdd(&cnt[x >> 1], 1u << ((x & 1u) << 4));
+      }
+    }
+  }
+  __syncthreads();
+  // exclusive scan of the counts in place (thread t owns documents [t * dper, (t + 1) * dper))
+  {
+    const int dper = ((RD + GS_THREADS - 1) / GS_THREADS + 1) & ~1;  // even: whole words
+    const int x0 = min(RD, tid * dper), x1 = min(RD, x0 + dper);
+    uint32_t mine = 0;
+    for (int x = x0; x < x1; x++) mine += gs_get16(cnt, x);
+    uint32_t inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    __syncthreads();  // wsum of the first scan is no longer read
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t base = 0;
+    for (int w = 0; w < warp; w++) base += wsum[w];
+    base += inc - mine;
+    for (int x = x0; x < x1; x += 2) {
+      const uint32_t c0 = gs_get16(cnt, x), c1 = x + 1 < x1 ? gs_get16(cnt, x + 1) : 0u;
+      cnt[x >> 1] = base | ((base + c0) << 16);
+      base += c0 + c1;
+    }
+  }
+  __syncthreads();
+  // scatter: cursor(d) runs from start(d) to start(d) + count(d) = start(d + 1)
+  for (int e = tid; e < n; e += GS_THREADS) {
+    const uint32_t k = kin[e], x = k >> 12;
+    const uint32_t old = atomicAdd(&cnt[x >> 1], 1u << ((x & 1u) << 4));
+    kout[(old >> ((x & 1u) << 4)) & 0xffffu] = k;
+  }
+  __syncthreads();
+  // each key to its place in its document's run, ordered by (token, rank): its rank
+  // among the run's keys (all distinct)
+  for (int f = tid; f < n; f += GS_THREADS) {
+    const uint32_t k = kout[f], x = k >> 12;
+    const uint32_t end = gs_get16(cnt, (int)x), start = x == 0 ? 0u : gs_get16(cnt, (int)x - 1);
+    uint32_t below = 0;
+    for (uint32_t g = start; g < end; g++) below += kout[g] < k ? 1u : 0u;
+    kin[start + below] = k;
+  }
+  __syncthreads();
+  // S~ per document: the first key of each token run is the token's best rank; the tokens
+  // come in ascending i
+  float *out = dense + (int64_t)q * D + r0;
+  for (int b0 = 0; b0 < nd; b0 += GS_THREADS) {
+    const int x = b0 + tid;
+    int bin = -1;
+    if (x < nd) {
+      const uint32_t end = gs_get16(cnt, x), start = x == 0 ? 0u : gs_get16(cnt, x - 1);
+      float S = -INFINITY;
+      if (end > start) {
+        uint32_t prev = 0xffffffffu;
+        for (uint32_t f = start; f < end; f++) {
+          const uint32_t kf = kin[f], t = (kf >> 7) & 31u;
+          if (t != prev) {
+            const float v = sc[t * kc + (kf & 127u)];
+            S = (prev == 0xffffffffu) ? v : S + v;
+            prev = t;
+          }
+        }
+        bin = (int)(fkey(S) >> 20);
+      }
+      out[x] = S;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+    if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[bin], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  uint32_t *hq = hist + (int64_t)q * NBINS1;
+  for (int b = tid; b < NBINS1; b += GS_THREADS)
+    if (h[b]) atomicAdd(&hq[b], h[b]);
 }
 
 tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, const int32_t *top_ids,
-                             const float *top_s, int kc, float *dense, uint32_t *hist, uint32_t *flags,
-                             cudaStream_t s) {
+                             const float *top_s, int kc, float *dense, uint32_t *hist, int2 *ovf, int *novf,
+                             uint32_t *flags, cudaStream_t s) {
   if (nq <= 0) return TACHIOM_OK;
   TPROF("gather", s);
   TCUDA(cudaMemsetAsync(hist, 0, (size_t)nq * NBINS1 * 4, s));
-  const size_t smem = (size_t)ix.range_docs * 8 + NBINS1 * 4 + (size_t)G_SEGCAP * sizeof(GSeg);
-  TCUDA(cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(ix.n_ranges, nq);
-  k_gather<<<grid, G_THREADS, smem, s>>>(meta_qoff, top_ids, top_s, kc, ix.list_off, ix.list_doc, ix.list_roff,
-                                         ix.n_ranges + 1, ix.D, ix.range_docs, ix.C, dense, hist, flags);
+  TCUDA(cudaMemsetAsync(novf, 0, sizeof(int), s));
+  const int ecap = gs_ecap(kc, ix.range_docs);
+  const size_t sm1 = gs_fixed(kc, ix.range_docs) + (size_t)ecap * 8;
+  TCUDA(cudaFuncSetAttribute(k_gather_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+  k_gather_sort<<<dim3(ix.n_ranges, nq), GS_THREADS, sm1, s>>>(meta_qoff, top_ids, top_s, kc, ix.list_off,
+                                                              ix.list_doc, ix.list_roff, ix.n_ranges + 1, ix.D,
+                                                              ix.range_docs, ix.C, ecap, dense, hist, flags, ovf,
+                                                              novf);
+  TLAUNCH();
+  // the ranges that overflowed, token by token (a CTA per SM, each taking items in turn)
+  const size_t sm2 = (size_t)ix.range_docs * 8 + NBINS1 * 4 + (size_t)G_SEGCAP * sizeof(GSeg);
+  TCUDA(cudaFuncSetAttribute(k_gather_tok, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
+  k_gather_tok<<<sms, G_THREADS, sm2, s>>>(meta_qoff, top_ids, top_s, kc, ix.list_off, ix.list_doc, ix.list_roff,
+                                           ix.n_ranges + 1, ix.D, ix.range_docs, ix.C, dense, hist, flags, ovf,
+                                           novf);
   TLAUNCH();
   return TACHIOM_OK;
 }

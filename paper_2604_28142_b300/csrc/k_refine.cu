@@ -119,10 +119,17 @@ k_refine(const float *__restrict__ queries, const int32_t *__restrict__ meta, in
 #pragma unroll
       for (int g = 0; g < G; g++) ct[g] = 0.f;
       if (BF16C) {
+        // the row in two halves, each loaded whole (8 loads in flight), used in k order
         const uint4 *crow = reinterpret_cast<const uint4 *>(cent_bf16 + (int64_t)j * DIM);
-#pragma unroll 2
-        for (int k8 = 0; k8 < DIM / 8; k8++) {
-          uint4 u = crow[k8];
+#pragma unroll 1
+        for (int hh = 0; hh < 2; hh++) {
+        uint4 cr[DIM / 16];
+#pragma unroll
+        for (int k8 = 0; k8 < DIM / 16; k8++) cr[k8] = crow[hh * (DIM / 16) + k8];
+#pragma unroll
+        for (int kq = 0; kq < DIM / 16; kq++) {
+          const uint4 u = cr[kq];
+          const int k8 = hh * (DIM / 16) + kq;
           float c[8] = {__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
                         __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u),
                         __uint_as_float(u.z << 16), __uint_as_float(u.z & 0xffff0000u),
@@ -137,17 +144,27 @@ k_refine(const float *__restrict__ queries, const int32_t *__restrict__ meta, in
             ct[g] = a;
           }
         }
+        }
       } else {
+        // the row in batches, each loaded whole (4 or 8 loads in flight), used in k order
         const float4 *crow = reinterpret_cast<const float4 *>(cent_f32 + (int64_t)j * DIM);
-#pragma unroll 4
-        for (int k4 = 0; k4 < DIM / 4; k4++) {
-          float4 c = crow[k4];
+        constexpr int NB = G >= 16 ? DIM / 32 : DIM / 16;  // float4 per batch (register budget)
+#pragma unroll 1
+        for (int hh = 0; hh < DIM / 4 / NB; hh++) {
+          float4 cr[NB];
 #pragma unroll
-          for (int g = 0; g < G; g++) {
-            const float4 qa = *reinterpret_cast<const float4 *>(&qs[g * DIM + k4 * 4]);
-            float a = ct[g];
-            a = fmaf(qa.x, c.x, a); a = fmaf(qa.y, c.y, a); a = fmaf(qa.z, c.z, a); a = fmaf(qa.w, c.w, a);
-            ct[g] = a;
+          for (int k4 = 0; k4 < NB; k4++) cr[k4] = crow[hh * NB + k4];
+#pragma unroll
+          for (int k4 = 0; k4 < NB; k4++) {
+            const float4 c = cr[k4];
+            const int kk = hh * NB + k4;
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+              const float4 qa = *reinterpret_cast<const float4 *>(&qs[g * DIM + kk * 4]);
+              float a = ct[g];
+              a = fmaf(qa.x, c.x, a); a = fmaf(qa.y, c.y, a); a = fmaf(qa.z, c.z, a); a = fmaf(qa.w, c.w, a);
+              ct[g] = a;
+            }
           }
         }
       }
@@ -220,6 +237,208 @@ tachiom_status launch_refine(const Index &ix, const float *queries, const int32_
     case 8: return launch_refine_m<8>(ix, queries, meta, nq, cand, kd, part, flags, s);
     case 16: return launch_refine_m<16>(ix, queries, meta, nq, cand, kd, part, flags, s);
     case 32: return launch_refine_m<32>(ix, queries, meta, nq, cand, kd, part, flags, s);
+  }
+  return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
+}
+
+// ---------------------------------------------------------------------------------
+// The FP32 refine for a short list of documents (the window the reduced-precision
+// pass leaves), one CTA per (query, document). A document is taken in chunks of
+// 64 tokens: the chunk's centroid ids, codes and norms are loaded at once, then
+// its centroid rows and the codewords its codes select are copied to shared
+// memory with cp.async (one wave of copies per chunk). Lane i holds query token
+// i in registers; a warp takes 4 document tokens at a time (4 independent FMA
+// chains) and reads their rows and codewords from shared memory (broadcast).
+// Every number is the one k_refine produces: the centroid term is the same fmaf
+// chain over k = 0..127, each table entry T[m][code][i] is the same fmaf chain
+// over the subspace's dims (computed here instead of looked up), rs adds them in
+// ascending m from 0, fmaf(rho, rs, ct) is maxed over the tokens, and the group
+// partial sums are formed in the same order. So the scores are bit-identical to
+// k_refine's and k_final_topk ranks them as before. The list is compacted: the
+// first id < 0 ends it.
+constexpr int RW_WARPS = 8;
+constexpr int RW_THREADS = RW_WARPS * 32;
+constexpr int RW_CTAS = 16;      // CTAs per query, each taking documents blockIdx.x, +16, ...
+constexpr int RW_CHUNK = 64;     // document tokens staged at once
+constexpr int RW_TPW = 4;        // document tokens per warp step
+
+template <bool BF16C>
+constexpr size_t rw_smem() {
+  return (size_t)RW_CHUNK * DIM * (BF16C ? 2 : 4)        // centroid rows
+         + (size_t)RW_CHUNK * DIM * 4                      // the chunk's codewords (M x DS = 128 floats per token)
+         + (size_t)RW_CHUNK * (4 + 4 + 32)                 // centroid id, rho, codes (<= 32 bytes)
+         + (size_t)RW_WARPS * MAX_NTOK * 4;                // per-warp maxima
+}
+
+__device__ __forceinline__ void rw_cp16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+template <int M, bool BF16C>
+__global__ void __launch_bounds__(RW_THREADS, 1)
+k_refine_win(const float *__restrict__ queries, const int32_t *__restrict__ meta, int nq,
+             const int32_t *__restrict__ cand, int kd, const int64_t *__restrict__ doc_off,
+             const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
+             const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
+             const float *__restrict__ cent_f32, const __nv_bfloat16 *__restrict__ cent_bf16,
+             float *__restrict__ part, int ngroups, int64_t D, uint32_t *__restrict__ flags) {
+  constexpr int G = 128 / M;
+  constexpr int DS = 128 / M;
+  constexpr int RB = BF16C ? DIM * 2 : DIM * 4;  // bytes per centroid row
+  extern __shared__ __align__(16) unsigned char rwm[];
+  unsigned char *rows = rwm;                                                   // [CHUNK][RB]
+  float *cw = reinterpret_cast<float *>(rows + RW_CHUNK * RB);                 // [CHUNK][128]
+  int32_t *cid = reinterpret_cast<int32_t *>(cw + RW_CHUNK * DIM);             // [CHUNK]
+  float *rh = reinterpret_cast<float *>(cid + RW_CHUNK);                       // [CHUNK]
+  uint8_t *cds = reinterpret_cast<uint8_t *>(rh + RW_CHUNK);                   // [CHUNK][32]
+  float *mxs = reinterpret_cast<float *>(cds + RW_CHUNK * 32);                 // [WARPS][32]
+  const int q = blockIdx.y;
+  const int ntok = meta[3 * nq + 2 + q];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // this lane's query token, in registers
+  float qv[DIM];
+  {
+    const float4 *qr = reinterpret_cast<const float4 *>(queries + ((int64_t)meta[q] + min(lane, max(ntok - 1, 0))) * DIM);
+#pragma unroll
+    for (int k4 = 0; k4 < DIM / 4; k4++) {
+      const float4 v = qr[k4];
+      qv[4 * k4] = v.x; qv[4 * k4 + 1] = v.y; qv[4 * k4 + 2] = v.z; qv[4 * k4 + 3] = v.w;
+    }
+  }
+  const int gq = (ntok + G - 1) / G;
+  for (int slot = blockIdx.x; slot < kd; slot += gridDim.x) {
+    const int32_t d = cand[(int64_t)q * kd + slot];
+    if (d < 0) break;
+    if (d >= D) {
+      if (tid == 0) atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
+      if (tid < gq) part[((int64_t)q * ngroups + tid) * kd + slot] = 0.f;
+      continue;
+    }
+    __syncthreads();  // the previous document's maxima have been summed
+    const int64_t tb = doc_off[d], te = doc_off[d + 1];
+    float mx = -INFINITY;
+    for (int64_t c0 = tb; c0 < te; c0 += RW_CHUNK) {
+      const int nt = (int)min((int64_t)RW_CHUNK, te - c0);
+      __syncthreads();  // the previous chunk is no longer read
+      for (int x = tid; x < nt; x += RW_THREADS) {
+        cid[x] = tok_cid[c0 + x];
+        rh[x] = __half2float(__ushort_as_half(rnorm[c0 + x]));
+      }
+      for (int x = tid; x < nt * M; x += RW_THREADS) cds[(x / M) * 32 + x % M] = codes[c0 * M + x];
+      __syncthreads();
+      // rows: nt x (RB / 16) chunks of 16 bytes; codewords: nt x M x (DS * 4 / 16) chunks
+      constexpr int RC = RB / 16, WC = DS * 4 / 16;
+      for (int x = tid; x < nt * RC; x += RW_THREADS) {
+        const int t = x / RC, c = x % RC;
+        const unsigned char *src = BF16C ? reinterpret_cast<const unsigned char *>(cent_bf16 + (int64_t)cid[t] * DIM)
+                                         : reinterpret_cast<const unsigned char *>(cent_f32 + (int64_t)cid[t] * DIM);
+        rw_cp16(rows + t * RB + c * 16, src + c * 16);
+      }
+      for (int x = tid; x < nt * M * WC; x += RW_THREADS) {
+        const int t = x / (M * WC), r = x % (M * WC), m = r / WC, c = r % WC;
+        rw_cp16(cw + t * DIM + m * DS + c * 4, codebooks + ((int64_t)m * 256 + cds[t * 32 + m]) * DS + c * 4);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncthreads();
+      for (int t0 = warp * RW_TPW; t0 < nt; t0 += RW_WARPS * RW_TPW) {
+        int tt[RW_TPW];
+#pragma unroll
+        for (int j = 0; j < RW_TPW; j++) tt[j] = min(t0 + j, nt - 1);  // a missing token repeats the last one
+        float ct[RW_TPW], rs[RW_TPW];
+#pragma unroll
+        for (int j = 0; j < RW_TPW; j++) ct[j] = rs[j] = 0.f;
+        if (BF16C) {
+#pragma unroll
+          for (int k8 = 0; k8 < DIM / 8; k8++) {
+#pragma unroll
+            for (int j = 0; j < RW_TPW; j++) {
+              const uint4 u = reinterpret_cast<const uint4 *>(rows + tt[j] * RB)[k8];
+              const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+              for (int h = 0; h < 4; h++) {
+                ct[j] = fmaf(qv[k8 * 8 + 2 * h], __uint_as_float(w[h] << 16), ct[j]);
+                ct[j] = fmaf(qv[k8 * 8 + 2 * h + 1], __uint_as_float(w[h] & 0xffff0000u), ct[j]);
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k4 = 0; k4 < DIM / 4; k4++) {
+#pragma unroll
+            for (int j = 0; j < RW_TPW; j++) {
+              const float4 c = reinterpret_cast<const float4 *>(rows + tt[j] * RB)[k4];
+              ct[j] = fmaf(qv[k4 * 4 + 0], c.x, ct[j]);
+              ct[j] = fmaf(qv[k4 * 4 + 1], c.y, ct[j]);
+              ct[j] = fmaf(qv[k4 * 4 + 2], c.z, ct[j]);
+              ct[j] = fmaf(qv[k4 * 4 + 3], c.w, ct[j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < M; m++) {
+#pragma unroll
+          for (int j = 0; j < RW_TPW; j++) {
+            const float *wt = cw + tt[j] * DIM + m * DS;
+            float a = 0.f;
+#pragma unroll
+            for (int u = 0; u < DS; u++) a = fmaf(qv[m * DS + u], wt[u], a);
+            rs[j] += a;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < RW_TPW; j++) mx = fmaxf(mx, fmaf(rh[tt[j]], rs[j], ct[j]));
+      }
+    }
+    mxs[warp * MAX_NTOK + lane] = mx;
+    __syncthreads();
+    if (tid < gq) {
+      const int grp = tid, i0 = grp * G, ng = min(G, ntok - i0);
+      float sum = 0.f;
+      if (te > tb) {
+        for (int g = 0; g < ng; g++) {
+          float v = mxs[i0 + g];
+#pragma unroll
+          for (int w = 1; w < RW_WARPS; w++) v = fmaxf(v, mxs[w * MAX_NTOK + i0 + g]);
+          sum += v;
+        }
+      }
+      part[((int64_t)q * ngroups + grp) * kd + slot] = sum;
+    }
+  }
+}
+
+template <int M>
+static tachiom_status launch_refine_win_m(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                          const int32_t *cand, int kd, float *part, uint32_t *flags,
+                                          cudaStream_t s) {
+  dim3 grid(std::min(RW_CTAS, kd), nq);
+  if (ix.cdtype == TACHIOM_DTYPE_BF16) {
+    TCUDA(cudaFuncSetAttribute(k_refine_win<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)rw_smem<true>()));
+    k_refine_win<M, true><<<grid, RW_THREADS, rw_smem<true>(), s>>>(
+        queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks, ix.cent_f32,
+        ix.cent_bf16, part, refine_groups(M), ix.D, flags);
+  } else {
+    TCUDA(cudaFuncSetAttribute(k_refine_win<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)rw_smem<false>()));
+    k_refine_win<M, false><<<grid, RW_THREADS, rw_smem<false>(), s>>>(
+        queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks, ix.cent_f32,
+        ix.cent_bf16, part, refine_groups(M), ix.D, flags);
+  }
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
+tachiom_status launch_refine_win(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                 const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s) {
+  if (nq <= 0) return TACHIOM_OK;
+  TPROF("refine_win", s);
+  switch (ix.M) {
+    case 8: return launch_refine_win_m<8>(ix, queries, meta, nq, cand, kd, part, flags, s);
+    case 16: return launch_refine_win_m<16>(ix, queries, meta, nq, cand, kd, part, flags, s);
+    case 32: return launch_refine_win_m<32>(ix, queries, meta, nq, cand, kd, part, flags, s);
   }
   return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
 }

@@ -12,7 +12,8 @@
 //
 // Selection:
 //   pass    every group of 32 consecutive centroids reports, per query row, its
-//           maximum approximate score (one redux.sync per column) -> gmax; each
+//           maximum approximate score (one redux.sync per column), rounded up
+//           to fp16 (so a group is never dropped by the rounding) -> gmax; each
 //           epilogue lane also keeps, for each of its query rows, the TOPM
 //           largest group maxima it has seen (a stream = one CTA's TMEM lane
 //           quarter; tiles go to CTAs in a strided order, so the streams see
@@ -33,6 +34,7 @@
 // raises TACHIOM_FLAG_TIMEOUT, every role leaves its loop, in-flight copies
 // and MMAs are drained (again with a bound) and TMEM is freed before exit.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <cstring>
@@ -71,7 +73,7 @@ struct Ctl {
 constexpr int SMEM_BYTES = TILE_BYTES + (int)sizeof(Ctl) + 1024;
 
 // CTA (x, rb) takes the tiles x, x + splits, x + 2 splits, ... against query rows [rb * 256, +256).
-// MODE 1: maximum per group of 32 centroids -> (float) gmax[rb][tile * 4 + quarter][256], and per
+// MODE 1: maximum per group of 32 centroids, rounded up to fp16 -> gmax[rb][tile * 4 + quarter][256], and per
 //         query row the TOPM largest of its stream -> tops[row][x * 4 + quarter][TOPM] (descending)
 // MODE 3: raw scores to (float *)cand [R x C] (diagnostics and tests)
 template <int MODE>
@@ -216,14 +218,14 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           const int ch = pr * 2 + cc;
           if (MODE == 1) {
             // maximum score of the warp's 32 centroids, per query row (-inf: no valid centroid)
-            float *dst = reinterpret_cast<float *>(gmax) + ((int64_t)rb * G + tile * 4 + quarter) * BN + half * 128;
+            __half *dst = reinterpret_cast<__half *>(gmax) + ((int64_t)rb * G + tile * 4 + quarter) * BN + half * 128;
             float mine = -INFINITY;
 #pragma unroll
             for (int c = 0; c < 32; c++) {
               const float m = redux_fmax(jv ? __uint_as_float(v[cc][c]) : -INFINITY);
               mine = (c == lane) ? m : mine;
             }
-            dst[ch * 32 + lane] = mine;
+            dst[ch * 32 + lane] = __float2half_ru(mine);  // rounded up: the filter stays conservative
             if (pr == 0) insert(tm[0][cc], mine); else insert(tm[1][cc], mine);
           } else if (MODE == 3) {
             // diagnostic: raw scores [R x C]
@@ -305,7 +307,7 @@ k_gsel_lim(const float *__restrict__ tops, int R, int nvals, int kc, const float
 // one slice of the groups.
 constexpr int COL_PARTS = 16;
 __global__ void __launch_bounds__(256)
-k_gsel_collect(const float *__restrict__ gmax, int G, int R, const float *__restrict__ lim,
+k_gsel_collect(const __half *__restrict__ gmax, int G, int R, const float *__restrict__ lim,
                int32_t *__restrict__ glist, int32_t *__restrict__ gcount) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rb = blockIdx.x >> 3, slab = blockIdx.x & 7;
@@ -315,12 +317,12 @@ k_gsel_collect(const float *__restrict__ gmax, int G, int R, const float *__rest
   const float l = live ? lim[row] : INFINITY;
   const int per = (G + COL_PARTS - 1) / COL_PARTS;
   const int g0 = blockIdx.y * per, g1 = min(G, g0 + per);
-  const float *src = gmax + (int64_t)rb * G * BN + n;
+  const __half *src = gmax + (int64_t)rb * G * BN + n;
   int32_t *out = glist + (int64_t)row * GCAP;
   for (int g = g0 + warp * 8; g < g1; g += 64) {
     float x[8];
 #pragma unroll
-    for (int u = 0; u < 8; u++) x[u] = (g + u < g1) ? src[(int64_t)(g + u) * BN] : -INFINITY;
+    for (int u = 0; u < 8; u++) x[u] = (g + u < g1) ? __half2float(src[(int64_t)(g + u) * BN]) : -INFINITY;
 #pragma unroll
     for (int u = 0; u < 8; u++) {
       if (live && x[u] != -INFINITY && x[u] >= l) {
@@ -513,13 +515,13 @@ static int tc_splits(int ntiles, int rbs, int kc, int sms) {
   return std::max(1, std::min(sp, ntiles));
 }
 
-// gmax [rbs][groups][256] followed by tops [rows][streams][TOPM]
+// 32-bit words of: gmax [rbs][groups][256] fp16, then tops [rows][streams][TOPM] fp32
 size_t topc_tc_gmax_elems(const Index &ix, int rows) {
   using namespace tc;
   const int ntiles = (int)((ix.C + BM - 1) / BM);
   const int rbs = (rows + BN - 1) / BN;
   const int splits = tc_splits(ntiles, rbs, MAX_KC, tc_sms(ix.device));
-  return (size_t)rbs * ntiles * 4 * BN + (size_t)rows * splits * 4 * TOPM;
+  return (size_t)rbs * ntiles * 4 * BN / 2 + (size_t)rows * splits * 4 * TOPM;
 }
 
 // glist [rows][GCAP] followed by lim [rows]
@@ -539,7 +541,7 @@ tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, c
   const int rbs = (nrows + BN - 1) / BN;
   const int splits = tc_splits(ntiles, rbs, kc, tc_sms(ix.device));
   const int G = ntiles * 4;
-  float *tops = reinterpret_cast<float *>(gmax) + (int64_t)rbs * G * BN;
+  float *tops = reinterpret_cast<float *>(reinterpret_cast<__half *>(gmax) + (int64_t)rbs * G * BN);
   float *lim = reinterpret_cast<float *>(glist + (int64_t)nrows * GCAP);
   TCUDA(cudaFuncSetAttribute(k_topc_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   k_topc_tc<1><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, G, gmax, tops, nullptr,
@@ -548,7 +550,7 @@ tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, c
   k_gsel_lim<<<nrows, LIM_THREADS, 0, s>>>(tops, nrows, splits * 4 * TOPM, kc, margins, lim);
   TLAUNCH();
   TCUDA(cudaMemsetAsync(gcount, 0, (size_t)nrows * 4, s));
-  k_gsel_collect<<<dim3(rbs * 8, COL_PARTS), 256, 0, s>>>(reinterpret_cast<const float *>(gmax), G, nrows, lim,
+  k_gsel_collect<<<dim3(rbs * 8, COL_PARTS), 256, 0, s>>>(reinterpret_cast<const __half *>(gmax), G, nrows, lim,
                                                           glist, gcount);
   TLAUNCH();
   if (ix.cdtype == TACHIOM_DTYPE_BF16) {

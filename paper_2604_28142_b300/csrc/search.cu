@@ -105,6 +105,8 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   AL(w->d_gcount, rows * 4);
   AL(w->d_lossy, rows * 4);
   AL(w->d_hist, nq * NBINS1 * 4);
+  AL(w->d_govf, (nq * (int64_t)ix->n_ranges) * 8);
+  AL(w->d_govf_n, 16);
   AL(w->d_hist2, nq * NBINS1 * 4);
   AL(w->d_selstate, nq * 8 * 4);
   AL(w->d_selbuf, nq * (int64_t)SEL_CAP * 8);
@@ -341,7 +343,10 @@ static tachiom_status run_refine(Index *ix, Workspace *w, const tachiom_search_p
     float *sa = w->d_part, *da = w->d_part + (int64_t)nq * kd;  // consumed before the FP32 pass reuses d_part
     if ((st = launch_refine_dec(*ix, queries, w->d_meta, nq, cand, kd, sa, da, w->d_flags, stream))) return st;
     if ((st = launch_refine_window_b(*ix, w->d_meta, nq, cand, kd, sa, da, w->d_win, stream))) return st;
-    cand = w->d_win;
+    // the window is short: one CTA per (query, document), same FP32 numbers as k_refine
+    if ((st = launch_refine_win(*ix, queries, w->d_meta, nq, w->d_win, kd, w->d_part, w->d_flags, stream)))
+      return st;
+    return launch_final_topk(*ix, w->d_meta, nq, w->d_win, kd, w->d_part, out_ids, out_s, stream);
   } else if (rk == REFINE_TC) {
     if ((st = launch_refine_tc(*ix, queries, w->d_meta, nq, cand, kd, w->d_part, w->d_flags, stream))) return st;
     if ((st = launch_refine_window(*ix, w->d_meta, nq, cand, kd, w->d_part, refine_tc_delta(*ix), w->d_win,
@@ -394,6 +399,7 @@ static tachiom_status search_device(Index *ix, const tachiom_search_params *p, c
   if ((st = upload_meta(w, p, h_ntok, h_k, nq))) return st;
   if ((st = run_topc(ix, w, p, d_queries, b.rows, plan))) return st;
   if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, p->kappa_c, w->d_dense, w->d_hist,
+                          w->d_govf, w->d_govf_n,
                           w->d_flags, stream)))
     return st;
   if ((st = launch_select_kd(*ix, w->d_meta, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
@@ -544,6 +550,7 @@ extern "C" tachiom_status tachiom_gather(tachiom_index *index, const tachiom_sea
                                 w->d_flags, s)))
     return st;
   if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, params->kappa_c, w->d_dense, w->d_hist,
+                          w->d_govf, w->d_govf_n,
                           w->d_flags, s)))
     return st;
   return launch_select_kd(*ix, w->d_meta, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,

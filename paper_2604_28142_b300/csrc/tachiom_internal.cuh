@@ -151,6 +151,8 @@ struct Workspace {
   float *d_top_s = nullptr;            // [rows x kc]
   float *d_dense = nullptr;            // [B x D] S~ per query (-inf: not reached)
   uint32_t *d_hist = nullptr;          // [B x NBINS1]
+  int2 *d_govf = nullptr;              // [B x ranges] (range, query) pairs left to the token-serial gather
+  int *d_govf_n = nullptr;             // their count
   uint32_t *d_hist2 = nullptr;         // [B x NBINS1]
   uint32_t *d_selstate = nullptr;      // [B x 8]
   uint64_t *d_selbuf = nullptr;        // [B x SEL_CAP]
@@ -224,13 +226,15 @@ tachiom_status launch_score_pairs(const Index &ix, const float *rows, int nrows,
                                   int kc, int32_t *out_ids, float *scores, uint32_t *flags, cudaStream_t s);
 // step (b)
 tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, const int32_t *top_ids,
-                             const float *top_s, int kc, float *dense, uint32_t *hist,
+                             const float *top_s, int kc, float *dense, uint32_t *hist, int2 *ovf, int *novf,
                              uint32_t *flags, cudaStream_t s);
 tachiom_status launch_select_kd(const Index &ix, const int32_t *meta, int nq, int kd, const float *dense,
                                 const uint32_t *hist, uint32_t *hist2, uint32_t *state,
                                 uint64_t *selbuf, int32_t *cand, float *cand_s, int32_t *ncand,
                                 uint32_t *flags, cudaStream_t s);
 // steps (c), (d)
+tachiom_status launch_refine_win(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                 const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s);
 tachiom_status launch_refine(const Index &ix, const float *queries, const int32_t *meta, int nq,
                              const int32_t *cand, int kd, float *part, uint32_t *flags,
                              cudaStream_t s);
