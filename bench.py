@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--oracle-queries", type=int, default=16)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
+    ap.add_argument("--single-queries", type=int, default=32,
+                    help="queries of the FP32 one-query-at-a-time comparator")
+    ap.add_argument("--no-single", action="store_true")
     return ap.parse_args()
 
 
@@ -138,6 +141,37 @@ def load_workload(name, device, rank, world, log):
     else:
         ix = synth.load_or_make(name, device=device, log=log)
     return ix
+
+
+def fp32_one_at_a_time(T, G, a, batch, batched_ids, torch):
+    """The plain FP32 path (no tensor cores, no batching) on the first queries of a timed
+    batch, one query per search call; per-query latency from CUDA events, and whether
+    every result equals the batched reduced-precision one."""
+    dq, ntok = batch
+    n = min(a.single_queries, len(ntok))
+    off = np.concatenate([[0], np.cumsum(ntok)])
+    p32 = T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=T.PREC_FP32)
+    oi = torch.empty(a.k, dtype=torch.int32, device="cuda")
+    os_ = torch.empty(a.k, dtype=torch.float32, device="cuda")
+    k1 = np.array([a.k], np.int32)
+    stream = torch.cuda.current_stream()
+    same = True
+    lat = []
+    for rep in range(2):  # the first pass sizes the scratch and warms the caches
+        for u in range(n):
+            qu = dq[off[u]:off[u + 1]]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.search(p32, qu, ntok[u:u + 1], k1, oi, os_)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep == 1:
+                lat.append(e0.elapsed_time(e1))
+                same = same and bool(torch.equal(oi, batched_ids[u * a.k:(u + 1) * a.k]))
+    lat = np.array(lat)
+    return {"value": float(n / (lat.sum() / 1e3)), "unit": "queries/s", "queries": int(n),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "ids_equal_to_batched": same}
 
 
 def oracle_check(ix, qs, ntok, gi, gs, k, kc, kd, nsample):
@@ -280,6 +314,10 @@ def run_ours(a):
         if world > 1:
             torch.distributed.destroy_process_group()
         return
+    # ---- comparator: the plain FP32 path, one query per launch sequence ----
+    single = None
+    if not a.no_single:
+        single = fp32_one_at_a_time(T, G, a, batches[a.warmup], out_i[a.warmup], torch)
     # ---- accuracy on a sample of the timed queries, and the oracle's own time ----
     b0 = a.warmup
     gi = out_i[b0].cpu().numpy()
@@ -383,6 +421,7 @@ def run_ours(a):
                          "sample": f"{on} queries of the first timed batch, full cascade in FP64, OpenMP over queries"},
         "clocks": clocks,
         "e2e": e2e,
+        "fp32_one_query_at_a_time": single,
         "gpu_launches": _count_launches(prof),
     }
     print(json.dumps(line))

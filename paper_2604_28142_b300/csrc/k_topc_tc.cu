@@ -201,6 +201,7 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const int tile = tile_of(it);
       const int64_t j = (int64_t)tile * BM + quarter * 32 + lane;  // this thread's centroid
       const bool jv = j < C;
+      const bool full_tile = (int64_t)(tile + 1) * BM <= C;  // uniform: no centroid past C
 #pragma unroll 1
       for (int pr = 0; pr < 2; pr++) {
         uint32_t v[2][32];
@@ -217,16 +218,32 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         for (int cc = 0; cc < 2; cc++) {
           const int ch = pr * 2 + cc;
           if (MODE == 1) {
-            // maximum score of the warp's 32 centroids, per query row (-inf: no valid centroid)
+            // maximum score of the warp's 32 centroids, per query row (-inf: no valid centroid):
+            // one redux per column gives every lane all 32 maxima, a 5-level select tree
+            // leaves lane l the one of its row
             __half *dst = reinterpret_cast<__half *>(gmax) + ((int64_t)rb * G + tile * 4 + quarter) * BN + half * 128;
-            float mine = -INFINITY;
+            float m[32];
+            if (full_tile) {
 #pragma unroll
-            for (int c = 0; c < 32; c++) {
-              const float m = redux_fmax(jv ? __uint_as_float(v[cc][c]) : -INFINITY);
-              mine = (c == lane) ? m : mine;
+              for (int c = 0; c < 32; c++) m[c] = redux_fmax(__uint_as_float(v[cc][c]));
+            } else {
+#pragma unroll
+              for (int c = 0; c < 32; c++) m[c] = redux_fmax(jv ? __uint_as_float(v[cc][c]) : -INFINITY);
             }
+#pragma unroll
+            for (int w = 16; w >= 1; w >>= 1) {
+              const bool hi = (lane & w) != 0;
+#pragma unroll
+              for (int c = 0; c < w; c++) m[c] = hi ? m[c + w] : m[c];
+            }
+            const float mine = m[0];
             dst[ch * 32 + lane] = __float2half_ru(mine);  // rounded up: the filter stays conservative
-            if (pr == 0) insert(tm[0][cc], mine); else insert(tm[1][cc], mine);
+            // most values fall below every lane's current 8th largest: skip the insertion then
+            if (pr == 0) {
+              if (__any_sync(0xffffffffu, !(mine <= tm[0][cc][TOPM - 1]))) insert(tm[0][cc], mine);
+            } else {
+              if (__any_sync(0xffffffffu, !(mine <= tm[1][cc][TOPM - 1]))) insert(tm[1][cc], mine);
+            }
           } else if (MODE == 3) {
             // diagnostic: raw scores [R x C]
 #pragma unroll
