@@ -422,12 +422,13 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
 
 tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, const int32_t *top_ids,
                              const float *top_s, int kc, float *dense, uint32_t *hist, int2 *ovf, int *novf,
-                             uint32_t *flags, cudaStream_t s) {
+                             bool tok_only, uint32_t *flags, cudaStream_t s) {
   if (nq <= 0) return TACHIOM_OK;
   TPROF("gather", s);
   TCUDA(cudaMemsetAsync(hist, 0, (size_t)nq * NBINS1 * 4, s));
   TCUDA(cudaMemsetAsync(novf, 0, sizeof(int), s));
-  const int ecap = gs_ecap(kc, ix.range_docs);
+  // tok_only: no key buffer, so every range with entries goes to the token-serial kernel
+  const int ecap = tok_only ? 0 : gs_ecap(kc, ix.range_docs);
   const size_t sm1 = gs_fixed(kc, ix.range_docs) + (size_t)ecap * 8;
   TCUDA(cudaFuncSetAttribute(k_gather_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
   k_gather_sort<<<dim3(ix.n_ranges, nq), GS_THREADS, sm1, s>>>(meta_qoff, top_ids, top_s, kc, ix.list_off,

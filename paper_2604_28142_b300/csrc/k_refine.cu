@@ -246,7 +246,8 @@ tachiom_status launch_refine(const Index &ix, const float *queries, const int32_
 // pass leaves), one CTA per (query, document). A document is taken in chunks of
 // 64 tokens: the chunk's centroid ids, codes and norms are loaded at once, then
 // its centroid rows and the codewords its codes select are copied to shared
-// memory with cp.async (one wave of copies per chunk). Lane i holds query token
+// memory with cp.async (one wave of copies per chunk, the next chunk's issued
+// before the current one is computed: two buffers). Lane i holds query token
 // i in registers; a warp takes 4 document tokens at a time (4 independent FMA
 // chains) and reads their rows and codewords from shared memory (broadcast).
 // Every number is the one k_refine produces: the centroid term is the same fmaf
@@ -263,11 +264,14 @@ constexpr int RW_CHUNK = 64;     // document tokens staged at once
 constexpr int RW_TPW = 4;        // document tokens per warp step
 
 template <bool BF16C>
-constexpr size_t rw_smem() {
+constexpr size_t rw_buf_bytes() {
   return (size_t)RW_CHUNK * DIM * (BF16C ? 2 : 4)        // centroid rows
          + (size_t)RW_CHUNK * DIM * 4                      // the chunk's codewords (M x DS = 128 floats per token)
-         + (size_t)RW_CHUNK * (4 + 4 + 32)                 // centroid id, rho, codes (<= 32 bytes)
-         + (size_t)RW_WARPS * MAX_NTOK * 4;                // per-warp maxima
+         + (size_t)RW_CHUNK * (4 + 4 + 32);                // centroid id, rho, codes (<= 32 bytes)
+}
+template <bool BF16C>
+constexpr size_t rw_smem() {
+  return 2 * rw_buf_bytes<BF16C>() + (size_t)RW_WARPS * MAX_NTOK * 4;  // two chunk buffers, per-warp maxima
 }
 
 __device__ __forceinline__ void rw_cp16(void *dst, const void *src) {
@@ -286,13 +290,15 @@ k_refine_win(const float *__restrict__ queries, const int32_t *__restrict__ meta
   constexpr int G = 128 / M;
   constexpr int DS = 128 / M;
   constexpr int RB = BF16C ? DIM * 2 : DIM * 4;  // bytes per centroid row
+  constexpr size_t BUF = rw_buf_bytes<BF16C>();
   extern __shared__ __align__(16) unsigned char rwm[];
-  unsigned char *rows = rwm;                                                   // [CHUNK][RB]
-  float *cw = reinterpret_cast<float *>(rows + RW_CHUNK * RB);                 // [CHUNK][128]
-  int32_t *cid = reinterpret_cast<int32_t *>(cw + RW_CHUNK * DIM);             // [CHUNK]
-  float *rh = reinterpret_cast<float *>(cid + RW_CHUNK);                       // [CHUNK]
-  uint8_t *cds = reinterpret_cast<uint8_t *>(rh + RW_CHUNK);                   // [CHUNK][32]
-  float *mxs = reinterpret_cast<float *>(cds + RW_CHUNK * 32);                 // [WARPS][32]
+  // buffer b: rows [CHUNK][RB], codewords [CHUNK][128], centroid ids, rho, codes [CHUNK][32]
+  auto rows_of = [&](int b) { return rwm + b * BUF; };
+  auto cw_of = [&](int b) { return reinterpret_cast<float *>(rwm + b * BUF + RW_CHUNK * RB); };
+  auto cid_of = [&](int b) { return reinterpret_cast<int32_t *>(cw_of(b) + RW_CHUNK * DIM); };
+  auto rh_of = [&](int b) { return reinterpret_cast<float *>(cid_of(b) + RW_CHUNK); };
+  auto cds_of = [&](int b) { return reinterpret_cast<uint8_t *>(rh_of(b) + RW_CHUNK); };
+  float *mxs = reinterpret_cast<float *>(rwm + 2 * BUF);  // [WARPS][32]
   const int q = blockIdx.y;
   const int ntok = meta[3 * nq + 2 + q];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -306,6 +312,36 @@ k_refine_win(const float *__restrict__ queries, const int32_t *__restrict__ meta
       qv[4 * k4] = v.x; qv[4 * k4 + 1] = v.y; qv[4 * k4 + 2] = v.z; qv[4 * k4 + 3] = v.w;
     }
   }
+  // chunk staging: the ids, norms and codes (plain loads), then, after a barrier, the copies
+  // of the rows and of the selected codewords (cp.async, one commit group per chunk)
+  auto stage_meta = [&](int b, int64_t c0, int nt) {
+    int32_t *cid = cid_of(b);
+    float *rh = rh_of(b);
+    uint8_t *cds = cds_of(b);
+    for (int x = tid; x < nt; x += RW_THREADS) {
+      cid[x] = tok_cid[c0 + x];
+      rh[x] = __half2float(__ushort_as_half(rnorm[c0 + x]));
+    }
+    for (int x = tid; x < nt * M; x += RW_THREADS) cds[(x / M) * 32 + x % M] = codes[c0 * M + x];
+  };
+  auto stage_copy = [&](int b, int nt) {
+    constexpr int RC = RB / 16, WC = DS * 4 / 16;
+    unsigned char *rows = rows_of(b);
+    float *cw = cw_of(b);
+    const int32_t *cid = cid_of(b);
+    const uint8_t *cds = cds_of(b);
+    for (int x = tid; x < nt * RC; x += RW_THREADS) {
+      const int t = x / RC, c = x % RC;
+      const unsigned char *src = BF16C ? reinterpret_cast<const unsigned char *>(cent_bf16 + (int64_t)cid[t] * DIM)
+                                       : reinterpret_cast<const unsigned char *>(cent_f32 + (int64_t)cid[t] * DIM);
+      rw_cp16(rows + t * RB + c * 16, src + c * 16);
+    }
+    for (int x = tid; x < nt * M * WC; x += RW_THREADS) {
+      const int t = x / (M * WC), r = x % (M * WC), m = r / WC, c = r % WC;
+      rw_cp16(cw + t * DIM + m * DS + c * 4, codebooks + ((int64_t)m * 256 + cds[t * 32 + m]) * DS + c * 4);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
   const int gq = (ntok + G - 1) / G;
   for (int slot = blockIdx.x; slot < kd; slot += gridDim.x) {
     const int32_t d = cand[(int64_t)q * kd + slot];
@@ -315,33 +351,34 @@ k_refine_win(const float *__restrict__ queries, const int32_t *__restrict__ meta
       if (tid < gq) part[((int64_t)q * ngroups + tid) * kd + slot] = 0.f;
       continue;
     }
-    __syncthreads();  // the previous document's maxima have been summed
+    __syncthreads();  // the previous document's maxima have been summed, its buffers are free
     const int64_t tb = doc_off[d], te = doc_off[d + 1];
+    const int nch = (int)((te - tb + RW_CHUNK - 1) / RW_CHUNK);
     float mx = -INFINITY;
-    for (int64_t c0 = tb; c0 < te; c0 += RW_CHUNK) {
+    if (nch > 0) {
+      stage_meta(0, tb, (int)min((int64_t)RW_CHUNK, te - tb));
+      __syncthreads();
+      stage_copy(0, (int)min((int64_t)RW_CHUNK, te - tb));
+    }
+    for (int ch = 0; ch < nch; ch++) {
+      const int b = ch & 1;
+      const int64_t c0 = tb + (int64_t)ch * RW_CHUNK;
       const int nt = (int)min((int64_t)RW_CHUNK, te - c0);
-      __syncthreads();  // the previous chunk is no longer read
-      for (int x = tid; x < nt; x += RW_THREADS) {
-        cid[x] = tok_cid[c0 + x];
-        rh[x] = __half2float(__ushort_as_half(rnorm[c0 + x]));
+      if (ch + 1 < nch) {
+        // the next chunk goes to the other buffer while this one is computed
+        const int64_t c1 = c0 + RW_CHUNK;
+        const int nt1 = (int)min((int64_t)RW_CHUNK, te - c1);
+        stage_meta(b ^ 1, c1, nt1);
+        __syncthreads();
+        stage_copy(b ^ 1, nt1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
       }
-      for (int x = tid; x < nt * M; x += RW_THREADS) cds[(x / M) * 32 + x % M] = codes[c0 * M + x];
-      __syncthreads();
-      // rows: nt x (RB / 16) chunks of 16 bytes; codewords: nt x M x (DS * 4 / 16) chunks
-      constexpr int RC = RB / 16, WC = DS * 4 / 16;
-      for (int x = tid; x < nt * RC; x += RW_THREADS) {
-        const int t = x / RC, c = x % RC;
-        const unsigned char *src = BF16C ? reinterpret_cast<const unsigned char *>(cent_bf16 + (int64_t)cid[t] * DIM)
-                                         : reinterpret_cast<const unsigned char *>(cent_f32 + (int64_t)cid[t] * DIM);
-        rw_cp16(rows + t * RB + c * 16, src + c * 16);
-      }
-      for (int x = tid; x < nt * M * WC; x += RW_THREADS) {
-        const int t = x / (M * WC), r = x % (M * WC), m = r / WC, c = r % WC;
-        rw_cp16(cw + t * DIM + m * DS + c * 4, codebooks + ((int64_t)m * 256 + cds[t * 32 + m]) * DS + c * 4);
-      }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      __syncthreads();
+      __syncthreads();  // this chunk's copies are visible to every thread
+      const unsigned char *rows = rows_of(b);
+      const float *cw = cw_of(b);
+      const float *rh = rh_of(b);
       for (int t0 = warp * RW_TPW; t0 < nt; t0 += RW_WARPS * RW_TPW) {
         int tt[RW_TPW];
 #pragma unroll
@@ -390,6 +427,7 @@ k_refine_win(const float *__restrict__ queries, const int32_t *__restrict__ meta
 #pragma unroll
         for (int j = 0; j < RW_TPW; j++) mx = fmaxf(mx, fmaf(rh[tt[j]], rs[j], ct[j]));
       }
+      __syncthreads();  // buffer b is free for chunk ch + 2
     }
     mxs[warp * MAX_NTOK + lane] = mx;
     __syncthreads();

@@ -169,7 +169,7 @@ static Plan make_plan(const Index &ix, int rows, int kc, int precision, int plan
   splits = (int)std::min<int64_t>(splits, max_splits);
   p.capout = kc + 64;
   splits = std::min(splits, std::max(1, 16384 / p.capout));
-  const int forced = plan_id >= 0 ? (plan_id >> 4) : 0;
+  const int forced = plan_id >= 0 ? ((plan_id >> 4) & 0xfffff) : 0;
   if (forced > 0) {
     // an explicit slice count of the FP32 scan (autotuner)
     splits = std::max(1, std::min(forced, (int)std::min<int64_t>(max_splits, 16384 / p.capout)));
@@ -260,8 +260,12 @@ static bool use_tc(const tachiom_search_params *p) {
 //             kept groups, 3 FP32 CUDA-core scan
 //   bits 2-3  step (c) kernel: 0 default (3), 1 tensor-core centroid term + lookup tables, then the
 //             FP32 window, 2 FP32 refine only, 3 decode + tensor cores, then the FP32 window
-//   bits 4-   slices of the FP32 scan (0: default)
+//   bits 4-23 slices of the FP32 scan (0: default)
+//   bit 24    step (b): the token-serial gather for every range (default: the counting-sort
+//             gather, token-serial only for the ranges whose entries overflow its buffers)
 enum { SCAN_DEFAULT = 0, SCAN_TC1 = 1, SCAN_TC2 = 2, SCAN_F32 = 3 };
+constexpr int32_t PLAN_GATHER_TOK = 1 << 24;
+static bool gather_tok_only(const tachiom_search_params *p) { return p->plan_id >= 0 && (p->plan_id & PLAN_GATHER_TOK); }
 enum { REFINE_DEFAULT = 0, REFINE_TC = 1, REFINE_F32 = 2, REFINE_DEC = 3 };
 
 static int scan_kind(const tachiom_search_params *p) {
@@ -399,8 +403,7 @@ static tachiom_status search_device(Index *ix, const tachiom_search_params *p, c
   if ((st = upload_meta(w, p, h_ntok, h_k, nq))) return st;
   if ((st = run_topc(ix, w, p, d_queries, b.rows, plan))) return st;
   if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, p->kappa_c, w->d_dense, w->d_hist,
-                          w->d_govf, w->d_govf_n,
-                          w->d_flags, stream)))
+                          w->d_govf, w->d_govf_n, gather_tok_only(p), w->d_flags, stream)))
     return st;
   if ((st = launch_select_kd(*ix, w->d_meta, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
                              w->d_cand, w->d_cand_s, w->d_ncand, w->d_flags, stream)))
@@ -550,8 +553,7 @@ extern "C" tachiom_status tachiom_gather(tachiom_index *index, const tachiom_sea
                                 w->d_flags, s)))
     return st;
   if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, params->kappa_c, w->d_dense, w->d_hist,
-                          w->d_govf, w->d_govf_n,
-                          w->d_flags, s)))
+                          w->d_govf, w->d_govf_n, gather_tok_only(params), w->d_flags, s)))
     return st;
   return launch_select_kd(*ix, w->d_meta, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
                           d_cand_ids, d_cand_scores, d_ncand, w->d_flags, s);

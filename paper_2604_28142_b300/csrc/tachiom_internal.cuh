@@ -227,7 +227,7 @@ tachiom_status launch_score_pairs(const Index &ix, const float *rows, int nrows,
 // step (b)
 tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, const int32_t *top_ids,
                              const float *top_s, int kc, float *dense, uint32_t *hist, int2 *ovf, int *novf,
-                             uint32_t *flags, cudaStream_t s);
+                             bool tok_only, uint32_t *flags, cudaStream_t s);
 tachiom_status launch_select_kd(const Index &ix, const int32_t *meta, int nq, int kd, const float *dense,
                                 const uint32_t *hist, uint32_t *hist2, uint32_t *state,
                                 uint64_t *selbuf, int32_t *cand, float *cand_s, int32_t *ncand,

@@ -61,7 +61,9 @@ def test_every_plan_gives_the_same_results(env, prec):
     dq = torch.from_numpy(q["queries"]).cuda()
     best, ms = G.autotune(params, dq, q["ntok"], kk)
     assert best >= 0 and ms > 0
-    plans = [1 | 4, 1 | 8, 2 | 4, 2 | 8, 3 | 8] if prec == 1 else [3 | 8 | (s << 4) for s in (1, 7, 40)]
+    tok = 1 << 24  # the token-serial gather for every range
+    plans = ([1 | 4, 1 | 8, 2 | 4, 2 | 8, 3 | 8, 2 | 12 | tok] if prec == 1
+             else [3 | 8 | (s << 4) for s in (1, 7, 40)] + [3 | 8 | tok])
     for pl in plans + [best]:
         got = _run(T, G, params, q, kk, plan=pl)
         assert np.array_equal(got[0], want[0]), pl

@@ -37,9 +37,9 @@ class Case:
         self.T = T
         self.dq = torch.from_numpy(self.q).cuda()
 
-    def params(self, prec=0, kd=None, kc=None):
+    def params(self, prec=0, kd=None, kc=None, plan=-1):
         return self.T.SearchParams(kappa_c=self.kc if kc is None else kc,
-                                   kappa_d=self.kd if kd is None else kd, precision=prec)
+                                   kappa_d=self.kd if kd is None else kd, precision=prec, plan_id=plan)
 
 
 _CASES = {}
@@ -95,15 +95,20 @@ def test_step_a_top_centroids_fp32(name):
         check_ranking(gi[r], gs[r], o_ids[r], o_s[r], RTOL_FP32, GAP, what=f"row {r}")
 
 
+# plan bit 24: the token-serial gather for every range (the counting-sort gather's fallback)
+GATHER_PLANS = [-1, 1 << 24]
+
+
+@pytest.mark.parametrize("plan", GATHER_PLANS)
 @pytest.mark.parametrize("name", CASES)
-def test_step_b_gather_replay(name):
+def test_step_b_gather_replay(name, plan):
     c = get_case(name)
     o_ids, _ = c.O.top_centroids(c.q, c.kc)
     top = torch.from_numpy(o_ids).cuda()
     cid = torch.empty((c.nq, c.kd), dtype=torch.int32, device="cuda")
     cs = torch.empty((c.nq, c.kd), dtype=torch.float32, device="cuda")
     nc = torch.empty(c.nq, dtype=torch.int32, device="cuda")
-    c.G.gather(c.params(), c.dq, c.ntok, top, cid, cs, nc)
+    c.G.gather(c.params(plan=plan), c.dq, c.ntok, top, cid, cs, nc)
     torch.cuda.synchronize()
     gi, gs, gn = cid.cpu().numpy(), cs.cpu().numpy(), nc.cpu().numpy()
     for u in range(c.nq):
@@ -118,8 +123,9 @@ def test_step_b_gather_replay(name):
                       exact_scores=dict(zip(docs.tolist(), s.tolist())))
 
 
+@pytest.mark.parametrize("plan", GATHER_PLANS)
 @pytest.mark.parametrize("name", CASES)
-def test_step_b_reached_set_bit_exact(name):
+def test_step_b_reached_set_bit_exact(name, plan):
     # with kappa_d above the pool size the candidates are every reached doc: integer work
     c = get_case(name)
     o_ids, _ = c.O.top_centroids(c.q, c.kc)
@@ -128,7 +134,7 @@ def test_step_b_reached_set_bit_exact(name):
     cid = torch.empty((c.nq, kd), dtype=torch.int32, device="cuda")
     cs = torch.empty((c.nq, kd), dtype=torch.float32, device="cuda")
     nc = torch.empty(c.nq, dtype=torch.int32, device="cuda")
-    c.G.gather(c.params(kd=kd), c.dq, c.ntok, top, cid, cs, nc)
+    c.G.gather(c.params(kd=kd, plan=plan), c.dq, c.ntok, top, cid, cs, nc)
     torch.cuda.synchronize()
     gi, gn = cid.cpu().numpy(), nc.cpu().numpy()
     checked = 0
