@@ -274,6 +274,7 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
   }
   for (int b = tid; b < NBINS1; b += GS_THREADS) h[b] = 0u;
   for (int x = tid; x < (RD + 1) / 2; x += GS_THREADS) cnt[x] = 0u;
+  for (int x = tid; x < ecap; x += GS_THREADS) kout[x] = 0u;  // slice marks (below)
   __syncthreads();
   // exclusive prefix of the slice lengths: thread t owns descriptors [t * per, (t + 1) * per)
   uint32_t total;
@@ -300,6 +301,7 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
     for (int e = s0; e < s1; e++) {
       const int len = seg[e].pref;
       seg[e].pref = (int32_t)base;
+      if (len > 0 && base < (uint32_t)ecap) kout[base] = (uint32_t)e;  // a slice marks its first entry
       base += (uint32_t)len;
     }
   }
@@ -312,8 +314,32 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
     return;
   }
   __syncthreads();
-  // the keys (four entries per thread in flight) and the per-document counts
   const int n = (int)total;
+  // every entry's slice: a running maximum over the marks (slices are in prefix order)
+  {
+    const int per = (n + GS_THREADS - 1) / GS_THREADS;
+    const int e0 = min(n, tid * per), e1 = min(n, e0 + per);
+    uint32_t run = 0;
+    for (int e = e0; e < e1; e++) run = max(run, kout[e]);
+    uint32_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc = max(inc, y);
+    }
+    __syncthreads();  // wsum of the length scan is no longer read
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t before = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) before = 0;
+    for (int w = 0; w < warp; w++) before = max(before, wsum[w]);
+    for (int e = e0; e < e1; e++) {
+      before = max(before, kout[e]);
+      kout[e] = before;
+    }
+  }
+  __syncthreads();
+  // the keys (four entries per thread in flight) and the per-document counts
   for (int e0 = 0; e0 < n; e0 += 4 * GS_THREADS) {
     int64_t pos[4];
     uint32_t code[4];
@@ -323,13 +349,9 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
       pos[u] = 0;
       code[u] = 0u;
       if (e < n) {
-        int lo = 0, hi = nseg;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if ((uint32_t)seg[mid].pref <= (uint32_t)e) lo = mid; else hi = mid;
-        }
-        pos[u] = seg[lo].start + (e - seg[lo].pref);
-        code[u] = seg[lo].key;
+        const GSeg g = seg[kout[e]];
+        pos[u] = g.start + (e - g.pref);
+        code[u] = g.key;
       }
     }
     int32_t dv[4];
