@@ -253,24 +253,43 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
   const int nd = (int)min((int64_t)RD, D - r0);
   const int row_b = qoff[q], ntok = qoff[q + 1] - row_b;
   const int nseg = ntok * kc;
-  // slice descriptors (length in .pref until the scan), the scores, empty counts and histogram
-  for (int e = tid; e < nseg; e += GS_THREADS) {
-    int32_t jj = top_ids[(int64_t)row_b * kc + e];
-    if (jj >= C) {
-      atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
-      jj = -1;
+  // slice descriptors (length in .pref until the scan), the scores, empty counts and histogram;
+  // two descriptors per thread, their loads issued together
+  for (int e0 = tid; e0 < nseg; e0 += 2 * GS_THREADS) {
+    int32_t jj[2];
+    float sv[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const int e = e0 + u * GS_THREADS;
+      jj[u] = e < nseg ? top_ids[(int64_t)row_b * kc + e] : -1;
+      sv[u] = e < nseg ? top_s[(int64_t)row_b * kc + e] : 0.f;
     }
-    GSeg g;
-    g.start = 0;
-    g.pref = 0;
-    g.key = (uint32_t)((e / kc) << 7 | (e % kc));
-    if (jj >= 0) {
-      const int lo = list_roff[(int64_t)jj * nr1 + r], hi = list_roff[(int64_t)jj * nr1 + r + 1];
-      g.start = (int32_t)(list_off[jj] + lo);
-      g.pref = hi - lo;
+    int lo[2] = {0, 0}, hi[2] = {0, 0};
+    int64_t lb[2] = {0, 0};
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      if (jj[u] >= C) {
+        atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
+        jj[u] = -1;
+      }
+      if (jj[u] >= 0) {
+        lo[u] = list_roff[(int64_t)jj[u] * nr1 + r];
+        hi[u] = list_roff[(int64_t)jj[u] * nr1 + r + 1];
+        lb[u] = list_off[jj[u]];
+      }
     }
-    seg[e] = g;
-    sc[e] = top_s[(int64_t)row_b * kc + e];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const int e = e0 + u * GS_THREADS;
+      if (e < nseg) {
+        GSeg g;
+        g.start = (int32_t)(lb[u] + lo[u]);
+        g.pref = hi[u] - lo[u];
+        g.key = (uint32_t)((e / kc) << 7 | (e % kc));
+        seg[e] = g;
+        sc[e] = sv[u];
+      }
+    }
   }
   for (int b = tid; b < NBINS1; b += GS_THREADS) h[b] = 0u;
   for (int x = tid; x < (RD + 1) / 2; x += GS_THREADS) cnt[x] = 0u;
@@ -368,28 +387,37 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
     }
   }
   __syncthreads();
-  // exclusive scan of the counts in place (thread t owns documents [t * dper, (t + 1) * dper))
+  // exclusive scan of the counts in place: warp w owns a contiguous block of words (two
+  // documents each), read lane-consecutively (no bank conflicts): the block totals, then the
+  // block's words in rounds of 32 with a running carry
   {
-    const int dper = ((RD + GS_THREADS - 1) / GS_THREADS + 1) & ~1;  // even: whole words
-    const int x0 = min(RD, tid * dper), x1 = min(RD, x0 + dper);
-    uint32_t mine = 0;
-    for (int x = x0; x < x1; x++) mine += gs_get16(cnt, x);
-    uint32_t inc = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
+    const int nw = (RD + 1) / 2;
+    const int wper = ((nw + GS_THREADS / 32 - 1) / (GS_THREADS / 32) + 31) & ~31;  // words per warp
+    const int w0 = warp * wper, w1 = min(nw, w0 + wper);
+    uint32_t tot = 0;
+    for (int x = w0 + lane; x < w1; x += 32) {
+      const uint32_t v = cnt[x];
+      tot += (v & 0xffffu) + (v >> 16);
     }
-    __syncthreads();  // wsum of the first scan is no longer read
-    if (lane == 31) wsum[warp] = inc;
+    tot = __reduce_add_sync(0xffffffffu, tot);
+    __syncthreads();  // wsum of the slice scans is no longer read
+    if (lane == 0) wsum[warp] = tot;
     __syncthreads();
-    uint32_t base = 0;
-    for (int w = 0; w < warp; w++) base += wsum[w];
-    base += inc - mine;
-    for (int x = x0; x < x1; x += 2) {
-      const uint32_t c0 = gs_get16(cnt, x), c1 = x + 1 < x1 ? gs_get16(cnt, x + 1) : 0u;
-      cnt[x >> 1] = base | ((base + c0) << 16);
-      base += c0 + c1;
+    uint32_t carry = 0;
+    for (int w = 0; w < warp; w++) carry += wsum[w];
+    for (int xb = w0; xb < w1; xb += 32) {
+      const int x = xb + lane;
+      const uint32_t v = x < w1 ? cnt[x] : 0u;
+      const uint32_t c0 = v & 0xffffu, c1 = v >> 16, sw = c0 + c1;
+      uint32_t inc = sw;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      const uint32_t start = carry + inc - sw;
+      if (x < w1) cnt[x] = start | ((start + c0) << 16);
+      carry += __shfl_sync(0xffffffffu, inc, 31);
     }
   }
   __syncthreads();
@@ -433,8 +461,7 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
       }
       out[x] = S;
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, bin);
-    if (bin >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[bin], (uint32_t)__popc(peers));
+    if (bin >= 0) atomicAdd(&h[bin], 1u);  // about one lane in ten: little contention
   }
   __syncthreads();
   uint32_t *hq = hist + (int64_t)q * NBINS1;
