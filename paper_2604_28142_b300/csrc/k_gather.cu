@@ -248,7 +248,9 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
   uint32_t *kin = cnt + (RD + 1) / 2;                                                        // [ecap]
   uint32_t *kout = kin + ecap;                                                               // [ecap]
   __shared__ uint32_t wsum[GS_THREADS / 32];
+  __shared__ int s_nr;  // reached documents of the range
   const int r = blockIdx.x, q = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_nr = 0;
   const int64_t r0 = (int64_t)r * RD;
   const int nd = (int)min((int64_t)RD, D - r0);
   const int row_b = qoff[q], ntok = qoff[q + 1] - row_b;
@@ -332,6 +334,9 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
     }
     return;
   }
+  // every document of the range starts unreached (-inf); the reached ones are written below
+  float *out = dense + (int64_t)q * D + r0;
+  for (int x = tid; x < nd; x += GS_THREADS) out[x] = -INFINITY;
   __syncthreads();
   const int n = (int)total;
   // every entry's slice: a running maximum over the marks (slices are in prefix order)
@@ -438,30 +443,36 @@ k_gather_sort(const int32_t *__restrict__ qoff, const int32_t *__restrict__ top_
     kin[start + below] = k;
   }
   __syncthreads();
-  // S~ per document: the first key of each token run is the token's best rank; the tokens
-  // come in ascending i
-  float *out = dense + (int64_t)q * D + r0;
+  // the reached documents, listed in kout (free now) with warp-aggregated appends
   for (int b0 = 0; b0 < nd; b0 += GS_THREADS) {
     const int x = b0 + tid;
-    int bin = -1;
-    if (x < nd) {
-      const uint32_t end = gs_get16(cnt, x), start = x == 0 ? 0u : gs_get16(cnt, x - 1);
-      float S = -INFINITY;
-      if (end > start) {
-        uint32_t prev = 0xffffffffu;
-        for (uint32_t f = start; f < end; f++) {
-          const uint32_t kf = kin[f], t = (kf >> 7) & 31u;
-          if (t != prev) {
-            const float v = sc[t * kc + (kf & 127u)];
-            S = (prev == 0xffffffffu) ? v : S + v;
-            prev = t;
-          }
-        }
-        bin = (int)(fkey(S) >> 20);
+    bool reached = false;
+    if (x < nd) reached = gs_get16(cnt, x) > (x == 0 ? 0u : gs_get16(cnt, x - 1));
+    const unsigned m = __ballot_sync(0xffffffffu, reached);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(&s_nr, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (reached) kout[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)x;
+  }
+  __syncthreads();
+  // S~ per reached document: the first key of each token run is the token's best rank; the
+  // tokens come in ascending i
+  const int nr = s_nr;
+  for (int i = tid; i < nr; i += GS_THREADS) {
+    const int x = (int)kout[i];
+    const uint32_t end = gs_get16(cnt, x), start = x == 0 ? 0u : gs_get16(cnt, x - 1);
+    float S = 0.f;
+    uint32_t prev = 0xffffffffu;
+    for (uint32_t f = start; f < end; f++) {
+      const uint32_t kf = kin[f], t = (kf >> 7) & 31u;
+      if (t != prev) {
+        const float v = sc[t * kc + (kf & 127u)];
+        S = (prev == 0xffffffffu) ? v : S + v;
+        prev = t;
       }
-      out[x] = S;
     }
-    if (bin >= 0) atomicAdd(&h[bin], 1u);  // about one lane in ten: little contention
+    out[x] = S;
+    atomicAdd(&h[fkey(S) >> 20], 1u);
   }
   __syncthreads();
   uint32_t *hq = hist + (int64_t)q * NBINS1;
