@@ -229,7 +229,31 @@ def _per_type_kmeans(X, types, kappa, iters, g, device, log=None):
     occ = occ[np.argsort(-counts[occ], kind="stable")]
     PBUDGET = 1 << 21  # padded points per group
     DBUDGET = 1 << 27  # distance entries per bmm chunk
+    TRAIN_CAP = 1 << 24  # a larger type trains on its first 2^24 tokens, then assigns all of them
     i = 0
+    while i < len(occ) and int(counts[occ[i]]) > TRAIN_CAP:
+        j = int(occ[i])
+        n, kj = int(counts[j]), int(kappa[j])
+        tok = order[int(starts[j]):int(starts[j]) + n]
+        P = X[tok[:TRAIN_CAP]].to(torch.float32)[None]  # [1, cap, d]
+        valid = torch.ones(1, TRAIN_CAP, dtype=torch.bool, device=device)
+        keys = torch.rand(1, TRAIN_CAP, generator=g, device=device)
+        pick = torch.argsort(keys, dim=1)[:, :kj]
+        C0 = torch.gather(P, 1, pick[:, :, None].expand(1, kj, DIM))
+        cvalid = torch.ones(1, kj, dtype=torch.bool, device=device)
+        Cf, _ = _lloyd_group(P, valid, C0, cvalid, iters, max(1, DBUDGET // kj))
+        del P
+        cents[int(coff[j]):int(coff[j]) + kj] = Cf[0]
+        C = Cf[0]
+        cn = (C * C).sum(-1)
+        ch = max(1, DBUDGET // kj)
+        for s0 in range(0, n, ch):
+            e0 = min(n, s0 + ch)
+            x = X[tok[s0:e0]].to(torch.float32)
+            assign[tok[s0:e0]] = int(coff[j]) + (cn[None, :] - 2.0 * (x @ C.T)).argmin(-1)
+        i += 1
+        if log is not None:
+            log(f"kmeans of type {j}: {n} tokens (trained on {TRAIN_CAP}), k={kj}")
     while i < len(occ):
         n_max = int(counts[occ[i]])
         G = max(1, PBUDGET // max(1, n_max))
@@ -405,10 +429,15 @@ def load_or_make(name: str, device="cpu", log=None) -> dict:
         ix["centroid_dtype"] = str(ix["centroid_dtype"])
         return ix
     ix = make_index(cfg, device=dev, log=log)
-    os.makedirs(_cache_dir(), exist_ok=True)
-    tmp = path + ".tmp.npz"
-    np.savez(tmp, **ix)
-    os.replace(tmp, path)
+    if dev.type == "cuda":
+        torch.cuda.empty_cache()  # hand the generator's device memory back
+    try:
+        os.makedirs(_cache_dir(), exist_ok=True)
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, **ix)
+        os.replace(tmp, path)
+    except OSError:
+        pass  # no room for the cache: the index is regenerated next time
     return ix
 
 

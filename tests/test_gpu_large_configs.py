@@ -39,10 +39,29 @@ def test_large_workload_sampled(name, batch, lo, hi):
     oi = torch.empty(nq * k, dtype=torch.int32, device="cuda")
     os_ = torch.empty(nq * k, dtype=torch.float32, device="cuda")
     prec = T.PREC_BF16 if T.tc_available() else T.PREC_FP32
-    G.search(T.SearchParams(kappa_c=kc, kappa_d=kd, precision=prec), dq, q["ntok"], np.full(nq, k, np.int32), oi, os_)
+    kk = np.full(nq, k, np.int32)
+    params = T.SearchParams(kappa_c=kc, kappa_d=kd, precision=prec)
+    G.search(params, dq, q["ntok"], kk, oi, os_)
     torch.cuda.synchronize()
     assert G.stream_status() & ~3 == 0
     gi, gs = oi.cpu().numpy(), os_.cpu().numpy()
+    # the launch configuration's time, for the record
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        G.search(params, dq, q["ntok"], kk, oi, os_)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    print(f"\n{name}: batch {nq}, {ms:.2f} ms per batch, {nq / ms * 1e3:.0f} queries/s")
+    if prec == T.PREC_BF16:
+        # the reduced-precision path returns the FP32 path's results bit for bit
+        fi = torch.empty_like(oi)
+        fs = torch.empty_like(os_)
+        G.search(T.SearchParams(kappa_c=kc, kappa_d=kd, precision=T.PREC_FP32), dq, q["ntok"], kk, fi, fs)
+        torch.cuda.synchronize()
+        assert np.array_equal(fi.cpu().numpy(), gi)
+        assert np.array_equal(fs.cpu().numpy(), gs)
     off = np.concatenate([[0], np.cumsum(q["ntok"])])
     sample = [0, nq // 2, nq - 1]
     rows = np.concatenate([np.arange(off[u], off[u + 1]) for u in sample])
