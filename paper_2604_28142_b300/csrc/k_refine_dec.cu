@@ -47,10 +47,14 @@ template <int M>
 constexpr int rd_fixed_bytes() {
   return M * 256 * (128 / M) * 2 + M * 256 * 4 + 64 * 4 + 32 * RD_ROW;
 }
-template <int M>
+// per warp: two tiles, and in the window variant the chunk's row norms and the exact maxima
+template <bool WIN>
+constexpr int rd_warp_bytes() { return 2 * RD_TILE + (WIN ? 256 : 0); }
+template <int M, bool WIN>
 constexpr int rd_warps() {
-  return (RD_SMEM_MAX - rd_fixed_bytes<M>()) / (2 * RD_TILE) > 16 ? 16
-                                                                 : (RD_SMEM_MAX - rd_fixed_bytes<M>()) / (2 * RD_TILE);
+  return (RD_SMEM_MAX - rd_fixed_bytes<M>()) / rd_warp_bytes<WIN>() > 16
+             ? 16
+             : (RD_SMEM_MAX - rd_fixed_bytes<M>()) / rd_warp_bytes<WIN>();
 }
 
 __device__ __forceinline__ void rd_mma(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
@@ -75,9 +79,12 @@ struct DecPos {
 
 // next 16-token chunk of the warp's document, or the next document of the CTA's
 // slice (taken from a shared counter, so the warps stay balanced)
+// bad(slot, empty): answer a slot whose document is out of range (empty = false) or has no
+// tokens (empty = true); called by lane 0
+template <typename BadFn>
 __device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int *s_next, const int32_t *cand_q,
-                                         const int64_t *doc_off, int64_t D, float *sa_row, float *da_row,
-                                         uint32_t *flags, int lane) {
+                                         const int64_t *doc_off, int64_t D, BadFn bad, uint32_t *flags,
+                                         int lane) {
   if (p.c0 + 16 < p.te) {
     p.c0 += 16;
     return true;
@@ -93,18 +100,14 @@ __device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int *s_next, cons
     if (d >= D) {
       if (lane == 0) {
         atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
-        sa_row[slot] = -INFINITY;
-        da_row[slot] = 0.f;
+        bad(slot, false);
       }
       continue;
     }
     p.tb = doc_off[d];
     p.te = doc_off[d + 1];
     if (p.te == p.tb) {
-      if (lane == 0) {
-        sa_row[slot] = 0.f;
-        da_row[slot] = 0.f;
-      }
+      if (lane == 0) bad(slot, true);
       continue;
     }
     p.c0 = p.tb;
@@ -112,15 +115,74 @@ __device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int *s_next, cons
   }
 }
 
-// sa[q][slot] = approximate S, da[q][slot] = its bound Delta_d
-template <int M, int WARPS>
+// The FP32 path's score of query token i against document token t: the fmaf chain over
+// k = 0..127 of the centroid term, the table entries of the residual (each an fmaf chain over
+// its subspace's dims) added in ascending m from 0, then fmaf(rho, rs, ct) - k_refine's numbers.
+template <int M>
+__device__ __forceinline__ float dec_exact(const float *__restrict__ qi, int64_t t,
+                                           const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
+                                           const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
+                                           const float *__restrict__ cent_f32,
+                                           const __nv_bfloat16 *__restrict__ cent_bf16, bool bf16c) {
+  constexpr int DS = 128 / M;
+  const int32_t j = tok_cid[t];
+  float ct = 0.f;
+  const float4 *q4 = reinterpret_cast<const float4 *>(qi);
+  if (bf16c) {
+    const uint4 *crow = reinterpret_cast<const uint4 *>(cent_bf16 + (int64_t)j * DIM);
+#pragma unroll 4
+    for (int k8 = 0; k8 < DIM / 8; k8++) {
+      const uint4 u = crow[k8];
+      const float4 qa = q4[2 * k8], qb = q4[2 * k8 + 1];
+      ct = fmaf(qa.x, __uint_as_float(u.x << 16), ct);
+      ct = fmaf(qa.y, __uint_as_float(u.x & 0xffff0000u), ct);
+      ct = fmaf(qa.z, __uint_as_float(u.y << 16), ct);
+      ct = fmaf(qa.w, __uint_as_float(u.y & 0xffff0000u), ct);
+      ct = fmaf(qb.x, __uint_as_float(u.z << 16), ct);
+      ct = fmaf(qb.y, __uint_as_float(u.z & 0xffff0000u), ct);
+      ct = fmaf(qb.z, __uint_as_float(u.w << 16), ct);
+      ct = fmaf(qb.w, __uint_as_float(u.w & 0xffff0000u), ct);
+    }
+  } else {
+    const float4 *crow = reinterpret_cast<const float4 *>(cent_f32 + (int64_t)j * DIM);
+#pragma unroll 4
+    for (int k4 = 0; k4 < DIM / 4; k4++) {
+      const float4 c = crow[k4], qa = q4[k4];
+      ct = fmaf(qa.x, c.x, ct);
+      ct = fmaf(qa.y, c.y, ct);
+      ct = fmaf(qa.z, c.z, ct);
+      ct = fmaf(qa.w, c.w, ct);
+    }
+  }
+  float rs = 0.f;
+  const uint8_t *c8 = codes + t * M;
+#pragma unroll 4
+  for (int m = 0; m < M; m++) {
+    const float *w = codebooks + ((int64_t)m * 256 + c8[m]) * DS;
+    float a = 0.f;
+#pragma unroll
+    for (int u = 0; u < DS; u++) a = fmaf(qi[m * DS + u], w[u], a);
+    rs += a;
+  }
+  return fmaf(__half2float(__ushort_as_half(rnorm[t])), rs, ct);
+}
+
+// !WIN: sa[q][slot] = approximate S, da[q][slot] = its bound Delta_d, and per query token i
+//       thr[q][slot][i] = (approximate max_t v_it) - (the bound of its error); a token t whose
+//       approximate v_it plus its own bound is below thr cannot hold the exact maximum.
+// WIN:  the same pass over the compacted window list cand (first id < 0 ends it): the pairs
+//       (i, t) that pass the test against thr are scored exactly (dec_exact) and their maximum
+//       per query token gives the FP32 path's group partial sums part[q][group][slot].
+template <int M, int WARPS, bool WIN>
 __global__ void __launch_bounds__(WARPS * 32, 1)
 k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta, int nq,
              const int32_t *__restrict__ cand, int kd, const int64_t *__restrict__ doc_off,
              const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
              const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
-             const __nv_bfloat16 *__restrict__ cent_bf16, float cerr, float cnorm, float *__restrict__ sa,
-             float *__restrict__ da, int64_t D, uint32_t *__restrict__ flags) {
+             const __nv_bfloat16 *__restrict__ cent_bf16, const float *__restrict__ cent_f32, int bf16c,
+             float cerr, float cnorm, float *__restrict__ sa, float *__restrict__ da, float *__restrict__ thr,
+             const int32_t *__restrict__ win_slot, float *__restrict__ part, int ngroups, int64_t D,
+             uint32_t *__restrict__ flags) {
   constexpr int DS = 128 / M;
   constexpr int NT = WARPS * 32;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -133,9 +195,24 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
 
   const int q = blockIdx.y;
   const int ntok = meta[3 * nq + 2 + q];
-  const int s_begin = blockIdx.x * RD_DOCS_PER_CTA;
-  const int s_end = min(kd, s_begin + RD_DOCS_PER_CTA);
   const int32_t *cand_q = cand + (int64_t)q * kd;
+  int s_begin, s_end;
+  if (WIN) {
+    // the window list is compacted: its length is the number of ids >= 0
+    __shared__ int s_nv;
+    if (threadIdx.x == 0) s_nv = 0;
+    __syncthreads();
+    int nv = 0;
+    for (int i = threadIdx.x; i < kd; i += NT) nv += cand_q[i] >= 0 ? 1 : 0;
+    nv = __reduce_add_sync(0xffffffffu, nv);
+    if ((threadIdx.x & 31) == 0 && nv) atomicAdd(&s_nv, nv);
+    __syncthreads();
+    s_begin = 0;
+    s_end = s_nv;
+  } else {
+    s_begin = blockIdx.x * RD_DOCS_PER_CTA;
+    s_end = min(kd, s_begin + RD_DOCS_PER_CTA);
+  }
   {
     int any = 0;
     for (int i = s_begin + (int)threadIdx.x; i < s_end && !any; i += NT) any = cand_q[i] >= 0;
@@ -188,13 +265,28 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   __syncthreads();
 
   unsigned char *wt = tiles + warp * 2 * RD_TILE;
+  // window variant: this warp's chunk row norms (xn, en per row) and exact maxima per query token
+  float *rnx = reinterpret_cast<float *>(tiles + WARPS * 2 * RD_TILE + warp * 256);  // [16][2]
+  uint32_t *emx = reinterpret_cast<uint32_t *>(rnx + 32);                           // [32] fkey
+  if (WIN) emx[lane] = fkey(-INFINITY);
+  const int G = 128 / M;                   // query tokens per group of the FP32 path's partial sums
+  const int gq_n = (ntok + G - 1) / G;     // groups of this query
   const uint32_t wt_s = (uint32_t)__cvta_generic_to_shared(wt);
   const uint32_t qs_s = (uint32_t)__cvta_generic_to_shared(qsm);
   // ldmatrix row addresses: A (document tokens x dims) and B (query tokens x dims, two n-tiles per x4)
   const uint32_t la_off = (uint32_t)((((lane >> 3) & 1) * 8 + (lane & 7)) * RD_ROW + ((lane >> 4) * 8) * 2);
   const uint32_t lb_off = (uint32_t)((((lane >> 4) * 8) + (lane & 7)) * RD_ROW + ((lane >> 3) & 1) * 16);
-  float *sa_row = sa + (int64_t)q * kd;
-  float *da_row = da + (int64_t)q * kd;
+  float *sa_row = WIN ? nullptr : sa + (int64_t)q * kd;
+  float *da_row = WIN ? nullptr : da + (int64_t)q * kd;
+  // a slot whose document is out of range or empty: S = -inf (flagged) or 0, bound 0
+  auto bad = [&](int slot, bool empty) {
+    if (WIN) {
+      for (int g = 0; g < gq_n; g++) part[((int64_t)q * ngroups + g) * kd + slot] = 0.f;
+    } else {
+      sa_row[slot] = empty ? 0.f : -INFINITY;
+      da_row[slot] = 0.f;
+    }
+  };
   // decode layout: lane -> row lane & 15, dims (lane >> 4) * 64 .. +64 (the 8 lanes of a
   // 16-byte shared-memory phase then read 8 different rows: no bank conflicts)
   const int drow = lane & 15, dhalf = lane >> 4;
@@ -243,6 +335,9 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
 #pragma unroll
   for (int nt = 0; nt < 4; nt++) mx[nt][0] = mx[nt][1] = -INFINITY;
   float xmax = 0.f, exmax = 0.f;  // per document: max ||x_t|| and max ||e_xt|| (lane-local, reduced at the end)
+  float th[4][2];                  // window variant: thr of this lane's query tokens for the current document
+#pragma unroll
+  for (int nt = 0; nt < 4; nt++) th[nt][0] = th[nt][1] = INFINITY;
 
   // process the chunk P in stage B with codes CW and norm RH; HN: a next chunk exists, NSLOT its slot
   auto process = [&](const DecPos &P, const int B, const uint4 &CW, const float RH, const bool HN,
@@ -296,8 +391,13 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
       if (live) {
         const float slack = 1.f + ldexpf(1.f, -10);
         const float xn = sqrtf(x2) * slack;
+        const float en = (sqrtf(ex2) + RH * sqrtf(cwe2)) * slack + ldexpf(xn, -22);
         xmax = fmaxf(xmax, xn);
-        exmax = fmaxf(exmax, (sqrtf(ex2) + RH * sqrtf(cwe2)) * slack + ldexpf(xn, -22));
+        exmax = fmaxf(exmax, en);
+        if (WIN && dhalf == 0) {
+          rnx[2 * drow] = xn;
+          rnx[2 * drow + 1] = en;
+        }
       }
     }
     __syncwarp();
@@ -317,19 +417,73 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
         rd_mma(acc[2 * np + 1], a, bb[2], bb[3]);
       }
     }
-    // running max per query token over this thread's tokens (rows gq, gq + 8)
+    const int tig = lane & 3;
+    if (WIN) {
+      // thresholds of this lane's query tokens, at the document's first chunk
+      if (P.c0 == P.tb) {
+        const float *tq = thr + ((int64_t)q * kd + win_slot[(int64_t)q * kd + P.slot]) * 32;
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-      if (P.c0 + gq + h * 8 >= P.te) continue;
+        for (int nt = 0; nt < 4; nt++) {
+          th[nt][0] = tq[nt * 8 + tig * 2];
+          th[nt][1] = tq[nt * 8 + tig * 2 + 1];
+        }
+      }
+      // pairs whose approximate value plus its own bound reaches thr: scored exactly
+      uint32_t fl = 0u;
 #pragma unroll
-      for (int nt = 0; nt < 4; nt++) {
-        mx[nt][0] = fmaxf(mx[nt][0], acc[nt][h * 2 + 0]);
-        mx[nt][1] = fmaxf(mx[nt][1], acc[nt][h * 2 + 1]);
+      for (int h = 0; h < 2; h++) {
+        const int row = gq + h * 8;
+        if (P.c0 + row >= P.te) continue;
+        const float xn = rnx[2 * row], en = rnx[2 * row + 1];
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++) {
+#pragma unroll
+          for (int e = 0; e < 2; e++) {
+            const int i = nt * 8 + tig * 2 + e;
+            const float eps = (qn[i] * (xn + en + cerr) + qn[32 + i] * (en + cerr) + ldexpf(qn[32 + i] * xn, -17) +
+                               ldexpf((qn[i] + qn[32 + i]) * (xn + en + 2.f * cnorm), -16)) *
+                              (1.f + ldexpf(1.f, -9));
+            if (i < ntok && !(acc[nt][h * 2 + e] + eps < th[nt][e])) fl |= 1u << (h * 8 + nt * 2 + e);
+          }
+        }
+      }
+      while (__any_sync(0xffffffffu, fl != 0u)) {
+        if (fl) {
+          const int b = __ffs(fl) - 1;
+          fl &= fl - 1u;
+          const int h = b >> 3, nt = (b >> 1) & 3, e = b & 1;
+          const int i = nt * 8 + tig * 2 + e;
+          const float v = dec_exact<M>(qrow + (int64_t)i * DIM, P.c0 + gq + h * 8, tok_cid, codes, rnorm,
+                                       codebooks, cent_f32, cent_bf16, bf16c != 0);
+          atomicMax(&emx[i], fkey(v));
+        }
+      }
+    } else {
+      // running max per query token over this thread's tokens (rows gq, gq + 8)
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        if (P.c0 + gq + h * 8 >= P.te) continue;
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++) {
+          mx[nt][0] = fmaxf(mx[nt][0], acc[nt][h * 2 + 0]);
+          mx[nt][1] = fmaxf(mx[nt][1], acc[nt][h * 2 + 1]);
+        }
       }
     }
-    if (!HN || NSLOT != P.slot) {
+    if (WIN && (!HN || NSLOT != P.slot)) {
+      // document complete: the exact maxima, summed per group of query tokens as k_refine does
+      __syncwarp();
+      if (lane < gq_n) {
+        const int i0 = lane * G, ng = min(G, ntok - i0);
+        float sum = 0.f;
+        for (int g = 0; g < ng; g++) sum += funkey(emx[i0 + g]);
+        part[((int64_t)q * ngroups + lane) * kd + P.slot] = sum;
+      }
+      __syncwarp();
+      emx[lane] = fkey(-INFINITY);
+    }
+    if (!WIN && (!HN || NSLOT != P.slot)) {
       // document complete: max over the lanes sharing tig, sum over query tokens, the bound
-      const int tig = lane & 3;
       float xm = xmax, em = exmax;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -346,12 +500,17 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
           v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 8));
           v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 16));
           const int i = nt * 8 + tig * 2 + e;
+          float ti = -INFINITY;
           if (i < ntok) {
             sum += v;
             // |<q^, x^> - <q, x>| <= ||e_q|| ||x|| + ||q^|| ||x^ - x||, ||x|| <= ||x^|| + ||x^ - x||
-            dl += qn[i] * (xm + em + cerr) + qn[32 + i] * (em + cerr) + ldexpf(qn[32 + i] * xm, -17) +
-                  ldexpf((qn[i] + qn[32 + i]) * (xm + em + 2.f * cnorm), -16);
+            const float ei = qn[i] * (xm + em + cerr) + qn[32 + i] * (em + cerr) + ldexpf(qn[32 + i] * xm, -17) +
+                             ldexpf((qn[i] + qn[32 + i]) * (xm + em + 2.f * cnorm), -16);
+            dl += ei;
+            // the token of the approximate maximum is within ei of it: no exact maximum lies below
+            ti = v - ei * (1.f + ldexpf(1.f, -9)) - ldexpf(fabsf(v) + 1.f, -20);
           }
+          if (gq == 0) thr[((int64_t)q * kd + P.slot) * 32 + i] = ti;
           mx[nt][e] = -INFINITY;
         }
       }
@@ -367,11 +526,11 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     }
   };
 
-  bool has = dec_next(pa, s_end, &s_next, cand_q, doc_off, D, sa_row, da_row, flags, lane);
+  bool has = dec_next(pa, s_end, &s_next, cand_q, doc_off, D, bad, flags, lane);
   if (has) issue(pa, 0, cwa, rha);
   while (has) {
     pb = pa;
-    bool hn = dec_next(pb, s_end, &s_next, cand_q, doc_off, D, sa_row, da_row, flags, lane);
+    bool hn = dec_next(pb, s_end, &s_next, cand_q, doc_off, D, bad, flags, lane);
     if (hn) {
       issue(pb, 1, cwb, rhb);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -382,7 +541,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     __syncwarp();
     if (!hn) break;
     pa = pb;
-    has = dec_next(pa, s_end, &s_next, cand_q, doc_off, D, sa_row, da_row, flags, lane);
+    has = dec_next(pa, s_end, &s_next, cand_q, doc_off, D, bad, flags, lane);
     if (has) {
       issue(pa, 0, cwa, rha);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -394,30 +553,46 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   }
 }
 
-template <int M>
+template <int M, bool WIN>
 static tachiom_status launch_refine_dec_m(const Index &ix, const float *queries, const int32_t *meta, int nq,
-                                          const int32_t *cand, int kd, float *sa, float *da, uint32_t *flags,
-                                          cudaStream_t s) {
-  constexpr int W = rd_warps<M>();
+                                          const int32_t *cand, int kd, float *sa, float *da, float *thr,
+                                          const int32_t *win_slot, float *part, uint32_t *flags, cudaStream_t s) {
+  constexpr int W = rd_warps<M, WIN>();
   static_assert(W >= 4, "decode refine: shared memory for fewer than 4 warps");
-  const size_t smem = (size_t)rd_fixed_bytes<M>() + (size_t)W * 2 * RD_TILE;
-  dim3 grid((kd + RD_DOCS_PER_CTA - 1) / RD_DOCS_PER_CTA, nq);
-  TCUDA(cudaFuncSetAttribute(k_refine_dec<M, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_refine_dec<M, W><<<grid, W * 32, smem, s>>>(queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes,
-                                                 ix.rnorm, ix.codebooks, ix.cent_bf16, ix.cerr_max,
-                                                 ix.cnorm_max + ix.cerr_max, sa, da, ix.D, flags);
+  const size_t smem = (size_t)rd_fixed_bytes<M>() + (size_t)W * rd_warp_bytes<WIN>();
+  // the window variant takes a query's whole (short) list in one CTA
+  dim3 grid(WIN ? 1 : (kd + RD_DOCS_PER_CTA - 1) / RD_DOCS_PER_CTA, nq);
+  TCUDA(cudaFuncSetAttribute(k_refine_dec<M, W, WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_refine_dec<M, W, WIN><<<grid, W * 32, smem, s>>>(
+      queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks, ix.cent_bf16,
+      ix.cent_f32, ix.cdtype == TACHIOM_DTYPE_BF16 ? 1 : 0, ix.cerr_max, ix.cnorm_max + ix.cerr_max, sa, da, thr,
+      win_slot, part, refine_groups(M), ix.D, flags);
   TLAUNCH();
   return TACHIOM_OK;
 }
 
 tachiom_status launch_refine_dec(const Index &ix, const float *queries, const int32_t *meta, int nq,
-                                 const int32_t *cand, int kd, float *sa, float *da, uint32_t *flags, cudaStream_t s) {
+                                 const int32_t *cand, int kd, float *sa, float *da, float *thr, uint32_t *flags,
+                                 cudaStream_t s) {
   if (nq <= 0) return TACHIOM_OK;
   TPROF("refine_dec", s);
   switch (ix.M) {
-    case 8: return launch_refine_dec_m<8>(ix, queries, meta, nq, cand, kd, sa, da, flags, s);
-    case 16: return launch_refine_dec_m<16>(ix, queries, meta, nq, cand, kd, sa, da, flags, s);
-    case 32: return launch_refine_dec_m<32>(ix, queries, meta, nq, cand, kd, sa, da, flags, s);
+    case 8: return launch_refine_dec_m<8, false>(ix, queries, meta, nq, cand, kd, sa, da, thr, nullptr, nullptr, flags, s);
+    case 16: return launch_refine_dec_m<16, false>(ix, queries, meta, nq, cand, kd, sa, da, thr, nullptr, nullptr, flags, s);
+    case 32: return launch_refine_dec_m<32, false>(ix, queries, meta, nq, cand, kd, sa, da, thr, nullptr, nullptr, flags, s);
+  }
+  return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
+}
+
+tachiom_status launch_refine_dec_win(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                     const int32_t *win, const int32_t *win_slot, int kd, float *thr, float *part,
+                                     uint32_t *flags, cudaStream_t s) {
+  if (nq <= 0) return TACHIOM_OK;
+  TPROF("refine_win", s);
+  switch (ix.M) {
+    case 8: return launch_refine_dec_m<8, true>(ix, queries, meta, nq, win, kd, nullptr, nullptr, thr, win_slot, part, flags, s);
+    case 16: return launch_refine_dec_m<16, true>(ix, queries, meta, nq, win, kd, nullptr, nullptr, thr, win_slot, part, flags, s);
+    case 32: return launch_refine_dec_m<32, true>(ix, queries, meta, nq, win, kd, nullptr, nullptr, thr, win_slot, part, flags, s);
   }
   return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
 }

@@ -416,7 +416,8 @@ __device__ __forceinline__ void window_bounds(float s, float e, float *lo, float
 
 __global__ void __launch_bounds__(1024)
 k_refine_window_b(const int32_t *__restrict__ meta, int nq, const int32_t *__restrict__ cand, int kd,
-                  const float *__restrict__ sa, const float *__restrict__ da, int32_t *__restrict__ win) {
+                  const float *__restrict__ sa, const float *__restrict__ da, int32_t *__restrict__ win,
+                  int32_t *__restrict__ win_slot) {
   extern __shared__ __align__(16) uint64_t wsm2[];
   __shared__ float s_lim;
   const int q = blockIdx.x;
@@ -432,7 +433,7 @@ k_refine_window_b(const int32_t *__restrict__ meta, int nq, const int32_t *__res
         if (d >= 0 && s != -INFINITY) {
           float lo, up;
           window_bounds(s, da[(int64_t)q * kd + i], &lo, &up);
-          v = comp_key(pass == 0 ? lo : up, d);
+          v = comp_key(pass == 0 ? lo : up, i);  // the slot rides in the key: win_slot below
         }
       }
       wsm2[i] = v;
@@ -450,17 +451,21 @@ k_refine_window_b(const int32_t *__restrict__ meta, int nq, const int32_t *__res
   const float lim = s_lim;
   for (int i = threadIdx.x; i < kd; i += blockDim.x) {
     const uint64_t v = i < np ? wsm2[i] : 0ull;
-    win[(int64_t)q * kd + i] = (v && comp_score(v) >= lim) ? comp_id(v) : -1;
+    const bool in = v && comp_score(v) >= lim;
+    const int32_t slot = in ? comp_id(v) : -1;
+    win[(int64_t)q * kd + i] = in ? cand[(int64_t)q * kd + slot] : -1;
+    win_slot[(int64_t)q * kd + i] = slot;
   }
 }
 
 tachiom_status launch_refine_window_b(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
-                                      const float *sa, const float *da, int32_t *win, cudaStream_t s) {
+                                      const float *sa, const float *da, int32_t *win, int32_t *win_slot,
+                                      cudaStream_t s) {
   if (nq <= 0) return TACHIOM_OK;
   TPROF("refine_window", s);
   const size_t smem = (size_t)next_pow2(std::max(kd, 2)) * 8;
   TCUDA(cudaFuncSetAttribute(k_refine_window_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_refine_window_b<<<nq, 1024, smem, s>>>(meta, nq, cand, kd, sa, da, win);
+  k_refine_window_b<<<nq, 1024, smem, s>>>(meta, nq, cand, kd, sa, da, win, win_slot);
   TLAUNCH();
   return TACHIOM_OK;
 }

@@ -115,6 +115,8 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   AL(w->d_ncand, nq * 4);
   AL(w->d_part, nq * groups * kd * 4);
   AL(w->d_win, nq * kd * 4);
+  AL(w->d_win_slot, nq * kd * 4);
+  AL(w->d_thr, nq * kd * 32 * 4);
   AL(w->d_out_ids, nq * kd * 4);
   AL(w->d_out_s, nq * kd * 4);
 #undef AL
@@ -169,7 +171,7 @@ static Plan make_plan(const Index &ix, int rows, int kc, int precision, int plan
   splits = (int)std::min<int64_t>(splits, max_splits);
   p.capout = kc + 64;
   splits = std::min(splits, std::max(1, 16384 / p.capout));
-  const int forced = plan_id >= 0 ? ((plan_id >> 4) & 0xfffff) : 0;
+  const int forced = plan_id >= 0 ? ((plan_id >> 4) & 0xfffff) : 0;  // bits 4-23
   if (forced > 0) {
     // an explicit slice count of the FP32 scan (autotuner)
     splits = std::max(1, std::min(forced, (int)std::min<int64_t>(max_splits, 16384 / p.capout)));
@@ -263,8 +265,11 @@ static bool use_tc(const tachiom_search_params *p) {
 //   bits 4-23 slices of the FP32 scan (0: default)
 //   bit 24    step (b): the token-serial gather for every range (default: the counting-sort
 //             gather, token-serial only for the ranges whose entries overflow its buffers)
+//   bit 25    step (c), decode path: the window rescored over every (query token, document
+//             token) pair in FP32 (default: only the pairs that can hold a maximum)
 enum { SCAN_DEFAULT = 0, SCAN_TC1 = 1, SCAN_TC2 = 2, SCAN_F32 = 3 };
 constexpr int32_t PLAN_GATHER_TOK = 1 << 24;
+constexpr int32_t PLAN_WINDOW_ALL = 1 << 25;
 static bool gather_tok_only(const tachiom_search_params *p) { return p->plan_id >= 0 && (p->plan_id & PLAN_GATHER_TOK); }
 enum { REFINE_DEFAULT = 0, REFINE_TC = 1, REFINE_F32 = 2, REFINE_DEC = 3 };
 
@@ -345,11 +350,21 @@ static tachiom_status run_refine(Index *ix, Workspace *w, const tachiom_search_p
   const int rk = refine_kind(p);
   if (rk == REFINE_DEC) {
     float *sa = w->d_part, *da = w->d_part + (int64_t)nq * kd;  // consumed before the FP32 pass reuses d_part
-    if ((st = launch_refine_dec(*ix, queries, w->d_meta, nq, cand, kd, sa, da, w->d_flags, stream))) return st;
-    if ((st = launch_refine_window_b(*ix, w->d_meta, nq, cand, kd, sa, da, w->d_win, stream))) return st;
-    // the window is short: one CTA per (query, document), same FP32 numbers as k_refine
-    if ((st = launch_refine_win(*ix, queries, w->d_meta, nq, w->d_win, kd, w->d_part, w->d_flags, stream)))
+    if ((st = launch_refine_dec(*ix, queries, w->d_meta, nq, cand, kd, sa, da, w->d_thr, w->d_flags, stream)))
       return st;
+    if ((st = launch_refine_window_b(*ix, w->d_meta, nq, cand, kd, sa, da, w->d_win, w->d_win_slot, stream)))
+      return st;
+    if (p->plan_id >= 0 && (p->plan_id & PLAN_WINDOW_ALL)) {
+      // every pair of the window's documents in FP32
+      if ((st = launch_refine_win(*ix, queries, w->d_meta, nq, w->d_win, kd, w->d_part, w->d_flags, stream)))
+        return st;
+    } else {
+      // the window's documents: the decode pass again, and the FP32 path's numbers for the pairs
+      // that can hold a maximum
+      if ((st = launch_refine_dec_win(*ix, queries, w->d_meta, nq, w->d_win, w->d_win_slot, kd, w->d_thr,
+                                      w->d_part, w->d_flags, stream)))
+        return st;
+    }
     return launch_final_topk(*ix, w->d_meta, nq, w->d_win, kd, w->d_part, out_ids, out_s, stream);
   } else if (rk == REFINE_TC) {
     if ((st = launch_refine_tc(*ix, queries, w->d_meta, nq, cand, kd, w->d_part, w->d_flags, stream))) return st;
@@ -652,7 +667,8 @@ extern "C" tachiom_status tachiom_debug_refine_scores(tachiom_index *index, cons
   if (use_tc(params) && refine_kind(params) == REFINE_DEC) {
     // approximate S and its per-document bound
     float *bounds = d_bounds ? d_bounds : w->d_part;
-    return launch_refine_dec(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, d_scores, bounds, w->d_flags, s);
+    return launch_refine_dec(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, d_scores, bounds, w->d_thr, w->d_flags,
+                             s);
   } else if (use_tc(params)) {
     if ((st = launch_refine_tc(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, w->d_part, w->d_flags, s))) return st;
   } else {

@@ -161,6 +161,8 @@ struct Workspace {
   int32_t *d_ncand = nullptr;          // [B]
   float *d_part = nullptr;             // [B x groups x kd] refine partial sums
   int32_t *d_win = nullptr;            // [B x kd] FP32 rescoring window of the tensor-core refine
+  int32_t *d_win_slot = nullptr;       // [B x kd] each window entry's candidate slot
+  float *d_thr = nullptr;              // [B x kd x 32] per (slot, query token) thresholds of the window pass
   int32_t *d_out_ids = nullptr;        // staging for search_host
   float *d_out_s = nullptr;
   uint32_t *d_flags = nullptr;         // status word
@@ -245,9 +247,14 @@ int refine_groups(int M);
 tachiom_status launch_refine_tc(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                 const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s);
 tachiom_status launch_refine_dec(const Index &ix, const float *queries, const int32_t *meta, int nq,
-                                 const int32_t *cand, int kd, float *sa, float *da, uint32_t *flags, cudaStream_t s);
+                                 const int32_t *cand, int kd, float *sa, float *da, float *thr, uint32_t *flags,
+                                 cudaStream_t s);
+tachiom_status launch_refine_dec_win(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                     const int32_t *win, const int32_t *win_slot, int kd, float *thr, float *part,
+                                     uint32_t *flags, cudaStream_t s);
 tachiom_status launch_refine_window_b(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
-                                      const float *sa, const float *da, int32_t *win, cudaStream_t s);
+                                      const float *sa, const float *da, int32_t *win, int32_t *win_slot,
+                                      cudaStream_t s);
 tachiom_status launch_refine_sum(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
                                  const float *part, float *out, cudaStream_t s);
 tachiom_status launch_refine_window(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
