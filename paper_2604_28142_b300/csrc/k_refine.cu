@@ -286,7 +286,8 @@ k_refine_win(const float *__restrict__ queries, const int32_t *__restrict__ meta
              const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
              const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
              const float *__restrict__ cent_f32, const __nv_bfloat16 *__restrict__ cent_bf16,
-             float *__restrict__ part, int ngroups, int64_t D, uint32_t *__restrict__ flags) {
+             const int32_t *__restrict__ only, float *__restrict__ part, int ngroups, int64_t D,
+             uint32_t *__restrict__ flags) {
   constexpr int G = 128 / M;
   constexpr int DS = 128 / M;
   constexpr int RB = BF16C ? DIM * 2 : DIM * 4;  // bytes per centroid row
@@ -302,6 +303,15 @@ k_refine_win(const float *__restrict__ queries, const int32_t *__restrict__ meta
   const int q = blockIdx.y;
   const int ntok = meta[3 * nq + 2 + q];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (only) {
+    // nothing listed among this CTA's slots (the usual case): leave before any other load
+    int any = 0;
+    for (int slot = blockIdx.x + tid * gridDim.x; slot < kd && !any; slot += blockDim.x * gridDim.x) {
+      if (cand[(int64_t)q * kd + slot] < 0) break;
+      any = only[(int64_t)q * kd + slot];
+    }
+    if (!__syncthreads_or(any)) return;
+  }
   // this lane's query token, in registers
   float qv[DIM];
   {
@@ -346,6 +356,7 @@ k_refine_win(const float *__restrict__ queries, const int32_t *__restrict__ meta
   for (int slot = blockIdx.x; slot < kd; slot += gridDim.x) {
     const int32_t d = cand[(int64_t)q * kd + slot];
     if (d < 0) break;
+    if (only && !only[(int64_t)q * kd + slot]) continue;  // only the listed documents
     if (d >= D) {
       if (tid == 0) atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
       if (tid < gq) part[((int64_t)q * ngroups + tid) * kd + slot] = 0.f;
@@ -449,21 +460,21 @@ k_refine_win(const float *__restrict__ queries, const int32_t *__restrict__ meta
 
 template <int M>
 static tachiom_status launch_refine_win_m(const Index &ix, const float *queries, const int32_t *meta, int nq,
-                                          const int32_t *cand, int kd, float *part, uint32_t *flags,
-                                          cudaStream_t s) {
+                                          const int32_t *cand, int kd, const int32_t *only, float *part,
+                                          uint32_t *flags, cudaStream_t s) {
   dim3 grid(std::min(RW_CTAS, kd), nq);
   if (ix.cdtype == TACHIOM_DTYPE_BF16) {
     TCUDA(cudaFuncSetAttribute(k_refine_win<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)rw_smem<true>()));
     k_refine_win<M, true><<<grid, RW_THREADS, rw_smem<true>(), s>>>(
         queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks, ix.cent_f32,
-        ix.cent_bf16, part, refine_groups(M), ix.D, flags);
+        ix.cent_bf16, only, part, refine_groups(M), ix.D, flags);
   } else {
     TCUDA(cudaFuncSetAttribute(k_refine_win<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)rw_smem<false>()));
     k_refine_win<M, false><<<grid, RW_THREADS, rw_smem<false>(), s>>>(
         queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks, ix.cent_f32,
-        ix.cent_bf16, part, refine_groups(M), ix.D, flags);
+        ix.cent_bf16, only, part, refine_groups(M), ix.D, flags);
   }
   TLAUNCH();
   return TACHIOM_OK;
@@ -471,12 +482,18 @@ static tachiom_status launch_refine_win_m(const Index &ix, const float *queries,
 
 tachiom_status launch_refine_win(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                  const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s) {
+  return launch_refine_win_only(ix, queries, meta, nq, cand, kd, nullptr, part, flags, s);
+}
+
+tachiom_status launch_refine_win_only(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                      const int32_t *cand, int kd, const int32_t *only, float *part,
+                                      uint32_t *flags, cudaStream_t s) {
   if (nq <= 0) return TACHIOM_OK;
-  TPROF("refine_win", s);
+  TPROF(only ? "refine_win_fp32" : "refine_win", s);
   switch (ix.M) {
-    case 8: return launch_refine_win_m<8>(ix, queries, meta, nq, cand, kd, part, flags, s);
-    case 16: return launch_refine_win_m<16>(ix, queries, meta, nq, cand, kd, part, flags, s);
-    case 32: return launch_refine_win_m<32>(ix, queries, meta, nq, cand, kd, part, flags, s);
+    case 8: return launch_refine_win_m<8>(ix, queries, meta, nq, cand, kd, only, part, flags, s);
+    case 16: return launch_refine_win_m<16>(ix, queries, meta, nq, cand, kd, only, part, flags, s);
+    case 32: return launch_refine_win_m<32>(ix, queries, meta, nq, cand, kd, only, part, flags, s);
   }
   return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
 }

@@ -82,9 +82,9 @@ struct DecPos {
 // bad(slot, empty): answer a slot whose document is out of range (empty = false) or has no
 // tokens (empty = true); called by lane 0
 template <typename BadFn>
-__device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int *s_next, const int32_t *cand_q,
-                                         const int64_t *doc_off, int64_t D, BadFn bad, uint32_t *flags,
-                                         int lane) {
+__device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int stride, int off, int *s_next,
+                                         const int32_t *cand_q, const int64_t *doc_off, int64_t D, BadFn bad,
+                                         uint32_t *flags, int lane) {
   if (p.c0 + 16 < p.te) {
     p.c0 += 16;
     return true;
@@ -92,7 +92,7 @@ __device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int *s_next, cons
   for (;;) {
     int slot = 0;
     if (lane == 0) slot = atomicAdd(s_next, 1);
-    slot = __shfl_sync(0xffffffffu, slot, 0);
+    slot = __shfl_sync(0xffffffffu, slot, 0) * stride + off;  // the CTA's share of the slots
     if (slot >= s_end) return false;
     p.slot = slot;
     const int32_t d = cand_q[slot];
@@ -125,14 +125,23 @@ __device__ __forceinline__ float dec_exact(const float *__restrict__ qi, int64_t
                                            const float *__restrict__ cent_f32,
                                            const __nv_bfloat16 *__restrict__ cent_bf16, bool bf16c) {
   constexpr int DS = 128 / M;
+  // first the token's centroid id, codes and norm, then every row and codeword load at once
   const int32_t j = tok_cid[t];
-  float ct = 0.f;
+  uint8_t c8[M];
+#pragma unroll
+  for (int u = 0; u < M / 8; u++)
+    *reinterpret_cast<uint2 *>(c8 + 8 * u) = *reinterpret_cast<const uint2 *>(codes + t * M + 8 * u);
+  const float rho = __half2float(__ushort_as_half(rnorm[t]));
   const float4 *q4 = reinterpret_cast<const float4 *>(qi);
+  float ct = 0.f;
   if (bf16c) {
     const uint4 *crow = reinterpret_cast<const uint4 *>(cent_bf16 + (int64_t)j * DIM);
-#pragma unroll 4
+    uint4 cr[DIM / 8];
+#pragma unroll
+    for (int k8 = 0; k8 < DIM / 8; k8++) cr[k8] = crow[k8];
+#pragma unroll
     for (int k8 = 0; k8 < DIM / 8; k8++) {
-      const uint4 u = crow[k8];
+      const uint4 u = cr[k8];
       const float4 qa = q4[2 * k8], qb = q4[2 * k8 + 1];
       ct = fmaf(qa.x, __uint_as_float(u.x << 16), ct);
       ct = fmaf(qa.y, __uint_as_float(u.x & 0xffff0000u), ct);
@@ -145,34 +154,57 @@ __device__ __forceinline__ float dec_exact(const float *__restrict__ qi, int64_t
     }
   } else {
     const float4 *crow = reinterpret_cast<const float4 *>(cent_f32 + (int64_t)j * DIM);
-#pragma unroll 4
-    for (int k4 = 0; k4 < DIM / 4; k4++) {
-      const float4 c = crow[k4], qa = q4[k4];
-      ct = fmaf(qa.x, c.x, ct);
-      ct = fmaf(qa.y, c.y, ct);
-      ct = fmaf(qa.z, c.z, ct);
-      ct = fmaf(qa.w, c.w, ct);
+#pragma unroll
+    for (int hh = 0; hh < 2; hh++) {
+      float4 cr[DIM / 8];
+#pragma unroll
+      for (int k4 = 0; k4 < DIM / 8; k4++) cr[k4] = crow[hh * (DIM / 8) + k4];
+#pragma unroll
+      for (int k4 = 0; k4 < DIM / 8; k4++) {
+        const float4 c = cr[k4], qa = q4[hh * (DIM / 8) + k4];
+        ct = fmaf(qa.x, c.x, ct);
+        ct = fmaf(qa.y, c.y, ct);
+        ct = fmaf(qa.z, c.z, ct);
+        ct = fmaf(qa.w, c.w, ct);
+      }
     }
   }
+  // the residual: the subspaces' codewords in two batches of 64 floats
   float rs = 0.f;
-  const uint8_t *c8 = codes + t * M;
-#pragma unroll 4
-  for (int m = 0; m < M; m++) {
-    const float *w = codebooks + ((int64_t)m * 256 + c8[m]) * DS;
-    float a = 0.f;
 #pragma unroll
-    for (int u = 0; u < DS; u++) a = fmaf(qi[m * DS + u], w[u], a);
-    rs += a;
+  for (int hh = 0; hh < 2; hh++) {
+    float w[DIM / 2];
+#pragma unroll
+    for (int mm = 0; mm < M / 2; mm++) {
+      const int m = hh * (M / 2) + mm;
+      const float4 *src = reinterpret_cast<const float4 *>(codebooks + ((int64_t)m * 256 + c8[m]) * DS);
+#pragma unroll
+      for (int u4 = 0; u4 < DS / 4; u4++) {
+        const float4 v = src[u4];
+        w[mm * DS + 4 * u4] = v.x; w[mm * DS + 4 * u4 + 1] = v.y;
+        w[mm * DS + 4 * u4 + 2] = v.z; w[mm * DS + 4 * u4 + 3] = v.w;
+      }
+    }
+#pragma unroll
+    for (int mm = 0; mm < M / 2; mm++) {
+      const int m = hh * (M / 2) + mm;
+      float a = 0.f;
+#pragma unroll
+      for (int u = 0; u < DS; u++) a = fmaf(qi[m * DS + u], w[mm * DS + u], a);
+      rs += a;
+    }
   }
-  return fmaf(__half2float(__ushort_as_half(rnorm[t])), rs, ct);
+  return fmaf(rho, rs, ct);
 }
 
 // !WIN: sa[q][slot] = approximate S, da[q][slot] = its bound Delta_d, and per query token i
 //       thr[q][slot][i] = (approximate max_t v_it) - (the bound of its error); a token t whose
 //       approximate v_it plus its own bound is below thr cannot hold the exact maximum.
 // WIN:  the same pass over the compacted window list cand (first id < 0 ends it): the pairs
-//       (i, t) that pass the test against thr are scored exactly (dec_exact) and their maximum
-//       per query token gives the FP32 path's group partial sums part[q][group][slot].
+//       (i, t) that pass the test against thr are appended to the list wl ({q * kd + slot,
+//       (t - first token) << 5 | i}) for k_dec_exact_pairs; emx[q][slot][i] (the exact maxima
+//       that kernel forms) starts at -inf; a document whose pairs do not fit the list is
+//       marked in wovf[q][slot] for the all-pairs FP32 kernel.
 template <int M, int WARPS, bool WIN>
 __global__ void __launch_bounds__(WARPS * 32, 1)
 k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta, int nq,
@@ -181,7 +213,8 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
              const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
              const __nv_bfloat16 *__restrict__ cent_bf16, const float *__restrict__ cent_f32, int bf16c,
              float cerr, float cnorm, float *__restrict__ sa, float *__restrict__ da, float *__restrict__ thr,
-             const int32_t *__restrict__ win_slot, float *__restrict__ part, int ngroups, int64_t D,
+             const int32_t *__restrict__ win_slot, float *__restrict__ part, int ngroups, int2 *__restrict__ wl,
+             int *__restrict__ wl_n, int wl_cap, uint32_t *__restrict__ emx, int32_t *__restrict__ wovf, int64_t D,
              uint32_t *__restrict__ flags) {
   constexpr int DS = 128 / M;
   constexpr int NT = WARPS * 32;
@@ -261,14 +294,14 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
       qn[32 + i] = sqrtf(h2) * (1.f + ldexpf(1.f, -10));
     }
   }
-  if (tid == 0) s_next = s_begin;
+  // the window variant's CTAs of a query take every gridDim.x-th slot
+  const int stride = WIN ? (int)gridDim.x : 1, off = WIN ? (int)blockIdx.x : 0;
+  if (tid == 0) s_next = WIN ? 0 : s_begin;
   __syncthreads();
 
   unsigned char *wt = tiles + warp * 2 * RD_TILE;
-  // window variant: this warp's chunk row norms (xn, en per row) and exact maxima per query token
+  // window variant: this warp's chunk row norms (xn, en per row)
   float *rnx = reinterpret_cast<float *>(tiles + WARPS * 2 * RD_TILE + warp * 256);  // [16][2]
-  uint32_t *emx = reinterpret_cast<uint32_t *>(rnx + 32);                           // [32] fkey
-  if (WIN) emx[lane] = fkey(-INFINITY);
   const int G = 128 / M;                   // query tokens per group of the FP32 path's partial sums
   const int gq_n = (ntok + G - 1) / G;     // groups of this query
   const uint32_t wt_s = (uint32_t)__cvta_generic_to_shared(wt);
@@ -427,6 +460,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
           th[nt][0] = tq[nt * 8 + tig * 2];
           th[nt][1] = tq[nt * 8 + tig * 2 + 1];
         }
+        emx[((int64_t)q * kd + P.slot) * 32 + lane] = fkey(-INFINITY);
       }
       // pairs whose approximate value plus its own bound reaches thr: scored exactly
       uint32_t fl = 0u;
@@ -447,15 +481,30 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
           }
         }
       }
-      while (__any_sync(0xffffffffu, fl != 0u)) {
-        if (fl) {
-          const int b = __ffs(fl) - 1;
-          fl &= fl - 1u;
-          const int h = b >> 3, nt = (b >> 1) & 3, e = b & 1;
-          const int i = nt * 8 + tig * 2 + e;
-          const float v = dec_exact<M>(qrow + (int64_t)i * DIM, P.c0 + gq + h * 8, tok_cid, codes, rnorm,
-                                       codebooks, cent_f32, cent_bf16, bf16c != 0);
-          atomicMax(&emx[i], fkey(v));
+      // append them to the list: a warp-wide scan of the counts, one atomic per warp
+      const int nf = __popc(fl);
+      int pre = nf;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += y;
+      }
+      const int tot = __shfl_sync(0xffffffffu, pre, 31);
+      if (tot > 0) {
+        int base = 0;
+        if (lane == 31) base = atomicAdd(wl_n, tot);
+        base = __shfl_sync(0xffffffffu, base, 31) + pre - nf;
+        if (base + nf > wl_cap) {
+          if (nf) wovf[(int64_t)q * kd + P.slot] = 1;  // the list is full: this document goes to the FP32 kernel
+        } else {
+          const int sid = q * kd + P.slot;
+          while (fl) {
+            const int b = __ffs(fl) - 1;
+            fl &= fl - 1u;
+            const int h = b >> 3, nt = (b >> 1) & 3, e = b & 1;
+            const int i = nt * 8 + tig * 2 + e;
+            wl[base++] = make_int2(sid, (int)((P.c0 + gq + h * 8 - P.tb) << 5) | i);
+          }
         }
       }
     } else {
@@ -469,18 +518,6 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
           mx[nt][1] = fmaxf(mx[nt][1], acc[nt][h * 2 + 1]);
         }
       }
-    }
-    if (WIN && (!HN || NSLOT != P.slot)) {
-      // document complete: the exact maxima, summed per group of query tokens as k_refine does
-      __syncwarp();
-      if (lane < gq_n) {
-        const int i0 = lane * G, ng = min(G, ntok - i0);
-        float sum = 0.f;
-        for (int g = 0; g < ng; g++) sum += funkey(emx[i0 + g]);
-        part[((int64_t)q * ngroups + lane) * kd + P.slot] = sum;
-      }
-      __syncwarp();
-      emx[lane] = fkey(-INFINITY);
     }
     if (!WIN && (!HN || NSLOT != P.slot)) {
       // document complete: max over the lanes sharing tig, sum over query tokens, the bound
@@ -526,11 +563,11 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     }
   };
 
-  bool has = dec_next(pa, s_end, &s_next, cand_q, doc_off, D, bad, flags, lane);
+  bool has = dec_next(pa, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane);
   if (has) issue(pa, 0, cwa, rha);
   while (has) {
     pb = pa;
-    bool hn = dec_next(pb, s_end, &s_next, cand_q, doc_off, D, bad, flags, lane);
+    bool hn = dec_next(pb, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane);
     if (hn) {
       issue(pb, 1, cwb, rhb);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -541,7 +578,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     __syncwarp();
     if (!hn) break;
     pa = pb;
-    has = dec_next(pa, s_end, &s_next, cand_q, doc_off, D, bad, flags, lane);
+    has = dec_next(pa, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane);
     if (has) {
       issue(pa, 0, cwa, rha);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -553,21 +590,79 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   }
 }
 
+// One thread per listed pair: the FP32 path's value of (query token i, document token t)
+// (dec_exact), max-reduced into emx[q][slot][i] (order-preserving keys).
+template <int M>
+__global__ void __launch_bounds__(256)
+k_dec_exact_pairs(const float *__restrict__ queries, const int32_t *__restrict__ meta, int kd,
+                  const int32_t *__restrict__ win, const int64_t *__restrict__ doc_off,
+                  const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
+                  const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
+                  const float *__restrict__ cent_f32, const __nv_bfloat16 *__restrict__ cent_bf16, int bf16c,
+                  const int2 *__restrict__ wl, const int *__restrict__ wl_n, int wl_cap, uint32_t *__restrict__ emx) {
+  const int n = min(*wl_n, wl_cap);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int2 e = wl[k];
+    const int sid = e.x, q = sid / kd, i = e.y & 31;
+    const int64_t t = doc_off[win[sid]] + (e.y >> 5);
+    const float v = dec_exact<M>(queries + ((int64_t)meta[q] + i) * DIM, t, tok_cid, codes, rnorm, codebooks,
+                                 cent_f32, cent_bf16, bf16c != 0);
+    atomicMax(&emx[(int64_t)sid * 32 + i], fkey(v));
+  }
+}
+
+// Per window document: the exact maxima summed per group of query tokens, as k_refine forms
+// part[q][group][slot]. Empty and out-of-range documents were answered by the window pass;
+// a document marked in wovf is left to the all-pairs FP32 kernel.
+__global__ void __launch_bounds__(256)
+k_win_sums(const int32_t *__restrict__ meta, int nq, const int32_t *__restrict__ win, int kd,
+           const int64_t *__restrict__ doc_off, int64_t D, const uint32_t *__restrict__ emx,
+           const int32_t *__restrict__ wovf, int G, int ngroups, float *__restrict__ part) {
+  const int q = blockIdx.y;
+  const int ntok = meta[3 * nq + 2 + q];
+  const int gq_n = (ntok + G - 1) / G;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < kd * gq_n; x += gridDim.x * blockDim.x) {
+    const int slot = x / gq_n, grp = x % gq_n;
+    const int64_t sid = (int64_t)q * kd + slot;
+    const int32_t d = win[sid];
+    if (d < 0) continue;
+    if (d >= D || doc_off[d + 1] == doc_off[d] || wovf[sid]) continue;
+    const int i0 = grp * G, ng = min(G, ntok - i0);
+    float sum = 0.f;
+    for (int g = 0; g < ng; g++) sum += funkey(emx[sid * 32 + i0 + g]);
+    part[((int64_t)q * ngroups + grp) * kd + slot] = sum;
+  }
+}
+
 template <int M, bool WIN>
 static tachiom_status launch_refine_dec_m(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                           const int32_t *cand, int kd, float *sa, float *da, float *thr,
-                                          const int32_t *win_slot, float *part, uint32_t *flags, cudaStream_t s) {
+                                          const int32_t *win_slot, float *part, const WinScratch *ws,
+                                          uint32_t *flags, cudaStream_t s) {
   constexpr int W = rd_warps<M, WIN>();
   static_assert(W >= 4, "decode refine: shared memory for fewer than 4 warps");
   const size_t smem = (size_t)rd_fixed_bytes<M>() + (size_t)W * rd_warp_bytes<WIN>();
   // the window variant takes a query's whole (short) list in one CTA
-  dim3 grid(WIN ? 1 : (kd + RD_DOCS_PER_CTA - 1) / RD_DOCS_PER_CTA, nq);
+  dim3 grid(WIN ? 2 : (kd + RD_DOCS_PER_CTA - 1) / RD_DOCS_PER_CTA, nq);
   TCUDA(cudaFuncSetAttribute(k_refine_dec<M, W, WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_refine_dec<M, W, WIN><<<grid, W * 32, smem, s>>>(
       queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks, ix.cent_bf16,
       ix.cent_f32, ix.cdtype == TACHIOM_DTYPE_BF16 ? 1 : 0, ix.cerr_max, ix.cnorm_max + ix.cerr_max, sa, da, thr,
-      win_slot, part, refine_groups(M), ix.D, flags);
+      win_slot, part, refine_groups(M), ws ? ws->wl : nullptr, ws ? ws->wl_n : nullptr, ws ? ws->wl_cap : 0,
+      ws ? ws->emx : nullptr, ws ? ws->wovf : nullptr, ix.D, flags);
   TLAUNCH();
+  if (WIN) {
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
+    k_dec_exact_pairs<M><<<sms * 4, 256, 0, s>>>(queries, meta, kd, cand, ix.doc_off, ix.tok_cid, ix.codes,
+                                                 ix.rnorm, ix.codebooks, ix.cent_f32, ix.cent_bf16,
+                                                 ix.cdtype == TACHIOM_DTYPE_BF16 ? 1 : 0, ws->wl, ws->wl_n,
+                                                 ws->wl_cap, ws->emx);
+    TLAUNCH();
+    k_win_sums<<<dim3((kd * 4 + 255) / 256, nq), 256, 0, s>>>(meta, nq, cand, kd, ix.doc_off, ix.D, ws->emx, ws->wovf,
+                                                              128 / M, refine_groups(M), part);
+    TLAUNCH();
+  }
   return TACHIOM_OK;
 }
 
@@ -577,22 +672,24 @@ tachiom_status launch_refine_dec(const Index &ix, const float *queries, const in
   if (nq <= 0) return TACHIOM_OK;
   TPROF("refine_dec", s);
   switch (ix.M) {
-    case 8: return launch_refine_dec_m<8, false>(ix, queries, meta, nq, cand, kd, sa, da, thr, nullptr, nullptr, flags, s);
-    case 16: return launch_refine_dec_m<16, false>(ix, queries, meta, nq, cand, kd, sa, da, thr, nullptr, nullptr, flags, s);
-    case 32: return launch_refine_dec_m<32, false>(ix, queries, meta, nq, cand, kd, sa, da, thr, nullptr, nullptr, flags, s);
+    case 8: return launch_refine_dec_m<8, false>(ix, queries, meta, nq, cand, kd, sa, da, thr, nullptr, nullptr, nullptr, flags, s);
+    case 16: return launch_refine_dec_m<16, false>(ix, queries, meta, nq, cand, kd, sa, da, thr, nullptr, nullptr, nullptr, flags, s);
+    case 32: return launch_refine_dec_m<32, false>(ix, queries, meta, nq, cand, kd, sa, da, thr, nullptr, nullptr, nullptr, flags, s);
   }
   return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
 }
 
 tachiom_status launch_refine_dec_win(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                      const int32_t *win, const int32_t *win_slot, int kd, float *thr, float *part,
-                                     uint32_t *flags, cudaStream_t s) {
+                                     const WinScratch &ws, uint32_t *flags, cudaStream_t s) {
   if (nq <= 0) return TACHIOM_OK;
   TPROF("refine_win", s);
+  TCUDA(cudaMemsetAsync(ws.wl_n, 0, sizeof(int), s));
+  TCUDA(cudaMemsetAsync(ws.wovf, 0, (size_t)nq * kd * sizeof(int32_t), s));
   switch (ix.M) {
-    case 8: return launch_refine_dec_m<8, true>(ix, queries, meta, nq, win, kd, nullptr, nullptr, thr, win_slot, part, flags, s);
-    case 16: return launch_refine_dec_m<16, true>(ix, queries, meta, nq, win, kd, nullptr, nullptr, thr, win_slot, part, flags, s);
-    case 32: return launch_refine_dec_m<32, true>(ix, queries, meta, nq, win, kd, nullptr, nullptr, thr, win_slot, part, flags, s);
+    case 8: return launch_refine_dec_m<8, true>(ix, queries, meta, nq, win, kd, nullptr, nullptr, thr, win_slot, part, &ws, flags, s);
+    case 16: return launch_refine_dec_m<16, true>(ix, queries, meta, nq, win, kd, nullptr, nullptr, thr, win_slot, part, &ws, flags, s);
+    case 32: return launch_refine_dec_m<32, true>(ix, queries, meta, nq, win, kd, nullptr, nullptr, thr, win_slot, part, &ws, flags, s);
   }
   return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
 }

@@ -117,6 +117,10 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   AL(w->d_win, nq * kd * 4);
   AL(w->d_win_slot, nq * kd * 4);
   AL(w->d_thr, nq * kd * 32 * 4);
+  AL(w->d_wl, nq * (int64_t)WL_PER_QUERY * 8);
+  AL(w->d_wl_n, 16);
+  AL(w->d_emx, nq * kd * 32 * 4);
+  AL(w->d_wovf, nq * kd * 4);
   AL(w->d_out_ids, nq * kd * 4);
   AL(w->d_out_s, nq * kd * 4);
 #undef AL
@@ -361,8 +365,14 @@ static tachiom_status run_refine(Index *ix, Workspace *w, const tachiom_search_p
     } else {
       // the window's documents: the decode pass again, and the FP32 path's numbers for the pairs
       // that can hold a maximum
+      WinScratch ws{w->d_wl, w->d_wl_n, (int)std::min<int64_t>((int64_t)nq * WL_PER_QUERY, INT32_MAX), w->d_emx,
+                    w->d_wovf};
       if ((st = launch_refine_dec_win(*ix, queries, w->d_meta, nq, w->d_win, w->d_win_slot, kd, w->d_thr,
-                                      w->d_part, w->d_flags, stream)))
+                                      w->d_part, ws, w->d_flags, stream)))
+        return st;
+      // the documents whose pairs did not fit the list (normally none): every pair in FP32
+      if ((st = launch_refine_win_only(*ix, queries, w->d_meta, nq, w->d_win, kd, w->d_wovf, w->d_part, w->d_flags,
+                                       stream)))
         return st;
     }
     return launch_final_topk(*ix, w->d_meta, nq, w->d_win, kd, w->d_part, out_ids, out_s, stream);

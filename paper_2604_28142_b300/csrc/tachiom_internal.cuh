@@ -163,6 +163,10 @@ struct Workspace {
   int32_t *d_win = nullptr;            // [B x kd] FP32 rescoring window of the tensor-core refine
   int32_t *d_win_slot = nullptr;       // [B x kd] each window entry's candidate slot
   float *d_thr = nullptr;              // [B x kd x 32] per (slot, query token) thresholds of the window pass
+  int2 *d_wl = nullptr;                // [B x WL_PER_QUERY] candidate pairs of the window pass
+  int *d_wl_n = nullptr;
+  uint32_t *d_emx = nullptr;           // [B x kd x 32] their exact maxima
+  int32_t *d_wovf = nullptr;           // [B x kd] documents left to the all-pairs FP32 kernel
   int32_t *d_out_ids = nullptr;        // staging for search_host
   float *d_out_s = nullptr;
   uint32_t *d_flags = nullptr;         // status word
@@ -249,9 +253,21 @@ tachiom_status launch_refine_tc(const Index &ix, const float *queries, const int
 tachiom_status launch_refine_dec(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                  const int32_t *cand, int kd, float *sa, float *da, float *thr, uint32_t *flags,
                                  cudaStream_t s);
+// scratch of the window pass: the candidate pairs, their exact maxima, the overflowed documents
+constexpr int WL_PER_QUERY = 8192;  // candidate pairs a query's window may list
+struct WinScratch {
+  int2 *wl;
+  int *wl_n;
+  int wl_cap;
+  uint32_t *emx;   // [B x kd x 32]
+  int32_t *wovf;   // [B x kd]
+};
 tachiom_status launch_refine_dec_win(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                      const int32_t *win, const int32_t *win_slot, int kd, float *thr, float *part,
-                                     uint32_t *flags, cudaStream_t s);
+                                     const WinScratch &ws, uint32_t *flags, cudaStream_t s);
+tachiom_status launch_refine_win_only(const Index &ix, const float *queries, const int32_t *meta, int nq,
+                                      const int32_t *cand, int kd, const int32_t *only, float *part,
+                                      uint32_t *flags, cudaStream_t s);
 tachiom_status launch_refine_window_b(const Index &ix, const int32_t *meta, int nq, const int32_t *cand, int kd,
                                       const float *sa, const float *da, int32_t *win, int32_t *win_slot,
                                       cudaStream_t s);
