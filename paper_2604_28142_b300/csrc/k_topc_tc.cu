@@ -319,6 +319,34 @@ k_gsel_lim(const float *__restrict__ tops, int R, int nvals, int kc, const float
   }
 }
 
+// Same, one warp per row when the union holds at most 32 x LIM_VPL values (no barriers).
+constexpr int LIM_VPL = 24;
+__global__ void __launch_bounds__(128)
+k_gsel_lim_warp(const float *__restrict__ tops, int R, int nvals, int kc, const float *__restrict__ margins,
+                float *__restrict__ lim) {
+  const int row = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= R) return;
+  const float *src = tops + (int64_t)row * nvals;
+  uint32_t key[LIM_VPL];
+#pragma unroll
+  for (int u = 0; u < LIM_VPL; u++) {
+    const int i = lane + u * 32;
+    key[u] = i < nvals ? fkey(src[i]) : 0u;
+  }
+  uint32_t T = 0u;
+  for (int bit = 31; bit >= 0; bit--) {
+    const uint32_t cand = T | (1u << bit);
+    int c = 0;
+#pragma unroll
+    for (int u = 0; u < LIM_VPL; u++) c += key[u] >= cand ? 1 : 0;
+    if (__reduce_add_sync(0xffffffffu, c) >= kc) T = cand;
+  }
+  if (lane == 0) {
+    const float v = funkey(T);
+    lim[row] = (nvals >= kc && T > fkey(-INFINITY) && v == v) ? v - margins[row] : -INFINITY;
+  }
+}
+
 // Every group whose maximum is >= lim[row] goes to the row's list. Block =
 // 8 warps on the same 32 rows (lane = row), each warp a strided share of
 // one slice of the groups.
@@ -390,23 +418,28 @@ k_group_rescore(const float *__restrict__ rows, int R, const float *__restrict__
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   const int32_t *gl = glist + (int64_t)r * GCAP;
-  for (int g = warp; g < ng; g += RS_WARPS) {
+  // the group's rows in registers, loaded one group ahead (a row past C reads row C - 1: unused)
+  uint4 v[CH];
+  auto load_group = [&](int g) {
     const int64_t j0 = (int64_t)gl[g] * 32;
-    uint4 v[CH];
 #pragma unroll
     for (int u = 0; u < CH; u++) {
       const int c = u * 32 + lane, row = c / CH, pc = c % CH;
-      v[u] = make_uint4(0u, 0u, 0u, 0u);
-      if (j0 + row < C)
-        v[u] = BF16C ? reinterpret_cast<const uint4 *>(cent_bf16 + (j0 + row) * DIM)[pc]
-                     : reinterpret_cast<const uint4 *>(cent_f32 + (j0 + row) * DIM)[pc];
+      const int64_t jr = min(j0 + row, C - 1);
+      v[u] = BF16C ? reinterpret_cast<const uint4 *>(cent_bf16 + jr * DIM)[pc]
+                   : reinterpret_cast<const uint4 *>(cent_f32 + jr * DIM)[pc];
     }
+  };
+  if (warp < ng) load_group(warp);
+  for (int g = warp; g < ng; g += RS_WARPS) {
+    const int64_t j0 = (int64_t)gl[g] * 32;
 #pragma unroll
     for (int u = 0; u < CH; u++) {
       const int c = u * 32 + lane, row = c / CH, pc = c % CH;
       *reinterpret_cast<uint4 *>(st + row * RB + pc * 16) = v[u];
     }
     __syncwarp();
+    if (g + RS_WARPS < ng) load_group(g + RS_WARPS);  // in flight while this group is scored
     const int64_t j = j0 + lane;
     if (j < C) {
       float acc = 0.f;
@@ -564,7 +597,10 @@ tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, c
   k_topc_tc<1><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, G, gmax, tops, nullptr,
                                                                flags);
   TLAUNCH();
-  k_gsel_lim<<<nrows, LIM_THREADS, 0, s>>>(tops, nrows, splits * 4 * TOPM, kc, margins, lim);
+  if (splits * 4 * TOPM <= 32 * LIM_VPL)
+    k_gsel_lim_warp<<<(nrows + 3) / 4, 128, 0, s>>>(tops, nrows, splits * 4 * TOPM, kc, margins, lim);
+  else
+    k_gsel_lim<<<nrows, LIM_THREADS, 0, s>>>(tops, nrows, splits * 4 * TOPM, kc, margins, lim);
   TLAUNCH();
   TCUDA(cudaMemsetAsync(gcount, 0, (size_t)nrows * 4, s));
   k_gsel_collect<<<dim3(rbs * 8, COL_PARTS), 256, 0, s>>>(reinterpret_cast<const __half *>(gmax), G, nrows, lim,
