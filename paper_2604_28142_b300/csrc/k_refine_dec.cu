@@ -324,9 +324,11 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   // 16-byte shared-memory phase then read 8 different rows: no bank conflicts)
   const int drow = lane & 15, dhalf = lane >> 4;
 
-  auto issue = [&](const DecPos &p, int b, uint4 &cw, float &rh) {
-    const int64_t tl = p.c0 + (lane & 15);
-    const int32_t cid_l = (tl < p.te) ? tok_cid[tl] : 0;
+  // a chunk's centroid ids: lane l holds row l & 15 (a row past the document repeats its last
+  // token, masked later); loaded a chunk ahead of the copies that use it
+  auto load_cid = [&](const DecPos &p) -> int32_t { return tok_cid[min(p.c0 + (lane & 15), p.te - 1)]; };
+  // copies of the chunk's 16 centroid rows into stage b, and this lane's codes and norm
+  auto issue_rows = [&](const DecPos &p, int32_t cid_l, int b, uint4 &cw, float &rh) {
     const uint32_t dst0 = wt_s + (uint32_t)(b * RD_TILE);
 #pragma unroll
     for (int it = 0; it < 8; it++) {
@@ -339,31 +341,31 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     // this lane decodes row drow, half dhalf: codes of its subspaces, and the norm
-    const int64_t t = p.c0 + drow;
-    cw = make_uint4(0u, 0u, 0u, 0u);
-    rh = 0.f;
-    if (t < p.te) {
-      if constexpr (M == 32) {
-        cw = *reinterpret_cast<const uint4 *>(codes + t * M + dhalf * 16);
-      } else if constexpr (M == 16) {
-        const uint2 v = *reinterpret_cast<const uint2 *>(codes + t * M + dhalf * 8);
-        cw = make_uint4(v.x, v.y, 0u, 0u);
-      } else {
-        const uint32_t v = *reinterpret_cast<const uint32_t *>(codes + t * M + dhalf * 4);
-        cw = make_uint4(v, 0u, 0u, 0u);
-      }
-      rh = __half2float(__ushort_as_half(rnorm[t]));
+    const int64_t t = min(p.c0 + drow, p.te - 1);
+    if constexpr (M == 32) {
+      cw = *reinterpret_cast<const uint4 *>(codes + t * M + dhalf * 16);
+    } else if constexpr (M == 16) {
+      const uint2 v = *reinterpret_cast<const uint2 *>(codes + t * M + dhalf * 8);
+      cw = make_uint4(v.x, v.y, 0u, 0u);
+    } else {
+      const uint32_t v = *reinterpret_cast<const uint32_t *>(codes + t * M + dhalf * 4);
+      cw = make_uint4(v, 0u, 0u, 0u);
     }
+    rh = __half2float(__ushort_as_half(rnorm[t]));
   };
 
-  // chunk pipeline: the chunk of (pa, stage 0, cwa, rha) is processed while the next
-  // one's copies and loads land in (pb, stage 1, cwb, rhb), then the roles swap; the
-  // loop is unrolled twice so no register holding a load in flight is copied
-  DecPos pa, pb;
-  pa.slot = pb.slot = 0;
-  pa.tb = pa.te = pa.c0 = 0;
+  // chunk pipeline: chunk n is decoded and multiplied (rows in stage n & 1, codes and norm
+  // in the set X) while the rows of chunk n + 1 are copied to the other stage (its ids were
+  // loaded a step earlier into the set Y) and the ids of chunk n + 2 load into X. The two
+  // register sets swap roles in a loop unrolled twice, so no register holding a load in
+  // flight is copied; only chunk positions (already resolved) move between p0, p1, p2.
+  DecPos p0, p1, p2;
+  p0.slot = p1.slot = p2.slot = 0;
+  p0.tb = p0.te = p0.c0 = 0;
+  p1 = p2 = p0;
   uint4 cwa = make_uint4(0u, 0u, 0u, 0u), cwb = make_uint4(0u, 0u, 0u, 0u);
   float rha = 0.f, rhb = 0.f;
+  int32_t cida = 0, cidb = 0;
   float mx[4][2];
 #pragma unroll
   for (int nt = 0; nt < 4; nt++) mx[nt][0] = mx[nt][1] = -INFINITY;
@@ -563,35 +565,41 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     }
   };
 
-  bool has = dec_next(pa, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane);
-  if (has) issue(pa, 0, cwa, rha);
-  while (has) {
-    pb = pa;
-    bool hn = dec_next(pb, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane);
-    if (hn) {
-      issue(pb, 1, cwb, rhb);
+  bool v0 = dec_next(p0, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane), v1 = false, v2 = false;
+  if (v0) {
+    cida = load_cid(p0);
+    issue_rows(p0, cida, 0, cwa, rha);
+    p1 = p0;
+    v1 = dec_next(p1, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane);
+    if (v1) cidb = load_cid(p1);
+  }
+  int n = 0;
+  auto step = [&](int32_t &xcid, const uint4 &xcw, const float &xrh, const int32_t &ycid, uint4 &ycw, float &yrh) {
+    v2 = false;
+    if (v1) {
+      p2 = p1;
+      v2 = dec_next(p2, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane);
+      if (v2) xcid = load_cid(p2);
+      issue_rows(p1, ycid, (n + 1) & 1, ycw, yrh);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
     } else {
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    process(pa, 0, cwa, rha, hn, pb.slot);
+    process(p0, n & 1, xcw, xrh, v1, p1.slot);
     __syncwarp();
-    if (!hn) break;
-    pa = pb;
-    has = dec_next(pa, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane);
-    if (has) {
-      issue(pa, 0, cwa, rha);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
-    process(pb, 1, cwb, rhb, has, pa.slot);
-    __syncwarp();
+    p0 = p1;
+    v0 = v1;
+    p1 = p2;
+    v1 = v2;
+    n++;
+  };
+  while (v0) {
+    step(cida, cwa, rha, cidb, cwb, rhb);
+    if (!v0) break;
+    step(cidb, cwb, rhb, cida, cwa, rha);
   }
 }
 
-// One thread per listed pair: the FP32 path's value of (query token i, document token t)
-// (dec_exact), max-reduced into emx[q][slot][i] (order-preserving keys).
 template <int M>
 __global__ void __launch_bounds__(256)
 k_dec_exact_pairs(const float *__restrict__ queries, const int32_t *__restrict__ meta, int kd,
