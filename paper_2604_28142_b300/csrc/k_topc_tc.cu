@@ -6,9 +6,9 @@
 // rows resident in shared memory (64 KB, loaded once by TMA) and streams
 // 128-centroid tiles (32 KB) through a 4-stage TMA/mbarrier ring. Two
 // 256-column FP32 accumulators (all 512 TMEM columns) let the MMA of tile t+1
-// run while 8 epilogue warps drain tile t with tcgen05.ld. Warp roles: warp 0
-// issues TMA, warp 1 owns TMEM and issues the MMAs, warps 2..9 are the
-// epilogue (warp w reads TMEM lanes 32*(w%4).., column half (w-2)/4).
+// run while 16 epilogue warps drain tile t with tcgen05.ld. Warp roles: warp 0
+// issues TMA, warp 1 owns TMEM and issues the MMAs, warps 2..17 are the
+// epilogue (warp w reads TMEM lanes 32*(w%4).., columns 64*((w-2)/4)..+64).
 //
 // Selection:
 //   pass    every group of 32 consecutive centroids reports, per query row, its
@@ -55,8 +55,8 @@ constexpr int A_STAGE = 2 * A_HALF;        // 32 KB
 constexpr int B_HALF = BN * KH * 2;        // 32 KB
 constexpr int B_BYTES = 2 * B_HALF;        // 64 KB
 constexpr int TILE_BYTES = B_BYTES + STAGES * A_STAGE;  // 192 KB
-constexpr int THREADS = 320;       // 10 warps
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;      // 4 per TMEM lane quarter, 64 columns each
+constexpr int THREADS = 64 + 32 * EPI_WARPS;  // TMA warp, MMA warp, epilogue
 constexpr int TMEM_COLS = 512;
 constexpr int TOPM = 8;            // group maxima kept per (query row, stream)
 
@@ -170,15 +170,13 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     // ---------------- epilogue ----------------
     const int e = warp - 2;
     const int quarter = warp & 3;       // TMEM lane quarter this warp may access
-    const int half = e >> 2;            // column half: query rows [half*128, +128)
-    // running TOPM largest group maxima of this lane's rows half*128 + ch*32 + lane (descending)
-    float tm[2][2][TOPM];
+    const int cblk = e >> 2;            // column block: query rows [cblk * 64, +64)
+    // running TOPM largest group maxima of this lane's rows cblk * 64 + ch * 32 + lane (descending)
+    float tm[2][TOPM];
 #pragma unroll
     for (int a = 0; a < 2; a++)
 #pragma unroll
-      for (int b = 0; b < 2; b++)
-#pragma unroll
-        for (int k = 0; k < TOPM; k++) tm[a][b][k] = -INFINITY;
+      for (int k = 0; k < TOPM; k++) tm[a][k] = -INFINITY;
     auto insert = [](float (&t)[TOPM], float x) {
       x = (x == x) ? x : -INFINITY;
 #pragma unroll
@@ -197,71 +195,62 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       if (!ok) break;
       __syncwarp();
       fence_after();
-      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + half * 128);
+      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + cblk * 64);
       const int tile = tile_of(it);
       const int64_t j = (int64_t)tile * BM + quarter * 32 + lane;  // this thread's centroid
       const bool jv = j < C;
       const bool full_tile = (int64_t)(tile + 1) * BM <= C;  // uniform: no centroid past C
-#pragma unroll 1
-      for (int pr = 0; pr < 2; pr++) {
-        uint32_t v[2][32];
-        TC_LD32(ta + pr * 64, v[0]);
-        TC_LD32(ta + pr * 64 + 32, v[1]);
+#pragma unroll
+      for (int ch = 0; ch < 2; ch++) {
+        uint32_t v[32];
+        TC_LD32(ta + ch * 32, v);
         tmem_ld_wait();
-        if (pr == 1) {
-          // every column of this buffer has been read: hand it back to the MMA warp
+        if (ch == 1) {
+          // every column of this warp's share of the buffer has been read: hand it back
           fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&ctl->tempty[buf]);
         }
+        if (MODE == 1) {
+          // maximum score of the warp's 32 centroids, per query row (-inf: no valid centroid):
+          // one redux per column gives every lane all 32 maxima, a 5-level select tree
+          // leaves lane l the one of its row
+          __half *dst = reinterpret_cast<__half *>(gmax) + ((int64_t)rb * G + tile * 4 + quarter) * BN + cblk * 64;
+          float m[32];
+          if (full_tile) {
 #pragma unroll
-        for (int cc = 0; cc < 2; cc++) {
-          const int ch = pr * 2 + cc;
-          if (MODE == 1) {
-            // maximum score of the warp's 32 centroids, per query row (-inf: no valid centroid):
-            // one redux per column gives every lane all 32 maxima, a 5-level select tree
-            // leaves lane l the one of its row
-            __half *dst = reinterpret_cast<__half *>(gmax) + ((int64_t)rb * G + tile * 4 + quarter) * BN + half * 128;
-            float m[32];
-            if (full_tile) {
+            for (int c = 0; c < 32; c++) m[c] = redux_fmax(__uint_as_float(v[c]));
+          } else {
 #pragma unroll
-              for (int c = 0; c < 32; c++) m[c] = redux_fmax(__uint_as_float(v[cc][c]));
-            } else {
+            for (int c = 0; c < 32; c++) m[c] = redux_fmax(jv ? __uint_as_float(v[c]) : -INFINITY);
+          }
 #pragma unroll
-              for (int c = 0; c < 32; c++) m[c] = redux_fmax(jv ? __uint_as_float(v[cc][c]) : -INFINITY);
-            }
+          for (int w = 16; w >= 1; w >>= 1) {
+            const bool hi = (lane & w) != 0;
 #pragma unroll
-            for (int w = 16; w >= 1; w >>= 1) {
-              const bool hi = (lane & w) != 0;
+            for (int c = 0; c < w; c++) m[c] = hi ? m[c + w] : m[c];
+          }
+          const float mine = m[0];
+          dst[ch * 32 + lane] = __float2half_ru(mine);  // rounded up: the filter stays conservative
+          // most values fall below every lane's current 8th largest: skip the insertion then
+          if (__any_sync(0xffffffffu, !(mine <= tm[ch][TOPM - 1]))) insert(tm[ch], mine);
+        } else if (MODE == 3) {
+          // diagnostic: raw scores [R x C]
 #pragma unroll
-              for (int c = 0; c < w; c++) m[c] = hi ? m[c + w] : m[c];
-            }
-            const float mine = m[0];
-            dst[ch * 32 + lane] = __float2half_ru(mine);  // rounded up: the filter stays conservative
-            // most values fall below every lane's current 8th largest: skip the insertion then
-            if (pr == 0) {
-              if (__any_sync(0xffffffffu, !(mine <= tm[0][cc][TOPM - 1]))) insert(tm[0][cc], mine);
-            } else {
-              if (__any_sync(0xffffffffu, !(mine <= tm[1][cc][TOPM - 1]))) insert(tm[1][cc], mine);
-            }
-          } else if (MODE == 3) {
-            // diagnostic: raw scores [R x C]
-#pragma unroll
-            for (int c = 0; c < 32; c++) {
-              const int row = rb * BN + half * 128 + ch * 32 + c;
-              if (jv && row < R) reinterpret_cast<float *>(cand)[(int64_t)row * C + j] = __uint_as_float(v[cc][c]);
-            }
+          for (int c = 0; c < 32; c++) {
+            const int row = rb * BN + cblk * 64 + ch * 32 + c;
+            if (jv && row < R) reinterpret_cast<float *>(cand)[(int64_t)row * C + j] = __uint_as_float(v[c]);
           }
         }
       }
     }
     if (MODE == 1) {
 #pragma unroll
-      for (int ch = 0; ch < 4; ch++) {
-        const int row = rb * BN + half * 128 + ch * 32 + lane;
+      for (int ch = 0; ch < 2; ch++) {
+        const int row = rb * BN + cblk * 64 + ch * 32 + lane;
         if (row < R) {
           float4 *d = reinterpret_cast<float4 *>(tops + ((int64_t)row * splits * 4 + blockIdx.x * 4 + quarter) * TOPM);
-          const float *t = tm[ch >> 1][ch & 1];
+          const float *t = tm[ch];
 #pragma unroll
           for (int k = 0; k < TOPM / 4; k++) d[k] = make_float4(t[4 * k], t[4 * k + 1], t[4 * k + 2], t[4 * k + 3]);
         }
