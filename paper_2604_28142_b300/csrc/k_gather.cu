@@ -515,6 +515,7 @@ tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, 
 // keys >= kmin), 5 collected count, 6 tie mode, 7 spare.
 constexpr int S_PREFIX = 0, S_LEVEL = 1, S_ABOVE = 2, S_DONE = 3, S_KMIN = 4, S_CNT = 5, S_TIES = 6;
 constexpr int SEL_CHUNK = 8192;
+constexpr int SEL_LOCAL = 1024;  // keys a collect block gathers before reserving them
 constexpr int SEL_THREADS = 256;
 
 // level L bins: L1 key>>20 (4096), L2 (key>>8)&0xfff (4096), L3 key&0xff (256)
@@ -663,15 +664,35 @@ k_sel_collect(const float *__restrict__ dense, int64_t D, uint32_t *__restrict__
   const int64_t e0 = min(D, b0 + SEL_CHUNK);
   const float *dq = dense + (int64_t)q * D;
   uint64_t *buf = selbuf + (int64_t)q * SEL_CAP;
+  // the block's keys are gathered in shared memory and reserved in the query's buffer with one
+  // atomic (the per-query counter is shared by every block of the query)
+  __shared__ uint64_t sk[SEL_LOCAL];
+  __shared__ uint32_t scnt, sbase;
+  if (threadIdx.x == 0) scnt = 0u;
+  __syncthreads();
   sel_scan(dq, (int64_t)q * D, b0, e0, [&](int64_t x, float v) {
     if (v == -INFINITY) return;
     const uint32_t k = fkey(v);
     if (ties ? (k > kmin) : (k >= kmin)) {
-      const uint32_t pos = atomicAdd(&st[S_CNT], 1u);
-      if (pos < (uint32_t)SEL_CAP) buf[pos] = comp_key(v, (int32_t)x);
-      else atomicOr(flags, TACHIOM_FLAG_CAPACITY);
+      const uint32_t p = atomicAdd(&scnt, 1u);
+      if (p < (uint32_t)SEL_LOCAL) {
+        sk[p] = comp_key(v, (int32_t)x);
+      } else {
+        const uint32_t pos = atomicAdd(&st[S_CNT], 1u);
+        if (pos < (uint32_t)SEL_CAP) buf[pos] = comp_key(v, (int32_t)x);
+        else atomicOr(flags, TACHIOM_FLAG_CAPACITY);
+      }
     }
   });
+  __syncthreads();
+  const uint32_t n = min(scnt, (uint32_t)SEL_LOCAL);
+  if (threadIdx.x == 0) sbase = n ? atomicAdd(&st[S_CNT], n) : 0u;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t pos = sbase + i;
+    if (pos < (uint32_t)SEL_CAP) buf[pos] = sk[i];
+    else atomicOr(flags, TACHIOM_FLAG_CAPACITY);
+  }
 }
 
 // ordered pass for a cut inside a long run of equal keys: the lowest doc ids win
