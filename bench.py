@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--single-queries", type=int, default=32,
                     help="queries of the FP32 one-query-at-a-time comparator")
     ap.add_argument("--no-single", action="store_true")
+    ap.add_argument("--no-rerank", action="store_true", help="skip the rerank-only measurement")
     return ap.parse_args()
 
 
@@ -189,6 +190,44 @@ def fp32_one_at_a_time(T, G, a, batch, batched_ids, torch):
     return {"value": float(n / (lat.sum() / 1e3)), "unit": "queries/s", "queries": int(n),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "ids_equal_to_batched": same}
+
+
+def rerank_only(T, G, a, params, batches, n_docs, flush, torch):
+    """Steps (c)-(d) alone (tachiom_refine) over candidate lists that come from outside the
+    cascade, as a reranker of another retriever's output gets them: per query kappa_d distinct
+    seeded document ids in random order. Inputs device-resident, L2 flushed between batches
+    outside the events; CUDA events per batch on the launching stream."""
+    rng = np.random.default_rng(20260428)
+    nl = min(6, len(batches))
+    cands = []
+    for _ in range(nl):
+        rows = []
+        for _ in range(a.batch):
+            ids = np.unique(rng.integers(0, n_docs, size=2 * a.kd))
+            if ids.size < a.kd:
+                ids = rng.choice(n_docs, size=a.kd, replace=False)
+            rows.append(rng.permutation(ids[:a.kd]).astype(np.int32))
+        cands.append(torch.from_numpy(np.stack(rows)).cuda())
+    kk = np.full(a.batch, a.k, np.int32)
+    oi = torch.empty(a.batch * a.k, dtype=torch.int32, device="cuda")
+    os_ = torch.empty(a.batch * a.k, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for b in range(min(2, nl)):
+        G.refine(params, batches[b][0], batches[b][1], kk, cands[b], oi, os_)
+    torch.cuda.synchronize()
+    ms = []
+    for b in range(nl):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.refine(params, batches[b][0], batches[b][1], kk, cands[b], oi, os_)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ms = np.array(ms)
+    return {"value": float(a.batch * nl / (ms.sum() / 1e3)), "unit": "queries/s", "batches": nl,
+            "ms_per_batch": float(ms.mean()), "batch": a.batch, "kappa_d": a.kd, "k": a.k,
+            "lists": "per query kappa_d distinct seeded document ids, random order"}
 
 
 def oracle_check(ix, qs, ntok, gi, gs, k, kc, kd, nsample):
@@ -335,6 +374,10 @@ def run_ours(a):
     single = None
     if not a.no_single:
         single = fp32_one_at_a_time(T, G, a, batches[a.warmup], out_i[a.warmup], torch)
+    # ---- the rerank-only use of steps (c)-(d): external candidate lists ----
+    rerank = None
+    if not a.no_rerank:
+        rerank = rerank_only(T, G, a, params, batches, int(ix["doc_offsets"].shape[0] - 1), flush, torch)
     # ---- accuracy on a sample of the timed queries, and the oracle's own time ----
     b0 = a.warmup
     gi = out_i[b0].cpu().numpy()
@@ -439,6 +482,7 @@ def run_ours(a):
         "clocks": clocks,
         "e2e": e2e,
         "fp32_one_query_at_a_time": single,
+        "rerank_only": rerank,
         "gpu_launches": _count_launches(prof),
     }
     print(json.dumps(line))

@@ -63,13 +63,18 @@ def get_case(name):
         ix = synth.random_index(3001, 777, len_min=0, len_max=40, seed=5, empty_docs=50)
         q = synth.random_queries(9, 1, 32, seed=6)
         c = Case(name, ix, q, 7, 300, 25)
+    elif name == "random_m8":
+        # 8 subspaces of 16 dims: the widest codewords the decode pass takes
+        ix = synth.random_index(2001, 777, pq_m=8, len_min=0, len_max=40, seed=8, empty_docs=20)
+        q = synth.random_queries(9, 1, 32, seed=9)
+        c = Case(name, ix, q, 7, 300, 25)
     else:
         raise KeyError(name)
     _CASES[name] = c
     return c
 
 
-CASES = ["tiny", "small", "small32", "random_edges"]
+CASES = ["tiny", "small", "small32", "random_edges", "random_m8"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -167,6 +172,46 @@ def test_step_cd_refine_replay(name):
         rs = c.O.refine(c.q[c.qoff[u]:c.qoff[u + 1]], cd)
         check_ranking(gi[sl], gs[sl], res["ids"][sl], res["scores"][sl], RTOL_FP32, GAP,
                       what=f"query {u}", exact_scores=dict(zip(cd.tolist(), rs.tolist())))
+
+
+def _external_lists(c, seed):
+    """Seeded candidate lists from outside the cascade: per query a random count of distinct
+    document ids in random order, the unused slots (-1) scattered among them."""
+    D = c.ix["doc_offsets"].shape[0] - 1
+    kd = min(c.kd, D)
+    rng = np.random.default_rng(seed)
+    cand = np.full((c.nq, kd), -1, np.int32)
+    for u in range(c.nq):
+        n = int(rng.integers(kd // 2, kd + 1))
+        cand[u, :n] = rng.choice(D, size=n, replace=False)
+        rng.shuffle(cand[u])
+    return cand
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["small", "small32", "random_edges", "random_m8"])
+def test_rerank_external_lists(name, prec):
+    # refine alone over lists it did not produce (the rerank-only use of steps c-d): the
+    # result is the exact top-k of each list, FP32 and reduced precision alike
+    c = get_case(name)
+    cand = _external_lists(c, seed=77)
+    kd = cand.shape[1]
+    kk = np.full(c.nq, c.k, np.int32)
+    oi = torch.empty(c.nq * c.k, dtype=torch.int32, device="cuda")
+    os_ = torch.empty(c.nq * c.k, dtype=torch.float32, device="cuda")
+    c.G.refine(c.params(prec, kd=kd), c.dq, c.ntok, kk, torch.from_numpy(cand).cuda(), oi, os_)
+    torch.cuda.synchronize()
+    gi, gs = oi.cpu().numpy(), os_.cpu().numpy()
+    for u in range(c.nq):
+        cd = cand[u][cand[u] >= 0]
+        rs = c.O.refine(c.q[c.qoff[u]:c.qoff[u + 1]], cd)
+        order = np.lexsort((cd, -rs))[:c.k]
+        want_i = np.full(c.k, -1, np.int32)
+        want_s = np.full(c.k, -np.inf)
+        want_i[:len(order)], want_s[:len(order)] = cd[order], rs[order]
+        sl = slice(u * c.k, (u + 1) * c.k)
+        check_ranking(gi[sl], gs[sl], want_i, want_s, RTOL_FP32, GAP, what=f"query {u}",
+                      exact_scores=dict(zip(cd.tolist(), rs.tolist())))
 
 
 def _search(c, prec=0, kk=None):
@@ -354,7 +399,7 @@ def test_bf16_kappa_c_above_group_count():
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("name", ["small", "small32", "random_edges"])
+@pytest.mark.parametrize("name", ["small", "small32", "random_edges", "random_m8"])
 def test_refine_tc_within_error_bound(name):
     # approximate refined scores (decode + tensor cores) are within the per-document bound
     # the FP32 repair of the top-k window relies on; the FP32 kernel is within 1e-5
