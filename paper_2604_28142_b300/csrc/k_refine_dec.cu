@@ -75,16 +75,17 @@ __device__ __forceinline__ void rd_ldm4(uint32_t *r, uint32_t addr) {
 struct DecPos {
   int slot;
   int64_t tb, te, c0;
+  float2 xe;  // main pass: the document's norm maxima (k_doc_decode_norms), loaded with its bounds
 };
 
 // next 16-token chunk of the warp's document, or the next document of the CTA's
 // slice (taken from a shared counter, so the warps stay balanced)
 // bad(slot, empty): answer a slot whose document is out of range (empty = false) or has no
-// tokens (empty = true); called by lane 0
+// tokens (empty = true); called by lane 0. doc_xe: null in the window variant.
 template <typename BadFn>
 __device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int stride, int off, int *s_next,
-                                         const int32_t *cand_q, const int64_t *doc_off, int64_t D, BadFn bad,
-                                         uint32_t *flags, int lane) {
+                                         const int32_t *cand_q, const int64_t *doc_off, const float2 *doc_xe,
+                                         int64_t D, BadFn bad, uint32_t *flags, int lane) {
   if (p.c0 + 16 < p.te) {
     p.c0 += 16;
     return true;
@@ -106,6 +107,7 @@ __device__ __forceinline__ bool dec_next(DecPos &p, int s_end, int stride, int o
     }
     p.tb = doc_off[d];
     p.te = doc_off[d + 1];
+    if (doc_xe) p.xe = doc_xe[d];
     if (p.te == p.tb) {
       if (lane == 0) bad(slot, true);
       continue;
@@ -212,7 +214,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
              const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
              const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
              const __nv_bfloat16 *__restrict__ cent_bf16, const float *__restrict__ cent_f32, int bf16c,
-             float cerr, float cnorm, float *__restrict__ sa, float *__restrict__ da, float *__restrict__ thr,
+             const float2 *__restrict__ doc_xe, float cerr, float cnorm, float *__restrict__ sa, float *__restrict__ da, float *__restrict__ thr,
              const int32_t *__restrict__ win_slot, float *__restrict__ part, int ngroups, int2 *__restrict__ wl,
              int *__restrict__ wl_n, int wl_cap, uint32_t *__restrict__ emx, int32_t *__restrict__ wovf, int64_t D,
              uint32_t *__restrict__ flags) {
@@ -362,6 +364,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   DecPos p0, p1, p2;
   p0.slot = p1.slot = p2.slot = 0;
   p0.tb = p0.te = p0.c0 = 0;
+  p0.xe = make_float2(0.f, 0.f);
   p1 = p2 = p0;
   uint4 cwa = make_uint4(0u, 0u, 0u, 0u), cwb = make_uint4(0u, 0u, 0u, 0u);
   float rha = 0.f, rhb = 0.f;
@@ -369,7 +372,6 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   float mx[4][2];
 #pragma unroll
   for (int nt = 0; nt < 4; nt++) mx[nt][0] = mx[nt][1] = -INFINITY;
-  float xmax = 0.f, exmax = 0.f;  // per document: max ||x_t|| and max ||e_xt|| (lane-local, reduced at the end)
   float th[4][2];                  // window variant: thr of this lane's query tokens for the current document
 #pragma unroll
   for (int nt = 0; nt < 4; nt++) th[nt][0] = th[nt][1] = INFINITY;
@@ -383,10 +385,13 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     {
       unsigned char *xrow = wt + B * RD_TILE + drow * RD_ROW + dhalf * 128;
       const uint8_t *cb8 = reinterpret_cast<const uint8_t *>(&CW);  // codes of this lane's subspaces
-      const bool live = P.c0 + drow < P.te;
+      // the window variant measures each row's norms (its per-pair test needs them); the main
+      // pass takes the document's maxima from doc_xe, formed at index load by the same arithmetic
       float x2 = 0.f, ex2 = 0.f, cwe2 = 0.f;
+      if constexpr (WIN) {
 #pragma unroll
-      for (int mm = 0; mm < M / 2; mm++) cwe2 += cerr2[(dhalf * (M / 2) + mm) * 256 + cb8[mm]];
+        for (int mm = 0; mm < M / 2; mm++) cwe2 += cerr2[(dhalf * (M / 2) + mm) * 256 + cb8[mm]];
+      }
 #pragma unroll
       for (int v = 0; v < 8; v++) {  // 8 dims per step
         const uint4 cu = *reinterpret_cast<const uint4 *>(xrow + v * 16);
@@ -411,27 +416,26 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
           const float c0 = __uint_as_float(cwd[h] << 16), c1 = __uint_as_float(cwd[h] & 0xffff0000u);
           const float xs0 = fmaf(RH, w.x, c0), xs1 = fmaf(RH, w.y, c1);
           const __half2 xb = __floats2half2_rn(xs0, xs1);
-          const float2 xf = __half22float2(xb);
-          x2 = fmaf(xf.x, xf.x, fmaf(xf.y, xf.y, x2));
-          ex2 = fmaf(xf.x - xs0, xf.x - xs0, fmaf(xf.y - xs1, xf.y - xs1, ex2));
+          if constexpr (WIN) {
+            const float2 xf = __half22float2(xb);
+            x2 = fmaf(xf.x, xf.x, fmaf(xf.y, xf.y, x2));
+            ex2 = fmaf(xf.x - xs0, xf.x - xs0, fmaf(xf.y - xs1, xf.y - xs1, ex2));
+          }
           ob[h] = *reinterpret_cast<const uint32_t *>(&xb);
         }
         *reinterpret_cast<uint4 *>(xrow + v * 16) = make_uint4(ob[0], ob[1], ob[2], ob[3]);
       }
-      // the two halves of the row: ||x^||, ||e_x|| (fp16 rounding of x~, plus rho times the
-      // codeword rounding, plus the FP32 rounding of x~ itself)
-      x2 += __shfl_xor_sync(0xffffffffu, x2, 16);
-      ex2 += __shfl_xor_sync(0xffffffffu, ex2, 16);
-      cwe2 += __shfl_xor_sync(0xffffffffu, cwe2, 16);
-      if (live) {
-        const float slack = 1.f + ldexpf(1.f, -10);
-        const float xn = sqrtf(x2) * slack;
-        const float en = (sqrtf(ex2) + RH * sqrtf(cwe2)) * slack + ldexpf(xn, -22);
-        xmax = fmaxf(xmax, xn);
-        exmax = fmaxf(exmax, en);
-        if (WIN && dhalf == 0) {
+      if constexpr (WIN) {
+        // the two halves of the row: ||x^||, ||e_x|| (fp16 rounding of x~, plus rho times the
+        // codeword rounding, plus the FP32 rounding of x~ itself)
+        x2 += __shfl_xor_sync(0xffffffffu, x2, 16);
+        ex2 += __shfl_xor_sync(0xffffffffu, ex2, 16);
+        cwe2 += __shfl_xor_sync(0xffffffffu, cwe2, 16);
+        if (P.c0 + drow < P.te && dhalf == 0) {
+          const float slack = 1.f + ldexpf(1.f, -10);
+          const float xn = sqrtf(x2) * slack;
           rnx[2 * drow] = xn;
-          rnx[2 * drow + 1] = en;
+          rnx[2 * drow + 1] = (sqrtf(ex2) + RH * sqrtf(cwe2)) * slack + ldexpf(xn, -22);
         }
       }
     }
@@ -523,12 +527,8 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     }
     if (!WIN && (!HN || NSLOT != P.slot)) {
       // document complete: max over the lanes sharing tig, sum over query tokens, the bound
-      float xm = xmax, em = exmax;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, o));
-        em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
-      }
+      // (xm, em: max over the document's tokens of ||x^_t|| and ||e_x,t||)
+      const float xm = P.xe.x, em = P.xe.y;
       float sum = 0.f, dl = 0.f;
 #pragma unroll
       for (int nt = 0; nt < 4; nt++) {
@@ -561,16 +561,15 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
         sa_row[P.slot] = sum;
         da_row[P.slot] = dl * (1.f + ldexpf(1.f, -10)) + ldexpf(fabsf(sum) + 1.f, -20) * 8.f;
       }
-      xmax = exmax = 0.f;
     }
   };
 
-  bool v0 = dec_next(p0, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane), v1 = false, v2 = false;
+  bool v0 = dec_next(p0, s_end, stride, off, &s_next, cand_q, doc_off, WIN ? nullptr : doc_xe, D, bad, flags, lane), v1 = false, v2 = false;
   if (v0) {
     cida = load_cid(p0);
     issue_rows(p0, cida, 0, cwa, rha);
     p1 = p0;
-    v1 = dec_next(p1, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane);
+    v1 = dec_next(p1, s_end, stride, off, &s_next, cand_q, doc_off, WIN ? nullptr : doc_xe, D, bad, flags, lane);
     if (v1) cidb = load_cid(p1);
   }
   int n = 0;
@@ -578,7 +577,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     v2 = false;
     if (v1) {
       p2 = p1;
-      v2 = dec_next(p2, s_end, stride, off, &s_next, cand_q, doc_off, D, bad, flags, lane);
+      v2 = dec_next(p2, s_end, stride, off, &s_next, cand_q, doc_off, WIN ? nullptr : doc_xe, D, bad, flags, lane);
       if (v2) xcid = load_cid(p2);
       issue_rows(p1, ycid, (n + 1) & 1, ycw, yrh);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -642,6 +641,85 @@ k_win_sums(const int32_t *__restrict__ meta, int nq, const int32_t *__restrict__
   }
 }
 
+// Per document d, the two norms the main pass's bound Delta_d takes: the max over d's tokens of
+// ||h(x~_t)|| and of ||e_x,t||, where x~_t = fmaf(rho_t, h(w), c_t) element by element (c_t the BF16
+// centroid row, h(w) the fp16 codeword), h() the rounding to fp16, and e_x,t the fp16 rounding of
+// x~_t plus rho_t times the codeword rounding plus the FP32 rounding of x~_t. The per-element values
+// are the decode pass's own; the sums run in another order, which the slack of 2^-10 covers (the
+// FP32 rounding of a 128-term sum of squares is below 2^-16 of it). Depends on the index only, so it
+// is formed once at load. One warp per document, lane l on dims 4l .. 4l + 3 of each token; an empty
+// document gets (0, 0).
+template <int M>
+__global__ void __launch_bounds__(256)
+k_doc_decode_norms(const int64_t *__restrict__ doc_off, int64_t D, const int32_t *__restrict__ tok_cid,
+                   const uint8_t *__restrict__ codes, const uint16_t *__restrict__ rnorm,
+                   const float *__restrict__ codebooks, const __nv_bfloat16 *__restrict__ cent_bf16,
+                   float2 *__restrict__ doc_xe) {
+  constexpr int DS = 128 / M;
+  static_assert(DS % 4 == 0, "a lane's 4 dims lie in one subspace");
+  const int lane = threadIdx.x & 31;
+  const int m = (4 * lane) / DS, u0 = (4 * lane) % DS;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t d = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5); d < D; d += nw) {
+    float xmax = 0.f, emax = 0.f;
+    const int64_t te = doc_off[d + 1];
+    for (int64_t t = doc_off[d]; t < te; t++) {
+      const uint2 cr = *reinterpret_cast<const uint2 *>(cent_bf16 + (int64_t)tok_cid[t] * DIM + 4 * lane);
+      const int code = codes[t * M + m];
+      const float4 w4 = *reinterpret_cast<const float4 *>(codebooks + ((int64_t)m * 256 + code) * DS + u0);
+      const float rh = __half2float(__ushort_as_half(rnorm[t]));
+      const float c[4] = {__uint_as_float(cr.x << 16), __uint_as_float(cr.x & 0xffff0000u),
+                          __uint_as_float(cr.y << 16), __uint_as_float(cr.y & 0xffff0000u)};
+      const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+      float x2 = 0.f, ex2 = 0.f, cwe2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const float wr = __half2float(__float2half_rn(w[k]));
+        cwe2 = fmaf(wr - w[k], wr - w[k], cwe2);
+        const float xs = fmaf(rh, wr, c[k]);
+        const float xf = __half2float(__float2half_rn(xs));
+        x2 = fmaf(xf, xf, x2);
+        ex2 = fmaf(xf - xs, xf - xs, ex2);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+        ex2 += __shfl_xor_sync(0xffffffffu, ex2, o);
+        cwe2 += __shfl_xor_sync(0xffffffffu, cwe2, o);
+      }
+      const float slack = 1.f + ldexpf(1.f, -10);
+      const float xn = sqrtf(x2) * slack;
+      xmax = fmaxf(xmax, xn);
+      emax = fmaxf(emax, (sqrtf(ex2) + rh * sqrtf(cwe2)) * slack + ldexpf(xn, -22));
+    }
+    if (lane == 0) doc_xe[d] = make_float2(xmax, emax);
+  }
+}
+
+tachiom_status launch_doc_decode_norms(const Index &ix, cudaStream_t s) {
+  if (ix.D <= 0) return TACHIOM_OK;
+  const int64_t blocks = (ix.D + 7) / 8;
+  const unsigned grid = (unsigned)(blocks < 8192 ? blocks : 8192);
+  switch (ix.M) {
+    case 8:
+      k_doc_decode_norms<8><<<grid, 256, 0, s>>>(ix.doc_off, ix.D, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks,
+                                                 ix.cent_bf16, ix.doc_xe);
+      break;
+    case 16:
+      k_doc_decode_norms<16><<<grid, 256, 0, s>>>(ix.doc_off, ix.D, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks,
+                                                  ix.cent_bf16, ix.doc_xe);
+      break;
+    case 32:
+      k_doc_decode_norms<32><<<grid, 256, 0, s>>>(ix.doc_off, ix.D, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks,
+                                                  ix.cent_bf16, ix.doc_xe);
+      break;
+    default:
+      return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
+  }
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
 template <int M, bool WIN>
 static tachiom_status launch_refine_dec_m(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                           const int32_t *cand, int kd, float *sa, float *da, float *thr,
@@ -655,7 +733,7 @@ static tachiom_status launch_refine_dec_m(const Index &ix, const float *queries,
   TCUDA(cudaFuncSetAttribute(k_refine_dec<M, W, WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_refine_dec<M, W, WIN><<<grid, W * 32, smem, s>>>(
       queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks, ix.cent_bf16,
-      ix.cent_f32, ix.cdtype == TACHIOM_DTYPE_BF16 ? 1 : 0, ix.cerr_max, ix.cnorm_max + ix.cerr_max, sa, da, thr,
+      ix.cent_f32, ix.cdtype == TACHIOM_DTYPE_BF16 ? 1 : 0, ix.doc_xe, ix.cerr_max, ix.cnorm_max + ix.cerr_max, sa, da, thr,
       win_slot, part, refine_groups(M), ws ? ws->wl : nullptr, ws ? ws->wl_n : nullptr, ws ? ws->wl_cap : 0,
       ws ? ws->emx : nullptr, ws ? ws->wovf : nullptr, ix.D, flags);
   TLAUNCH();
