@@ -77,7 +77,8 @@ static void free_index(Index *ix) {
   for (auto &kv : ix->ws) ws_destroy(kv.second);
   ix->ws.clear();
   void *ptrs[] = {ix->cent_f32, ix->cent_bf16, ix->cent_type, ix->doc_off, ix->tok_cid, ix->codes,
-                  ix->rnorm, ix->codebooks, ix->doc_xe, ix->list_off, ix->list_doc, ix->list_roff};
+                  ix->rnorm, ix->codebooks, ix->doc_xe, ix->cbk_h16, ix->cbk_err2, ix->list_off,
+                  ix->list_doc, ix->list_roff};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(prev);
@@ -269,7 +270,9 @@ extern "C" tachiom_status tachiom_index_load(const tachiom_index_desc *desc, int
     TRY(upload(ix, &ix->rnorm, ones.data(), (size_t)T));
   }
   TRY(dalloc(ix, &ix->doc_xe, (size_t)D));
-  TRY(launch_doc_decode_norms(*ix, 0));
+  TRY(dalloc(ix, &ix->cbk_h16, (size_t)ix->M * 256 * ix->ds));
+  TRY(dalloc(ix, &ix->cbk_err2, (size_t)ix->M * 256));
+  TRY(launch_decode_tables(*ix, 0));
   TRY(upload(ix, &ix->list_off, loff.data(), (size_t)C + 1));
   TRY(upload(ix, &ix->list_doc, ldoc.data(), (size_t)ix->n_list));
   TRY(upload(ix, &ix->list_roff, roff.data(), roff.size()));

@@ -36,9 +36,24 @@
 namespace tachiom {
 
 constexpr int RD_DOCS_PER_CTA = 64;
-constexpr int RD_ROW = 272;              // 128 2-byte values + 16 bytes padding (conflict-free ldmatrix)
-constexpr int RD_TILE = 16 * RD_ROW;     // one 16-token tile
+constexpr int RD_ROW = 272;              // query tile row: 128 2-byte values + 16 bytes padding (conflict-free ldmatrix)
 constexpr int RD_SMEM_MAX = 227 * 1024;
+
+// Document tiles (16 rows of 128 fp16 values). With codewords of 8 or more dims (M = 8, 16) the
+// rows are unpadded and XOR-swizzled: 16-byte chunk c of row r sits at chunk c ^ (r & 7). The
+// codebook is then code-major ([256][M][ds]), so the piece of a codeword that covers chunk c lies
+// in 16-byte bank group c & 7 whatever the code; lane j of a decode phase takes its chunks in the
+// order (alpha j) ^ v, v = 0..7 (alpha j: j times x in GF(8), x^3 = x + 1), so in every step the 8
+// lanes of a phase read 8 different codeword bank groups and - as (alpha + 1) j ^ v is also a
+// permutation of j - 8 different row bank groups. With 4-dim codewords (M = 32) the rows keep the
+// query tile's padding and the codebook stays subspace-major ([M][256][ds]).
+template <int M>
+constexpr bool rd_swz() { return 128 / M >= 8; }
+template <int M>
+constexpr int rd_pitch() { return rd_swz<M>() ? 256 : RD_ROW; }
+template <int M>
+constexpr int rd_tile() { return 16 * rd_pitch<M>(); }
+__host__ __device__ constexpr int rd_gf8_mulx(int j) { return ((j << 1) & 7) ^ ((j & 4) ? 3 : 0); }
 
 // shared memory: fp16 codebooks, codeword error table, query norms, the fp16
 // query tile [32][RD_ROW], then per warp two tiles (centroid rows land by
@@ -48,13 +63,13 @@ constexpr int rd_fixed_bytes() {
   return M * 256 * (128 / M) * 2 + M * 256 * 4 + 64 * 4 + 32 * RD_ROW;
 }
 // per warp: two tiles, and in the window variant the chunk's row norms and the exact maxima
-template <bool WIN>
-constexpr int rd_warp_bytes() { return 2 * RD_TILE + (WIN ? 256 : 0); }
+template <int M, bool WIN>
+constexpr int rd_warp_bytes() { return 2 * rd_tile<M>() + (WIN ? 256 : 0); }
 template <int M, bool WIN>
 constexpr int rd_warps() {
-  return (RD_SMEM_MAX - rd_fixed_bytes<M>()) / rd_warp_bytes<WIN>() > 16
+  return (RD_SMEM_MAX - rd_fixed_bytes<M>()) / rd_warp_bytes<M, WIN>() > 16
              ? 16
-             : (RD_SMEM_MAX - rd_fixed_bytes<M>()) / rd_warp_bytes<WIN>();
+             : (RD_SMEM_MAX - rd_fixed_bytes<M>()) / rd_warp_bytes<M, WIN>();
 }
 
 __device__ __forceinline__ void rd_mma(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
@@ -212,16 +227,18 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
 k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta, int nq,
              const int32_t *__restrict__ cand, int kd, const int64_t *__restrict__ doc_off,
              const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
-             const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
-             const __nv_bfloat16 *__restrict__ cent_bf16, const float *__restrict__ cent_f32, int bf16c,
-             const float2 *__restrict__ doc_xe, float cerr, float cnorm, float *__restrict__ sa, float *__restrict__ da, float *__restrict__ thr,
+             const uint16_t *__restrict__ rnorm, const __half *__restrict__ cbk_h16,
+             const float *__restrict__ cbk_err2, const __nv_bfloat16 *__restrict__ cent_bf16,
+             const float *__restrict__ cent_f32, int bf16c, const float2 *__restrict__ doc_xe, float cerr, float cnorm, float *__restrict__ sa, float *__restrict__ da, float *__restrict__ thr,
              const int32_t *__restrict__ win_slot, float *__restrict__ part, int ngroups, int2 *__restrict__ wl,
              int *__restrict__ wl_n, int wl_cap, uint32_t *__restrict__ emx, int32_t *__restrict__ wovf, int64_t D,
              uint32_t *__restrict__ flags) {
   constexpr int DS = 128 / M;
   constexpr int NT = WARPS * 32;
+  constexpr bool SWZ = rd_swz<M>();
+  constexpr int PITCH = rd_pitch<M>(), TILE = rd_tile<M>();
   extern __shared__ __align__(16) unsigned char dsm[];
-  __half *cbk = reinterpret_cast<__half *>(dsm);                           // [M][256][DS] fp16 codewords
+  __half *cbk = reinterpret_cast<__half *>(dsm);                           // fp16 codewords (layout above)
   float *cerr2 = reinterpret_cast<float *>(dsm + M * 256 * DS * 2);        // [M][256] ||h(w) - w||^2
   float *qn = cerr2 + M * 256;                                             // [32] ||e_q||, [32] ||h(q)||
   unsigned char *qsm = reinterpret_cast<unsigned char *>(qn + 64);         // [32][RD_ROW] fp16 query tokens
@@ -255,18 +272,16 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gq = lane >> 2;
-  // codebooks to fp16, with the squared rounding error of each codeword
-  for (int mj = tid; mj < M * 256; mj += NT) {
-    float e2 = 0.f;
-#pragma unroll
-    for (int u = 0; u < DS; u++) {
-      const float w = codebooks[(int64_t)mj * DS + u];
-      const __half wb = __float2half_rn(w);
-      cbk[mj * DS + u] = wb;
-      const float d = __half2float(wb) - w;
-      e2 = fmaf(d, d, e2);
+  // the fp16 codebooks (formed at index load in this kernel's layout) and, for the window
+  // variant, the squared rounding error of each codeword
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(cbk_h16);
+    uint4 *dst = reinterpret_cast<uint4 *>(cbk);
+#pragma unroll 8
+    for (int x = tid; x < 128 * 256 * 2 / 16; x += NT) dst[x] = src[x];
+    if constexpr (WIN) {
+      for (int x = tid; x < M * 256; x += NT) cerr2[x] = cbk_err2[x];
     }
-    cerr2[mj] = e2;
   }
   // query tokens: the fp16 tile (B operand, zero rows past ntok) and the norms of the rounding error
   const float *qrow = queries + (int64_t)meta[q] * DIM;
@@ -301,15 +316,17 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   if (tid == 0) s_next = WIN ? 0 : s_begin;
   __syncthreads();
 
-  unsigned char *wt = tiles + warp * 2 * RD_TILE;
+  unsigned char *wt = tiles + warp * 2 * TILE;
   // window variant: this warp's chunk row norms (xn, en per row)
-  float *rnx = reinterpret_cast<float *>(tiles + WARPS * 2 * RD_TILE + warp * 256);  // [16][2]
+  float *rnx = reinterpret_cast<float *>(tiles + WARPS * 2 * TILE + warp * 256);  // [16][2]
   const int G = 128 / M;                   // query tokens per group of the FP32 path's partial sums
   const int gq_n = (ntok + G - 1) / G;     // groups of this query
   const uint32_t wt_s = (uint32_t)__cvta_generic_to_shared(wt);
   const uint32_t qs_s = (uint32_t)__cvta_generic_to_shared(qsm);
   // ldmatrix row addresses: A (document tokens x dims) and B (query tokens x dims, two n-tiles per x4)
-  const uint32_t la_off = (uint32_t)((((lane >> 3) & 1) * 8 + (lane & 7)) * RD_ROW + ((lane >> 4) * 8) * 2);
+  // (swizzled tiles: row ((lane >> 3) & 1) * 8 + (lane & 7), logical chunk 2 s + (lane >> 4) of k-step s)
+  const uint32_t la_off = SWZ ? (uint32_t)((((lane >> 3) & 1) * 8 + (lane & 7)) * PITCH)
+                              : (uint32_t)((((lane >> 3) & 1) * 8 + (lane & 7)) * PITCH + ((lane >> 4) * 8) * 2);
   const uint32_t lb_off = (uint32_t)((((lane >> 4) * 8) + (lane & 7)) * RD_ROW + ((lane >> 3) & 1) * 16);
   float *sa_row = WIN ? nullptr : sa + (int64_t)q * kd;
   float *da_row = WIN ? nullptr : da + (int64_t)q * kd;
@@ -325,19 +342,21 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
   // decode layout: lane -> row lane & 15, dims (lane >> 4) * 64 .. +64 (the 8 lanes of a
   // 16-byte shared-memory phase then read 8 different rows: no bank conflicts)
   const int drow = lane & 15, dhalf = lane >> 4;
+  const int j7 = drow & 7, ja = rd_gf8_mulx(j7);  // swizzled tiles: the lane's chunk order is ja ^ v
 
   // a chunk's centroid ids: lane l holds row l & 15 (a row past the document repeats its last
   // token, masked later); loaded a chunk ahead of the copies that use it
   auto load_cid = [&](const DecPos &p) -> int32_t { return tok_cid[min(p.c0 + (lane & 15), p.te - 1)]; };
   // copies of the chunk's 16 centroid rows into stage b, and this lane's codes and norm
   auto issue_rows = [&](const DecPos &p, int32_t cid_l, int b, uint4 &cw, float &rh) {
-    const uint32_t dst0 = wt_s + (uint32_t)(b * RD_TILE);
+    const uint32_t dst0 = wt_s + (uint32_t)(b * TILE);
 #pragma unroll
     for (int it = 0; it < 8; it++) {
       const int qq = it * 32 + lane;
       const int row = qq >> 4, pc = qq & 15;
       const int32_t cr = __shfl_sync(0xffffffffu, cid_l, row);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst0 + (uint32_t)(row * RD_ROW + pc * 16)),
+      const int pcs = SWZ ? (pc ^ (row & 7)) : pc;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst0 + (uint32_t)(row * PITCH + pcs * 16)),
                    "l"(cent_bf16 + (int64_t)cr * DIM + pc * 8)
                    : "memory");
     }
@@ -383,7 +402,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     // decode in place: x~ = c + rho * w (fp16 codewords), rounded to fp16.
     // This lane: row drow, dims [dhalf * 64, +64) = subspaces [dhalf * M / 2, +M / 2).
     {
-      unsigned char *xrow = wt + B * RD_TILE + drow * RD_ROW + dhalf * 128;
+      unsigned char *xrow = wt + B * TILE + drow * PITCH;             // this lane's row
       const uint8_t *cb8 = reinterpret_cast<const uint8_t *>(&CW);  // codes of this lane's subspaces
       // the window variant measures each row's norms (its per-pair test needs them); the main
       // pass takes the document's maxima from doc_xe, formed at index load by the same arithmetic
@@ -394,13 +413,18 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
       }
 #pragma unroll
       for (int v = 0; v < 8; v++) {  // 8 dims per step
-        const uint4 cu = *reinterpret_cast<const uint4 *>(xrow + v * 16);
+        // the step's 16-byte chunk of the lane's half: in the lane's own order on swizzled tiles
+        const int ch = SWZ ? (ja ^ v) : v;
+        const int coff = SWZ ? ((dhalf * 8 + ch) ^ j7) << 4 : dhalf * 128 + v * 16;
+        const uint4 cu = *reinterpret_cast<const uint4 *>(xrow + coff);
         const uint32_t cwd[4] = {cu.x, cu.y, cu.z, cu.w};
         uint32_t wv[4];
-        if constexpr (DS >= 8) {
-          const int mm = (v * 8) / DS;
-          const int m = dhalf * (M / 2) + mm;
-          const uint4 t = *reinterpret_cast<const uint4 *>(cbk + (m * 256 + cb8[mm]) * DS + (v * 8) % DS);
+        if constexpr (SWZ) {
+          // code-major codebook: the piece of codeword (code, m) for dims (ch * 8) % DS .. +8
+          const int mloc = (ch * 8) / DS;
+          const int m = dhalf * (M / 2) + mloc;
+          const int code = (int)(__byte_perm(CW.x, CW.y, (uint32_t)mloc) & 0xffu);
+          const uint4 t = *reinterpret_cast<const uint4 *>(cbk + (code * M + m) * DS + (ch * 8) % DS);
           wv[0] = t.x; wv[1] = t.y; wv[2] = t.z; wv[3] = t.w;
         } else {
           const int mm = 2 * v;
@@ -423,7 +447,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
           }
           ob[h] = *reinterpret_cast<const uint32_t *>(&xb);
         }
-        *reinterpret_cast<uint4 *>(xrow + v * 16) = make_uint4(ob[0], ob[1], ob[2], ob[3]);
+        *reinterpret_cast<uint4 *>(xrow + coff) = make_uint4(ob[0], ob[1], ob[2], ob[3]);
       }
       if constexpr (WIN) {
         // the two halves of the row: ||x^||, ||e_x|| (fp16 rounding of x~, plus rho times the
@@ -443,11 +467,11 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
     float acc[4][4];
 #pragma unroll
     for (int nt = 0; nt < 4; nt++) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-    const uint32_t la = wt_s + (uint32_t)(B * RD_TILE) + la_off;
+    const uint32_t la = wt_s + (uint32_t)(B * TILE) + la_off;
 #pragma unroll
     for (int s = 0; s < 8; s++) {
       uint32_t a[4];
-      rd_ldm4(a, la + s * 32);
+      rd_ldm4(a, SWZ ? la + (uint32_t)((((2 * s) + (lane >> 4)) ^ (lane & 7)) << 4) : la + s * 32);
 #pragma unroll
       for (int np = 0; np < 2; np++) {
         uint32_t bb[4];
@@ -696,28 +720,49 @@ k_doc_decode_norms(const int64_t *__restrict__ doc_off, int64_t D, const int32_t
   }
 }
 
-tachiom_status launch_doc_decode_norms(const Index &ix, cudaStream_t s) {
-  if (ix.D <= 0) return TACHIOM_OK;
-  const int64_t blocks = (ix.D + 7) / 8;
-  const unsigned grid = (unsigned)(blocks < 8192 ? blocks : 8192);
-  switch (ix.M) {
-    case 8:
-      k_doc_decode_norms<8><<<grid, 256, 0, s>>>(ix.doc_off, ix.D, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks,
-                                                 ix.cent_bf16, ix.doc_xe);
-      break;
-    case 16:
-      k_doc_decode_norms<16><<<grid, 256, 0, s>>>(ix.doc_off, ix.D, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks,
-                                                  ix.cent_bf16, ix.doc_xe);
-      break;
-    case 32:
-      k_doc_decode_norms<32><<<grid, 256, 0, s>>>(ix.doc_off, ix.D, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks,
-                                                  ix.cent_bf16, ix.doc_xe);
-      break;
-    default:
-      return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
+// The decode pass's fp16 codebook, in the layout it keeps in shared memory (code-major
+// [256][M][ds] for M = 8, 16; subspace-major [M][256][ds] for M = 32), each value rounded to
+// nearest; and per codeword (m, j) the squared norm of its rounding error, [M][256].
+template <int M>
+__global__ void __launch_bounds__(256)
+k_codebook_h16(const float *__restrict__ codebooks, __half *__restrict__ out, float *__restrict__ err2) {
+  constexpr int DS = 128 / M;
+  for (int mj = blockIdx.x * blockDim.x + threadIdx.x; mj < M * 256; mj += gridDim.x * blockDim.x) {
+    const int m = mj / 256, j = mj % 256;
+    __half *o = out + (rd_swz<M>() ? (j * M + m) * DS : mj * DS);
+    float e2 = 0.f;
+    for (int u = 0; u < DS; u++) {
+      const float w = codebooks[(int64_t)mj * DS + u];
+      const __half wb = __float2half_rn(w);
+      o[u] = wb;
+      const float d = __half2float(wb) - w;
+      e2 = fmaf(d, d, e2);
+    }
+    err2[mj] = e2;
   }
+}
+
+template <int M>
+static tachiom_status launch_decode_tables_m(const Index &ix, cudaStream_t s) {
+  k_codebook_h16<M><<<M, 256, 0, s>>>(ix.codebooks, reinterpret_cast<__half *>(ix.cbk_h16), ix.cbk_err2);
   TLAUNCH();
+  if (ix.D > 0) {
+    const int64_t blocks = (ix.D + 7) / 8;
+    const unsigned grid = (unsigned)(blocks < 8192 ? blocks : 8192);
+    k_doc_decode_norms<M><<<grid, 256, 0, s>>>(ix.doc_off, ix.D, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks,
+                                               ix.cent_bf16, ix.doc_xe);
+    TLAUNCH();
+  }
   return TACHIOM_OK;
+}
+
+tachiom_status launch_decode_tables(const Index &ix, cudaStream_t s) {
+  switch (ix.M) {
+    case 8: return launch_decode_tables_m<8>(ix, s);
+    case 16: return launch_decode_tables_m<16>(ix, s);
+    case 32: return launch_decode_tables_m<32>(ix, s);
+  }
+  return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
 }
 
 template <int M, bool WIN>
@@ -727,13 +772,14 @@ static tachiom_status launch_refine_dec_m(const Index &ix, const float *queries,
                                           uint32_t *flags, cudaStream_t s) {
   constexpr int W = rd_warps<M, WIN>();
   static_assert(W >= 4, "decode refine: shared memory for fewer than 4 warps");
-  const size_t smem = (size_t)rd_fixed_bytes<M>() + (size_t)W * rd_warp_bytes<WIN>();
+  const size_t smem = (size_t)rd_fixed_bytes<M>() + (size_t)W * rd_warp_bytes<M, WIN>();
   // the window variant takes a query's whole (short) list in one CTA
   dim3 grid(WIN ? 2 : (kd + RD_DOCS_PER_CTA - 1) / RD_DOCS_PER_CTA, nq);
   TCUDA(cudaFuncSetAttribute(k_refine_dec<M, W, WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_refine_dec<M, W, WIN><<<grid, W * 32, smem, s>>>(
-      queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes, ix.rnorm, ix.codebooks, ix.cent_bf16,
-      ix.cent_f32, ix.cdtype == TACHIOM_DTYPE_BF16 ? 1 : 0, ix.doc_xe, ix.cerr_max, ix.cnorm_max + ix.cerr_max, sa, da, thr,
+      queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid, ix.codes, ix.rnorm,
+      reinterpret_cast<const __half *>(ix.cbk_h16), ix.cbk_err2, ix.cent_bf16, ix.cent_f32,
+      ix.cdtype == TACHIOM_DTYPE_BF16 ? 1 : 0, ix.doc_xe, ix.cerr_max, ix.cnorm_max + ix.cerr_max, sa, da, thr,
       win_slot, part, refine_groups(M), ws ? ws->wl : nullptr, ws ? ws->wl_n : nullptr, ws ? ws->wl_cap : 0,
       ws ? ws->emx : nullptr, ws ? ws->wovf : nullptr, ix.D, flags);
   TLAUNCH();

@@ -116,6 +116,8 @@ struct Index {
   float *codebooks = nullptr;           // [M x 256 x ds]
   float2 *doc_xe = nullptr;             // [D] per document, max over its tokens of the decode pass's
                                         // ||h(x~_t)|| and ||e_x,t|| bounds (k_doc_decode_norms)
+  uint16_t *cbk_h16 = nullptr;          // [M x 256 x ds] fp16 codewords in the decode pass's layout
+  float *cbk_err2 = nullptr;            // [M x 256] squared norm of each codeword's fp16 rounding error
   int64_t *list_off = nullptr;          // [C+1]
   int32_t *list_doc = nullptr;          // [n_list]
   int64_t n_list = 0;
@@ -255,8 +257,9 @@ tachiom_status launch_refine_tc(const Index &ix, const float *queries, const int
 tachiom_status launch_refine_dec(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                  const int32_t *cand, int kd, float *sa, float *da, float *thr, uint32_t *flags,
                                  cudaStream_t s);
-// fills ix.doc_xe (allocated by the caller) from the index's codes, norms, codebooks and BF16 centroids
-tachiom_status launch_doc_decode_norms(const Index &ix, cudaStream_t s);
+// fills ix.cbk_h16, ix.cbk_err2 and ix.doc_xe (allocated by the caller) from the index's codebooks,
+// codes, norms and BF16 centroids: the tables of the decode pass of step (c)
+tachiom_status launch_decode_tables(const Index &ix, cudaStream_t s);
 // scratch of the window pass: the candidate pairs, their exact maxima, the overflowed documents
 constexpr int WL_PER_QUERY = 8192;  // candidate pairs a query's window may list
 struct WinScratch {
