@@ -54,18 +54,79 @@ def parse():
     return ap.parse_args()
 
 
+# clock-event reason bits of NVML (nvmlClocksEventReason*), the ones a bench line reports
+_NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+
+def _nvml_handle(dev):
+    """NVML handle of CUDA device `dev` (matched by PCI bus id, else by index), or None."""
+    try:
+        import pynvml
+        pynvml.nvmlInit()
+    except Exception:
+        return None
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        for fmt in ("{:08x}:{:02x}:{:02x}.0", "{:04x}:{:02x}:{:02x}.0"):
+            try:
+                return pynvml.nvmlDeviceGetHandleByPciBusId(fmt.format(p.pci_domain_id, p.pci_bus_id,
+                                                                      p.pci_device_id).encode())
+            except Exception:
+                pass
+    except Exception:
+        pass
+    try:
+        return pynvml.nvmlDeviceGetHandleByIndex(dev)
+    except Exception:
+        return None
+
+
 class Clocks:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """SM clock and clock-event (throttle) reasons sampled during the timed region: NVML reads
+    every 2 ms from a thread plus the samples the timing loop takes with mark() while the device
+    is busy (a step takes a few ms, too short for nvidia-smi's polling); nvidia-smi at 100 ms
+    when NVML is unavailable. Reads only: no clock or other setting is changed."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, dev):
         self.dev = dev
-        self.rows = []
+        self.samples = []   # (sm MHz, max sm MHz, set of active reasons)
         self.proc = None
+        self.h = None
+        self.stop = threading.Event()
+        self.t = None
+
+    def _nvml_sample(self):
+        import pynvml
+        try:
+            sm = pynvml.nvmlDeviceGetClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            mx = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            get = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                pynvml.nvmlDeviceGetCurrentClocksThrottleReasons
+            bits = int(get(self.h))
+        except Exception:
+            return
+        self.samples.append((float(sm), float(mx), {n for b, n in _NVML_REASONS.items() if bits & b}))
+
+    def mark(self):
+        """One sample now (call while the device runs the timed work)."""
+        if self.h is not None:
+            self._nvml_sample()
+
+    def _poll(self):
+        while not self.stop.is_set():
+            self._nvml_sample()
+            self.stop.wait(0.002)
 
     def __enter__(self):
+        self.h = _nvml_handle(self.dev)
+        if self.h is not None:
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
@@ -77,30 +138,40 @@ class Clocks:
         return self
 
     def _read(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            r = [x.strip() for x in line.split(",")]
+            try:
+                sm, mx = float(r[1]), float(r[2])
+            except (IndexError, ValueError):
+                continue
+            self.samples.append((sm, mx, {n for i, n in enumerate(names) if len(r) > 5 + i and
+                                          r[5 + i].lower() == "active"}))
 
     def __exit__(self, *a):
+        self.stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if self.t is not None and self.h is not None:
+            self.t.join(timeout=1)
 
     def summary(self):
-        if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for r in self.rows:
-            for i, n in enumerate(names):
-                if len(r) > 5 + i and r[5 + i].lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+        return clocks_summary(self.samples, "nvml" if self.h is not None else "nvidia-smi")
+
+
+def clocks_summary(samples, source):
+    """Median SM clock, max SM clock and the union of active reasons over the samples."""
+    if not samples:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0, "source": source}
+    reasons = set()
+    for _, _, r in samples:
+        reasons |= r
+    return {"sm_mhz": float(np.median([x[0] for x in samples])), "sm_max_mhz": max(x[1] for x in samples),
+            "reasons": sorted(reasons), "samples": len(samples), "source": source}
 
 
 def dist_env():
@@ -342,6 +413,7 @@ def run_ours(a):
             evs[s][0].record(stream)
             G.search(params, batches[b][0], batches[b][1], kk, out_i[b], out_s[b])
             evs[s][1].record(stream)
+            clk.mark()
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
