@@ -58,26 +58,65 @@ def parse():
 _NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
 
-def _nvml_handle(dev):
-    """NVML handle of CUDA device `dev` (matched by PCI bus id, else by index), or None."""
-    try:
-        import pynvml
-        pynvml.nvmlInit()
-    except Exception:
-        return None
+def _nvml_open(dev):
+    """A function returning (SM MHz, max SM MHz, clock-event reason bits) of CUDA device `dev`, read
+    through NVML - the pynvml module where it is installed, else the driver's libnvidia-ml through
+    ctypes - or None when neither answers. Only read calls; the device is matched by PCI bus id."""
+    bus = []
     try:
         import torch
         p = torch.cuda.get_device_properties(dev)
-        for fmt in ("{:08x}:{:02x}:{:02x}.0", "{:04x}:{:02x}:{:02x}.0"):
-            try:
-                return pynvml.nvmlDeviceGetHandleByPciBusId(fmt.format(p.pci_domain_id, p.pci_bus_id,
-                                                                      p.pci_device_id).encode())
-            except Exception:
-                pass
+        bus = [f.format(p.pci_domain_id, p.pci_bus_id, p.pci_device_id).encode()
+               for f in ("{:08X}:{:02X}:{:02X}.0", "{:04X}:{:02X}:{:02X}.0")]
     except Exception:
         pass
     try:
-        return pynvml.nvmlDeviceGetHandleByIndex(dev)
+        import pynvml
+        pynvml.nvmlInit()
+        h = None
+        for b in bus:
+            try:
+                h = pynvml.nvmlDeviceGetHandleByPciBusId(b)
+                break
+            except Exception:
+                pass
+        if h is None:
+            h = pynvml.nvmlDeviceGetHandleByIndex(dev)
+        get = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            pynvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lambda: (pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM),
+                        pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM), int(get(h)))
+    except Exception:
+        pass
+    try:
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        ptr, u, ull = ctypes.c_void_p, ctypes.c_uint, ctypes.c_ulonglong
+        lib.nvmlInit_v2.restype = ctypes.c_int
+        lib.nvmlDeviceGetHandleByPciBusId_v2.argtypes = [ctypes.c_char_p, ctypes.POINTER(ptr)]
+        lib.nvmlDeviceGetHandleByIndex_v2.argtypes = [u, ctypes.POINTER(ptr)]
+        lib.nvmlDeviceGetClockInfo.argtypes = [ptr, ctypes.c_int, ctypes.POINTER(u)]
+        lib.nvmlDeviceGetMaxClockInfo.argtypes = [ptr, ctypes.c_int, ctypes.POINTER(u)]
+        rfn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        rfn.argtypes = [ptr, ctypes.POINTER(ull)]
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ptr()
+        if not (any(lib.nvmlDeviceGetHandleByPciBusId_v2(b, ctypes.byref(h)) == 0 for b in bus) or
+                lib.nvmlDeviceGetHandleByIndex_v2(dev, ctypes.byref(h)) == 0):
+            return None
+        nvml_clock_sm = 1
+
+        def read():
+            sm, mx, bits = u(), u(), ull()
+            if (lib.nvmlDeviceGetClockInfo(h, nvml_clock_sm, ctypes.byref(sm)) or
+                    lib.nvmlDeviceGetMaxClockInfo(h, nvml_clock_sm, ctypes.byref(mx)) or
+                    rfn(h, ctypes.byref(bits))):
+                raise RuntimeError("NVML read failed")
+            return sm.value, mx.value, bits.value
+        read()
+        return read
     except Exception:
         return None
 
@@ -95,25 +134,20 @@ class Clocks:
         self.dev = dev
         self.samples = []   # (sm MHz, max sm MHz, set of active reasons)
         self.proc = None
-        self.h = None
+        self.read = None
         self.stop = threading.Event()
         self.t = None
 
     def _nvml_sample(self):
-        import pynvml
         try:
-            sm = pynvml.nvmlDeviceGetClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-            mx = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-            get = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-                pynvml.nvmlDeviceGetCurrentClocksThrottleReasons
-            bits = int(get(self.h))
+            sm, mx, bits = self.read()
         except Exception:
             return
         self.samples.append((float(sm), float(mx), {n for b, n in _NVML_REASONS.items() if bits & b}))
 
     def mark(self):
         """One sample now (call while the device runs the timed work)."""
-        if self.h is not None:
+        if self.read is not None:
             self._nvml_sample()
 
     def _poll(self):
@@ -122,8 +156,8 @@ class Clocks:
             self.stop.wait(0.002)
 
     def __enter__(self):
-        self.h = _nvml_handle(self.dev)
-        if self.h is not None:
+        self.read = _nvml_open(self.dev)
+        if self.read is not None:
             self.t = threading.Thread(target=self._poll, daemon=True)
             self.t.start()
             return self
@@ -156,11 +190,11 @@ class Clocks:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-        if self.t is not None and self.h is not None:
+        if self.t is not None and self.read is not None:
             self.t.join(timeout=1)
 
     def summary(self):
-        return clocks_summary(self.samples, "nvml" if self.h is not None else "nvidia-smi")
+        return clocks_summary(self.samples, "nvml" if self.read is not None else "nvidia-smi")
 
 
 def clocks_summary(samples, source):
