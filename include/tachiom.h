@@ -326,6 +326,34 @@ tachiom_status tachiom_debug_refine_scores(tachiom_index *index, const tachiom_s
 tachiom_status tachiom_debug_topc_groups(tachiom_index *index, const tachiom_search_params *params,
                                          const float *d_rows, int32_t nrows, int32_t *h_groups);
 
+/* ---- Token-Aware Clustering: centroid allotment (Sec. 2.1, Phases 1-4) ----
+ * Shares a centroid budget over token types before each type is clustered on
+ * its own. Phase 1: a type with 0 < n_j < mu occurrences gets 1 centroid, one
+ * with mu <= n_j < tau gets 2. Phase 2: every other type ("active", n_j >= tau)
+ * gets floor(w_j / sum(w) * B), w_j = sqrt(n_j) * s_j, B = the budget left after
+ * Phase 1, sum(w) over the active types. Phase 3: clamped to
+ * [min(eps, cap_j), cap_j], cap_j = min(n_j, max(1, floor(n_j / theta))).
+ * Phase 4: one centroid at a time to the active type below its cap with the
+ * largest share_j - kappa_j (ties: lower id), or from the active type above its
+ * floor with the smallest (ties: higher id), until the total is the budget.
+ * The paper gives no values for mu, tau, eps, theta and no reconciliation
+ * rule: these are the library's readings. Host-only, synchronous, no GPU. */
+typedef struct {
+  int64_t mu;    /* types with fewer occurrences get 1 centroid */
+  int64_t tau;   /* types with fewer occurrences (and >= mu) get 2 */
+  int32_t eps;   /* floor of an active type's allotment */
+  double theta;  /* an active type keeps at least theta vectors per centroid (> 0) */
+} tachiom_tac_params;
+
+/* n: host int64 [n_types] occurrences per type (<= 0: absent, 0 centroids);
+ * s: host float64 [n_types] spread s_j = mean squared distance of the type's
+ * vectors to their mean (read for active types; must be finite and >= 0);
+ * kappa: host int32 [n_types] output, summing to `budget`. Returns
+ * TACHIOM_ERR_INVALID (kappa unspecified) on a bad argument or when the bounds
+ * cannot meet the budget. */
+tachiom_status tachiom_tac_allot(const int64_t *n, const double *s, int32_t n_types, int64_t budget,
+                                 const tachiom_tac_params *p, int32_t *kappa);
+
 /* Library version string. */
 const char *tachiom_version(void);
 

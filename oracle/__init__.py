@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for the gather-and-refine scoring path (test infrastructure).
+"""FP64 CPU oracle for the gather-and-refine scoring path and for Token-Aware Clustering's
+centroid allotment (`oracle.tac`) (test infrastructure).
 
 Only the tests, the smoke check and the benchmark's CPU-baseline leg may
 import this package. The CUDA library never calls it, and it shares no code

@@ -1,0 +1,123 @@
+"""FP64 oracle of Token-Aware Clustering's centroid allotment (test infrastructure only).
+
+Sec. 2.1, "Token-Aware Clustering": the centroid budget kappa is shared out over the token types
+in four phases, then each type is clustered on its own. This module follows the four phases in
+the paper's order with plain Python loops over the types, in float64, for a reader to check by
+eye; it shares no code with the library.
+
+Readings of points the paper leaves open (each is a parameter or a rule here):
+* mu, tau, eps, theta (Phases 1 and 3) have no values in the paper: they are arguments.
+* A type with no occurrence gets no centroid; the paper's sum over w_i runs over the active types
+  (the weights exist only for them), and B is the budget left after Phase 1.
+* Phase 3 with both bounds: the cap floor(n_j / theta) (at least 1, at most n_j) wins over the
+  floor eps when they conflict, since a centroid needs vectors.
+* Phase 4: units are added one at a time to the active type whose allotment is furthest below
+  its share w_j / sum(w) * B (largest r_j = share - kappa_j, ties to the lower type id) among those
+  below their cap, or removed one at a time from the active type furthest above its share
+  (smallest r_j, ties to the higher type id) among those above their floor. A budget that cannot
+  be met within the bounds is an error.
+"""
+from __future__ import annotations
+
+import math
+
+
+class AllotError(ValueError):
+    pass
+
+
+def spread(vectors, types, n_types):
+    """Phase 2's spread s_j = (1 / n_j) sum_i ||t_{j,i} - mean_j||^2 of each type (0 for an
+    absent type), in float64 with two passes over the vectors (the mean, then the squares)."""
+    d = len(vectors[0]) if len(vectors) else 0
+    cnt = [0] * n_types
+    mean = [[0.0] * d for _ in range(n_types)]
+    for v, t in zip(vectors, types):
+        cnt[t] += 1
+        row = mean[t]
+        for k in range(d):
+            row[k] += float(v[k])
+    for t in range(n_types):
+        if cnt[t]:
+            mean[t] = [x / cnt[t] for x in mean[t]]
+    acc = [0.0] * n_types
+    for v, t in zip(vectors, types):
+        acc[t] += sum((float(v[k]) - mean[t][k]) ** 2 for k in range(d))
+    return [acc[t] / cnt[t] if cnt[t] else 0.0 for t in range(n_types)]
+
+
+def allot(n, s, budget, mu, tau, eps, theta):
+    """Centroids per token type, kappa_j, following Phases 1-4 of Sec. 2.1.
+
+    n: occurrences n_j per type; s: spread s_j per type (read for active types only);
+    budget: the total kappa. Returns a list of ints summing to `budget`."""
+    T = len(n)
+    kappa = [0] * T
+    # Phase 1: tail handling - micro types (n < mu) get 1 centroid, small types (mu <= n < tau) 2
+    active = []
+    for j in range(T):
+        if n[j] <= 0:
+            continue
+        if n[j] < mu:
+            kappa[j] = 1
+        elif n[j] < tau:
+            kappa[j] = 2
+        else:
+            active.append(j)
+    B = budget - sum(kappa)
+    if B < 0:
+        raise AllotError("the budget is below the tail's fixed allotment")
+    # Phase 2: damped scoring w_j = sqrt(n_j) * s_j, kappa_j = floor(w_j / sum(w) * B)
+    w = {}
+    for j in active:
+        w[j] = math.sqrt(n[j]) * s[j]
+    W = 0.0
+    for j in active:
+        W += w[j]
+    share = {}
+    for j in active:
+        share[j] = (w[j] / W) * B if W > 0 else 0.0
+        kappa[j] = math.floor(share[j])
+    # Phase 3: bounding - at least eps, at most n_j / theta vectors per centroid (the cap wins)
+    lo, hi = {}, {}
+    for j in active:
+        hi[j] = min(n[j], max(1, math.floor(n[j] / theta)))
+        lo[j] = min(eps, hi[j])
+        kappa[j] = min(max(kappa[j], lo[j]), hi[j])
+    # Phase 4: budget reconciliation, one centroid at a time
+    delta = budget - sum(kappa)
+    while delta > 0:
+        best = None
+        for j in active:  # ascending j: a tie keeps the lower id
+            if kappa[j] < hi[j]:
+                r = share[j] - kappa[j]
+                if best is None or r > best[0]:
+                    best = (r, j)
+        if best is None:
+            raise AllotError("the budget exceeds what the caps allow")
+        kappa[best[1]] += 1
+        delta -= 1
+    while delta < 0:
+        best = None
+        for j in active:  # ascending j with <=: a tie moves to the higher id
+            if kappa[j] > lo[j]:
+                r = share[j] - kappa[j]
+                if best is None or r <= best[0]:
+                    best = (r, j)
+        if best is None:
+            raise AllotError("the budget is below what the floors require")
+        kappa[best[1]] -= 1
+        delta += 1
+    return kappa
+
+
+def speedup_lower_bound(n, s):
+    """Sec. 2.1's lower bound on TAC's speed-up over k-means, sum(w) / max(w), over the types
+    with n_j > 0, and the exact ratio kappa N / sum_j kappa_j n_j it bounds for the unrounded
+    allotment kappa_j = w_j / sum(w) * kappa (independent of kappa)."""
+    js = [j for j in range(len(n)) if n[j] > 0]
+    w = [math.sqrt(n[j]) * s[j] for j in js]
+    W = sum(w)
+    N = sum(n[j] for j in js)
+    ratio = N / sum((wj / W) * n[j] for wj, j in zip(w, js))
+    return W / max(w), ratio

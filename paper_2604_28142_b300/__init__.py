@@ -18,5 +18,6 @@ from .binding import (  # noqa: F401
     lib_path,
     profile_enable,
     profile_read,
+    tac_allot,
     tc_available,
 )

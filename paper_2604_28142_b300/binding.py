@@ -63,6 +63,23 @@ def profile_read(stream=None) -> dict:
     return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(n.value)}
 
 
+class TacParams(ct.Structure):
+    _fields_ = [("mu", ct.c_int64), ("tau", ct.c_int64), ("eps", ct.c_int32), ("theta", ct.c_double)]
+
+
+def tac_allot(n, s, budget: int, mu: int, tau: int, eps: int, theta: float) -> np.ndarray:
+    """Centroids per token type by Token-Aware Clustering's allotment (tachiom_tac_allot): n int64
+    occurrences and s float64 spreads per type; returns int32 [n_types] summing to budget."""
+    n = np.ascontiguousarray(n, dtype=np.int64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    if n.shape != s.shape or n.ndim != 1:
+        raise ValueError("n and s must be 1-d arrays of the same length")
+    out = np.zeros(n.shape[0], np.int32)
+    p = TacParams(int(mu), int(tau), int(eps), float(theta))
+    _check(lib().tachiom_tac_allot(_hp(n), _hp(s), int(n.shape[0]), int(budget), ct.byref(p), _hp(out)))
+    return out
+
+
 def tc_available() -> bool:
     """True when the current device runs the tensor-core step (a)."""
     return bool(lib().tachiom_tc_available())
@@ -126,6 +143,7 @@ def lib():
                               ct.POINTER(ct.c_float), P], ct.c_int),
         "tachiom_last_error": ([], ct.c_char_p),
         "tachiom_version": ([], ct.c_char_p),
+        "tachiom_tac_allot": ([P, P, I32, I64, ct.POINTER(TacParams), P], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -1,0 +1,203 @@
+"""Token-Aware Clustering's centroid allotment (Sec. 2.1, Phases 1-4), on the CPU.
+
+The oracle (oracle/tac.py) is pinned to hand-worked allotments, closed forms and the paper's
+speed-up bound; the library's host implementation (tachiom_tac_allot) must return the oracle's
+integers exactly on seeded inputs shaped like a Zipfian vocabulary.
+"""
+import json
+import math
+import os
+import types
+
+import numpy as np
+import pytest
+
+from oracle import tac as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = json.load(open(os.path.join(HERE, "golden", "tac_allot.json")))
+
+
+def _native():
+    import paper_2604_28142_b300 as T
+    return T
+
+
+PROP_M = [8, 9, 11, 13, 23]
+
+
+def _args(c):
+    return c["budget"], c["mu"], c["tau"], c["eps"], c["theta"]
+
+
+def _feasible(n, mu, tau, eps, theta):
+    """(smallest, largest) total the bounds allow: the tail's fixed allotment plus every active
+    type at its floor, resp. at its cap."""
+    tail = sum(1 if 0 < x < mu else 2 if mu <= x < tau else 0 for x in n)
+    caps = [min(x, max(1, math.floor(x / theta))) for x in n if x >= tau and x > 0]
+    return tail + sum(min(eps, c) for c in caps), tail + sum(caps)
+
+
+# ---- pins of the oracle ---------------------------------------------------------------
+
+@pytest.mark.parametrize("i", range(len(GOLD["cases"])))
+def test_oracle_golden(i):
+    c = GOLD["cases"][i]
+    assert O.allot(GOLD["n"], GOLD["s"], *_args(c)) == c["expected"]
+
+
+def test_oracle_exact_proportional_shares():
+    # every type active, no bounds in the way, n_j = m_j^2 and s_j = 1: w_j = m_j, and a budget
+    # of c * sum(m) makes every share the integer c * m_j (sum(m) = 64: exact in binary) within
+    # the caps n_j, so Phase 4 has nothing to do
+    m = PROP_M
+    n = [x * x for x in m]
+    for c in (1, 2, 7):
+        k = O.allot(n, [1.0] * len(m), c * sum(m), mu=0, tau=0, eps=0, theta=1e-9)
+        assert k == [c * x for x in m]
+
+
+def test_oracle_spread_closed_forms():
+    rng = np.random.default_rng(3)
+    v = rng.normal(size=(60, 5))
+    t = rng.integers(0, 4, size=60)
+    got = O.spread(v.tolist(), t.tolist(), 5)
+    for j in range(4):
+        x = v[t == j]
+        assert got[j] == pytest.approx(float(x.var(axis=0).sum()), rel=1e-12)  # population variance
+    assert got[4] == 0.0
+    # two points at +-a e1: every point is at distance a from the mean
+    assert O.spread([[2.5, 0.0], [-2.5, 0.0]], [0, 0], 1) == [pytest.approx(6.25)]
+
+
+def test_oracle_tail_bounds_and_total():
+    rng = np.random.default_rng(11)
+    n = (1000.0 / np.arange(1, 401) ** 1.1).astype(np.int64)
+    s = rng.uniform(0.2, 1.0, size=n.size)
+    mu, tau, eps, theta = 3, 12, 2, 8.0
+    lo, hi = _feasible(n.tolist(), mu, tau, eps, theta)
+    budget = (lo + hi) // 2
+    k = O.allot(n.tolist(), s.tolist(), budget, mu, tau, eps, theta)
+    assert sum(k) == budget
+    for j in range(n.size):
+        if n[j] <= 0:
+            assert k[j] == 0
+        elif n[j] < mu:
+            assert k[j] == 1
+        elif n[j] < tau:
+            assert k[j] == 2
+        else:
+            cap = min(n[j], max(1, math.floor(n[j] / theta)))
+            assert min(eps, cap) <= k[j] <= cap
+
+
+def test_oracle_speedup_bound():
+    # Sec. 2.1: kappa N / sum_j kappa_j n_j >= sum(w) / max(w) for the unrounded allotment,
+    # with equality when every type has the same n and s
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        n = rng.integers(1, 10000, size=50)
+        s = rng.uniform(0.01, 2.0, size=50)
+        bound, ratio = O.speedup_lower_bound(n.tolist(), s.tolist())
+        assert ratio >= bound * (1 - 1e-12)
+    bound, ratio = O.speedup_lower_bound([64] * 10, [0.5] * 10)
+    assert bound == pytest.approx(10.0) and ratio == pytest.approx(10.0)
+
+
+def test_oracle_infeasible_budgets():
+    n, s = GOLD["n"], GOLD["s"]
+    with pytest.raises(O.AllotError):
+        O.allot(n, s, 2, 5, 50, 2, 10.0)      # below the tail's 1 + 2
+    with pytest.raises(O.AllotError):
+        O.allot(n, s, 8, 5, 50, 2, 10.0)      # floors need 3 + 2 * 3
+    with pytest.raises(O.AllotError):
+        O.allot(n, s, 10**6, 5, 50, 2, 10.0)  # caps allow 3 + 10 + 40 + 90
+
+
+# planted mistakes: each must fail one of the pins above
+_MUTANTS = [
+    ("w[j] = math.sqrt(n[j]) * s[j]", "w[j] = n[j] * s[j]"),       # no damping
+    ("if n[j] < mu:\n            kappa[j] = 1", "if n[j] < mu:\n            kappa[j] = 2"),
+    ("B = budget - sum(kappa)", "B = budget"),                      # tail not taken off the budget
+    ("if best is None or r > best[0]:", "if best is None or r < best[0]:"),  # adds to the wrong type
+    ("kappa[j] = min(max(kappa[j], lo[j]), hi[j])", "kappa[j] = max(kappa[j], lo[j])"),  # no cap
+    ("share[j] = (w[j] / W) * B if W > 0 else 0.0", "share[j] = (w[j] / W) * budget if W > 0 else 0.0"),
+]
+
+
+def _pins_pass(mod):
+    try:
+        for c in GOLD["cases"]:
+            if mod.allot(GOLD["n"], GOLD["s"], *_args(c)) != c["expected"]:
+                return False
+        m = PROP_M
+        if mod.allot([x * x for x in m], [1.0] * len(m), 2 * sum(m), 0, 0, 0, 1e-9) != [2 * x for x in m]:
+            return False
+    except Exception:
+        return False
+    return True
+
+
+@pytest.mark.parametrize("i", range(len(_MUTANTS)))
+def test_oracle_mutant_caught(i):
+    src = open(O.__file__).read()
+    a, b = _MUTANTS[i]
+    assert src.count(a) == 1, a
+    mod = types.ModuleType("tac_mutant")
+    exec(compile(src.replace(a, b), "tac_mutant", "exec"), mod.__dict__)
+    assert _pins_pass(O)
+    assert not _pins_pass(mod)
+
+
+# ---- the library against the oracle -------------------------------------------------
+
+@pytest.mark.parametrize("i", range(len(GOLD["cases"])))
+def test_native_golden(i):
+    T = _native()
+    c = GOLD["cases"][i]
+    assert T.tac_allot(GOLD["n"], GOLD["s"], *_args(c)).tolist() == c["expected"]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_native_equals_oracle_zipf(seed):
+    # a Zipfian vocabulary (a few very frequent types, a long tail, some absent types),
+    # spreads in [0.05, 1], budgets across the feasible range
+    T = _native()
+    rng = np.random.default_rng(100 + seed)
+    nt = int(rng.integers(50, 1500))
+    n = np.floor(20000.0 / np.arange(1, nt + 1) ** rng.uniform(0.8, 1.3)).astype(np.int64)
+    n[rng.choice(nt, size=nt // 20, replace=False)] = 0
+    rng.shuffle(n)
+    s = rng.uniform(0.05, 1.0, size=nt)
+    mu, tau = int(rng.integers(1, 6)), int(rng.integers(6, 40))
+    eps, theta = int(rng.integers(1, 4)), float(rng.uniform(4.0, 64.0))
+    lo, hi = _feasible(n.tolist(), mu, tau, eps, theta)
+    for frac in (0.0, 0.3, 0.7, 1.0):
+        budget = int(lo + frac * (hi - lo))
+        want = O.allot(n.tolist(), s.tolist(), budget, mu, tau, eps, theta)
+        got = T.tac_allot(n, s, budget, mu, tau, eps, theta)
+        assert got.tolist() == want
+        assert int(got.sum()) == budget
+
+
+def test_native_ties_and_zero_spread():
+    # equal weights: reconciliation order falls to the type ids; all-zero spreads: shares are 0
+    T = _native()
+    n = [100] * 7
+    for s, budget in (([1.0] * 7, 10), ([1.0] * 7, 4 * 7 - 2), ([0.0] * 7, 9)):
+        want = O.allot(n, s, budget, 1, 2, 1, 25.0)
+        assert T.tac_allot(n, s, budget, 1, 2, 1, 25.0).tolist() == want
+
+
+def test_native_rejects_bad_arguments():
+    T = _native()
+    n, s = GOLD["n"], GOLD["s"]
+    for args in ((2, 5, 50, 2, 10.0), (8, 5, 50, 2, 10.0), (10**6, 5, 50, 2, 10.0),
+                 (40, 5, 50, 2, 0.0), (40, -1, 50, 2, 10.0), (-1, 5, 50, 2, 10.0)):
+        with pytest.raises(T.TachiomError):
+            T.tac_allot(n, s, *args)
+    with pytest.raises(T.TachiomError):
+        T.tac_allot(n, [0.0, 0.0, -1.0, 1.0, 1.0], 40, 5, 50, 2, 10.0)
+    with pytest.raises(T.TachiomError):
+        T.tac_allot(n, [0.0, 0.0, float("nan"), 1.0, 1.0], 40, 5, 50, 2, 10.0)
+    assert T.tac_allot(np.zeros(0, np.int64), np.zeros(0), 0, 1, 2, 1, 1.0).shape == (0,)
