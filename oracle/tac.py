@@ -121,3 +121,85 @@ def speedup_lower_bound(n, s):
     N = sum(n[j] for j in js)
     ratio = N / sum((wj / W) * n[j] for wj, j in zip(w, js))
     return W / max(w), ratio
+
+
+# ---- the clustering and encoding that follow the allotment (Sec. 2.1) ----------------------
+# Plain definitions in float64 with explicit loops over points and centroids. Readings: distance
+# is squared L2; a tie goes to the lower centroid (or codeword) index; a cluster left empty by an
+# assignment keeps its previous centroid; the initial centroids are an input (the caller draws
+# them), so every step here is deterministic.
+
+def _sqdist(a, b):
+    return sum((float(x) - float(y)) ** 2 for x, y in zip(a, b))
+
+
+def assign(points, centroids):
+    """Index of the nearest centroid of every point (ties to the lower index)."""
+    out = []
+    for p in points:
+        best, bi = None, -1
+        for i, c in enumerate(centroids):
+            dd = _sqdist(p, c)
+            if best is None or dd < best:
+                best, bi = dd, i
+        out.append(bi)
+    return out
+
+
+def inertia(points, centroids, labels):
+    """Within-cluster sum of squares of Sec. 2.1's k-means objective."""
+    return sum(_sqdist(p, centroids[l]) for p, l in zip(points, labels))
+
+
+def lloyd(points, init, iters):
+    """kappa_j-means of one token type: `iters` rounds of assignment then mean update, from the
+    centroids `init`. Returns (centroids, labels of the last assignment, inertia after each
+    round's update)."""
+    c = [[float(x) for x in row] for row in init]
+    d = len(c[0]) if c else 0
+    hist = []
+    labels = []
+    for _ in range(iters):
+        labels = assign(points, c)
+        sums = [[0.0] * d for _ in c]
+        cnt = [0] * len(c)
+        for p, l in zip(points, labels):
+            cnt[l] += 1
+            for k in range(d):
+                sums[l][k] += float(p[k])
+        for i in range(len(c)):
+            if cnt[i]:
+                c[i] = [x / cnt[i] for x in sums[i]]
+        hist.append(inertia(points, c, labels))
+    if iters:
+        labels = assign(points, c)
+    return c, labels, hist
+
+
+def pq_encode(vectors, centroids, labels, codebooks):
+    """Residual compression of Sec. 2.1: r = t - c_a(t), rho = ||r||, r / rho split into M
+    contiguous subspaces of d / M dims, each coded by its nearest codeword (ties to the lower code);
+    a zero residual gets rho = 0 and code 0 everywhere. codebooks[m][j] is codeword j of subspace m.
+    Returns (codes [T][M], rho [T]) with rho in float64 (the index stores it as fp16)."""
+    M = len(codebooks)
+    codes, rhos = [], []
+    for t, l in zip(vectors, labels):
+        r = [float(x) - float(y) for x, y in zip(t, centroids[l])]
+        ds = len(r) // M
+        rho = math.sqrt(sum(x * x for x in r))
+        rhos.append(rho)
+        if rho == 0.0:
+            codes.append([0] * M)
+            continue
+        u = [x / rho for x in r]
+        row = []
+        for m in range(M):
+            sub = u[m * ds:(m + 1) * ds]
+            best, bj = None, -1
+            for j, w in enumerate(codebooks[m]):
+                dd = _sqdist(sub, w)
+                if best is None or dd < best:
+                    best, bj = dd, j
+            row.append(bj)
+        codes.append(row)
+    return codes, rhos

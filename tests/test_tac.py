@@ -201,3 +201,97 @@ def test_native_rejects_bad_arguments():
     with pytest.raises(T.TachiomError):
         T.tac_allot(n, [0.0, 0.0, float("nan"), 1.0, 1.0], 40, 5, 50, 2, 10.0)
     assert T.tac_allot(np.zeros(0, np.int64), np.zeros(0), 0, 1, 2, 1, 1.0).shape == (0,)
+
+
+# ---- clustering and residual encoding after the allotment --------------------------------
+
+def test_oracle_assign_brute_force_and_ties():
+    rng = np.random.default_rng(21)
+    x, c = rng.normal(size=(40, 6)), rng.normal(size=(9, 6))
+    want = np.argmin(((x[:, None, :] - c[None, :, :]) ** 2).sum(-1), axis=1)  # first minimum
+    assert O.assign(x.tolist(), c.tolist()) == want.tolist()
+    # equidistant from centroids 2 and 5 (mirror images): the lower index wins
+    cc = [[9.0, 9.0], [8.0, 8.0], [1.0, 0.0], [7.0, 7.0], [6.0, 6.0], [-1.0, 0.0]]
+    assert O.assign([[0.0, 3.0]], cc) == [2]
+
+
+def test_oracle_lloyd_closed_forms():
+    rng = np.random.default_rng(22)
+    x = rng.normal(size=(50, 4))
+    # one centroid: the mean after one round
+    c, lab, _ = O.lloyd(x.tolist(), [[5.0, 5.0, 5.0, 5.0]], 1)
+    assert np.allclose(c[0], x.mean(axis=0), rtol=0, atol=1e-12) and set(lab) == {0}
+    # Lloyd's rounds never increase the inertia
+    _, _, hist = O.lloyd(x.tolist(), x[:6].tolist(), 12)
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(hist, hist[1:]))
+    # three tight blobs started at their means stay put; a far centroid no point joins is kept
+    means = np.array([[0.0, 0.0], [10.0, 0.0], [0.0, 10.0]])
+    pts = np.concatenate([m + 0.01 * rng.normal(size=(20, 2)) for m in means])
+    start = [pts[:20].mean(0).tolist(), pts[20:40].mean(0).tolist(), pts[40:].mean(0).tolist(), [500.0, 500.0]]
+    c, lab, _ = O.lloyd(pts.tolist(), start, 5)
+    assert np.allclose(c[:3], start[:3], atol=1e-12) and c[3] == [500.0, 500.0]
+    assert lab == [0] * 20 + [1] * 20 + [2] * 20
+
+
+def _unit_codebooks(rng, M=4, ds=2, K=16):
+    # codewords of norm 1 / sqrt(M): any M of them, one per subspace, concatenate to a unit vector
+    a = rng.uniform(0, 2 * np.pi, size=(M, K))
+    return [[[math.cos(t) / math.sqrt(M), math.sin(t) / math.sqrt(M)] for t in a[m]] for m in range(M)]
+
+
+def test_oracle_pq_encode_lossless_zero_and_ties():
+    rng = np.random.default_rng(23)
+    cb = _unit_codebooks(rng)
+    cent = rng.normal(size=(3, 8)).tolist()
+    want_codes = rng.integers(0, 16, size=(25, 4))
+    rho = rng.uniform(0.1, 2.0, size=25)
+    lab = rng.integers(0, 3, size=25).tolist()
+    vec = [(np.array(cent[l]) + r * np.concatenate([cb[m][k] for m, k in enumerate(code)])).tolist()
+           for l, r, code in zip(lab, rho, want_codes)]
+    codes, rhos = O.pq_encode(vec, cent, lab, cb)
+    assert codes == want_codes.tolist()
+    assert np.allclose(rhos, rho, rtol=1e-12, atol=0)
+    # a token equal to its centroid: rho 0, codes 0
+    codes, rhos = O.pq_encode([cent[1]], cent, [1], cb)
+    assert codes == [[0, 0, 0, 0]] and rhos == [0.0]
+    # a codeword repeated at codes 3 and 7 of subspace 0: the lower code is chosen
+    cb2 = [list(row) for row in cb]
+    cb2[0][7] = list(cb2[0][3])
+    v = (np.array(cent[0]) + np.concatenate([cb2[0][7], cb2[1][0], cb2[2][0], cb2[3][0]])).tolist()
+    codes, _ = O.pq_encode([v], cent, [0], cb2)
+    assert codes[0][0] == 3
+
+
+_CLUSTER_MUTANTS = [
+    ("            if best is None or dd < best:\n                best, bi = dd, i",
+     "            if best is None or dd <= best:\n                best, bi = dd, i"),       # ties to the higher index
+    ("            if cnt[i]:\n                c[i] = [x / cnt[i] for x in sums[i]]",
+     "            c[i] = [x / max(cnt[i], 1) for x in sums[i]]"),                          # empty cluster zeroed
+    ("r = [float(x) - float(y) for x, y in zip(t, centroids[l])]",
+     "r = [float(y) - float(x) for x, y in zip(t, centroids[l])]"),                    # residual sign
+]
+
+
+@pytest.mark.parametrize("i", range(len(_CLUSTER_MUTANTS)))
+def test_oracle_cluster_mutant_caught(i):
+    src = open(O.__file__).read()
+    a, b = _CLUSTER_MUTANTS[i]
+    assert src.count(a) == 1, a
+    mod = types.ModuleType("tac_mutant")
+    exec(compile(src.replace(a, b), "tac_mutant", "exec"), mod.__dict__)
+    pins = (test_oracle_assign_brute_force_and_ties, test_oracle_lloyd_closed_forms,
+            test_oracle_pq_encode_lossless_zero_and_ties)
+    failed = 0
+    saved = O.__dict__.copy()
+    try:
+        for name in ("assign", "lloyd", "pq_encode", "inertia", "_sqdist"):
+            setattr(O, name, getattr(mod, name))
+        for pin in pins:
+            try:
+                pin()
+            except AssertionError:
+                failed += 1
+    finally:
+        for name in ("assign", "lloyd", "pq_encode", "inertia", "_sqdist"):
+            setattr(O, name, saved[name])
+    assert failed >= 1
