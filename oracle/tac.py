@@ -203,3 +203,37 @@ def pq_encode(vectors, centroids, labels, codebooks):
             row.append(bj)
         codes.append(row)
     return codes, rhos
+
+
+def init_positions(n_j, kappa_j):
+    """Initial centroids of one type: its points at positions floor((r + 1/2) n_j / kappa_j),
+    r = 0 .. kappa_j - 1, in the order the points appear in the collection (evenly spaced, distinct
+    as kappa_j <= n_j; deterministic, so no random draw needs to be shared)."""
+    return [math.floor((r + 0.5) * n_j / kappa_j) for r in range(kappa_j)]
+
+
+def cluster(vectors, types, n_types, budget, mu, tau, eps, theta, iters):
+    """Token-Aware Clustering end to end (Sec. 2.1): counts and spreads per type, the allotment,
+    then kappa_j-means of every type on its own from the evenly spaced initial points.
+    Returns (kappa [n_types], centroids grouped by type in type order [budget][d],
+    centroid type [budget], label of every vector as a global centroid id [N])."""
+    n = [0] * n_types
+    members = [[] for _ in range(n_types)]
+    for i, t in enumerate(types):
+        n[t] += 1
+        members[t].append(i)
+    s = spread(vectors, types, n_types)
+    kappa = allot(n, s, budget, mu, tau, eps, theta)
+    cents, ctype, labels = [], [], [0] * len(types)
+    for j in range(n_types):
+        if kappa[j] == 0:
+            continue
+        pts = [vectors[i] for i in members[j]]
+        init = [pts[p] for p in init_positions(n[j], kappa[j])]
+        c, lab, _ = lloyd(pts, init, iters)
+        base = len(cents)
+        cents.extend(c)
+        ctype.extend([j] * kappa[j])
+        for i, l in zip(members[j], lab):
+            labels[i] = base + l
+    return kappa, cents, ctype, labels

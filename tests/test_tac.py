@@ -295,3 +295,33 @@ def test_oracle_cluster_mutant_caught(i):
         for name in ("assign", "lloyd", "pq_encode", "inertia", "_sqdist"):
             setattr(O, name, saved[name])
     assert failed >= 1
+
+
+def test_oracle_init_positions_and_cluster():
+    # evenly spaced, distinct, in range
+    for nj, kj in ((1, 1), (10, 3), (1000, 17), (17, 17)):
+        pos = O.init_positions(nj, kj)
+        assert len(set(pos)) == kj and 0 <= min(pos) and max(pos) < nj
+    assert O.init_positions(10, 3) == [1, 5, 8]
+    # end to end on separated blobs: the centroid count per type is the allotment, every vector's
+    # label is the nearest centroid of its own type, and every non-empty centroid is the mean of its
+    # members (Lloyd has converged on this input)
+    rng = np.random.default_rng(31)
+    vecs, types = [], []
+    for j, (cnt, nb) in enumerate(((120, 3), (60, 2), (4, 1), (30, 2))):
+        centers = rng.normal(size=(nb, 8)) * 10
+        for i in range(cnt):
+            vecs.append((centers[i % nb] + 0.01 * rng.normal(size=8)).tolist())
+            types.append(j)
+    kappa, cents, ctype, labels = O.cluster(vecs, types, 5, 8, mu=5, tau=20, eps=1, theta=10.0, iters=20)
+    assert kappa == O.allot([120, 60, 4, 30, 0], O.spread(vecs, types, 5), 8, 5, 20, 1, 10.0)
+    assert sum(kappa) == 8 and len(cents) == 8 and kappa[4] == 0 and kappa[2] == 1
+    assert ctype == sorted(ctype) and [ctype.count(j) for j in range(5)] == kappa
+    v, t, lab = np.array(vecs), np.array(types), np.array(labels)
+    for j in range(4):
+        ids = [g for g in range(8) if ctype[g] == j]
+        d2 = ((v[t == j][:, None, :] - np.array([cents[g] for g in ids])[None]) ** 2).sum(-1)
+        assert [ids[x] for x in d2.argmin(1)] == lab[t == j].tolist()
+        for g in ids:
+            if (lab == g).any():
+                assert np.allclose(cents[g], v[lab == g].mean(0), atol=1e-12)
