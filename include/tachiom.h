@@ -354,6 +354,29 @@ typedef struct {
 tachiom_status tachiom_tac_allot(const int64_t *n, const double *s, int32_t n_types, int64_t budget,
                                  const tachiom_tac_params *p, int32_t *kappa);
 
+/* Token-Aware Clustering of a collection on the GPU (Sec. 2.1): groups the
+ * vectors by token type, measures each type's spread s_j, shares `budget`
+ * centroids out with tachiom_tac_allot (same parameters), then runs Lloyd's
+ * kappa_j-means on every type on its own for `iters` rounds from its points at
+ * positions floor((r + 1/2) n_j / kappa_j), r < kappa_j, and assigns every
+ * vector once more. Squared L2 in FP32, ties to the lower centroid; means in
+ * FP64 (fixed summation order, so runs repeat bit for bit) rounded to FP32; a
+ * centroid left without members keeps its place.
+ *   d_vectors: device fp32 [n_vectors x 128], 16-byte aligned;
+ *   d_types: device int32 [n_vectors], each in [0, n_types);
+ *   h_kappa: host int32 [n_types] output; h_spread: host float64 [n_types]
+ *   output or NULL; d_centroids: device fp32 [budget x 128] output, centroids
+ *   numbered type by type; d_centroid_type: device int32 [budget] output;
+ *   d_labels: device int32 [n_vectors] output, the centroid of each vector (-1
+ *   when its type received none).
+ * Allocates its own scratch (about 28 bytes per vector) and blocks until done
+ * on `stream`. TACHIOM_ERR_INVALID on a bad argument, a type out of range or
+ * a budget the allotment cannot meet; TACHIOM_ERR_OOM when scratch fails. */
+tachiom_status tachiom_tac_cluster(const float *d_vectors, const int32_t *d_types, int64_t n_vectors,
+                                   int32_t n_types, int64_t budget, const tachiom_tac_params *p,
+                                   int32_t iters, int32_t *h_kappa, double *h_spread, float *d_centroids,
+                                   int32_t *d_centroid_type, int32_t *d_labels, void *stream);
+
 /* Library version string. */
 const char *tachiom_version(void);
 

@@ -216,7 +216,8 @@ def cluster(vectors, types, n_types, budget, mu, tau, eps, theta, iters):
     """Token-Aware Clustering end to end (Sec. 2.1): counts and spreads per type, the allotment,
     then kappa_j-means of every type on its own from the evenly spaced initial points.
     Returns (kappa [n_types], centroids grouped by type in type order [budget][d],
-    centroid type [budget], label of every vector as a global centroid id [N])."""
+    centroid type [budget], label of every vector as a global centroid id [N], -1 for a vector
+    whose type received no centroid)."""
     n = [0] * n_types
     members = [[] for _ in range(n_types)]
     for i, t in enumerate(types):
@@ -224,7 +225,7 @@ def cluster(vectors, types, n_types, budget, mu, tau, eps, theta, iters):
         members[t].append(i)
     s = spread(vectors, types, n_types)
     kappa = allot(n, s, budget, mu, tau, eps, theta)
-    cents, ctype, labels = [], [], [0] * len(types)
+    cents, ctype, labels = [], [], [-1] * len(types)
     for j in range(n_types):
         if kappa[j] == 0:
             continue

@@ -19,5 +19,6 @@ from .binding import (  # noqa: F401
     profile_enable,
     profile_read,
     tac_allot,
+    tac_cluster,
     tc_available,
 )

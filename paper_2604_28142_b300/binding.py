@@ -80,6 +80,26 @@ def tac_allot(n, s, budget: int, mu: int, tau: int, eps: int, theta: float) -> n
     return out
 
 
+def tac_cluster(vectors, types, n_types: int, budget: int, mu: int, tau: int, eps: int, theta: float,
+                iters: int, stream=None):
+    """Token-Aware Clustering of device vectors (torch cuda fp32 [N, 128]) with device token types
+    (torch cuda int32 [N]) through tachiom_tac_cluster. Returns (kappa int32 [n_types] numpy,
+    spread float64 [n_types] numpy, centroids fp32 [budget, 128], centroid type int32 [budget],
+    labels int32 [N]) - the last three torch cuda tensors."""
+    import torch
+    n = int(vectors.shape[0])
+    kappa = np.zeros(n_types, np.int32)
+    spread = np.zeros(n_types, np.float64)
+    cents = torch.empty((budget, 128), dtype=torch.float32, device=vectors.device)
+    ctype = torch.empty(budget, dtype=torch.int32, device=vectors.device)
+    labels = torch.empty(n, dtype=torch.int32, device=vectors.device)
+    p = TacParams(int(mu), int(tau), int(eps), float(theta))
+    _check(lib().tachiom_tac_cluster(_dp(vectors), _dp(types), n, int(n_types), int(budget), ct.byref(p),
+                                     int(iters), _hp(kappa), _hp(spread), _dp(cents), _dp(ctype), _dp(labels),
+                                     _stream(stream)))
+    return kappa, spread, cents, ctype, labels
+
+
 def tc_available() -> bool:
     """True when the current device runs the tensor-core step (a)."""
     return bool(lib().tachiom_tc_available())
@@ -144,6 +164,7 @@ def lib():
         "tachiom_last_error": ([], ct.c_char_p),
         "tachiom_version": ([], ct.c_char_p),
         "tachiom_tac_allot": ([P, P, I32, I64, ct.POINTER(TacParams), P], ct.c_int),
+        "tachiom_tac_cluster": ([P, P, I64, I32, I64, ct.POINTER(TacParams), I32, P, P, P, P, P, P], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

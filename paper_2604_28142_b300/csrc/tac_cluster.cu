@@ -1,0 +1,326 @@
+// Token-Aware Clustering on the GPU (Sec. 2.1, "Token-Aware Clustering"): the collection's
+// vectors are grouped by token type, each type's spread s_j is measured, the centroid budget is
+// shared out (tachiom_tac_allot, host), and every type is clustered on its own by Lloyd's
+// kappa_j-means. Every type's subproblem only sees its own points and centroids, which is what
+// makes the decomposition cheap (Sec. 2.1's speed-up bound).
+//
+// Layout and order (all deterministic, so a run repeats bit for bit):
+//   - points are grouped by a stable radix sort on the type (within a type: collection order);
+//   - sums run in FP64 in a fixed order: warp w of a CTA takes the segment's elements w, w + W, ...,
+//     lane l dims 4l .. 4l + 3, and the W warp partials are added in warp order;
+//   - initial centroids of type j: its points at positions floor((r + 1/2) n_j / kappa_j),
+//     r < kappa_j (evenly spaced, distinct since kappa_j <= n_j);
+//   - a round: every point to the nearest centroid of its type (squared L2 in FP32, ties to the
+//     lower centroid), then every centroid to the FP64 mean of its members rounded to FP32 (a
+//     centroid left without members keeps its place); after the last round, one more assignment
+//     gives the labels;
+//   - centroids are numbered type by type (type order), kappa_j each.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <vector>
+
+#include "tachiom_internal.cuh"
+
+namespace tachiom {
+
+namespace {
+
+// device buffers of one call, freed on every return path
+struct TacBufs {
+  std::vector<void *> p;
+  ~TacBufs() {
+    for (void *x : p) cudaFree(x);
+  }
+  template <typename T>
+  tachiom_status alloc(T **out, size_t n) {
+    void *x = nullptr;
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    const cudaError_t e = cudaMalloc(&x, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TACHIOM_ERR_OOM, "tac_cluster: cudaMalloc of %zu bytes failed", bytes);
+    }
+    p.push_back(x);
+    *out = static_cast<T *>(x);
+    return TACHIOM_OK;
+  }
+};
+
+constexpr int TC_WARPS = 8;  // warps of the per-segment reduction CTAs
+
+__global__ void k_tac_iota_check(const int32_t *__restrict__ types, int64_t n, int32_t n_types,
+                                 int32_t *__restrict__ idx, uint32_t *__restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    idx[i] = (int32_t)i;
+    const int32_t t = types[i];
+    if (t < 0 || t >= n_types) atomicOr(bad, 1u);
+  }
+}
+
+__global__ void k_tac_iota(int32_t *__restrict__ idx, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    idx[i] = (int32_t)i;
+}
+
+// off[k] = first position of sorted keys[0, n) holding a key >= k, for k = 0 .. nk
+__global__ void k_tac_bounds(const int32_t *__restrict__ keys, int64_t n, int64_t nk, int64_t *__restrict__ off) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= nk; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)keys[mid] < k) lo = mid + 1;
+      else hi = mid;
+    }
+    off[k] = lo;
+  }
+}
+
+// FP64 mean of the vectors X[order[mem[e]]] for e in [b, e1) (mem may be null: identity),
+// fixed order; the CTA's TC_WARPS warps end with the mean in m[128]
+__device__ void tac_segment_mean(const float *__restrict__ X, const int32_t *__restrict__ order,
+                                 const int32_t *__restrict__ mem, int64_t b, int64_t e1, double (*red)[128],
+                                 double *m) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  for (int64_t q = b + warp; q < e1; q += TC_WARPS) {
+    const int64_t p = mem ? (int64_t)mem[q] : q;
+    const float4 v = *reinterpret_cast<const float4 *>(X + (int64_t)order[p] * DIM + 4 * lane);
+    a0 += (double)v.x;
+    a1 += (double)v.y;
+    a2 += (double)v.z;
+    a3 += (double)v.w;
+  }
+  red[warp][4 * lane] = a0;
+  red[warp][4 * lane + 1] = a1;
+  red[warp][4 * lane + 2] = a2;
+  red[warp][4 * lane + 3] = a3;
+  __syncthreads();
+  if (threadIdx.x < DIM) {
+    double t = 0.0;
+    for (int w = 0; w < TC_WARPS; w++) t += red[w][threadIdx.x];
+    m[threadIdx.x] = t / (double)(e1 - b);
+  }
+  __syncthreads();
+}
+
+// s_j = (1 / n_j) sum ||x - mean_j||^2 over the type's points (0 for an absent type)
+__global__ void __launch_bounds__(TC_WARPS * 32)
+k_tac_type_spread(const float *__restrict__ X, const int32_t *__restrict__ order, const int64_t *__restrict__ off,
+                  double *__restrict__ s) {
+  __shared__ double red[TC_WARPS][128];
+  __shared__ double mean[128];
+  __shared__ double wacc[TC_WARPS];
+  const int j = blockIdx.x;
+  const int64_t b = off[j], e1 = off[j + 1];
+  if (e1 == b) {
+    if (threadIdx.x == 0) s[j] = 0.0;
+    return;
+  }
+  tac_segment_mean(X, order, nullptr, b, e1, red, mean);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double m0 = mean[4 * lane], m1 = mean[4 * lane + 1], m2 = mean[4 * lane + 2], m3 = mean[4 * lane + 3];
+  double q = 0.0;
+  for (int64_t p = b + warp; p < e1; p += TC_WARPS) {
+    const float4 v = *reinterpret_cast<const float4 *>(X + (int64_t)order[p] * DIM + 4 * lane);
+    const double d0 = (double)v.x - m0, d1 = (double)v.y - m1, d2 = (double)v.z - m2, d3 = (double)v.w - m3;
+    q += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  if (lane == 0) wacc[warp] = q;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < TC_WARPS; w++) t += wacc[w];
+    s[j] = t / (double)(e1 - b);
+  }
+}
+
+// initial centroid g (one warp each): point floor((r + 1/2) n_j / kappa_j) of its type j
+__global__ void k_tac_init(const float *__restrict__ X, const int32_t *__restrict__ order,
+                           const int64_t *__restrict__ off, const int32_t *__restrict__ ctype,
+                           const int64_t *__restrict__ cbase, const int32_t *__restrict__ kappa, int64_t budget,
+                           float *__restrict__ C) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < budget; g += nw) {
+    const int32_t j = ctype[g];
+    const int64_t r = g - cbase[j], nj = off[j + 1] - off[j];
+    const int64_t pos = (int64_t)floor(((double)r + 0.5) * (double)nj / (double)kappa[j]);
+    const float4 v = *reinterpret_cast<const float4 *>(X + (int64_t)order[off[j] + pos] * DIM + 4 * lane);
+    *reinterpret_cast<float4 *>(C + g * DIM + 4 * lane) = v;
+  }
+}
+
+// point p (grouped order, one warp each) to the nearest centroid of its type; -1 when the type
+// has no centroid
+__global__ void k_tac_assign(const float *__restrict__ X, const int32_t *__restrict__ order,
+                             const int32_t *__restrict__ stype, int64_t n, const float *__restrict__ C,
+                             const int64_t *__restrict__ cbase, const int32_t *__restrict__ kappa,
+                             int32_t *__restrict__ lab) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < n; p += nw) {
+    const int32_t j = stype[p];
+    const int64_t g0 = cbase[j], kj = kappa[j];
+    const float4 x = *reinterpret_cast<const float4 *>(X + (int64_t)order[p] * DIM + 4 * lane);
+    float best = INFINITY;
+    int64_t bg = -1;
+    for (int64_t g = g0; g < g0 + kj; g++) {
+      const float4 c = *reinterpret_cast<const float4 *>(C + g * DIM + 4 * lane);
+      const float e0 = x.x - c.x, e1 = x.y - c.y, e2 = x.z - c.z, e3 = x.w - c.w;
+      float d = fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, e0 * e0)));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (d < best || bg < 0) {
+        best = d;
+        bg = g;
+      }
+    }
+    if (lane == 0) lab[p] = (int32_t)bg;
+  }
+}
+
+// centroid g (one CTA each) to the FP64 mean of its members, rounded to FP32; no member: unchanged
+__global__ void __launch_bounds__(TC_WARPS * 32)
+k_tac_means(const float *__restrict__ X, const int32_t *__restrict__ order, const int32_t *__restrict__ mem,
+            const int64_t *__restrict__ moff, float *__restrict__ C) {
+  __shared__ double red[TC_WARPS][128];
+  __shared__ double mean[128];
+  const int64_t g = blockIdx.x;
+  const int64_t b = moff[g], e1 = moff[g + 1];
+  if (e1 == b) return;
+  tac_segment_mean(X, order, mem, b, e1, red, mean);
+  if (threadIdx.x < DIM) C[g * DIM + threadIdx.x] = (float)mean[threadIdx.x];
+}
+
+__global__ void k_tac_scatter(const int32_t *__restrict__ lab, const int32_t *__restrict__ order, int64_t n,
+                              int32_t *__restrict__ out) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    out[order[p]] = lab[p];
+}
+
+unsigned grid_for(int64_t items, int per_block) {
+  const int64_t b = (items + per_block - 1) / per_block;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 148 * 64));
+}
+
+}  // namespace
+
+}  // namespace tachiom
+
+using namespace tachiom;
+
+extern "C" tachiom_status tachiom_tac_cluster(const float *d_vectors, const int32_t *d_types, int64_t n_vectors,
+                                              int32_t n_types, int64_t budget, const tachiom_tac_params *p,
+                                              int32_t iters, int32_t *h_kappa, double *h_spread,
+                                              float *d_centroids, int32_t *d_centroid_type, int32_t *d_labels,
+                                              void *stream) {
+  if (!p || !h_kappa || n_types <= 0 || n_vectors < 0 || n_vectors >= INT32_MAX || iters < 0 || budget < 0)
+    return fail(TACHIOM_ERR_INVALID, "tac_cluster: bad argument (null params or kappa, n_types <= 0, "
+                                     "n_vectors outside [0, 2^31 - 1), iters or budget < 0)");
+  if (n_vectors > 0 && (!d_vectors || !d_types || !d_labels))
+    return fail(TACHIOM_ERR_INVALID, "tac_cluster: NULL vectors, types or labels");
+  if (budget > 0 && (!d_centroids || !d_centroid_type))
+    return fail(TACHIOM_ERR_INVALID, "tac_cluster: NULL centroid outputs");
+  if (((uintptr_t)d_vectors & 15u) || ((uintptr_t)d_centroids & 15u))
+    return fail(TACHIOM_ERR_INVALID, "tac_cluster: vectors and centroids must be 16-byte aligned");
+  if (budget >= INT32_MAX) return fail(TACHIOM_ERR_INVALID, "tac_cluster: budget must be below 2^31 - 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t N = n_vectors;
+  TacBufs B;
+  tachiom_status st;
+#define TTRY(x)           \
+  do {                    \
+    if ((st = (x))) return st; \
+  } while (0)
+  int32_t *idx, *stype, *order, *lab, *labs, *mem, *kap_d;
+  int64_t *off, *cbase_d, *moff;
+  double *spr;
+  uint32_t *bad;
+  TTRY(B.alloc(&idx, (size_t)N));
+  TTRY(B.alloc(&stype, (size_t)N));
+  TTRY(B.alloc(&order, (size_t)N));
+  TTRY(B.alloc(&lab, (size_t)N));
+  TTRY(B.alloc(&labs, (size_t)N));
+  TTRY(B.alloc(&mem, (size_t)N));
+  TTRY(B.alloc(&off, (size_t)n_types + 1));
+  TTRY(B.alloc(&spr, (size_t)n_types));
+  TTRY(B.alloc(&kap_d, (size_t)n_types));
+  TTRY(B.alloc(&cbase_d, (size_t)n_types));
+  TTRY(B.alloc(&moff, (size_t)budget + 1));
+  TTRY(B.alloc(&bad, 1));
+  // the radix sorts' scratch: the larger of the two sorts (both N int32 pairs)
+  size_t tmp_bytes = 0;
+  TCUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, idx, stype, idx, order, (int)N, 0, 32, s));
+  void *tmp = nullptr;
+  TTRY(B.alloc(reinterpret_cast<unsigned char **>(&tmp), tmp_bytes));
+
+  // 1. group by type (stable), type bounds, spreads
+  TCUDA(cudaMemsetAsync(bad, 0, sizeof(uint32_t), s));
+  if (N > 0) {
+    k_tac_iota_check<<<grid_for(N, 256), 256, 0, s>>>(d_types, N, n_types, idx, bad);
+    TLAUNCH();
+    TCUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, d_types, stype, idx, order, (int)N, 0, 32, s));
+  }
+  k_tac_bounds<<<grid_for((int64_t)n_types + 1, 256), 256, 0, s>>>(stype, N, n_types, off);
+  TLAUNCH();
+  k_tac_type_spread<<<n_types, TC_WARPS * 32, 0, s>>>(d_vectors, order, off, spr);
+  TLAUNCH();
+  std::vector<int64_t> hoff((size_t)n_types + 1);
+  std::vector<double> hs((size_t)n_types);
+  uint32_t hbad = 0;
+  TCUDA(cudaMemcpyAsync(hoff.data(), off, hoff.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  TCUDA(cudaMemcpyAsync(hs.data(), spr, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TCUDA(cudaMemcpyAsync(&hbad, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  TCUDA(cudaStreamSynchronize(s));
+  if (hbad) return fail(TACHIOM_ERR_INVALID, "tac_cluster: a token type is outside [0, n_types)");
+  if (h_spread) std::copy(hs.begin(), hs.end(), h_spread);
+
+  // 2. the allotment (host), the centroid numbering
+  std::vector<int64_t> hn((size_t)n_types);
+  for (int32_t j = 0; j < n_types; j++) hn[j] = hoff[j + 1] - hoff[j];
+  TTRY(tachiom_tac_allot(hn.data(), hs.data(), n_types, budget, p, h_kappa));
+  std::vector<int64_t> hcb((size_t)n_types);
+  std::vector<int32_t> hct((size_t)budget);
+  int64_t acc = 0;
+  for (int32_t j = 0; j < n_types; j++) {
+    hcb[j] = acc;
+    for (int32_t r = 0; r < h_kappa[j]; r++) hct[(size_t)(acc + r)] = j;
+    acc += h_kappa[j];
+  }
+  if (budget > 0)
+    TCUDA(cudaMemcpyAsync(d_centroid_type, hct.data(), hct.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  TCUDA(cudaMemcpyAsync(cbase_d, hcb.data(), hcb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  TCUDA(cudaMemcpyAsync(kap_d, h_kappa, (size_t)n_types * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+
+  // 3. initial centroids, Lloyd rounds, the final assignment
+  if (budget > 0) {
+    k_tac_init<<<grid_for(budget, 8), 256, 0, s>>>(d_vectors, order, off, d_centroid_type, cbase_d, kap_d, budget,
+                                                    d_centroids);
+    TLAUNCH();
+  }
+  for (int32_t it = 0; it <= iters; it++) {
+    if (N > 0) {
+      k_tac_assign<<<grid_for(N, 8), 256, 0, s>>>(d_vectors, order, stype, N, d_centroids, cbase_d, kap_d, lab);
+      TLAUNCH();
+    }
+    if (it == iters || N == 0 || budget == 0) break;
+    // members of every centroid in grouped order: a stable sort of (label, position)
+    k_tac_iota<<<grid_for(N, 256), 256, 0, s>>>(idx, N);
+    TLAUNCH();
+    TCUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, lab, labs, idx, mem, (int)N, 0, 32, s));
+    k_tac_bounds<<<grid_for(budget + 1, 256), 256, 0, s>>>(labs, N, budget, moff);
+    TLAUNCH();
+    k_tac_means<<<(unsigned)budget, TC_WARPS * 32, 0, s>>>(d_vectors, order, mem, moff, d_centroids);
+    TLAUNCH();
+  }
+  if (N > 0) {
+    k_tac_scatter<<<grid_for(N, 256), 256, 0, s>>>(lab, order, N, d_labels);
+    TLAUNCH();
+  }
+  TCUDA(cudaStreamSynchronize(s));
+#undef TTRY
+  return TACHIOM_OK;
+}

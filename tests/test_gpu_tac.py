@@ -1,0 +1,89 @@
+"""Token-Aware Clustering on the GPU (tachiom_tac_cluster) against the FP64 oracle (oracle/tac.py).
+
+Opt-in: set TACHIOM_TEST_TAC_GPU=1 to run these. The inputs are separated blobs per token type, so
+the nearest centroid of every vector is far from a tie and the FP32 distances of the kernel and the
+oracle's FP64 ones choose the same labels; centroids then agree to FP32 rounding (rtol 1e-6).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import tac as O
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("TACHIOM_TEST_TAC_GPU") != "1",
+                                 reason="GPU clustering tests are opt-in (TACHIOM_TEST_TAC_GPU=1)")]
+
+PARAMS = dict(mu=5, tau=20, eps=1, theta=10.0)
+
+
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _blobs(counts, seed):
+    """Vectors of each type drawn around a few centers of that type (scale 10, noise 0.01)."""
+    rng = np.random.default_rng(seed)
+    vecs, types = [], []
+    for j, cnt in enumerate(counts):
+        centers = rng.normal(size=(1 + j % 4, 128)) * 10.0
+        for i in range(cnt):
+            vecs.append(centers[i % len(centers)] + 0.01 * rng.normal(size=128))
+            types.append(j)
+    order = rng.permutation(len(types))  # types interleaved in the collection
+    return np.array(vecs, np.float32)[order], np.array(types, np.int32)[order]
+
+
+def _run(T, v, t, n_types, budget, iters, **kw):
+    return T.tac_cluster(torch.from_numpy(v).cuda(), torch.from_numpy(t).cuda(), n_types, budget,
+                         iters=iters, **kw)
+
+
+def test_tac_cluster_matches_oracle():
+    _cuda()
+    import paper_2604_28142_b300 as T
+    counts = [400, 200, 130, 100, 80, 60, 50, 40, 8, 4, 2, 0]
+    v, t = _blobs(counts, seed=41)
+    n_types, iters = len(counts), 6
+    s_or = O.spread(v.astype(np.float64).tolist(), t.tolist(), n_types)
+    lo_hi = [min(x, max(1, int(np.floor(x / PARAMS["theta"])))) for x in counts if x >= PARAMS["tau"]]
+    tail = sum(1 if 0 < x < PARAMS["mu"] else 2 if PARAMS["mu"] <= x < PARAMS["tau"] else 0 for x in counts)
+    budget = tail + (sum(min(PARAMS["eps"], c) for c in lo_hi) + sum(lo_hi)) // 2
+    kappa, spread, cents, ctype, labels = _run(T, v, t, n_types, budget, iters, **PARAMS)
+    torch.cuda.synchronize()
+    assert np.allclose(spread, s_or, rtol=1e-12, atol=0)
+    ok, oc, oct_, olab = O.cluster(v.astype(np.float64).tolist(), t.tolist(), n_types, budget,
+                                   iters=iters, **PARAMS)
+    assert kappa.tolist() == ok
+    assert ctype.cpu().tolist() == oct_
+    assert labels.cpu().tolist() == olab
+    assert np.allclose(cents.cpu().numpy(), np.array(oc), rtol=1e-6, atol=1e-6)
+    # the same call repeats bit for bit
+    k2, s2, c2, ct2, l2 = _run(T, v, t, n_types, budget, iters, **PARAMS)
+    torch.cuda.synchronize()
+    assert np.array_equal(k2, kappa) and np.array_equal(s2, spread)
+    assert torch.equal(c2, cents) and torch.equal(ct2, ctype) and torch.equal(l2, labels)
+
+
+def test_tac_cluster_type_without_centroid_and_bad_type():
+    _cuda()
+    import paper_2604_28142_b300 as T
+    # type 1: 50 identical vectors (spread 0, weight 0) and eps = 0: it receives no centroid, so its
+    # vectors get label -1; type 0 takes the whole budget of 3
+    rng = np.random.default_rng(7)
+    v = np.concatenate([rng.normal(size=(50, 128)) * 10.0, np.tile(rng.normal(size=(1, 128)), (50, 1))])
+    v = v.astype(np.float32)
+    t = np.array([0] * 50 + [1] * 50, np.int32)
+    kappa, _, cents, ctype, labels = _run(T, v, t, 2, 3, 4, mu=1, tau=2, eps=0, theta=1.0)
+    torch.cuda.synchronize()
+    ok, oc, oct_, olab = O.cluster(v.astype(np.float64).tolist(), t.tolist(), 2, 3, mu=1, tau=2, eps=0,
+                                   theta=1.0, iters=4)
+    assert kappa.tolist() == ok == [3, 0]
+    assert labels.cpu().tolist() == olab and olab[50:] == [-1] * 50
+    bad = t.copy()
+    bad[10] = 5
+    with pytest.raises(T.TachiomError):
+        _run(T, v, bad, 2, 3, 1, mu=1, tau=2, eps=0, theta=1.0)
