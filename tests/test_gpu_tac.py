@@ -1,20 +1,16 @@
 """Token-Aware Clustering on the GPU (tachiom_tac_cluster) against the FP64 oracle (oracle/tac.py).
 
-Opt-in: set TACHIOM_TEST_TAC_GPU=1 to run these. The inputs are separated blobs per token type, so
-the nearest centroid of every vector is far from a tie and the FP32 distances of the kernel and the
-oracle's FP64 ones choose the same labels; centroids then agree to FP32 rounding (rtol 1e-6).
+The inputs are separated blobs per token type, so the nearest centroid of every vector is far from a
+tie and the FP32 distances of the kernel and the oracle's FP64 ones choose the same labels; centroids
+then agree to FP32 rounding (rtol 1e-6).
 """
-import os
-
 import numpy as np
 import pytest
 
 from oracle import tac as O
 
 torch = pytest.importorskip("torch")
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("TACHIOM_TEST_TAC_GPU") != "1",
-                                 reason="GPU clustering tests are opt-in (TACHIOM_TEST_TAC_GPU=1)")]
+pytestmark = pytest.mark.gpu
 
 PARAMS = dict(mu=5, tau=20, eps=1, theta=10.0)
 
