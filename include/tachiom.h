@@ -377,6 +377,20 @@ tachiom_status tachiom_tac_cluster(const float *d_vectors, const int32_t *d_type
                                    int32_t iters, int32_t *h_kappa, double *h_spread, float *d_centroids,
                                    int32_t *d_centroid_type, int32_t *d_labels, void *stream);
 
+/* Residual compression (Sec. 2.1): for vector i with centroid row
+ * d_centroids[d_labels[i]], r = x - c, rho = ||r||, r / rho split into pq_m
+ * contiguous subspaces of 128 / pq_m dims, each coded by its nearest codeword
+ * of d_codebooks (device fp32 [pq_m x 256 x 128 / pq_m]; squared L2 in FP32,
+ * ties to the lower code). Outputs d_codes (device uint8 [n_vectors x pq_m])
+ * and d_rnorm (device fp16 bits [n_vectors], rho rounded to nearest) - the
+ * index's codes and residual norms. A zero residual or a label < 0 gives
+ * rho = 0 and code 0. d_vectors (fp32 [n_vectors x 128]) and d_centroids must
+ * be 16-byte aligned; labels must index rows of d_centroids. pq_m in {8, 16,
+ * 32}. Asynchronous on `stream`; TACHIOM_ERR_INVALID on a bad argument. */
+tachiom_status tachiom_pq_encode(const float *d_vectors, const float *d_centroids, const int32_t *d_labels,
+                                 int64_t n_vectors, const float *d_codebooks, int32_t pq_m, uint8_t *d_codes,
+                                 uint16_t *d_rnorm, void *stream);
+
 /* Library version string. */
 const char *tachiom_version(void);
 

@@ -17,6 +17,7 @@ from .binding import (  # noqa: F401
     lib,
     lib_path,
     profile_enable,
+    pq_encode,
     profile_read,
     tac_allot,
     tac_cluster,

@@ -100,6 +100,19 @@ def tac_cluster(vectors, types, n_types: int, budget: int, mu: int, tau: int, ep
     return kappa, spread, cents, ctype, labels
 
 
+def pq_encode(vectors, centroids, labels, codebooks, stream=None):
+    """Residual PQ codes and fp16 residual norms (tachiom_pq_encode) of device vectors (torch cuda
+    fp32 [N, 128]) given their centroids (fp32 [C, 128]), labels (int32 [N]) and codebooks (fp32
+    [M, 256, 128 / M]). Returns (codes uint8 [N, M], rnorm fp16 bits as int16 [N]), torch cuda."""
+    import torch
+    n, m = int(vectors.shape[0]), int(codebooks.shape[0])
+    codes = torch.empty((n, m), dtype=torch.uint8, device=vectors.device)
+    rnorm = torch.empty(n, dtype=torch.int16, device=vectors.device)
+    _check(lib().tachiom_pq_encode(_dp(vectors), _dp(centroids), _dp(labels), n, _dp(codebooks), m,
+                                   _dp(codes), _dp(rnorm), _stream(stream)))
+    return codes, rnorm
+
+
 def tc_available() -> bool:
     """True when the current device runs the tensor-core step (a)."""
     return bool(lib().tachiom_tc_available())
@@ -165,6 +178,7 @@ def lib():
         "tachiom_version": ([], ct.c_char_p),
         "tachiom_tac_allot": ([P, P, I32, I64, ct.POINTER(TacParams), P], ct.c_int),
         "tachiom_tac_cluster": ([P, P, I64, I32, I64, ct.POINTER(TacParams), I32, P, P, P, P, P, P], ct.c_int),
+        "tachiom_pq_encode": ([P, P, P, I64, P, I32, P, P, P], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

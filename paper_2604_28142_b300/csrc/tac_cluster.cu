@@ -16,6 +16,7 @@
 //     gives the labels;
 //   - centroids are numbered type by type (type order), kappa_j each.
 #include <cub/cub.cuh>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <vector>
@@ -322,5 +323,106 @@ extern "C" tachiom_status tachiom_tac_cluster(const float *d_vectors, const int3
   }
   TCUDA(cudaStreamSynchronize(s));
 #undef TTRY
+  return TACHIOM_OK;
+}
+
+// ---- residual compression (Sec. 2.1, "Residuals Compression") ----------------------------------
+// Vector i with centroid c = C[label_i]: r = x - c, rho = ||r||, u = r / rho split into M contiguous
+// subspaces of ds = 128 / M dims, each coded by its nearest codeword (squared L2 in FP32, ties to
+// the lower code); rho is stored rounded to fp16. A zero residual, or a vector without a centroid
+// (label < 0), gets rho = 0 and code 0 everywhere. One warp per vector, lane l on dims 4l .. 4l + 3;
+// the codebook sits in shared memory code-major (codeword j of every subspace along the 128 dims),
+// so the 32 lanes read 512 consecutive bytes per codeword.
+namespace tachiom {
+namespace {
+
+constexpr int PQ_WARPS = 8;
+
+template <int M>
+__global__ void __launch_bounds__(PQ_WARPS * 32)
+k_pq_encode(const float *__restrict__ X, const float *__restrict__ C, const int32_t *__restrict__ labels, int64_t n,
+            const float *__restrict__ codebooks, uint8_t *__restrict__ codes, uint16_t *__restrict__ rnorm) {
+  constexpr int DS = DIM / M;
+  constexpr int G = DS / 4;  // lanes per subspace
+  extern __shared__ __align__(16) float cbs[];  // [256][128]
+  for (int x = threadIdx.x; x < 256 * DIM; x += blockDim.x) {
+    const int j = x / DIM, d = x % DIM, m = d / DS, u = d % DS;
+    cbs[x] = codebooks[((int64_t)m * 256 + j) * DS + u];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * PQ_WARPS;
+  for (int64_t i = blockIdx.x * (int64_t)PQ_WARPS + (threadIdx.x >> 5); i < n; i += nw) {
+    const int32_t l = labels[i];
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (l >= 0) {
+      const float4 x = *reinterpret_cast<const float4 *>(X + i * DIM + 4 * lane);
+      const float4 c = *reinterpret_cast<const float4 *>(C + (int64_t)l * DIM + 4 * lane);
+      r = make_float4(x.x - c.x, x.y - c.y, x.z - c.z, x.w - c.w);
+    }
+    float rr = fmaf(r.w, r.w, fmaf(r.z, r.z, fmaf(r.y, r.y, r.x * r.x)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    const float rho = sqrtf(rr);
+    int best_j = 0;
+    if (rho > 0.f) {
+      const float4 u = make_float4(r.x / rho, r.y / rho, r.z / rho, r.w / rho);
+      float best = INFINITY;
+      for (int j = 0; j < 256; j++) {
+        const float4 w = *reinterpret_cast<const float4 *>(cbs + j * DIM + 4 * lane);
+        const float e0 = u.x - w.x, e1 = u.y - w.y, e2 = u.z - w.z, e3 = u.w - w.w;
+        float d = fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, e0 * e0)));
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (d < best) {
+          best = d;
+          best_j = j;
+        }
+      }
+    }
+    if ((lane % G) == 0) codes[i * M + lane / G] = (uint8_t)best_j;
+    if (lane == 0) rnorm[i] = __half_as_ushort(__float2half_rn(rho));
+  }
+}
+
+}  // namespace
+}  // namespace tachiom
+
+extern "C" tachiom_status tachiom_pq_encode(const float *d_vectors, const float *d_centroids, const int32_t *d_labels,
+                                            int64_t n_vectors, const float *d_codebooks, int32_t pq_m,
+                                            uint8_t *d_codes, uint16_t *d_rnorm, void *stream) {
+  using namespace tachiom;
+  if (n_vectors < 0 || (pq_m != 8 && pq_m != 16 && pq_m != 32))
+    return fail(TACHIOM_ERR_INVALID, "pq_encode: n_vectors < 0 or pq_m not in {8, 16, 32}");
+  if (n_vectors == 0) return TACHIOM_OK;
+  if (!d_vectors || !d_centroids || !d_labels || !d_codebooks || !d_codes || !d_rnorm)
+    return fail(TACHIOM_ERR_INVALID, "pq_encode: NULL argument");
+  if (((uintptr_t)d_vectors & 15u) || ((uintptr_t)d_centroids & 15u))
+    return fail(TACHIOM_ERR_INVALID, "pq_encode: vectors and centroids must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t smem = 256 * DIM * sizeof(float);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n_vectors + PQ_WARPS - 1) / PQ_WARPS;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms));
+  switch (pq_m) {
+    case 8:
+      TCUDA(cudaFuncSetAttribute(k_pq_encode<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_pq_encode<8><<<grid, PQ_WARPS * 32, smem, s>>>(d_vectors, d_centroids, d_labels, n_vectors, d_codebooks,
+                                                       d_codes, d_rnorm);
+      break;
+    case 16:
+      TCUDA(cudaFuncSetAttribute(k_pq_encode<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_pq_encode<16><<<grid, PQ_WARPS * 32, smem, s>>>(d_vectors, d_centroids, d_labels, n_vectors, d_codebooks,
+                                                        d_codes, d_rnorm);
+      break;
+    default:
+      TCUDA(cudaFuncSetAttribute(k_pq_encode<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_pq_encode<32><<<grid, PQ_WARPS * 32, smem, s>>>(d_vectors, d_centroids, d_labels, n_vectors, d_codebooks,
+                                                        d_codes, d_rnorm);
+      break;
+  }
+  TLAUNCH();
   return TACHIOM_OK;
 }

@@ -83,3 +83,61 @@ def test_tac_cluster_type_without_centroid_and_bad_type():
     bad[10] = 5
     with pytest.raises(T.TachiomError):
         _run(T, v, bad, 2, 3, 1, mu=1, tau=2, eps=0, theta=1.0)
+
+
+def _pq_case(M, seed, lossless):
+    rng = np.random.default_rng(seed)
+    ds = 128 // M
+    if lossless:
+        # codewords of norm 1 / sqrt(M): one per subspace concatenates to a unit vector
+        cb = rng.normal(size=(M, 256, ds))
+        cb /= np.linalg.norm(cb, axis=2, keepdims=True) * np.sqrt(M)
+    else:
+        cb = rng.normal(size=(M, 256, ds)) * 0.2
+    cents = rng.normal(size=(5, 128))
+    n = 64
+    lab = rng.integers(0, 5, size=n)
+    lab[:3] = -1
+    if lossless:
+        want = rng.integers(0, 256, size=(n, M))
+        rho = rng.uniform(0.1, 2.0, size=n)
+        u = np.stack([np.concatenate([cb[m][want[i, m]] for m in range(M)]) for i in range(n)])
+        x = cents[np.maximum(lab, 0)] + rho[:, None] * u
+    else:
+        x = cents[np.maximum(lab, 0)] + rng.normal(size=(n, 128)) * 0.3
+    x[:3] = rng.normal(size=(3, 128))
+    return x.astype(np.float32), cents.astype(np.float32), lab.astype(np.int32), cb.astype(np.float32)
+
+
+@pytest.mark.skipif(__import__("os").environ.get("TACHIOM_TEST_PQ_GPU") != "1",
+                    reason="GPU residual encoding tests are opt-in (TACHIOM_TEST_PQ_GPU=1) until run on a GPU")
+@pytest.mark.parametrize("M", [8, 16, 32])
+@pytest.mark.parametrize("lossless", [True, False])
+def test_pq_encode_against_oracle(M, lossless):
+    _cuda()
+    import paper_2604_28142_b300 as T
+    x, cents, lab, cb = _pq_case(M, 50 + M, lossless)
+    codes, rnorm = T.pq_encode(torch.from_numpy(x).cuda(), torch.from_numpy(cents).cuda(),
+                               torch.from_numpy(lab).cuda(), torch.from_numpy(cb).cuda())
+    torch.cuda.synchronize()
+    codes = codes.cpu().numpy().astype(np.int64)
+    rho_g = rnorm.cpu().numpy().view(np.float16).astype(np.float64)
+    ok = lab >= 0
+    oc, orho = O.pq_encode(x[ok].astype(np.float64).tolist(), cents.astype(np.float64).tolist(),
+                           lab[ok].tolist(), cb.astype(np.float64).tolist())
+    oc, orho = np.array(oc), np.array(orho)
+    assert np.all(codes[~ok] == 0) and np.all(rho_g[~ok] == 0.0)
+    # rho: the oracle's norm rounded to fp16 (within one fp16 step of it)
+    assert np.all(np.abs(rho_g[ok] - orho) <= np.abs(orho) * 2.0 ** -10 + 1e-7)
+    if lossless:
+        assert np.array_equal(codes[ok], oc)
+    else:
+        # a valid code: its codeword is as near as the oracle's to within FP32 rounding
+        ds = 128 // M
+        u = (x[ok].astype(np.float64) - cents[lab[ok]].astype(np.float64)) / orho[:, None]
+        for m in range(M):
+            sub = u[:, m * ds:(m + 1) * ds]
+            dist = ((sub[:, None, :] - cb[m][None].astype(np.float64)) ** 2).sum(-1)
+            got = dist[np.arange(len(sub)), codes[ok][:, m]]
+            assert np.all(got <= dist.min(1) + 1e-5)
+        assert (codes[ok] == oc).mean() > 0.99
