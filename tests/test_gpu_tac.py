@@ -109,8 +109,6 @@ def _pq_case(M, seed, lossless):
     return x.astype(np.float32), cents.astype(np.float32), lab.astype(np.int32), cb.astype(np.float32)
 
 
-@pytest.mark.skipif(__import__("os").environ.get("TACHIOM_TEST_PQ_GPU") != "1",
-                    reason="GPU residual encoding tests are opt-in (TACHIOM_TEST_PQ_GPU=1) until run on a GPU")
 @pytest.mark.parametrize("M", [8, 16, 32])
 @pytest.mark.parametrize("lossless", [True, False])
 def test_pq_encode_against_oracle(M, lossless):
