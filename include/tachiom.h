@@ -391,6 +391,21 @@ tachiom_status tachiom_pq_encode(const float *d_vectors, const float *d_centroid
                                  int64_t n_vectors, const float *d_codebooks, int32_t pq_m, uint8_t *d_codes,
                                  uint16_t *d_rnorm, void *stream);
 
+/* Codebooks of the residual compression (Sec. 2.1), trained on the GPU: the
+ * normalised residuals r / ||r|| (r = x - d_centroids[label]; the zero vector
+ * for a zero residual or a label < 0) of `sample` vectors at positions
+ * floor((s + 1/2) n_vectors / sample), split into pq_m subspaces, each
+ * clustered into 256 codewords by `iters` Lloyd rounds from the sample points
+ * at positions floor((j + 1/2) sample / 256) (squared L2 in FP32, ties to the
+ * lower codeword, FP64 means in a fixed order rounded to FP32, an empty
+ * codeword keeps its place). d_codebooks: device fp32 [pq_m x 256 x
+ * 128 / pq_m] output, the layout tachiom_pq_encode and the index take.
+ * 256 <= sample <= n_vectors. Allocates its scratch and blocks until done on
+ * `stream`; TACHIOM_ERR_INVALID on a bad argument, TACHIOM_ERR_OOM. */
+tachiom_status tachiom_pq_train(const float *d_vectors, const float *d_centroids, const int32_t *d_labels,
+                                int64_t n_vectors, int32_t pq_m, int32_t sample, int32_t iters,
+                                float *d_codebooks, void *stream);
+
 /* Library version string. */
 const char *tachiom_version(void);
 

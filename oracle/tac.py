@@ -238,3 +238,33 @@ def cluster(vectors, types, n_types, budget, mu, tau, eps, theta, iters):
         for i, l in zip(members[j], lab):
             labels[i] = base + l
     return kappa, cents, ctype, labels
+
+
+def pq_sample_positions(n, s):
+    """The training sample of the codebooks: vectors at positions floor((r + 1/2) n / s), r < s."""
+    return [math.floor((r + 0.5) * n / s) for r in range(s)]
+
+
+def pq_train(vectors, centroids, labels, M, sample, iters, K=256):
+    """Codebooks of the residual compression (Sec. 2.1): the normalised residuals r / ||r|| of the
+    sampled vectors (the zero vector for a zero residual or a label < 0), split into M subspaces of
+    d / M dims, each clustered by Lloyd from its sample points at positions floor((j + 1/2) S / K),
+    j < K. Returns codebooks [M][K][d / M]."""
+    d = len(vectors[0])
+    ds = d // M
+    us = []
+    for i in pq_sample_positions(len(vectors), sample):
+        l = labels[i]
+        if l < 0:
+            us.append([0.0] * d)
+            continue
+        r = [float(x) - float(y) for x, y in zip(vectors[i], centroids[l])]
+        rho = math.sqrt(sum(x * x for x in r))
+        us.append([x / rho for x in r] if rho > 0.0 else [0.0] * d)
+    books = []
+    for m in range(M):
+        pts = [u[m * ds:(m + 1) * ds] for u in us]
+        init = [pts[p] for p in init_positions(sample, K)]
+        c, _, _ = lloyd(pts, init, iters)
+        books.append(c)
+    return books

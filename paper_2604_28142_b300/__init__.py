@@ -18,6 +18,7 @@ from .binding import (  # noqa: F401
     lib_path,
     profile_enable,
     pq_encode,
+    pq_train,
     profile_read,
     tac_allot,
     tac_cluster,

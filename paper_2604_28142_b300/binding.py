@@ -113,6 +113,16 @@ def pq_encode(vectors, centroids, labels, codebooks, stream=None):
     return codes, rnorm
 
 
+def pq_train(vectors, centroids, labels, pq_m: int, sample: int, iters: int, stream=None):
+    """Residual PQ codebooks fp32 [pq_m, 256, 128 / pq_m] (torch cuda) trained on `sample` of the
+    device vectors (tachiom_pq_train), given their centroids and labels."""
+    import torch
+    books = torch.empty((pq_m, 256, 128 // pq_m), dtype=torch.float32, device=vectors.device)
+    _check(lib().tachiom_pq_train(_dp(vectors), _dp(centroids), _dp(labels), int(vectors.shape[0]), int(pq_m),
+                                  int(sample), int(iters), _dp(books), _stream(stream)))
+    return books
+
+
 def tc_available() -> bool:
     """True when the current device runs the tensor-core step (a)."""
     return bool(lib().tachiom_tc_available())
@@ -179,6 +189,7 @@ def lib():
         "tachiom_tac_allot": ([P, P, I32, I64, ct.POINTER(TacParams), P], ct.c_int),
         "tachiom_tac_cluster": ([P, P, I64, I32, I64, ct.POINTER(TacParams), I32, P, P, P, P, P, P], ct.c_int),
         "tachiom_pq_encode": ([P, P, P, I64, P, I32, P, P, P], ct.c_int),
+        "tachiom_pq_train": ([P, P, P, I64, I32, I32, I32, P, P], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

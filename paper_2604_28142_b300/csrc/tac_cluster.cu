@@ -338,50 +338,150 @@ namespace {
 
 constexpr int PQ_WARPS = 8;
 
+// stage the codebook [M][256][DS] into shared memory code-major ([256][128]); all threads
 template <int M>
-__global__ void __launch_bounds__(PQ_WARPS * 32)
-k_pq_encode(const float *__restrict__ X, const float *__restrict__ C, const int32_t *__restrict__ labels, int64_t n,
-            const float *__restrict__ codebooks, uint8_t *__restrict__ codes, uint16_t *__restrict__ rnorm) {
+__device__ __forceinline__ void pq_stage(const float *__restrict__ codebooks, float *cbs) {
   constexpr int DS = DIM / M;
-  constexpr int G = DS / 4;  // lanes per subspace
-  extern __shared__ __align__(16) float cbs[];  // [256][128]
   for (int x = threadIdx.x; x < 256 * DIM; x += blockDim.x) {
     const int j = x / DIM, d = x % DIM, m = d / DS, u = d % DS;
     cbs[x] = codebooks[((int64_t)m * 256 + j) * DS + u];
   }
+}
+
+// nearest codeword (squared L2 in FP32, ties to the lower code) of this lane's subspace for the
+// unit vector whose dims 4 lane .. 4 lane + 3 are u; every lane of the subspace gets the answer
+template <int M>
+__device__ __forceinline__ int pq_nearest(const float4 u, const float *cbs, int lane) {
+  constexpr int G = DIM / M / 4;  // lanes per subspace
+  float best = INFINITY;
+  int best_j = 0;
+  for (int j = 0; j < 256; j++) {
+    const float4 w = *reinterpret_cast<const float4 *>(cbs + j * DIM + 4 * lane);
+    const float e0 = u.x - w.x, e1 = u.y - w.y, e2 = u.z - w.z, e3 = u.w - w.w;
+    float d = fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, e0 * e0)));
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (d < best) {
+      best = d;
+      best_j = j;
+    }
+  }
+  return best_j;
+}
+
+// vector i's residual from its centroid (zero for a label < 0), this lane's 4 dims, and its norm
+__device__ __forceinline__ float4 pq_residual(const float *__restrict__ X, const float *__restrict__ C, int32_t l,
+                                              int64_t i, int lane, float &rho) {
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (l >= 0) {
+    const float4 x = *reinterpret_cast<const float4 *>(X + i * DIM + 4 * lane);
+    const float4 c = *reinterpret_cast<const float4 *>(C + (int64_t)l * DIM + 4 * lane);
+    r = make_float4(x.x - c.x, x.y - c.y, x.z - c.z, x.w - c.w);
+  }
+  float rr = fmaf(r.w, r.w, fmaf(r.z, r.z, fmaf(r.y, r.y, r.x * r.x)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+  rho = sqrtf(rr);
+  return r;
+}
+
+template <int M>
+__global__ void __launch_bounds__(PQ_WARPS * 32)
+k_pq_encode(const float *__restrict__ X, const float *__restrict__ C, const int32_t *__restrict__ labels, int64_t n,
+            const float *__restrict__ codebooks, uint8_t *__restrict__ codes, uint16_t *__restrict__ rnorm) {
+  constexpr int G = DIM / M / 4;  // lanes per subspace
+  extern __shared__ __align__(16) float cbs[];  // [256][128]
+  pq_stage<M>(codebooks, cbs);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * PQ_WARPS;
   for (int64_t i = blockIdx.x * (int64_t)PQ_WARPS + (threadIdx.x >> 5); i < n; i += nw) {
-    const int32_t l = labels[i];
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (l >= 0) {
-      const float4 x = *reinterpret_cast<const float4 *>(X + i * DIM + 4 * lane);
-      const float4 c = *reinterpret_cast<const float4 *>(C + (int64_t)l * DIM + 4 * lane);
-      r = make_float4(x.x - c.x, x.y - c.y, x.z - c.z, x.w - c.w);
-    }
-    float rr = fmaf(r.w, r.w, fmaf(r.z, r.z, fmaf(r.y, r.y, r.x * r.x)));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
-    const float rho = sqrtf(rr);
+    float rho;
+    const float4 r = pq_residual(X, C, labels[i], i, lane, rho);
     int best_j = 0;
-    if (rho > 0.f) {
-      const float4 u = make_float4(r.x / rho, r.y / rho, r.z / rho, r.w / rho);
-      float best = INFINITY;
-      for (int j = 0; j < 256; j++) {
-        const float4 w = *reinterpret_cast<const float4 *>(cbs + j * DIM + 4 * lane);
-        const float e0 = u.x - w.x, e1 = u.y - w.y, e2 = u.z - w.z, e3 = u.w - w.w;
-        float d = fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, e0 * e0)));
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        if (d < best) {
-          best = d;
-          best_j = j;
-        }
-      }
-    }
+    if (rho > 0.f) best_j = pq_nearest<M>(make_float4(r.x / rho, r.y / rho, r.z / rho, r.w / rho), cbs, lane);
     if ((lane % G) == 0) codes[i * M + lane / G] = (uint8_t)best_j;
     if (lane == 0) rnorm[i] = __half_as_ushort(__float2half_rn(rho));
+  }
+}
+
+// codebook training, sample r (one warp each): the normalised residual of vector
+// floor((r + 1/2) n / S), the zero vector for a zero residual or a label < 0
+__global__ void k_pq_sample(const float *__restrict__ X, const float *__restrict__ C,
+                            const int32_t *__restrict__ labels, int64_t n, int32_t S, float *__restrict__ U) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < S; r += nw) {
+    const int64_t i = (int64_t)floor(((double)r + 0.5) * (double)n / (double)S);
+    float rho;
+    const float4 v = pq_residual(X, C, labels[i], i, lane, rho);
+    const float4 u = rho > 0.f ? make_float4(v.x / rho, v.y / rho, v.z / rho, v.w / rho) : make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4 *>(U + r * DIM + 4 * lane) = u;
+  }
+}
+
+// initial codeword (m, j): sub-vector m of sample point floor((j + 1/2) S / 256)
+template <int M>
+__global__ void k_pq_init(const float *__restrict__ U, int32_t S, float *__restrict__ books) {
+  constexpr int DS = DIM / M;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < M * 256 * DS; x += gridDim.x * blockDim.x) {
+    const int m = x / (256 * DS), j = (x / DS) % 256, u = x % DS;
+    const int64_t p = (int64_t)floor(((double)j + 0.5) * (double)S / 256.0);
+    books[x] = U[p * DIM + m * DS + u];
+  }
+}
+
+// sample s (one warp each) to its nearest codeword of every subspace: key m * 256 + code at
+// [m * S + s], value s
+template <int M>
+__global__ void __launch_bounds__(PQ_WARPS * 32)
+k_pq_assign_unit(const float *__restrict__ U, int32_t S, const float *__restrict__ books, int32_t *__restrict__ keys,
+                 int32_t *__restrict__ vals) {
+  constexpr int G = DIM / M / 4;
+  extern __shared__ __align__(16) float cbs[];
+  pq_stage<M>(books, cbs);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * PQ_WARPS;
+  for (int64_t s = blockIdx.x * (int64_t)PQ_WARPS + (threadIdx.x >> 5); s < S; s += nw) {
+    const float4 u = *reinterpret_cast<const float4 *>(U + s * DIM + 4 * lane);
+    const int j = pq_nearest<M>(u, cbs, lane);
+    if ((lane % G) == 0) {
+      const int m = lane / G;
+      keys[(int64_t)m * S + s] = m * 256 + j;
+      vals[(int64_t)m * S + s] = (int32_t)s;
+    }
+  }
+}
+
+// codeword k = m * 256 + j (one warp each) to the FP64 mean of its members' sub-vectors m, rounded
+// to FP32 (lane l sums members l, l + 32, ...; the lanes are added by a fixed butterfly); a
+// codeword without members keeps its place
+template <int M>
+__global__ void k_pq_means(const float *__restrict__ U, const int32_t *__restrict__ vals,
+                           const int64_t *__restrict__ off, float *__restrict__ books) {
+  constexpr int DS = DIM / M;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t k = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); k < M * 256; k += nw) {
+    const int64_t b = off[k], e1 = off[k + 1];
+    if (b == e1) continue;
+    const int m = (int)(k / 256);
+    double acc[DS];
+#pragma unroll
+    for (int u = 0; u < DS; u++) acc[u] = 0.0;
+    for (int64_t q = b + lane; q < e1; q += 32) {
+      const float *src = U + (int64_t)vals[q] * DIM + m * DS;
+#pragma unroll
+      for (int u = 0; u < DS; u++) acc[u] += (double)src[u];
+    }
+#pragma unroll
+    for (int u = 0; u < DS; u++) {
+      double t = acc[u];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) books[k * DS + u] = (float)(t / (double)(e1 - b));
+    }
   }
 }
 
@@ -425,4 +525,65 @@ extern "C" tachiom_status tachiom_pq_encode(const float *d_vectors, const float 
   }
   TLAUNCH();
   return TACHIOM_OK;
+}
+
+namespace {
+template <int M>
+tachiom_status pq_train_m(const float *X, const float *C, const int32_t *labels, int64_t n, int32_t S, int32_t iters,
+                          float *books, cudaStream_t s) {
+  using namespace tachiom;
+  TacBufs B;
+  tachiom_status st;
+  float *U;
+  int32_t *keys, *vals, *keys_s, *vals_s;
+  int64_t *off;
+  const int64_t nk = (int64_t)M * S;
+  if ((st = B.alloc(&U, (size_t)S * DIM))) return st;
+  if ((st = B.alloc(&keys, (size_t)nk))) return st;
+  if ((st = B.alloc(&vals, (size_t)nk))) return st;
+  if ((st = B.alloc(&keys_s, (size_t)nk))) return st;
+  if ((st = B.alloc(&vals_s, (size_t)nk))) return st;
+  if ((st = B.alloc(&off, (size_t)M * 256 + 1))) return st;
+  size_t tmp_bytes = 0;
+  TCUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys_s, vals, vals_s, (int)nk, 0, 32, s));
+  unsigned char *tmp;
+  if ((st = B.alloc(&tmp, tmp_bytes))) return st;
+  const size_t smem = 256 * DIM * sizeof(float);
+  TCUDA(cudaFuncSetAttribute(k_pq_assign_unit<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_pq_sample<<<grid_for(S, 8), 256, 0, s>>>(X, C, labels, n, S, U);
+  TLAUNCH();
+  k_pq_init<M><<<grid_for((int64_t)M * 256 * (DIM / M), 256), 256, 0, s>>>(U, S, books);
+  TLAUNCH();
+  for (int32_t it = 0; it < iters; it++) {
+    k_pq_assign_unit<M><<<grid_for(S, PQ_WARPS), PQ_WARPS * 32, smem, s>>>(U, S, books, keys, vals);
+    TLAUNCH();
+    TCUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys_s, vals, vals_s, (int)nk, 0, 32, s));
+    k_tac_bounds<<<grid_for((int64_t)M * 256 + 1, 256), 256, 0, s>>>(keys_s, nk, (int64_t)M * 256, off);
+    TLAUNCH();
+    k_pq_means<M><<<grid_for((int64_t)M * 256, 8), 256, 0, s>>>(U, vals_s, off, books);
+    TLAUNCH();
+  }
+  TCUDA(cudaStreamSynchronize(s));
+  return TACHIOM_OK;
+}
+}  // namespace
+
+extern "C" tachiom_status tachiom_pq_train(const float *d_vectors, const float *d_centroids, const int32_t *d_labels,
+                                           int64_t n_vectors, int32_t pq_m, int32_t sample, int32_t iters,
+                                           float *d_codebooks, void *stream) {
+  using namespace tachiom;
+  if (pq_m != 8 && pq_m != 16 && pq_m != 32)
+    return fail(TACHIOM_ERR_INVALID, "pq_train: pq_m must be 8, 16 or 32");
+  if (sample < 256 || sample > n_vectors || iters < 0 || (int64_t)sample * pq_m >= INT32_MAX)
+    return fail(TACHIOM_ERR_INVALID, "pq_train: need 256 <= sample <= n_vectors, sample * pq_m < 2^31, iters >= 0");
+  if (!d_vectors || !d_centroids || !d_labels || !d_codebooks)
+    return fail(TACHIOM_ERR_INVALID, "pq_train: NULL argument");
+  if (((uintptr_t)d_vectors & 15u) || ((uintptr_t)d_centroids & 15u))
+    return fail(TACHIOM_ERR_INVALID, "pq_train: vectors and centroids must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (pq_m) {
+    case 8: return pq_train_m<8>(d_vectors, d_centroids, d_labels, n_vectors, sample, iters, d_codebooks, s);
+    case 16: return pq_train_m<16>(d_vectors, d_centroids, d_labels, n_vectors, sample, iters, d_codebooks, s);
+    default: return pq_train_m<32>(d_vectors, d_centroids, d_labels, n_vectors, sample, iters, d_codebooks, s);
+  }
 }

@@ -139,3 +139,50 @@ def test_pq_encode_against_oracle(M, lossless):
             got = dist[np.arange(len(sub)), codes[ok][:, m]]
             assert np.all(got <= dist.min(1) + 1e-5)
         assert (codes[ok] == oc).mean() > 0.99
+
+
+def _pq_train_case(M, seed):
+    """Vectors whose sampled normalised residuals fall, in every subspace, into 256 tight clusters of
+    two consecutive sample points: the evenly spaced initial codewords (positions 2 j + 1) take one
+    point of each cluster, so Lloyd's answer is the mean of every pair."""
+    rng = np.random.default_rng(seed)
+    ds = 128 // M
+    true = rng.normal(size=(M, 256, ds))
+    true /= np.linalg.norm(true, axis=2, keepdims=True) * np.sqrt(M)
+    perm = np.stack([rng.permutation(256) for _ in range(M)])
+    n = 512
+    cid = perm[:, np.arange(n) // 2]                               # [M, n]: cluster of sample r
+    u = np.concatenate([true[m][cid[m]] for m in range(M)], axis=1) + 1e-5 * rng.normal(size=(n, 128))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    cents = rng.normal(size=(4, 128))
+    lab = rng.integers(0, 4, size=n)
+    x = cents[lab] + rng.uniform(0.2, 2.0, size=(n, 1)) * u
+    return x.astype(np.float32), cents.astype(np.float32), lab.astype(np.int32), cid
+
+
+@pytest.mark.skipif(__import__("os").environ.get("TACHIOM_TEST_PQ_TRAIN_GPU") != "1",
+                    reason="GPU codebook training tests are opt-in (TACHIOM_TEST_PQ_TRAIN_GPU=1) until run on a GPU")
+@pytest.mark.parametrize("M", [8, 16, 32])
+def test_pq_train_closed_form(M):
+    _cuda()
+    import paper_2604_28142_b300 as T
+    x, cents, lab, cid = _pq_train_case(M, 70 + M)
+    dx, dc, dl = torch.from_numpy(x).cuda(), torch.from_numpy(cents).cuda(), torch.from_numpy(lab).cuda()
+    books = T.pq_train(dx, dc, dl, M, sample=512, iters=3)
+    torch.cuda.synchronize()
+    # the sample is every vector (positions floor(r + 1/2) = r); its normalised residuals in FP64
+    r = x.astype(np.float64) - cents[lab].astype(np.float64)
+    u = r / np.linalg.norm(r, axis=1, keepdims=True)
+    ds = 128 // M
+    b = books.cpu().numpy().astype(np.float64)
+    for m in range(M):
+        sub = u[:, m * ds:(m + 1) * ds]
+        for j in range(256):
+            want = sub[2 * j:2 * j + 2].mean(0)  # codeword j started at sample 2 j + 1: cluster of pair j
+            assert np.allclose(b[m, j], want, atol=1e-6), (m, j)
+    # encoding the sample with the trained codebooks gives back each sample's pair
+    codes, _ = T.pq_encode(dx, dc, dl, books)
+    torch.cuda.synchronize()
+    assert np.array_equal(codes.cpu().numpy().astype(np.int64), np.repeat(np.arange(256), 2)[:, None].repeat(M, 1))
+    # the same call repeats bit for bit
+    assert torch.equal(T.pq_train(dx, dc, dl, M, sample=512, iters=3), books)

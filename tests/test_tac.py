@@ -325,3 +325,22 @@ def test_oracle_init_positions_and_cluster():
         for g in ids:
             if (lab == g).any():
                 assert np.allclose(cents[g], v[lab == g].mean(0), atol=1e-12)
+
+
+def test_oracle_pq_train_closed_forms():
+    rng = np.random.default_rng(61)
+    x, c = rng.normal(size=(64, 8)), rng.normal(size=(3, 8))
+    lab = rng.integers(0, 3, size=64)
+    lab[5] = -1
+    r = x - c[np.maximum(lab, 0)]
+    u = r / np.linalg.norm(r, axis=1, keepdims=True)
+    u[5] = 0.0  # a label < 0 trains as the zero vector
+    # K = S: every sampled vector is its own codeword (the sample is every vector when S = N)
+    books = O.pq_train(x.tolist(), c.tolist(), lab.tolist(), M=2, sample=64, iters=2, K=64)
+    for m in range(2):
+        assert np.allclose(np.array(books[m]), u[:, 4 * m:4 * m + 4], atol=1e-12)
+    # K = 1: the mean of the sampled sub-vectors
+    books = O.pq_train(x.tolist(), c.tolist(), lab.tolist(), M=4, sample=32, iters=1, K=1)
+    pos = O.pq_sample_positions(64, 32)
+    for m in range(4):
+        assert np.allclose(books[m][0], u[pos, 2 * m:2 * m + 2].mean(0), atol=1e-12)
