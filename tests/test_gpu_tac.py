@@ -186,3 +186,47 @@ def test_pq_train_closed_form(M):
     assert np.array_equal(codes.cpu().numpy().astype(np.int64), np.repeat(np.arange(256), 2)[:, None].repeat(M, 1))
     # the same call repeats bit for bit
     assert torch.equal(T.pq_train(dx, dc, dl, M, sample=512, iters=3), books)
+
+
+@pytest.mark.skipif(__import__("os").environ.get("TACHIOM_TEST_PQ_TRAIN_GPU") != "1",
+                    reason="index building uses the GPU codebook training, opt-in until run on a GPU")
+@pytest.mark.parametrize("centroid_dtype", ["f32", "bf16"])
+def test_index_built_on_gpu_searches_like_the_oracle(centroid_dtype):
+    # an index built from raw vectors by the library's kernels, searched in both precisions, gives
+    # the FP64 oracle's results on the same index arrays
+    _cuda()
+    import paper_2604_28142_b300 as T
+    from paper_2604_28142_b300.index_build import build_index
+    from oracle import Oracle
+    from compare import check_ranking
+    rng = np.random.default_rng(81)
+    n_types, n_docs = 60, 400
+    lens = rng.integers(4, 40, size=n_docs)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    Tn = int(off[-1])
+    p = 1.0 / np.arange(1, n_types + 1) ** 1.1
+    types = rng.choice(n_types, size=Tn, p=p / p.sum()).astype(np.int32)
+    dirs = rng.normal(size=(n_types, 3, 128))
+    v = dirs[types, rng.integers(0, 3, size=Tn)] + 0.4 * rng.normal(size=(Tn, 128))
+    v = (v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+    ix = build_index(torch.from_numpy(v).cuda(), torch.from_numpy(types).cuda(), off, n_types, 512,
+                     mu=3, tau=12, eps=1, theta=4.0, iters=5, pq_m=16, pq_sample=1024, pq_iters=4,
+                     centroid_dtype=centroid_dtype)
+    assert ix["centroids"].shape[0] == 512 and ix["token_centroid"].min() >= 0
+    G, O_ = T.Index(ix, 0), Oracle(ix)
+    qi = rng.integers(0, Tn, size=(6, 16))
+    q = v[qi].reshape(-1, 128) + 0.05 * rng.normal(size=(96, 128)).astype(np.float32)
+    q = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    ntok = np.full(6, 16, np.int32)
+    k, kc, kd = 10, 8, 100
+    want = O_.search(q, ntok, k, kc, kd)
+    for prec in (T.PREC_FP32, T.PREC_BF16):
+        oi = torch.empty(6 * k, dtype=torch.int32, device="cuda")
+        os_ = torch.empty(6 * k, dtype=torch.float32, device="cuda")
+        G.search(T.SearchParams(kappa_c=kc, kappa_d=kd, precision=prec), torch.from_numpy(q).cuda(), ntok,
+                 np.full(6, k, np.int32), oi, os_)
+        torch.cuda.synchronize()
+        gi, gs = oi.cpu().numpy(), os_.cpu().numpy()
+        for u in range(6):
+            sl = slice(u * k, (u + 1) * k)
+            check_ranking(gi[sl], gs[sl], want["ids"][sl], want["scores"][sl], 1e-5, 1e-4, what=f"query {u}")
