@@ -2,10 +2,12 @@
 """Throughput of the gather-and-refine scoring path (QPS, p50/p99 batch latency).
 
 One step = one batch of queries through all four steps (top centroids, gather,
-refine, top-k) on synthetic data shaped like the passage-ranking workload
-(1M docs, ~70M tokens, 262,144 bf16 centroids, 16-byte PQ codes, batches of
-64 queries x 32 tokens, k = 10). Every reported number states its accuracy
-against the FP64 oracle on a sample of the timed queries.
+refine, top-k) on synthetic data shaped like the full-scale passage-ranking
+workload (8.8M docs, ~594M tokens, 2,097,152 bf16 centroids, 16-byte PQ codes,
+batches of 256 queries x 32 tokens, k = 10); --workload picks another one
+(msmarco-1M: 1M docs, batches of 64; lotte-2.8M: 2.8M docs, 32-byte codes,
+512 queries of 8-32 tokens). Every reported number states its accuracy against
+the FP64 oracle on a sample of the timed queries.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
 
@@ -29,7 +31,10 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOAD = "msmarco-1M"
+WORKLOAD = "msmarco-8.8M"
+# per workload: queries per batch, token count range of a query
+SHAPES = {"tiny": (16, 32, 32), "msmarco-1M": (64, 32, 32), "msmarco-8.8M": (256, 32, 32),
+          "lotte-2.8M": (512, 8, 32)}
 
 
 def parse():
@@ -39,19 +44,32 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=0, help="queries per batch (0: the workload's)")
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--kc", type=int, default=40)
     ap.add_argument("--kd", type=int, default=1000)
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
-    ap.add_argument("--oracle-queries", type=int, default=16)
+    ap.add_argument("--oracle-queries", type=int, default=0,
+                    help="queries checked against the oracle (0: one per host core, at most 16)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="short run for ncu captures")
     ap.add_argument("--single-queries", type=int, default=32,
                     help="queries of the FP32 one-query-at-a-time comparator")
     ap.add_argument("--no-single", action="store_true")
     ap.add_argument("--no-rerank", action="store_true", help="skip the rerank-only measurement")
-    return ap.parse_args()
+    ap.add_argument("--no-sweep", action="store_true", help="skip the k = 100 / 1000 and FP32 batched lines")
+    a = ap.parse_args()
+    shape = SHAPES.get(a.workload, (64, 32, 32))
+    if a.batch <= 0:
+        a.batch = shape[0]
+    a.ntok_min, a.ntok_max = shape[1], shape[2]
+    if a.oracle_queries <= 0:
+        a.oracle_queries = min(16, host_cores())
+    return a
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
 # clock-event reason bits of NVML (nvmlClocksEventReason*), the ones a bench line reports
@@ -254,9 +272,11 @@ def measured_traffic(kernel, workload, batch):
     or None when there is none or the kernel's source has changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.txt")
-    if batch != 64 or not os.path.exists(path):
+    if not os.path.exists(path):
         return None
     for line in open(path):
+        if line.startswith("# batch ") and int(line.split()[2]) != batch:
+            return None
         f = line.split()
         if len(f) != 4 or line.startswith("#") or f[0] != kernel:
             continue
@@ -264,6 +284,47 @@ def measured_traffic(kernel, workload, batch):
         if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest() == f[3]:
             return int(f[1])
     return None
+
+
+def data_desc(a):
+    shape = "long-tail QA" if a.workload.startswith("lotte") else "passage-ranking"
+    return f"synthetic (seeded generator shaped like the {shape} workload)"
+
+
+def workload_desc(a, ix):
+    return (f"{a.workload}: {ix['doc_offsets'].shape[0] - 1} docs, {int(ix['doc_offsets'][-1])} tokens, "
+            f"C={ix['centroids'].shape[0]} {ix['centroid_dtype']}, PQ {ix['pq_codebooks'].shape[0]}x8b")
+
+
+def tok_desc(a):
+    return a.ntok_min if a.ntok_min == a.ntok_max else f"{a.ntok_min}-{a.ntok_max} (uniform, packed)"
+
+
+def time_batches(G, params, batches, idx, k, flush, torch):
+    """CUDA-event time of G.search over the batches idx (k per query), L2 flushed between
+    batches outside the events; returns the per-batch ms and the status flags."""
+    stream = torch.cuda.current_stream()
+    out = []
+    for b in idx[:2]:  # sizes the scratch for this k
+        nq = len(batches[b][1])
+        oi = torch.empty(nq * k, dtype=torch.int32, device="cuda")
+        os_ = torch.empty(nq * k, dtype=torch.float32, device="cuda")
+        G.search(params, batches[b][0], batches[b][1], np.full(nq, k, np.int32), oi, os_)
+    torch.cuda.synchronize()
+    G.stream_status()
+    for b in idx:
+        nq = len(batches[b][1])
+        kk = np.full(nq, k, np.int32)
+        oi = torch.empty(nq * k, dtype=torch.int32, device="cuda")
+        os_ = torch.empty(nq * k, dtype=torch.float32, device="cuda")
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.search(params, batches[b][0], batches[b][1], kk, oi, os_)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return np.array(out), G.stream_status()
 
 
 def fp32_one_at_a_time(T, G, a, batch, batched_ids, torch):
@@ -378,7 +439,9 @@ def algorithmic_traffic(T_idx, ix, params, dq, ntok, k, kc, kd, torch):
     lens = (off[t + 1] - off[t]).astype(np.int64)
     entries = int(lens.sum())
     D = ix["doc_offsets"].shape[0] - 1
-    gather_bytes = entries * 4 + R * kc * 8 + nq * D * 4
+    # the algorithmic bytes of step (b): every list entry walked (4 B), every Top_i entry (id and
+    # score, 8 B) and the kappa_d (doc, score) outputs of each query (8 B)
+    gather_bytes = entries * 4 + R * kc * 8 + nq * kd * 8
     cand = cid.cpu().numpy()
     doff = ix["doc_offsets"]
     c = cand[cand >= 0]
@@ -387,7 +450,7 @@ def algorithmic_traffic(T_idx, ix, params, dq, ntok, k, kc, kd, torch):
     cbytes = 2 if ix["centroid_dtype"] == "bf16" else 4
     refine_bytes = ntoks * (4 + M + 2 + 128 * cbytes)
     return {"list_entries": entries, "gather_bytes": gather_bytes, "refine_tokens": ntoks,
-            "refine_bytes": refine_bytes, "select_bytes": nq * D * 4, "_cand": cid}
+            "refine_bytes": refine_bytes, "select_bytes": nq * kd * 8, "_cand": cid}
 
 
 def run_ours(a):
@@ -411,8 +474,8 @@ def run_ours(a):
         prec = T.PREC_BF16 if a.precision == "bf16" else T.PREC_FP32
     params = T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=prec)
     nb = a.warmup + a.steps
-    q = synth.make_queries(cfg, n_queries=nb * a.batch, seed=rank_query_seed(cfg, rank), ntok_min=32,
-                           ntok_max=32)
+    q = synth.make_queries(cfg, n_queries=nb * a.batch, seed=rank_query_seed(cfg, rank), ntok_min=a.ntok_min,
+                           ntok_max=a.ntok_max)
     qs, ntok = q["queries"], q["ntok"]
     qoff = np.concatenate([[0], np.cumsum(ntok)])
     batches = []
@@ -480,6 +543,22 @@ def run_ours(a):
     single = None
     if not a.no_single:
         single = fp32_one_at_a_time(T, G, a, batches[a.warmup], out_i[a.warmup], torch)
+    # ---- the same batches with k = 100 and k = 1000 (kappa_d = max(1000, 4k)), and the FP32 path batched ----
+    sweep = None
+    if not a.no_sweep:
+        idx = list(range(a.warmup, min(nb, a.warmup + 5)))
+        sweep = {}
+        for kx in (100, 1000):
+            pk = T.SearchParams(kappa_c=a.kc, kappa_d=0, precision=prec)
+            ms, fl = time_batches(G, pk, batches, idx, kx, flush, torch)
+            sweep[f"k{kx}"] = {"value": float(a.batch * len(ms) / (ms.sum() / 1e3)), "unit": "queries/s",
+                               "ms_per_step": float(ms.mean()), "kappa_d": min(4096, max(1000, 4 * kx)),
+                               "status_flags": int(fl)}
+        if prec != T.PREC_FP32:
+            ms, fl = time_batches(G, T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=T.PREC_FP32), batches,
+                                  idx, a.k, flush, torch)
+            sweep["fp32_batched"] = {"value": float(a.batch * len(ms) / (ms.sum() / 1e3)), "unit": "queries/s",
+                                     "ms_per_step": float(ms.mean()), "k": a.k, "status_flags": int(fl)}
     # ---- the rerank-only use of steps (c)-(d): external candidate lists ----
     rerank = None
     if not a.no_rerank:
@@ -524,14 +603,14 @@ def run_ours(a):
     name, (launches, ms) = dom
     per_launch_ms = ms / max(1, launches)
     clocks = clk.summary()
-    R = a.batch * 32
+    R = float(np.mean([len(batches[a.warmup + s][0]) for s in range(a.steps)]))  # query rows per batch
     C = ix["centroids"].shape[0]
     gemm_flops = 2.0 * R * C * 128
-    hbm_kernels = {"gather": ("k_gather_sort", traffic["gather_bytes"]),
+    hbm_kernels = {"gather": ("k_gather_pool", traffic["gather_bytes"]),
                    "refine": ("k_refine", traffic["refine_bytes"]),
                    "refine_tc": ("k_refine_tc", traffic["refine_bytes"]),
                    "refine_dec": ("k_refine_dec", traffic["refine_bytes"]),
-                   "select_kd": ("k_sel_*", traffic["select_bytes"])}
+                   "select_kd": ("k_pool_select", traffic["select_bytes"])}
     if name in hbm_kernels:
         kname, nbytes = hbm_kernels[name]
         roof = {"kernel": kname, "bound": "hbm", "achieved": nbytes / (per_launch_ms * 1e-3) / 1e9,
@@ -555,7 +634,7 @@ def run_ours(a):
     roof["peak_source"] = peak_src
     roof["traffic"] = measured_traffic(roof["kernel"], a.workload, a.batch)
     roof["per_launch_ms"] = per_launch_ms
-    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ncores = min(on, host_cores())  # the oracle runs one thread per query
     lat = step_ms
     line = {
         "metric": "QPS at top-10 overlap >=0.99 vs FP64 oracle; p50/p99 latency ms",
@@ -569,10 +648,9 @@ def run_ours(a):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "bf16/f32" if prec == T.PREC_BF16 else "f32",
-        "data": "synthetic (seeded generator shaped like the passage-ranking workload)",
-        "config": {"workload": f"{a.workload}: {ix['doc_offsets'].shape[0] - 1} docs, {int(ix['doc_offsets'][-1])} "
-                               f"tokens, C={ix['centroids'].shape[0]} {ix['centroid_dtype']}, PQ {ix['pq_codebooks'].shape[0]}x8b",
-                   "batch": a.batch, "tokens_per_query": 32, "k": a.k, "kappa_c": a.kc, "kappa_d": a.kd,
+        "data": data_desc(a),
+        "config": {"workload": workload_desc(a, ix),
+                   "batch": a.batch, "tokens_per_query": tok_desc(a), "k": a.k, "kappa_c": a.kc, "kappa_d": a.kd,
                    "precision": "bf16" if prec == T.PREC_BF16 else "fp32",
                    "l2": "flushed between steps (256 MiB write outside the step's events)",
                    "parallelism": f"replicas x{world}"},
@@ -588,6 +666,7 @@ def run_ours(a):
         "clocks": clocks,
         "e2e": e2e,
         "fp32_one_query_at_a_time": single,
+        "sweep": sweep,
         "rerank_only": rerank,
         "gpu_launches": _count_launches(prof),
     }
@@ -597,9 +676,8 @@ def run_ours(a):
 
 
 def _count_launches(prof):
-    # kernels per launcher call: select_kd launches 8 kernels, topc_tc 4 (GEMM, lim, collect,
-    # rescoring), topc_merge 2, the others 1
-    per = {"select_kd": 8, "topc_merge": 2, "topc_tc": 4}
+    # kernels per launcher call: topc_tc 4 (GEMM, lim, collect, rescoring), topc_merge 2, the others 1
+    per = {"topc_merge": 2, "topc_tc": 4}
     return sum(v[0] * per.get(k, 1) for k, v in prof.items())
 
 
@@ -613,9 +691,11 @@ def run_reference(a):
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     ix = synth.load_or_make(a.workload, device=dev)
     O = Oracle(ix)
-    per_step = 8
+    # one query per host core and step (the oracle runs its queries in parallel), at most 16
+    per_step = max(1, min(16, host_cores()))
     nb = a.warmup + a.steps
-    q = synth.make_queries(cfg, n_queries=nb * per_step, seed=cfg.query_seed, ntok_min=32, ntok_max=32)
+    q = synth.make_queries(cfg, n_queries=nb * per_step, seed=cfg.query_seed, ntok_min=a.ntok_min,
+                           ntok_max=a.ntok_max)
     qs, ntok = q["queries"], q["ntok"]
     qoff = np.concatenate([[0], np.cumsum(ntok)])
     times = []
@@ -627,14 +707,14 @@ def run_reference(a):
             times.append(time.perf_counter() - t0)
     tot = sum(times)
     qps = a.steps * per_step / tot
-    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ncores = min(per_step, host_cores())
     line = {
         "impl": "reference",
         "metric": "QPS at top-10 overlap >=0.99 vs FP64 oracle; p50/p99 latency ms",
         "value": qps, "unit": "queries/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded generator shaped like the passage-ranking workload)",
-        "config": {"workload": a.workload, "batch": per_step, "tokens_per_query": 32, "k": a.k,
+        "dtype": "f64", "data": data_desc(a),
+        "config": {"workload": workload_desc(a, ix), "batch": per_step, "tokens_per_query": tok_desc(a), "k": a.k,
                    "kappa_c": a.kc, "kappa_d": a.kd},
         "latency_ms": {"p50": float(np.percentile(times, 50) * 1e3), "p99": float(np.percentile(times, 99) * 1e3)},
         "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": ncores, "kind": "oracle",

@@ -69,9 +69,8 @@ enum {
 enum {
   TACHIOM_FLAG_TOPC_RESCUED = 1u << 0,   /* a row's candidate buffer overflowed in step (a);
                                             that row was recomputed exactly */
-  TACHIOM_FLAG_SELECT_TIES = 1u << 1,    /* the kappa_d cut fell in a run of exactly equal
-                                            scores wider than the fast buffer; the ordered
-                                            tie pass ran */
+  TACHIOM_FLAG_SELECT_TIES = 1u << 1,    /* reserved (no longer raised: the kappa_d selection
+                                            orders equal scores by doc id in every case) */
   TACHIOM_FLAG_CAPACITY = 1u << 2,       /* a buffer overflow that could not be rescued: the
                                             affected query's result may be incomplete */
   TACHIOM_FLAG_BAD_INPUT = 1u << 3,      /* a device-side range check failed */

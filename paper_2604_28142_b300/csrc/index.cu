@@ -4,6 +4,7 @@
 // assigned to centroid c_j (Sec. 2.2, "Index Structure"); each list is kept
 // deduplicated and in ascending doc order so that a gather range [r0, r0+R)
 // of documents is one contiguous slice of every list.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -36,9 +37,17 @@ tachiom_status fail(tachiom_status st, const char *fmt, ...) {
   return st;
 }
 
-// documents per gather range: the gather kernel keeps two 4-byte words per
-// document of its range in shared memory
-constexpr int kRangeDocs = 24576;
+// Gather ranges: a range is a block of consecutive document ids; the offset
+// table gives the slice of every list that starts at a range boundary, and the
+// gather finds finer cuts by binary search inside a slice. The ranges are sized
+// so that a 32-token query with kappa_c = 40 has about kRangeEntries of its list
+// entries in one range when its tokens hit lists of the token-weighted length
+// Lw = sum_j n_j |L_j| / T (the gather merges consecutive ranges into one piece
+// of work when a query's entries are sparser than that), and the table is kept
+// below the size of the lists themselves. Document offsets inside a range must
+// fit 20 bits.
+constexpr int64_t kRangeEntries = 2048;
+constexpr int64_t kRangeDocsMax = 1 << 20;
 
 __global__ void k_widen_bf16(const uint16_t *__restrict__ in, float *__restrict__ out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -195,16 +204,32 @@ extern "C" tachiom_status tachiom_index_load(const tachiom_index_desc *desc, int
         if (last[j] != (int32_t)d) { last[j] = (int32_t)d; ldoc[fill[j]++] = (int32_t)d; }
       }
   }
+  // range size from the token-weighted list length
+  {
+    std::vector<int64_t> ntokj(C, 0);
+    for (int64_t t = 0; t < T; t++) ntokj[cid[t]]++;
+    double lw = 0.0;
+    for (int64_t j = 0; j < C; j++) lw += (double)ntokj[j] * (double)(loff[j + 1] - loff[j]);
+    lw = T > 0 ? lw / (double)T : 0.0;
+    const double entries = (double)MAX_NTOK * 40.0 * lw;
+    int64_t nr = (int64_t)std::ceil(entries / (double)kRangeEntries);
+    nr = std::max<int64_t>(nr, (D + kRangeDocsMax - 1) / kRangeDocsMax);
+    const int64_t nr_cap = std::max<int64_t>(1, std::max<int64_t>(ix->n_list, 16LL << 20) / std::max<int64_t>(1, C)) - 1;
+    nr = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(nr, nr_cap), D));
+    int64_t rd = (D + nr - 1) / nr;
+    if (rd > kRangeDocsMax) rd = kRangeDocsMax;
+    ix->range_docs = (int)rd;
+    ix->n_ranges = (int)((D + rd - 1) / rd);
+  }
   // range offsets: roff[j][r] = position in L_j of the first doc >= r * R
-  ix->range_docs = kRangeDocs;
-  ix->n_ranges = (int)((D + kRangeDocs - 1) / kRangeDocs);
+  const int64_t RD = ix->range_docs;
   const int nr1 = ix->n_ranges + 1;
   std::vector<int32_t> roff((size_t)C * nr1);
   for (int64_t j = 0; j < C; j++) {
     int64_t p = loff[j], e = loff[j + 1];
     int32_t *row = &roff[(size_t)j * nr1];
     for (int r = 0; r < nr1; r++) {
-      int64_t bound = (int64_t)r * kRangeDocs;
+      int64_t bound = (int64_t)r * RD;
       while (p < e && ldoc[p] < bound) p++;
       row[r] = (int32_t)(p - loff[j]);
     }

@@ -54,14 +54,14 @@ void ws_release(Index *ix, cudaStream_t stream) {
 }
 
 struct Need {
-  int64_t nq = 0, rows = 0, kc = 0, kd = 0, split_entries = 0, dense = 0, gmax = 0;
+  int64_t nq = 0, rows = 0, kc = 0, kd = 0, split_entries = 0, pool = 0, gmax = 0;
 };
 
 // (Re)allocate the device scratch for a batch. Growth synchronises the stream
 // first, so memory still in use by earlier work on it is never freed early.
 static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   bool grow = n.nq > w->cap_q || n.rows > w->cap_rows || n.kc > w->cap_kc || n.kd > w->cap_kd ||
-              n.split_entries > w->cap_split_entries || n.dense > w->cap_dense || n.gmax > w->cap_gmax;
+              n.split_entries > w->cap_split_entries || n.pool > w->cap_pool || n.gmax > w->cap_gmax;
   if (!grow) return TACHIOM_OK;
   TCUDA(cudaStreamSynchronize(w->stream));
   for (void *p : w->blocks)
@@ -71,7 +71,7 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   int64_t nq = std::max<int64_t>(n.nq, w->cap_q), rows = std::max<int64_t>(n.rows, w->cap_rows);
   int64_t kc = std::max<int64_t>(n.kc, w->cap_kc), kd = std::max<int64_t>(n.kd, w->cap_kd);
   int64_t se = std::max<int64_t>(n.split_entries, w->cap_split_entries);
-  int64_t dn = std::max<int64_t>(n.dense, w->cap_dense);
+  int64_t pl = std::max<int64_t>(n.pool, w->cap_pool);
   int64_t gm = std::max<int64_t>(n.gmax, w->cap_gmax);
   const int groups = refine_groups(32);  // the largest group count of any pq_m
   auto al = [&](void **p, size_t bytes) -> tachiom_status {
@@ -97,19 +97,14 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   AL(w->d_split_cnt, (se + rows) * 4);
   AL(w->d_top_ids, rows * kc * 4);
   AL(w->d_top_s, rows * kc * 4);
-  AL(w->d_dense, dn * 4);
+  AL(w->d_pool, pl * 8);
+  AL(w->d_pool_n, (int64_t)nq * 64 * 4);
   AL(w->d_gmax, gm * 4);
   AL(w->d_tau, rows * 4);
   AL(w->d_margin, rows * 4);
   AL(w->d_glist, (int64_t)topc_tc_glist_elems((int)rows) * 4);
   AL(w->d_gcount, rows * 4);
   AL(w->d_lossy, rows * 4);
-  AL(w->d_hist, nq * NBINS1 * 4);
-  AL(w->d_govf, (nq * (int64_t)ix->n_ranges) * 8);
-  AL(w->d_govf_n, 16);
-  AL(w->d_hist2, nq * NBINS1 * 4);
-  AL(w->d_selstate, nq * 8 * 4);
-  AL(w->d_selbuf, nq * (int64_t)SEL_CAP * 8);
   AL(w->d_cand, nq * kd * 4);
   AL(w->d_cand_s, nq * kd * 4);
   AL(w->d_ncand, nq * 4);
@@ -129,7 +124,7 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   w->cap_kc = kc;
   w->cap_kd = kd;
   w->cap_split_entries = se;
-  w->cap_dense = dn;
+  w->cap_pool = pl;
   w->cap_gmax = gm;
   return TACHIOM_OK;
 }
@@ -267,14 +262,15 @@ static bool use_tc(const tachiom_search_params *p) {
 //   bits 2-3  step (c) kernel: 0 default (3), 1 tensor-core centroid term + lookup tables, then the
 //             FP32 window, 2 FP32 refine only, 3 decode + tensor cores, then the FP32 window
 //   bits 4-23 slices of the FP32 scan (0: default)
-//   bit 24    step (b): the token-serial gather for every range (default: the counting-sort
-//             gather, token-serial only for the ranges whose entries overflow its buffers)
+//   bit 24    step (b): every document range cut into pieces of at most 256 list entries, the
+//             path the gather takes for a range whose entries exceed its buffers (default:
+//             pieces only where a range does not fit)
 //   bit 25    step (c), decode path: the window rescored over every (query token, document
 //             token) pair in FP32 (default: only the pairs that can hold a maximum)
 enum { SCAN_DEFAULT = 0, SCAN_TC1 = 1, SCAN_TC2 = 2, SCAN_F32 = 3 };
-constexpr int32_t PLAN_GATHER_TOK = 1 << 24;
+constexpr int32_t PLAN_GATHER_SPLIT = 1 << 24;
 constexpr int32_t PLAN_WINDOW_ALL = 1 << 25;
-static bool gather_tok_only(const tachiom_search_params *p) { return p->plan_id >= 0 && (p->plan_id & PLAN_GATHER_TOK); }
+static bool gather_split(const tachiom_search_params *p) { return p->plan_id >= 0 && (p->plan_id & PLAN_GATHER_SPLIT); }
 enum { REFINE_DEFAULT = 0, REFINE_TC = 1, REFINE_F32 = 2, REFINE_DEC = 3 };
 
 static int scan_kind(const tachiom_search_params *p) {
@@ -423,15 +419,15 @@ static tachiom_status search_device(Index *ix, const tachiom_search_params *p, c
   n.kc = p->kappa_c;
   n.kd = kd;
   need_topc(*ix, p, b.rows, plan, &n);
-  n.dense = (int64_t)nq * ix->D;
+  n.pool = (int64_t)gather_pool_elems(*ix, nq, kd);
   if ((st = ws_reserve(ix, w, n))) return st;
   if ((st = upload_meta(w, p, h_ntok, h_k, nq))) return st;
   if ((st = run_topc(ix, w, p, d_queries, b.rows, plan))) return st;
-  if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, p->kappa_c, w->d_dense, w->d_hist,
-                          w->d_govf, w->d_govf_n, gather_tok_only(p), w->d_flags, stream)))
+  if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, p->kappa_c, kd, w->d_pool, w->d_pool_n,
+                          gather_split(p), w->d_flags, stream)))
     return st;
-  if ((st = launch_select_kd(*ix, w->d_meta, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
-                             w->d_cand, w->d_cand_s, w->d_ncand, w->d_flags, stream)))
+  if ((st = launch_select_kd(*ix, w->d_meta, nq, kd, w->d_pool, w->d_pool_n, w->d_cand, w->d_cand_s, w->d_ncand,
+                             stream)))
     return st;
   return run_refine(ix, w, p, d_queries, nq, w->d_cand, kd, d_out_ids, d_out_scores, stream);
 }
@@ -476,7 +472,7 @@ extern "C" tachiom_status tachiom_search_host(tachiom_index *index, const tachio
   n.kc = params->kappa_c;
   n.kd = std::max<int64_t>(kd, (b.total_k + nq - 1) / nq + 1);
   need_topc(*ix, params, b.rows, plan, &n);
-  n.dense = (int64_t)nq * ix->D;
+  n.pool = (int64_t)gather_pool_elems(*ix, nq, kd);
   if ((st = ws_reserve(ix, w, n))) return st;
   if (b.total_k > w->cap_q * w->cap_kd) return fail(TACHIOM_ERR_CAPACITY, "sum(k) beyond scratch");
   // pinned staging for queries and results
@@ -540,7 +536,6 @@ extern "C" tachiom_status tachiom_top_centroids(tachiom_index *index, const tach
   n.kc = params->kappa_c;
   n.kd = 1;
   need_topc(*ix, params, nrows, plan, &n);
-  n.dense = 0;
   if ((st = ws_reserve(ix, w, n))) return st;
   if ((st = run_topc(ix, w, params, d_rows, nrows, plan))) return st;
   TCUDA(cudaMemcpyAsync(d_top_ids, w->d_top_ids, (size_t)nrows * params->kappa_c * 4, cudaMemcpyDeviceToDevice, s));
@@ -571,17 +566,16 @@ extern "C" tachiom_status tachiom_gather(tachiom_index *index, const tachiom_sea
   n.rows = b.rows;
   n.kc = params->kappa_c;
   n.kd = kd;
-  n.dense = (int64_t)nq * ix->D;
+  n.pool = (int64_t)gather_pool_elems(*ix, nq, kd);
   if ((st = ws_reserve(ix, w, n))) return st;
   if ((st = upload_meta(w, params, h_ntok, nullptr, nq))) return st;
   if ((st = launch_score_pairs(*ix, d_queries, b.rows, d_top_ids, params->kappa_c, w->d_top_ids, w->d_top_s,
                                 w->d_flags, s)))
     return st;
-  if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, params->kappa_c, w->d_dense, w->d_hist,
-                          w->d_govf, w->d_govf_n, gather_tok_only(params), w->d_flags, s)))
+  if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, params->kappa_c, kd, w->d_pool, w->d_pool_n,
+                          gather_split(params), w->d_flags, s)))
     return st;
-  return launch_select_kd(*ix, w->d_meta, nq, kd, w->d_dense, w->d_hist, w->d_hist2, w->d_selstate, w->d_selbuf,
-                          d_cand_ids, d_cand_scores, d_ncand, w->d_flags, s);
+  return launch_select_kd(*ix, w->d_meta, nq, kd, w->d_pool, w->d_pool_n, d_cand_ids, d_cand_scores, d_ncand, s);
 }
 
 extern "C" tachiom_status tachiom_refine(tachiom_index *index, const tachiom_search_params *params,

@@ -82,10 +82,10 @@ struct Server {
 
 namespace {
 
-// scratch a batch may hold: the dense S~ array dominates, plus per-row buffers
+// scratch a batch may hold: the step (a) survivors per row, the gather's candidate parts and the
+// refine's per-candidate buffers
 int64_t batch_scratch(const Index &ix, int nq, int rows, int kd, int kc) {
-  return (int64_t)nq * ix.D * 4 + (int64_t)rows * (kc * 8 + 4096 * 8) + (int64_t)nq * kd * 64 +
-         (int64_t)nq * SEL_CAP * 8;
+  return (int64_t)rows * (kc * 8 + 4096 * 8) + (int64_t)gather_pool_elems(ix, nq, kd) * 8 + (int64_t)nq * kd * 64;
 }
 
 void finish_slot(Server *S, Slot &sl) {

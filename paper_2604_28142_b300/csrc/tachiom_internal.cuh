@@ -17,8 +17,7 @@ constexpr int DIM = 128;
 constexpr int MAX_NTOK = 32;   // query tokens per query
 constexpr int MAX_KC = 128;    // kappa_c
 constexpr int MAX_KD = 4096;   // kappa_d
-constexpr int NBINS1 = 4096;   // first-level histogram of the kappa_d selection
-constexpr int SEL_CAP = 16384; // candidates a query's exact kappa_d sort takes at once
+constexpr int SEL_CAP = 16384; // candidates a query's exact kappa_d selection takes at once
 
 // ---- errors -----------------------------------------------------------------
 void set_error(const char *fmt, ...);
@@ -121,7 +120,7 @@ struct Index {
   int64_t *list_off = nullptr;          // [C+1]
   int32_t *list_doc = nullptr;          // [n_list]
   int64_t n_list = 0;
-  int range_docs = 0;                   // documents per gather range
+  int range_docs = 0;                   // documents per gather range (<= 2^20)
   int n_ranges = 0;
   int32_t *list_roff = nullptr;         // [C x (n_ranges+1)] offset in L_j of the first doc
                                         // of each range
@@ -137,7 +136,7 @@ struct Workspace {
   std::vector<void *> blocks;          // device allocations, freed with the workspace
   // capacities
   int64_t cap_rows = 0, cap_q = 0, cap_kc = 0, cap_kd = 0, cap_split_entries = 0;
-  int64_t cap_dense = 0;
+  int64_t cap_pool = 0;
   // device buffers
   int32_t *d_meta = nullptr;           // qoff [B+1] | koff [B+1] | k [B] | ntok [B]
   float *d_rows_f32 = nullptr;         // staging of host queries (search_host)
@@ -153,13 +152,8 @@ struct Workspace {
   int32_t *d_split_cnt = nullptr;      // [rows x splits]
   int32_t *d_top_ids = nullptr;        // [rows x kc]
   float *d_top_s = nullptr;            // [rows x kc]
-  float *d_dense = nullptr;            // [B x D] S~ per query (-inf: not reached)
-  uint32_t *d_hist = nullptr;          // [B x NBINS1]
-  int2 *d_govf = nullptr;              // [B x ranges] (range, query) pairs left to the token-serial gather
-  int *d_govf_n = nullptr;             // their count
-  uint32_t *d_hist2 = nullptr;         // [B x NBINS1]
-  uint32_t *d_selstate = nullptr;      // [B x 8]
-  uint64_t *d_selbuf = nullptr;        // [B x SEL_CAP]
+  uint64_t *d_pool = nullptr;          // [B x groups x kd] each range group's top-kappa_d (S~, doc) keys
+  int32_t *d_pool_n = nullptr;         // [B x groups] their counts
   int32_t *d_cand = nullptr;           // [B x kd]
   float *d_cand_s = nullptr;           // [B x kd]
   int32_t *d_ncand = nullptr;          // [B]
@@ -234,14 +228,15 @@ int topc_tc1_splits(const Index &ix, int nrows);
 size_t topc_tc_gmax_elems(const Index &ix, int rows);
 tachiom_status launch_score_pairs(const Index &ix, const float *rows, int nrows, const int32_t *ids,
                                   int kc, int32_t *out_ids, float *scores, uint32_t *flags, cudaStream_t s);
-// step (b)
-tachiom_status launch_gather(const Index &ix, const int32_t *meta_qoff, int nq, const int32_t *top_ids,
-                             const float *top_s, int kc, float *dense, uint32_t *hist, int2 *ovf, int *novf,
-                             bool tok_only, uint32_t *flags, cudaStream_t s);
-tachiom_status launch_select_kd(const Index &ix, const int32_t *meta, int nq, int kd, const float *dense,
-                                const uint32_t *hist, uint32_t *hist2, uint32_t *state,
-                                uint64_t *selbuf, int32_t *cand, float *cand_s, int32_t *ncand,
-                                uint32_t *flags, cudaStream_t s);
+// step (b): per (query, range group) the group's top-kappa_d keys into pool, then per query the
+// exact top-kappa_d of its groups' parts
+int gather_groups(const Index &ix, int nq, int kd);
+size_t gather_pool_elems(const Index &ix, int nq, int kd);
+tachiom_status launch_gather(const Index &ix, const int32_t *meta, int nq, const int32_t *top_ids, const float *top_s,
+                             int kc, int kd, uint64_t *pool, int32_t *pool_n, bool force_split, uint32_t *flags,
+                             cudaStream_t s);
+tachiom_status launch_select_kd(const Index &ix, const int32_t *meta, int nq, int kd, const uint64_t *pool,
+                                const int32_t *pool_n, int32_t *cand, float *cand_s, int32_t *ncand, cudaStream_t s);
 // steps (c), (d)
 tachiom_status launch_refine_win(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                  const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s);

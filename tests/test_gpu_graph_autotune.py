@@ -61,7 +61,7 @@ def test_every_plan_gives_the_same_results(env, prec):
     dq = torch.from_numpy(q["queries"]).cuda()
     best, ms = G.autotune(params, dq, q["ntok"], kk)
     assert best >= 0 and ms > 0
-    tok = 1 << 24  # the token-serial gather for every range
+    tok = 1 << 24  # every gather range cut into small pieces
     win_all = 1 << 25  # the FP32 window over every pair
     plans = ([1 | 4, 1 | 8, 2 | 4, 2 | 8, 3 | 8, 2 | 12 | tok, 2 | 12 | win_all] if prec == 1
              else [3 | 8 | (s << 4) for s in (1, 7, 40)] + [3 | 8 | tok])

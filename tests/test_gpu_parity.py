@@ -100,7 +100,8 @@ def test_step_a_top_centroids_fp32(name):
         check_ranking(gi[r], gs[r], o_ids[r], o_s[r], RTOL_FP32, GAP, what=f"row {r}")
 
 
-# plan bit 24: the token-serial gather for every range (the counting-sort gather's fallback)
+# plan bit 24: every document range cut into pieces of at most 256 list entries, the path the
+# gather takes when a range's entries exceed its shared-memory buffers
 GATHER_PLANS = [-1, 1 << 24]
 
 
