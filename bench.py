@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--kc", type=int, default=40)
     ap.add_argument("--kd", type=int, default=1000)
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16", "fp8"])
     ap.add_argument("--oracle-queries", type=int, default=0,
                     help="queries checked against the oracle (0: one per host core, at most 16)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--no-single", action="store_true")
     ap.add_argument("--no-rerank", action="store_true", help="skip the rerank-only measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the k = 100 / 1000 and FP32 batched lines")
+    ap.add_argument("--rescore-margin", type=float, default=0.0,
+                    help="FP8 repair window of the timed path (0: the library's default)")
+    ap.add_argument("--fp8-windows", type=float, nargs="*", default=[0.1],
+                    help="FP8 repair windows (multiples of the rigorous bound) timed in the sweep")
     a = ap.parse_args()
     shape = SHAPES.get(a.workload, (64, 32, 32))
     if a.batch <= 0:
@@ -407,6 +411,11 @@ def oracle_check(ix, qs, ntok, gi, gs, k, kc, kd, nsample):
     t0 = time.perf_counter()
     res = O.search(qs[rows], ntok[sel], k, kc, kd)
     dt = time.perf_counter() - t0
+    return accuracy_vs(res, sel, gi, gs, k), dt, len(sel), res
+
+
+def accuracy_vs(res, sel, gi, gs, k):
+    """Top-10 overlap and score error of a GPU result against the oracle's result on queries sel."""
     ov, err = [], []
     for j, u in enumerate(sel):
         g = gi[u * k:(u + 1) * k]
@@ -419,7 +428,7 @@ def oracle_check(ix, qs, ntok, gi, gs, k, kc, kd, nsample):
         err.append(float(np.max(np.abs(gs[u * k:(u + 1) * k][m] - os_[m]) / np.maximum(1, np.abs(os_[m])))
                    if m.any() else 0.0))
     return {"queries": int(len(sel)), "overlap_at_10": float(np.mean(ov)), "min_overlap_at_10": float(np.min(ov)),
-            "max_rel_score_err": float(np.max(err))}, dt, len(sel)
+            "max_rel_score_err": float(np.max(err))}
 
 
 def algorithmic_traffic(T_idx, ix, params, dq, ntok, k, kc, kd, torch):
@@ -471,8 +480,8 @@ def run_ours(a):
     if a.precision == "auto":
         prec = T.PREC_BF16 if T.tc_available() else T.PREC_FP32
     else:
-        prec = T.PREC_BF16 if a.precision == "bf16" else T.PREC_FP32
-    params = T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=prec)
+        prec = {"bf16": T.PREC_BF16, "fp8": T.PREC_FP8, "fp32": T.PREC_FP32}[a.precision]
+    params = T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=prec, rescore_margin=a.rescore_margin)
     nb = a.warmup + a.steps
     q = synth.make_queries(cfg, n_queries=nb * a.batch, seed=rank_query_seed(cfg, rank), ntok_min=a.ntok_min,
                            ntok_max=a.ntok_max)
@@ -494,7 +503,7 @@ def run_ours(a):
         for b in range(a.warmup, nb):
             G.search(params, batches[b][0], batches[b][1], kk, out_i[b], out_s[b])
         torch.cuda.synchronize()
-        print(json.dumps({"profile_only": True}))
+        print(json.dumps({"profile_only": True, "status_flags": G.stream_status()}))
         return
     # ---- timed region (device-resident inputs) ----
     T.profile_enable(True)
@@ -554,11 +563,26 @@ def run_ours(a):
             sweep[f"k{kx}"] = {"value": float(a.batch * len(ms) / (ms.sum() / 1e3)), "unit": "queries/s",
                                "ms_per_step": float(ms.mean()), "kappa_d": min(4096, max(1000, 4 * kx)),
                                "status_flags": int(fl)}
-        if prec != T.PREC_FP32:
-            ms, fl = time_batches(G, T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=T.PREC_FP32), batches,
-                                  idx, a.k, flush, torch)
-            sweep["fp32_batched"] = {"value": float(a.batch * len(ms) / (ms.sum() / 1e3)), "unit": "queries/s",
-                                     "ms_per_step": float(ms.mean()), "k": a.k, "status_flags": int(fl)}
+        T.profile_enable(True)
+        others = [("fp32_batched", T.PREC_FP32, 0.0)]
+        if T.tc_available():
+            others += [("bf16", T.PREC_BF16, 0.0)] + [(f"fp8_window{w}", T.PREC_FP8, w) for w in a.fp8_windows]
+        for nm, pr, w in others:
+            if pr == prec and pr != T.PREC_FP8:
+                continue
+            pp = T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=pr, rescore_margin=w)
+            T.profile_read()
+            ms, fl = time_batches(G, pp, batches, idx, a.k, flush, torch)
+            pf = T.profile_read()
+            sweep[nm] = {"value": float(a.batch * len(ms) / (ms.sum() / 1e3)), "unit": "queries/s",
+                         "ms_per_step": float(ms.mean()), "k": a.k, "status_flags": int(fl),
+                         "stage_ms_per_step": {kk: v[1] / (len(ms) + 2) for kk, v in pf.items()}}
+            if pr == T.PREC_FP8:
+                kg = G.debug_topc_groups(pp, batches[a.warmup][0])
+                sweep[nm]["rescore_margin"] = w
+                sweep[nm]["topc_candidates_per_row"] = {"mean": float(kg.mean()), "p99": float(np.percentile(kg, 99)),
+                                                        "max": int(kg.max())}
+        T.profile_enable(False)
     # ---- the rerank-only use of steps (c)-(d): external candidate lists ----
     rerank = None
     if not a.no_rerank:
@@ -568,14 +592,25 @@ def run_ours(a):
     gi = out_i[b0].cpu().numpy()
     gs = out_s[b0].cpu().numpy()
     qb = qs[qoff[b0 * a.batch]:qoff[(b0 + 1) * a.batch]]
-    acc, odt, on = oracle_check(ix, qb, batches[b0][1], gi, gs, a.k, a.kc, a.kd, a.oracle_queries)
+    acc, odt, on, ores = oracle_check(ix, qb, batches[b0][1], gi, gs, a.k, a.kc, a.kd, a.oracle_queries)
+    for nm, v in (sweep or {}).items():
+        if not nm.startswith("fp8"):
+            continue
+        # the FP8 path's result on the same queries against the same oracle result
+        nq0 = len(batches[b0][1])
+        oi8 = torch.empty(nq0 * a.k, dtype=torch.int32, device="cuda")
+        os8 = torch.empty(nq0 * a.k, dtype=torch.float32, device="cuda")
+        G.search(T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=T.PREC_FP8, rescore_margin=v["rescore_margin"]),
+                 batches[b0][0], batches[b0][1], np.full(nq0, a.k, np.int32), oi8, os8)
+        torch.cuda.synchronize()
+        v["accuracy"] = accuracy_vs(ores, np.arange(on), oi8.cpu().numpy(), os8.cpu().numpy(), a.k)
     # ---- roofline of the dominant launcher ----
     ix["_list_off"] = G.lists()[0]
     traffic = algorithmic_traffic(G, ix, params, batches[b0][0], batches[b0][1], a.k, a.kc, a.kd, torch)
     if prec == T.PREC_BF16:
         kg = G.debug_topc_groups(params, batches[b0][0])
-        traffic["kept_groups_per_row"] = {"mean": float(kg.mean()), "p99": float(np.percentile(kg, 99)),
-                                          "max": int(kg.max())}
+        traffic["topc_candidates_per_row"] = {"mean": float(kg.mean()), "p99": float(np.percentile(kg, 99)),
+                                              "max": int(kg.max())}
         # documents the decode-and-MMA refine leaves to the FP32 kernel (same rule as the window kernel)
         cand = traffic["_cand"]
         sa = torch.empty(cand.shape, dtype=torch.float32, device="cuda")
@@ -626,9 +661,10 @@ def run_ours(a):
         roof = {"kernel": "k_topc_tc1", "bound": "tensor",
                 "achieved": gemm_flops / (per_launch_ms * 1e-3) / 1e12, "peak": pk_t, "unit": "TFLOP/s"}
     else:
-        # tensor-core group maxima, group selection and exact rescoring, timed together
-        pk_t = peaks.get("bf16_tflops", 1800.0)
-        roof = {"kernel": "k_topc_tc + k_gsel_* + k_group_rescore", "bound": "tensor",
+        # tensor-core sample pass, threshold, emission pass and exact rescoring, timed together;
+        # FP8 against twice the measured BF16 peak (the nominal dense E4M3 : BF16 ratio)
+        pk_t = peaks.get("bf16_tflops", 1800.0) * (2.0 if prec == T.PREC_FP8 else 1.0)
+        roof = {"kernel": "k_topc_tc<sample> + k_gsel_lim + k_topc_tc<emit> + k_cand_rescore", "bound": "tensor",
                 "achieved": gemm_flops / (per_launch_ms * 1e-3) / 1e12, "peak": pk_t, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["peak_source"] = peak_src
@@ -647,11 +683,11 @@ def run_ours(a):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "bf16/f32" if prec == T.PREC_BF16 else "f32",
+        "dtype": {T.PREC_BF16: "bf16/f32", T.PREC_FP8: "e4m3/f32"}.get(prec, "f32"),
         "data": data_desc(a),
         "config": {"workload": workload_desc(a, ix),
                    "batch": a.batch, "tokens_per_query": tok_desc(a), "k": a.k, "kappa_c": a.kc, "kappa_d": a.kd,
-                   "precision": "bf16" if prec == T.PREC_BF16 else "fp32",
+                   "precision": {T.PREC_BF16: "bf16", T.PREC_FP8: "fp8"}.get(prec, "fp32"),
                    "l2": "flushed between steps (256 MiB write outside the step's events)",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

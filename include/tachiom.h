@@ -61,8 +61,15 @@ enum { TACHIOM_DTYPE_F32 = 0, TACHIOM_DTYPE_BF16 = 1 };
 /* arithmetic of step (a); steps (b)-(d) always accumulate in FP32 */
 enum {
   TACHIOM_PREC_FP32 = 0, /* FP32 CUDA-core products: the plain comparator path */
-  TACHIOM_PREC_BF16 = 1  /* BF16 tensor-core products with FP32 accumulation, then the
-                            candidates near each row's kappa_c boundary rescored in FP32 */
+  TACHIOM_PREC_BF16 = 1, /* BF16 tensor-core products with FP32 accumulation, then the
+                            candidates near each row's kappa_c boundary rescored in FP32;
+                            the window is the rigorous error bound, so the result is the
+                            FP32 path's, bit for bit */
+  TACHIOM_PREC_FP8 = 2   /* FP8-E4M3 tensor-core products (a power-of-two scale per query row
+                            and per centroid) with FP32 accumulation, then the candidates in a
+                            window of rescore_margin times the rigorous error bound rescored
+                            in FP32 (rescore_margin >= 1: the FP32 path's result; below 1:
+                            a narrower window, accuracy measured against the FP64 oracle) */
 };
 
 /* device status flags, OR-ed per stream since the last tachiom_stream_status */
@@ -128,6 +135,9 @@ typedef struct {
   int32_t precision;  /* TACHIOM_PREC_* for step (a) */
   int32_t plan_id;    /* -1: the library's choice of kernels; >= 0: a plan from tachiom_autotune
                          (bits 0-1 step (a) kernel, 2-3 step (c) kernel, 4- FP32 scan slices) */
+  float rescore_margin; /* TACHIOM_PREC_FP8 only: the FP32 repair window of step (a) as a multiple
+                           of the rigorous E4M3 error bound; <= 0 means 0.1 (about 4 standard
+                           deviations of the typical error of unit-norm rows). Ignored otherwise. */
 } tachiom_search_params;
 
 /* The whole path, steps (a)-(d), for a batch of nq queries.
@@ -319,9 +329,16 @@ tachiom_status tachiom_debug_refine_scores(tachiom_index *index, const tachiom_s
                                            const int32_t *d_cand_ids, float *d_scores, float *d_bounds,
                                            void *stream);
 
+/* Same with FP8-E4M3 products (each row and each centroid scaled by a power of
+ * two; the scales undone): d_out [nrows x C] fp32. d_margins (fp32 [nrows], may
+ * be NULL) receives twice the rigorous bound on |E4M3 score - FP32 score| of
+ * each row. TACHIOM_ERR_INVALID when the device has no tensor-core path.     */
+tachiom_status tachiom_debug_tc_scores_fp8(tachiom_index *index, const float *d_rows, int32_t nrows,
+                                           float *d_out, float *d_margins, void *stream);
+
 /* Diagnostics of the tensor-core step (a): runs it on nrows device rows on the
- * legacy default stream and copies, per row, the number of 32-centroid groups
- * kept for exact rescoring to h_groups int32 [nrows] (host). Blocking.     */
+ * legacy default stream and copies, per row, the number of candidate centroids
+ * emitted for exact FP32 rescoring to h_groups int32 [nrows] (host). Blocking. */
 tachiom_status tachiom_debug_topc_groups(tachiom_index *index, const tachiom_search_params *params,
                                          const float *d_rows, int32_t nrows, int32_t *h_groups);
 

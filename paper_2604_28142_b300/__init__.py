@@ -6,6 +6,7 @@ CPU fallback: loading fails loudly if the library is missing.
 """
 from .binding import (  # noqa: F401
     PREC_BF16,
+    PREC_FP8,
     PREC_FP32,
     FLAG_CAPACITY,
     FLAG_SELECT_TIES,

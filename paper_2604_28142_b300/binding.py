@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 
 TACHIOM_OK = 0
 DTYPE_F32, DTYPE_BF16 = 0, 1
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 FLAG_TOPC_RESCUED, FLAG_SELECT_TIES, FLAG_CAPACITY, FLAG_BAD_INPUT = 1, 2, 4, 8
 
 _STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "CAPACITY", 5: "TIMEOUT", 6: "BUSY"}
@@ -41,10 +41,10 @@ class _Desc(ct.Structure):
 
 class SearchParams(ct.Structure):
     _fields_ = [("kappa_c", ct.c_int32), ("kappa_d", ct.c_int32), ("precision", ct.c_int32),
-                ("plan_id", ct.c_int32)]
+                ("plan_id", ct.c_int32), ("rescore_margin", ct.c_float)]
 
-    def __init__(self, kappa_c=40, kappa_d=0, precision=PREC_FP32, plan_id=-1):
-        super().__init__(kappa_c, kappa_d, precision, plan_id)
+    def __init__(self, kappa_c=40, kappa_d=0, precision=PREC_FP32, plan_id=-1, rescore_margin=0.0):
+        super().__init__(kappa_c, kappa_d, precision, plan_id, rescore_margin)
 
 
 class ProfileEntry(ct.Structure):
@@ -168,6 +168,7 @@ def lib():
         "tachiom_refine_noalloc": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
         "tachiom_stream_status": ([P, P, U32p], ct.c_int),
         "tachiom_debug_tc_scores": ([P, P, I32, P, P], ct.c_int),
+        "tachiom_debug_tc_scores_fp8": ([P, P, I32, P, P, P], ct.c_int),
         "tachiom_tc_available": ([], ct.c_int),
         "tachiom_debug_topc_groups": ([P, ct.POINTER(SearchParams), P, I32, P], ct.c_int),
         "tachiom_debug_refine_scores": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P, P], ct.c_int),
@@ -314,6 +315,10 @@ class Index:
 
     def debug_tc_scores(self, rows, out, stream=None):
         _check(lib().tachiom_debug_tc_scores(self.h, _dp(rows), int(rows.shape[0]), _dp(out), _stream(stream)))
+
+    def debug_tc_scores_fp8(self, rows, out, margins=None, stream=None):
+        _check(lib().tachiom_debug_tc_scores_fp8(self.h, _dp(rows), int(rows.shape[0]), _dp(out),
+                                                 _dp(margins) if margins is not None else None, _stream(stream)))
 
     def debug_refine_scores(self, params: SearchParams, queries, ntok, cand_ids, out, bounds=None, stream=None):
         ntok = np.ascontiguousarray(ntok, dtype=np.int32)

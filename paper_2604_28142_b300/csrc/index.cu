@@ -85,7 +85,7 @@ static void free_index(Index *ix) {
   cudaSetDevice(ix->device);
   for (auto &kv : ix->ws) ws_destroy(kv.second);
   ix->ws.clear();
-  void *ptrs[] = {ix->cent_f32, ix->cent_bf16, ix->cent_type, ix->doc_off, ix->tok_cid, ix->codes,
+  void *ptrs[] = {ix->cent_f32, ix->cent_bf16, ix->cent_e4m3, ix->cent_inv_sc, ix->cent_type, ix->doc_off, ix->tok_cid, ix->codes,
                   ix->rnorm, ix->codebooks, ix->doc_xe, ix->cbk_h16, ix->cbk_err2, ix->list_off,
                   ix->list_doc, ix->list_roff};
   for (void *p : ptrs)
@@ -280,6 +280,10 @@ extern "C" tachiom_status tachiom_index_load(const tachiom_index_desc *desc, int
     ix->cnorm_max = f;
     ix->cerr_max = g;
   }
+  // the E4M3 operand of the FP8 step (a): a power-of-two scale per centroid
+  TRY(dalloc(ix, &ix->cent_e4m3, cn));
+  TRY(dalloc(ix, &ix->cent_inv_sc, (size_t)C));
+  TRY(launch_cent_e4m3(*ix, 0));
   if (desc->centroid_type) TRY(upload(ix, &ix->cent_type, desc->centroid_type, (size_t)C));
   TRY(upload(ix, &ix->doc_off, desc->doc_offsets, (size_t)D + 1));
   TRY(upload(ix, &ix->tok_cid, desc->token_centroid, (size_t)T));

@@ -128,107 +128,31 @@ __device__ void gp_block_runmax(uint32_t *v, int n, uint32_t *wsum) {
   __syncthreads();
 }
 
-// The kappa-th largest of the n distinct keys a[0..n) (1 <= kappa <= n), to every thread:
-// a radix select over 11-bit digits from the top (bits 63..53, 52..42, ...); once the digit
-// holding the cut has at most 64 keys, one warp sorts those. The bins are scanned from the top
-// by the whole block (thread t owns a contiguous run of bins). Uses hist[2048], small[64],
-// wsum[32] and sh[8]; ends with a barrier.
-constexpr int KS_BITS = 11;
-__device__ uint64_t gp_kth_largest(const uint64_t *a, int n, int kappa, uint32_t *hist, uint64_t *small,
-                                   uint32_t *wsum, uint32_t *sh) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  uint64_t prefix = 0ull, mask = 0ull;
-  uint32_t need = (uint32_t)kappa;
-  for (int top = 64; top > 0; top -= KS_BITS) {
-    const int shift = max(0, top - KS_BITS), bits = top - shift, nbin = 1 << bits;
-    const uint64_t dmask = (uint64_t)(nbin - 1);
-    for (int i = tid; i < nbin; i += blockDim.x) hist[i] = 0u;
-    __syncthreads();
-    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
-      const int i = i0 + tid;
-      int dg = -1;
-      if (i < n) {
-        const uint64_t k = a[i];
-        if ((k & mask) == prefix) dg = (int)((k >> shift) & dmask);
-      }
-      const unsigned peers = __match_any_sync(0xffffffffu, dg);
-      if (dg >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[dg], (uint32_t)__popc(peers));
-    }
-    __syncthreads();
-    // thread t: bins [hi - w, hi), hi = nbin - t w, counted from the top
-    const int w = (nbin + blockDim.x - 1) / blockDim.x;
-    const int bhi = max(0, nbin - tid * w), blo = max(0, bhi - w);
-    uint32_t c = 0;
-    for (int d = blo; d < bhi; d++) c += hist[d];
-    uint32_t inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane == 31) wsum[warp] = inc;
-    __syncthreads();
-    uint32_t before = 0;
-    for (int u = 0; u < warp; u++) before += wsum[u];
-    (void)nw;
-    const uint32_t excl = before + inc - c;
-    inc += before;
-    if (c > 0 && excl < need && need <= inc) {
-      uint32_t cum = excl;
-      int d = bhi - 1;
-      for (; d > blo; d--) {
-        if (cum + hist[d] >= need) break;
-        cum += hist[d];
-      }
-      sh[0] = (uint32_t)d;
-      sh[1] = need - cum;
-      sh[2] = hist[d];
-      sh[3] = 0u;
-    }
-    __syncthreads();
-    prefix |= (uint64_t)sh[0] << shift;
-    mask |= dmask << shift;
-    need = sh[1];
-    const uint32_t inbin = sh[2];
-    if (inbin <= 64u) {
-      // gather the bin's keys and pick the need-th largest
-      for (int i0 = 0; i0 < n; i0 += blockDim.x) {
-        const int i = i0 + tid;
-        if (i < n && (a[i] & mask) == prefix) small[atomicAdd(&sh[3], 1u)] = a[i];
-      }
-      __syncthreads();
-      if (warp == 0) {
-        for (int i = (int)inbin + lane; i < 64; i += 32) small[i] = 0ull;
-        __syncwarp();
-        warp_sort_desc(small, 64);
-      }
-      __syncthreads();
-      const uint64_t r = small[need - 1];
-      __syncthreads();  // small, wsum and sh are free again when this returns
-      return r;
-    }
-    __syncthreads();  // sh and wsum are read by every thread before the next pass rewrites them
-  }
-  return prefix;  // not reached: distinct keys leave a single key in the last digit's bin
-}
-
 // Keep the kappa keys of lbuf[0..n) at or above the kappa-th largest T (n > kappa): the kept
 // keys found beyond position kappa move into the dropped slots below it (their numbers are
 // equal). slots: >= kappa words of scratch. Returns T; ends with a barrier.
 __device__ uint64_t gp_compact(uint64_t *lbuf, int n, int kappa, uint32_t *slots, uint32_t *hist,
-                               uint64_t *small, uint32_t *wsum, uint32_t *sh) {
-  const uint64_t T = gp_kth_largest(lbuf, n, kappa, hist, small, wsum, sh);
+                               uint64_t *small, uint32_t *wsum, uint32_t *sh, uint32_t *flags) {
+  const uint64_t T = block_kth_largest(lbuf, n, kappa, hist, small, wsum, sh);
   if (threadIdx.x == 0) {
     sh[4] = 0u;
     sh[5] = 0u;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kappa; i += blockDim.x)
-    if (lbuf[i] < T) slots[atomicAdd(&sh[4], 1u)] = (uint32_t)i;
+    if (lbuf[i] < T) {
+      const uint32_t d = atomicAdd(&sh[4], 1u);
+      if (d < (uint32_t)kappa) slots[d] = (uint32_t)i;
+      else atomicOr(flags, TACHIOM_FLAG_CAPACITY);  // not reachable with distinct keys
+    }
   __syncthreads();
   for (int i = kappa + threadIdx.x; i < n; i += blockDim.x) {
     const uint64_t k = lbuf[i];
-    if (k >= T) lbuf[slots[atomicAdd(&sh[5], 1u)]] = k;
+    if (k >= T) {
+      const uint32_t d = atomicAdd(&sh[5], 1u);
+      if (d < min(sh[4], (uint32_t)kappa)) lbuf[slots[d]] = k;
+      else atomicOr(flags, TACHIOM_FLAG_CAPACITY);  // not reachable with distinct keys
+    }
   }
   __syncthreads();
   return T;
@@ -265,6 +189,7 @@ struct GpArgs {
   int split_cap;   // a piece with more entries is halved (ecap, or small to test the split path)
   uint64_t *pool;  // [nq x ng x kd]
   int32_t *pool_n; // [nq x ng]
+  int64_t nlist;   // list entries
   uint32_t *flags;
 };
 
@@ -435,7 +360,7 @@ k_gather_pool(const GpArgs A) {
       // room in the candidate buffer for every document of this piece
       if (s_lcount + E > A.lbcap) {
         const int n = s_lcount;
-        thr = gp_compact(S.lbuf, n, kdq, S.kin, S.cnt, small, wsum, sh);
+        thr = gp_compact(S.lbuf, n, kdq, S.kin, S.cnt, small, wsum, sh, A.flags);
         if (tid == 0) s_lcount = kdq;
         __syncthreads();
       }
@@ -471,12 +396,22 @@ k_gather_pool(const GpArgs A) {
         }
         int32_t dv[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) dv[u] = __ldg(A.list_doc + pos[u]);
+        for (int u = 0; u < 4; u++) {
+          if ((uint32_t)pos[u] >= (uint32_t)A.nlist) {  // a piece bound outside the lists: skipped
+            atomicOr(A.flags, TACHIOM_FLAG_CAPACITY);
+            pos[u] = 0;
+          }
+          dv[u] = __ldg(A.list_doc + pos[u]);
+        }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
           const int e = e0 + u * GP_THREADS + tid;
           if (e < E) {
-            const uint32_t x = (uint32_t)(dv[u] - (int32_t)r0);
+            uint32_t x = (uint32_t)(dv[u] - (int32_t)r0);
+            if (x >= (uint32_t)(x1 - x0)) {  // a document outside the piece: not reachable
+              atomicOr(A.flags, TACHIOM_FLAG_CAPACITY);
+              x = 0;
+            }
             const uint32_t t = kc == 1 ? sg[u] : __umulhi(sg[u], kc_magic), rk = sg[u] - t * (uint32_t)kc;
             S.kin[e] = (x << 12) | (t << 7) | rk;
             atomicAdd(&S.cnt[(x - (uint32_t)x0) >> bsh], 1u);
@@ -489,7 +424,9 @@ k_gather_pool(const GpArgs A) {
       for (int e = tid; e < E; e += GP_THREADS) {
         const uint32_t k = S.kin[e];
         const uint32_t b = ((k >> 12) - (uint32_t)x0) >> bsh;
-        S.kout[atomicAdd(&S.cnt[b], 1u)] = k;
+        const uint32_t d = atomicAdd(&S.cnt[b], 1u);
+        if (d < (uint32_t)E) S.kout[d] = k;
+        else atomicOr(A.flags, TACHIOM_FLAG_CAPACITY);
       }
       __syncthreads();
       // every key to its place in its bucket: its rank among the bucket's (distinct) keys
@@ -499,7 +436,8 @@ k_gather_pool(const GpArgs A) {
         const uint32_t end = S.cnt[b], st = b == 0 ? 0u : S.cnt[b - 1];
         uint32_t below = 0;
         for (uint32_t h = st; h < end; h++) below += S.kout[h] < k ? 1u : 0u;
-        S.kin[st + below] = k;
+        if (st + below < (uint32_t)E) S.kin[st + below] = k;
+        else atomicOr(A.flags, TACHIOM_FLAG_CAPACITY);
       }
       __syncthreads();
       // S~ of every reached document (the thread holding the first key of its run), kept if it
@@ -531,7 +469,11 @@ k_gather_pool(const GpArgs A) {
         int wb = 0;
         if (lane == 0 && m) wb = atomicAdd(&s_lcount, __popc(m));
         wb = __shfl_sync(0xffffffffu, wb, 0);
-        if (keep) S.lbuf[wb + __popc(m & ((1u << lane) - 1u))] = ck;
+        const int li = wb + __popc(m & ((1u << lane) - 1u));
+        if (keep) {
+          if (li < A.lbcap) S.lbuf[li] = ck;
+          else atomicOr(A.flags, TACHIOM_FLAG_CAPACITY);
+        }
       }
       __syncthreads();
     }
@@ -539,7 +481,7 @@ k_gather_pool(const GpArgs A) {
   // the group's exact top-kappa_d
   int n = s_lcount;
   if (n > kdq) {
-    gp_compact(S.lbuf, n, kdq, S.kin, S.cnt, small, wsum, sh);
+    gp_compact(S.lbuf, n, kdq, S.kin, S.cnt, small, wsum, sh, A.flags);
     n = kdq;
   }
   uint64_t *out = A.pool + ((int64_t)q * A.ng + g) * A.kd;
@@ -556,7 +498,7 @@ __global__ void __launch_bounds__(PS_THREADS)
 k_pool_select(const uint64_t *__restrict__ pool, const int32_t *__restrict__ pool_n, int ng, const int32_t *meta,
               int nq, int kd, int32_t *__restrict__ cand, float *__restrict__ cand_s, int32_t *__restrict__ ncand) {
   extern __shared__ __align__(16) uint64_t ssm[];  // [SEL_CAP] keys, then [next_pow2(kappa_d)] kept keys
-  __shared__ uint32_t hist[1 << KS_BITS];
+  __shared__ uint32_t hist[1 << KSEL_BITS];
   __shared__ uint64_t small[64];
   __shared__ uint32_t wsum[32];
   __shared__ uint32_t sh[8];
@@ -590,13 +532,16 @@ k_pool_select(const uint64_t *__restrict__ pool, const int32_t *__restrict__ poo
     __syncthreads();
     block_sort_desc(keys, np);
   } else {
-    const uint64_t T = gp_kth_largest(keys, n, kdq, hist, small, wsum, sh);
+    const uint64_t T = block_kth_largest(keys, n, kdq, hist, small, wsum, sh);
     uint64_t *kept = ssm + SEL_CAP;
     const int np = next_pow2(max(kdq, 2));
     for (int i = kdq + tid; i < np; i += PS_THREADS) kept[i] = 0ull;
     for (int i = tid; i < n; i += PS_THREADS) {
       const uint64_t k = keys[i];
-      if (k >= T) kept[atomicAdd(&s_cnt, 1)] = k;
+      if (k >= T) {
+        const int d = atomicAdd(&s_cnt, 1);
+        if (d < kdq) kept[d] = k;
+      }
     }
     __syncthreads();
     block_sort_desc(kept, np);
@@ -674,6 +619,7 @@ tachiom_status launch_gather(const Index &ix, const int32_t *meta, int nq, const
   A.split_cap = force_split ? GP_SPLIT_FORCED : ecap;
   A.pool = pool;
   A.pool_n = pool_n;
+  A.nlist = ix.n_list;
   A.flags = flags;
   const size_t smem = gp_smem_bytes(MAX_NTOK * kc, ecap, A.lbcap);
   TCUDA(cudaFuncSetAttribute(k_gather_pool, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

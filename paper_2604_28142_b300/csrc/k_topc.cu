@@ -15,6 +15,11 @@
 // The FP32 score of (row, centroid) is always the same sequence of fmaf over
 // k = 0..127, in the scan, in the rescoring and in k_score_pairs, so every
 // path produces bit-identical FP32 scores.
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <cstring>
+
 #include "tachiom_internal.cuh"
 
 namespace tachiom {
@@ -72,6 +77,92 @@ tachiom_status launch_quantize_rows(const Index &ix, const float *rows, __nv_bfl
   TPROF("quantize_bf16", s);
   k_quantize_rows<<<(nrows + 7) / 8, 256, 0, s>>>(rows, out, nrows, ix.cnorm_max, ix.cerr_max, margins);
   TLAUNCH();
+  return TACHIOM_OK;
+}
+
+// Rows to E4M3 (round to nearest, saturating) with a power-of-two scale per row: y = x * 2^s,
+// 2^s the largest power of two with max_k |x_k| * 2^s <= 448, so max |y| is in (224, 448] and the
+// scaling is exact; inv[r] = 2^-s and the decoded row is x~ = e4m3(y) * 2^-s. Per row, the rigorous
+// bound of the E4M3 score error against a centroid c with e4m3 copy c~ (Cauchy-Schwarz; products of
+// two E4M3 values are exact in FP32 and the accumulation of 128 of them adds at most 2^-15 ||x~|| cmax):
+//   |<x~, c~> - <x, c>| <= ||x~ - x|| cmax + ||x~|| (cerr8 + 2^-15 cmax) = delta
+// and margins[r] = 2 lambda delta (lambda = 1: the rigorous window). With err_max, the largest
+// ||x~ - x|| over the rows is folded in by atomicMax (index load). One warp per row.
+__global__ void k_quant_e4m3(const float *__restrict__ in, int64_t nrows, uint8_t *__restrict__ out,
+                             float *__restrict__ inv, float cmax, float cerr8, float lambda,
+                             float *__restrict__ margins, unsigned *__restrict__ err_max) {
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= nrows) return;
+  const float4 x = reinterpret_cast<const float4 *>(in + r * DIM)[lane];
+  const float xs[4] = {x.x, x.y, x.z, x.w};
+  float amax = fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  int s = 0;
+  if (amax > 0.f) {
+    int e;
+    frexpf(448.f / amax, &e);  // 448 / amax = f 2^e, f in [0.5, 1): 2^(e-1) <= 448 / amax
+    s = min(e - 1, 126);
+  }
+  const float scale = ldexpf(1.f, s), iscale = ldexpf(1.f, -s);
+  uint32_t packed = 0;
+  float e2 = 0.f, h2 = 0.f;
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const __nv_fp8_storage_t b = __nv_cvt_float_to_fp8(xs[u] * scale, __NV_SATFINITE, __NV_E4M3);
+    packed |= (uint32_t)b << (8 * u);
+    const __half_raw hr = __nv_cvt_fp8_to_halfraw(b, __NV_E4M3);
+    const float d = __half2float(__half(hr)) * iscale;
+    e2 = fmaf(d - xs[u], d - xs[u], e2);
+    h2 = fmaf(d, d, h2);
+  }
+  reinterpret_cast<uint32_t *>(out + r * DIM)[lane] = packed;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+    h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+  }
+  if (lane == 0) {
+    inv[r] = iscale;
+    if (margins) {
+      // the factor 1 + 2^-10 covers the FP32 rounding of these norms
+      const float d = (sqrtf(e2) * cmax + sqrtf(h2) * (cerr8 + ldexpf(cmax, -15))) * (1.f + ldexpf(1.f, -10)) + 1e-7f;
+      margins[r] = 2.f * lambda * d;
+    }
+    if (err_max) atomicMax(err_max, __float_as_uint(sqrtf(e2) * (1.f + ldexpf(1.f, -12))));
+  }
+}
+
+tachiom_status launch_quantize_e4m3(const Index &ix, const float *rows, int nrows, uint8_t *out, float *inv,
+                                    float lambda, float *margins, cudaStream_t s) {
+  if (nrows <= 0) return TACHIOM_OK;
+  TPROF("quantize_e4m3", s);
+  k_quant_e4m3<<<(nrows + 7) / 8, 256, 0, s>>>(rows, nrows, out, inv, ix.cnorm_max, ix.cerr8_max, lambda, margins,
+                                              nullptr);
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
+tachiom_status launch_cent_e4m3(Index &ix, cudaStream_t s) {
+  unsigned *d = nullptr;
+  if (cudaMalloc(&d, 4) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TACHIOM_ERR_OOM, "cudaMalloc of 4 bytes failed");
+  }
+  cudaMemsetAsync(d, 0, 4, s);
+  const int64_t blocks = (ix.C + 7) / 8;
+  k_quant_e4m3<<<(unsigned)blocks, 256, 0, s>>>(ix.cent_f32, ix.C, ix.cent_e4m3, ix.cent_inv_sc, 0.f, 0.f, 0.f,
+                                                nullptr, d);
+  unsigned h = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(TACHIOM_ERR_CUDA, "E4M3 centroid copy failed: %s", cudaGetErrorString(e));
+  float f;
+  memcpy(&f, &h, 4);
+  ix.cerr8_max = f;
   return TACHIOM_OK;
 }
 

@@ -1,34 +1,43 @@
-// Step (a) on the 5th-generation tensor cores: BF16 products, FP32 accumulation
-// (Sec. 2.2, Gather step 1 in exhaustive form), with a rigorous FP32 repair.
+// Step (a) on the 5th-generation tensor cores (Sec. 2.2, Gather step 1 in
+// exhaustive form): BF16 or FP8-E4M3 products with FP32 accumulation, then an
+// exact FP32 repair of the candidates near each row's kappa_c-th score.
 //
 // GEMM orientation: a tcgen05.mma tile is M = 128 centroids (TMEM lanes) by
 // N = 256 query rows (TMEM columns) by K = 128. The CTA keeps its 256 query
-// rows resident in shared memory (64 KB, loaded once by TMA) and streams
-// 128-centroid tiles (32 KB) through a 4-stage TMA/mbarrier ring. Two
-// 256-column FP32 accumulators (all 512 TMEM columns) let the MMA of tile t+1
-// run while 16 epilogue warps drain tile t with tcgen05.ld. Warp roles: warp 0
-// issues TMA, warp 1 owns TMEM and issues the MMAs, warps 2..17 are the
-// epilogue (warp w reads TMEM lanes 32*(w%4).., columns 64*((w-2)/4)..+64).
+// rows resident in shared memory (one TMA load) and streams 128-centroid tiles
+// through a TMA/mbarrier ring; two 256-column FP32 accumulators (all 512 TMEM
+// columns) let the MMA of tile t+1 run while 16 epilogue warps drain tile t
+// with tcgen05.ld. Warp 0 issues TMA, warp 1 owns TMEM and issues the MMAs,
+// warps 2..17 are the epilogue (warp w reads TMEM lanes 32*(w%4).., columns
+// 64*((w-2)/4)..+64).
+//   BF16: a 128-element row is two 128-byte swizzled halves; 8 MMAs of
+//         kind::f16 (K = 16) per tile; 4 pipeline stages (192 KB).
+//   E4M3: a row is one 128-byte swizzled row; 4 MMAs of kind::f8f6f4 (K = 32)
+//         per tile; 8 stages (160 KB). Every centroid and every query row is
+//         stored as x * 2^k with max |x| * 2^k in (224, 448] (a power of two, so
+//         the scaling is exact) and the epilogue undoes both scales:
+//         score = acc * 2^-k_j * 2^-k_i.
 //
-// Selection:
-//   pass    every group of 32 consecutive centroids reports, per query row, its
-//           maximum approximate score (one redux.sync per column), rounded up
-//           to fp16 (so a group is never dropped by the rounding) -> gmax; each
-//           epilogue lane also keeps, for each of its query rows, the TOPM
-//           largest group maxima it has seen (a stream = one CTA's TMEM lane
-//           quarter; tiles go to CTAs in a strided order, so the streams see
-//           interleaved parts of the centroid table);
-//   select  tau'_r = the kappa_c-th largest value in the union of the row's
-//           streams, a lower bound on its kappa_c-th largest group maximum
-//           (the union holds maxima of distinct groups); every group whose
-//           maximum is >= tau'_r - margin_r is kept. A centroid of the row's
-//           exact FP32 top-kappa_c has an approximate score >= (approximate
-//           kappa_c-th best) - 2 delta_r >= tau'_r - margin_r (margin_r =
-//           2 delta_r), so its group is kept: about kappa_c groups per row
-//           survive;
-//   rescore the centroids of the kept groups are scored exactly in FP32 (the
-//           same fmaf chain as the FP32 path) and the exact top-kappa_c is kept.
-// A row whose kept groups do not fit is recomputed by a full FP32 scan.
+// The same kernel runs three epilogues:
+//   sample  (MODE_SAMPLE) the CTAs walk every S-th centroid tile; per query row,
+//           each epilogue lane keeps the TOPM largest maxima over groups of 32
+//           centroids it has seen (a stream = one CTA's TMEM lane quarter) ->
+//           tops. k_gsel_lim then takes tau'_r = the kappa_c-th largest value of
+//           the union of the row's streams: the union holds maxima of distinct
+//           groups, so kappa_c distinct centroids score >= tau'_r approximately
+//           and >= tau'_r - delta_r exactly, and every centroid of the row's exact
+//           top-kappa_c scores >= tau'_r - 2 delta_r =: lim_r approximately;
+//   emit    (MODE_EMIT) every tile; each (row, centroid) whose approximate score
+//           is >= lim_r is appended to the row's candidate list;
+//   raw     (MODE_RAW) diagnostics: every approximate score.
+// k_cand_rescore then scores a row's candidates exactly in FP32 (the FP32
+// path's fmaf chain) and keeps the first kappa_c by (score desc, id asc). A
+// row whose list overflows is recomputed by the full FP32 scan.
+// delta_r is the rigorous bound of the row's rounding errors for BF16 (the
+// result is then the FP32 path's, bit for bit); for E4M3 it is lambda times
+// the same Cauchy-Schwarz bound (lambda = 1: rigorous; lambda < 1: a window
+// sized to the typical error, the path's accuracy then measured against the
+// FP64 oracle).
 //
 // Every wait on an mbarrier is bounded by %globaltimer; a wait that runs out
 // raises TACHIOM_FLAG_TIMEOUT, every role leaves its loop, in-flight copies
@@ -48,54 +57,97 @@ namespace tc {
 
 constexpr int BM = 128;            // centroids per tile (MMA M)
 constexpr int BN = 256;            // query rows per CTA (MMA N)
-constexpr int KH = 64;             // K elements per 128-byte swizzled half
-constexpr int STAGES = 4;
-constexpr int A_HALF = BM * KH * 2;        // 16 KB
-constexpr int A_STAGE = 2 * A_HALF;        // 32 KB
-constexpr int B_HALF = BN * KH * 2;        // 32 KB
-constexpr int B_BYTES = 2 * B_HALF;        // 64 KB
-constexpr int TILE_BYTES = B_BYTES + STAGES * A_STAGE;  // 192 KB
 constexpr int EPI_WARPS = 16;      // 4 per TMEM lane quarter, 64 columns each
 constexpr int THREADS = 64 + 32 * EPI_WARPS;  // TMA warp, MMA warp, epilogue
 constexpr int TMEM_COLS = 512;
 constexpr int TOPM = 8;            // group maxima kept per (query row, stream)
+constexpr int ECAP = 16384;        // E4M3: candidates a row may emit (over all CTAs of its row block)
+constexpr int SAMPLE_STRIDE = 16;  // the sample pass walks every 16th tile
+constexpr int GCAP = 256;          // groups of 32 centroids a row may keep (group selection)
 
+enum { MODE_SAMPLE = 1, MODE_EMIT = 2, MODE_RAW = 3 };
+
+// shared-memory geometry of the two operand types
+template <bool F8>
+struct Geo {
+  static constexpr int HALVES = F8 ? 1 : 2;            // 128-byte swizzled column blocks per row
+  static constexpr int KBOX = F8 ? 128 : 64;           // K elements per block
+  static constexpr int STAGES = F8 ? 8 : 4;
+  static constexpr int A_HALF = BM * 128;              // 16 KB
+  static constexpr int A_STAGE = HALVES * A_HALF;
+  static constexpr int B_HALF = BN * 128;              // 32 KB
+  static constexpr int B_BYTES = HALVES * B_HALF;
+  static constexpr int KSTEPS = F8 ? 4 : 8;            // MMAs per tile (32 bytes of K each)
+  static constexpr int TILE_BYTES = B_BYTES + STAGES * A_STAGE;
+};
+
+template <bool F8>
 struct Ctl {
-  uint64_t full[STAGES];
-  uint64_t empty[STAGES];
+  uint64_t full[Geo<F8>::STAGES];
+  uint64_t empty[Geo<F8>::STAGES];
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t bfull;
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
+  float lim[BN];  // MODE_EMIT: per query row, the emission threshold in the accumulator's scale
+  int ecnt[BN];   // MODE_EMIT: per query row, the candidates this CTA has emitted
 };
-constexpr int SMEM_BYTES = TILE_BYTES + (int)sizeof(Ctl) + 1024;
+template <bool F8>
+constexpr int smem_bytes() { return Geo<F8>::TILE_BYTES + (int)sizeof(Ctl<F8>) + 1024; }
 
-// CTA (x, rb) takes the tiles x, x + splits, x + 2 splits, ... against query rows [rb * 256, +256).
-// MODE 1: maximum per group of 32 centroids, rounded up to fp16 -> gmax[rb][tile * 4 + quarter][256], and per
-//         query row the TOPM largest of its stream -> tops[row][x * 4 + quarter][TOPM] (descending)
-// MODE 3: raw scores to (float *)cand [R x C] (diagnostics and tests)
-template <int MODE>
+// instruction descriptor: kind::f8f6f4 with A = B = E4M3 (format 0), D = F32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+struct TcArgs {
+  int64_t C;
+  int R;
+  int ntiles;        // centroid tiles of the table
+  int tstride;       // the CTA walks tiles (x + it * splits) * tstride
+  const float *inv_sc;   // E4M3: [C] 2^-k of every centroid
+  const float *inv_sq;   // E4M3: [R] 2^-k of every query row
+  const float *lim;      // MODE_EMIT: [R] emission threshold (score scale)
+  float *tops;           // MODE_SAMPLE: [R][splits * 4][TOPM]
+  uint32_t *gmax;        // MODE_SAMPLE, optional: [rbs][G][256] fp16 group maxima, rounded up
+  int G;                 // groups of the table (4 per tile)
+  int32_t *elist;        // MODE_EMIT: [R][splits][scap] each CTA's candidates of each row
+  int32_t *ecnt;         // MODE_EMIT: [R][splits] their counts (may exceed scap: overflow)
+  int scap;
+  float *raw;            // MODE_RAW: [R][C]
+  uint32_t *flags;
+};
+
+// CTA (x, rb) takes the tiles (x + it * splits) * tstride against query rows [rb * 256, +256).
+template <int MODE, bool F8>
 __global__ void __launch_bounds__(THREADS, 1)
-k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t C, int R,
-          int ntiles, int G, uint32_t *__restrict__ gmax, float *__restrict__ tops, uint64_t *__restrict__ cand,
-          uint32_t *__restrict__ flags) {
+k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs A) {
+  using G = Geo<F8>;
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
   unsigned char *tsm = (unsigned char *)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char *Bs = tsm;                  // [2 halves][256 rows][128 B]
-  unsigned char *As = tsm + B_BYTES;        // [STAGES][2 halves][128 rows][128 B]
-  Ctl *ctl = reinterpret_cast<Ctl *>(tsm + TILE_BYTES);
+  unsigned char *Bs = tsm;                  // [halves][256 rows][128 B]
+  unsigned char *As = tsm + G::B_BYTES;     // [STAGES][halves][128 rows][128 B]
+  Ctl<F8> *ctl = reinterpret_cast<Ctl<F8> *>(tsm + G::TILE_BYTES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rb = blockIdx.y;
-  const int splits = gridDim.x;
-  const int nt = max(0, (ntiles - (int)blockIdx.x + splits - 1) / splits);
-  auto tile_of = [&](int it) { return (int)blockIdx.x + it * splits; };
+  // the row block is the fastest grid index, so the CTAs resident at once share centroid tiles in L2
+  const int rb = blockIdx.x;
+  const int sx = blockIdx.y, splits = gridDim.y;
+  const int nts = (A.ntiles + A.tstride - 1) / A.tstride;  // tiles of the walk
+  const int nt = max(0, (nts - sx + splits - 1) / splits);
+  auto tile_of = [&](int it) { return (sx + it * splits) * A.tstride; };
   volatile int *abort = &ctl->abort;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; s++) {
+    for (int s = 0; s < G::STAGES; s++) {
       mbar_init(&ctl->full[s], 1);
       mbar_init(&ctl->empty[s], 1);
     }
@@ -107,6 +159,16 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     mbar_init(&ctl->drain, 1);
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (MODE == MODE_EMIT) {
+    // per row, the threshold in the accumulator's scale: lim / inv_sq (E4M3), +inf past the last row
+    for (int i = threadIdx.x; i < BN; i += THREADS) {
+      const int row = rb * BN + i;
+      float l = INFINITY;
+      if (row < A.R) l = F8 ? A.lim[row] / A.inv_sq[row] : A.lim[row];
+      ctl->lim[i] = l;
+      ctl->ecnt[i] = 0;
+    }
   }
   if (warp == 1) {
     __syncwarp();
@@ -124,40 +186,47 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     if (lane == 0 && nt > 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
-      mbar_expect_tx(&ctl->bfull, B_BYTES);
-      tma_load_2d(Bs, &tmB, 0, rb * BN, &ctl->bfull);
-      tma_load_2d(Bs + B_HALF, &tmB, KH, rb * BN, &ctl->bfull);
+      mbar_expect_tx(&ctl->bfull, G::B_BYTES);
+#pragma unroll
+      for (int h = 0; h < G::HALVES; h++) tma_load_2d(Bs + h * G::B_HALF, &tmB, h * G::KBOX, rb * BN, &ctl->bfull);
       int issued = 0;
       for (int it = 0; it < nt; it++) {
-        const int s = it % STAGES;
-        if (it >= STAGES && !mbar_wait(&ctl->empty[s], ((it / STAGES) & 1) ^ 1, abort, flags)) break;
-        unsigned char *a = As + s * A_STAGE;
-        mbar_expect_tx(&ctl->full[s], A_STAGE);
-        tma_load_2d(a, &tmA, 0, tile_of(it) * BM, &ctl->full[s]);
-        tma_load_2d(a + A_HALF, &tmA, KH, tile_of(it) * BM, &ctl->full[s]);
+        const int s = it % G::STAGES;
+        if (it >= G::STAGES && !mbar_wait(&ctl->empty[s], ((it / G::STAGES) & 1) ^ 1, abort, A.flags)) break;
+        unsigned char *a = As + s * G::A_STAGE;
+        mbar_expect_tx(&ctl->full[s], G::A_STAGE);
+#pragma unroll
+        for (int h = 0; h < G::HALVES; h++)
+          tma_load_2d(a + h * G::A_HALF, &tmA, h * G::KBOX, tile_of(it) * BM, &ctl->full[s]);
         issued = it + 1;
       }
       // drain: every copy this warp issued has landed before the CTA may exit
       mbar_drain(&ctl->bfull, 0);
-      for (int it = max(0, issued - STAGES); it < issued; it++) mbar_drain(&ctl->full[it % STAGES], (it / STAGES) & 1);
+      for (int it = max(0, issued - G::STAGES); it < issued; it++)
+        mbar_drain(&ctl->full[it % G::STAGES], (it / G::STAGES) & 1);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0 && nt > 0) {
-      bool ok = mbar_wait(&ctl->bfull, 0, abort, flags);
+      bool ok = mbar_wait(&ctl->bfull, 0, abort, A.flags);
       const uint32_t b_base = smem_u32(Bs);
       for (int it = 0; ok && it < nt; it++) {
-        const int s = it % STAGES, buf = it & 1;
-        if (!mbar_wait(&ctl->full[s], (it / STAGES) & 1, abort, flags)) break;
-        if (it >= 2 && !mbar_wait(&ctl->tempty[buf], ((it >> 1) - 1) & 1, abort, flags)) break;
+        const int s = it % G::STAGES, buf = it & 1;
+        if (!mbar_wait(&ctl->full[s], (it / G::STAGES) & 1, abort, A.flags)) break;
+        if (it >= 2 && !mbar_wait(&ctl->tempty[buf], ((it >> 1) - 1) & 1, abort, A.flags)) break;
         fence_after();
-        const uint32_t a_base = smem_u32(As + s * A_STAGE);
+        const uint32_t a_base = smem_u32(As + s * G::A_STAGE);
 #pragma unroll
-        for (int kk = 0; kk < 8; kk++) {
-          const uint32_t off = (uint32_t)((kk >> 2) * A_HALF + (kk & 3) * 32);
-          const uint32_t boff = (uint32_t)((kk >> 2) * B_HALF + (kk & 3) * 32);
-          mma_bf16(tmem + (uint32_t)(buf * BN), sdesc(a_base + off), sdesc(b_base + boff), idesc_bf16(BM, BN),
-                   kk > 0 ? 1u : 0u);
+        for (int kk = 0; kk < G::KSTEPS; kk++) {
+          // 32 bytes of K per MMA inside a 128-byte swizzled block
+          const uint32_t off = (uint32_t)((kk >> 2) * G::A_HALF + (kk & 3) * 32);
+          const uint32_t boff = (uint32_t)((kk >> 2) * G::B_HALF + (kk & 3) * 32);
+          if (F8)
+            mma_e4m3(tmem + (uint32_t)(buf * BN), sdesc(a_base + off), sdesc(b_base + boff), idesc_e4m3(BM, BN),
+                     kk > 0 ? 1u : 0u);
+          else
+            mma_bf16(tmem + (uint32_t)(buf * BN), sdesc(a_base + off), sdesc(b_base + boff), idesc_bf16(BM, BN),
+                     kk > 0 ? 1u : 0u);
         }
         mma_commit(&ctl->empty[s]);
         mma_commit(&ctl->tfull[buf]);
@@ -171,8 +240,7 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int e = warp - 2;
     const int quarter = warp & 3;       // TMEM lane quarter this warp may access
     const int cblk = e >> 2;            // column block: query rows [cblk * 64, +64)
-    // running TOPM largest group maxima of this lane's rows cblk * 64 + ch * 32 + lane (descending)
-    float tm[2][TOPM];
+    float tm[2][TOPM];                  // MODE_SAMPLE: running TOPM largest of this lane's two rows
 #pragma unroll
     for (int a = 0; a < 2; a++)
 #pragma unroll
@@ -186,11 +254,19 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         t[k] = hi;
       }
     };
+    float isq[2] = {1.f, 1.f};  // MODE_SAMPLE, E4M3: the scale of this lane's two rows
+    if (F8 && MODE == MODE_SAMPLE) {
+#pragma unroll
+      for (int ch = 0; ch < 2; ch++) {
+        const int row = rb * BN + cblk * 64 + ch * 32 + lane;
+        isq[ch] = row < A.R ? A.inv_sq[row] : 1.f;
+      }
+    }
     for (int it = 0; it < nt; it++) {
       const int buf = it & 1;
       // one lane waits, the whole warp follows its verdict (the TMEM loads below are warp-aligned)
       int ok = 0;
-      if (lane == 0) ok = mbar_wait(&ctl->tfull[buf], (it >> 1) & 1, abort, flags) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(&ctl->tfull[buf], (it >> 1) & 1, abort, A.flags) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       __syncwarp();
@@ -198,8 +274,9 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + cblk * 64);
       const int tile = tile_of(it);
       const int64_t j = (int64_t)tile * BM + quarter * 32 + lane;  // this thread's centroid
-      const bool jv = j < C;
-      const bool full_tile = (int64_t)(tile + 1) * BM <= C;  // uniform: no centroid past C
+      const bool jv = j < A.C;
+      const bool full_tile = (int64_t)(tile + 1) * BM <= A.C;  // uniform: no centroid past C
+      const float isc = F8 ? (jv ? __ldg(A.inv_sc + j) : 0.f) : 1.f;
 #pragma unroll
       for (int ch = 0; ch < 2; ch++) {
         uint32_t v[32];
@@ -211,18 +288,18 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           __syncwarp();
           if (lane == 0) mbar_arrive(&ctl->tempty[buf]);
         }
-        if (MODE == 1) {
+        if (MODE == MODE_SAMPLE) {
           // maximum score of the warp's 32 centroids, per query row (-inf: no valid centroid):
           // one redux per column gives every lane all 32 maxima, a 5-level select tree
           // leaves lane l the one of its row
-          __half *dst = reinterpret_cast<__half *>(gmax) + ((int64_t)rb * G + tile * 4 + quarter) * BN + cblk * 64;
           float m[32];
           if (full_tile) {
 #pragma unroll
-            for (int c = 0; c < 32; c++) m[c] = redux_fmax(__uint_as_float(v[c]));
+            for (int c = 0; c < 32; c++) m[c] = redux_fmax(F8 ? __uint_as_float(v[c]) * isc : __uint_as_float(v[c]));
           } else {
 #pragma unroll
-            for (int c = 0; c < 32; c++) m[c] = redux_fmax(jv ? __uint_as_float(v[c]) : -INFINITY);
+            for (int c = 0; c < 32; c++)
+              m[c] = redux_fmax(jv ? (F8 ? __uint_as_float(v[c]) * isc : __uint_as_float(v[c])) : -INFINITY);
           }
 #pragma unroll
           for (int w = 16; w >= 1; w >>= 1) {
@@ -230,26 +307,50 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 #pragma unroll
             for (int c = 0; c < w; c++) m[c] = hi ? m[c + w] : m[c];
           }
-          const float mine = m[0];
-          dst[ch * 32 + lane] = __float2half_ru(mine);  // rounded up: the filter stays conservative
+          const float mine = F8 ? m[0] * isq[ch] : m[0];
+          if (A.gmax) {
+            __half *dst = reinterpret_cast<__half *>(A.gmax) + ((int64_t)rb * A.G + tile * 4 + quarter) * BN + cblk * 64;
+            dst[ch * 32 + lane] = __float2half_ru(mine);  // rounded up: the filter stays conservative
+          }
           // most values fall below every lane's current 8th largest: skip the insertion then
           if (__any_sync(0xffffffffu, !(mine <= tm[ch][TOPM - 1]))) insert(tm[ch], mine);
-        } else if (MODE == 3) {
-          // diagnostic: raw scores [R x C]
+        } else if (MODE == MODE_EMIT) {
+          // the rare (row, centroid) pairs at or above the row's threshold go to its list
+          const float *lim = ctl->lim + cblk * 64 + ch * 32;
+          uint32_t hit = 0u;
+#pragma unroll
+          for (int c = 0; c < 32; c++) {
+            const float sv = F8 ? __uint_as_float(v[c]) * isc : __uint_as_float(v[c]);
+            hit |= (sv >= lim[c]) ? (1u << c) : 0u;
+          }
+          if (!jv) hit = 0u;
+          // the rare hits; the row's count lives in shared memory (no global round trip here)
+          while (hit) {
+            const int c = __ffs(hit) - 1;
+            hit &= hit - 1u;
+            const int lr = cblk * 64 + ch * 32 + c;
+            const int pos = atomicAdd(&ctl->ecnt[lr], 1);
+            if (pos < A.scap) A.elist[((int64_t)(rb * BN + lr) * splits + sx) * A.scap + pos] = (int32_t)j;
+          }
+        } else if (MODE == MODE_RAW) {
 #pragma unroll
           for (int c = 0; c < 32; c++) {
             const int row = rb * BN + cblk * 64 + ch * 32 + c;
-            if (jv && row < R) reinterpret_cast<float *>(cand)[(int64_t)row * C + j] = __uint_as_float(v[c]);
+            if (jv && row < A.R) {
+              float sv = __uint_as_float(v[c]);
+              if (F8) sv = sv * isc * A.inv_sq[row];
+              A.raw[(int64_t)row * A.C + j] = sv;
+            }
           }
         }
       }
     }
-    if (MODE == 1) {
+    if (MODE == MODE_SAMPLE) {
 #pragma unroll
       for (int ch = 0; ch < 2; ch++) {
         const int row = rb * BN + cblk * 64 + ch * 32 + lane;
-        if (row < R) {
-          float4 *d = reinterpret_cast<float4 *>(tops + ((int64_t)row * splits * 4 + blockIdx.x * 4 + quarter) * TOPM);
+        if (row < A.R) {
+          float4 *d = reinterpret_cast<float4 *>(A.tops + ((int64_t)row * splits * 4 + sx * 4 + quarter) * TOPM);
           const float *t = tm[ch];
 #pragma unroll
           for (int k = 0; k < TOPM / 4; k++) d[k] = make_float4(t[4 * k], t[4 * k + 1], t[4 * k + 2], t[4 * k + 3]);
@@ -259,6 +360,12 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   }
   fence_before();
   __syncthreads();
+  if (MODE == MODE_EMIT) {
+    for (int i = threadIdx.x; i < BN; i += THREADS) {
+      const int row = rb * BN + i;
+      if (row < A.R) A.ecnt[(int64_t)row * splits + sx] = ctl->ecnt[i];
+    }
+  }
   if (warp == 1) {
     __syncwarp();
     fence_after();
@@ -266,7 +373,6 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   }
 }
 
-constexpr int GCAP = 256;       // groups a row may keep (8192 centroids)
 constexpr int LIM_THREADS = 128;
 constexpr int LIM_VPT = 37;     // values per thread: up to 148 CTAs x 4 streams x TOPM per row
 
@@ -377,20 +483,20 @@ k_gsel_collect(const __half *__restrict__ gmax, int G, int R, const float *__res
 // the first kappa_c are the answer. A row whose groups overflowed the list,
 // or whose kept scores overflowed the buffer, is marked for the full FP32 scan.
 constexpr int FCAP = 2048;       // kept exact scores per row
-constexpr int RS_WARPS = 8;
+constexpr int GRS_WARPS = 8;
 
 template <bool BF16C>
-constexpr int rs_row_bytes() { return BF16C ? DIM * 2 + 16 : DIM * 4 + 16; }
+constexpr int grs_row_bytes() { return BF16C ? DIM * 2 + 16 : DIM * 4 + 16; }
 template <bool BF16C>
-constexpr size_t rs_smem() { return (size_t)FCAP * 8 + (size_t)RS_WARPS * 32 * rs_row_bytes<BF16C>(); }
+constexpr size_t grs_smem() { return (size_t)FCAP * 8 + (size_t)GRS_WARPS * 32 * grs_row_bytes<BF16C>(); }
 
 template <bool BF16C>
-__global__ void __launch_bounds__(RS_WARPS * 32)
+__global__ void __launch_bounds__(GRS_WARPS * 32)
 k_group_rescore(const float *__restrict__ rows, int R, const float *__restrict__ cent_f32,
                 const __nv_bfloat16 *__restrict__ cent_bf16, int64_t C, int kc, const int32_t *__restrict__ glist,
                 const int32_t *__restrict__ gcount, const float *__restrict__ lim, int32_t *__restrict__ top_ids,
                 float *__restrict__ top_s, int32_t *__restrict__ lossy_rows, uint32_t *__restrict__ flags) {
-  constexpr int RB = rs_row_bytes<BF16C>();
+  constexpr int RB = grs_row_bytes<BF16C>();
   constexpr int CH = BF16C ? DIM * 2 / 16 : DIM * 4 / 16;  // 16-byte chunks per centroid row
   extern __shared__ __align__(16) unsigned char rsm_raw[];
   uint64_t *keys = reinterpret_cast<uint64_t *>(rsm_raw);  // [FCAP]
@@ -420,7 +526,7 @@ k_group_rescore(const float *__restrict__ rows, int R, const float *__restrict__
     }
   };
   if (warp < ng) load_group(warp);
-  for (int g = warp; g < ng; g += RS_WARPS) {
+  for (int g = warp; g < ng; g += GRS_WARPS) {
     const int64_t j0 = (int64_t)gl[g] * 32;
 #pragma unroll
     for (int u = 0; u < CH; u++) {
@@ -428,7 +534,7 @@ k_group_rescore(const float *__restrict__ rows, int R, const float *__restrict__
       *reinterpret_cast<uint4 *>(st + row * RB + pc * 16) = v[u];
     }
     __syncwarp();
-    if (g + RS_WARPS < ng) load_group(g + RS_WARPS);  // in flight while this group is scored
+    if (g + GRS_WARPS < ng) load_group(g + GRS_WARPS);  // in flight while this group is scored
     const int64_t j = j0 + lane;
     if (j < C) {
       float acc = 0.f;
@@ -480,6 +586,133 @@ k_group_rescore(const float *__restrict__ rows, int R, const float *__restrict__
   }
 }
 
+// One block per query row: the row's candidates (the emit pass's per-CTA lists)
+// scored exactly in FP32 with the FP32 path's arithmetic, the fmaf chain over
+// k = 0..127; each lane loads its candidate's centroid row into registers
+// (16-byte loads). Only scores >= lim[row] are kept: kappa_c centroids score
+// >= lim + margin / 2 exactly, so the kappa_c-th exact score (ties included) is
+// above lim. The kappa_c-th largest key is found by a radix select, the kappa_c
+// keys at or above it are sorted by (score desc, id asc). A row whose lists
+// overflowed is marked for the full FP32 scan.
+constexpr int RS_THREADS = 256;
+constexpr size_t rs_smem() { return (size_t)ECAP * 8; }
+
+template <bool BF16C>
+__global__ void __launch_bounds__(RS_THREADS)
+k_cand_rescore(const float *__restrict__ rows, int R, const float *__restrict__ cent_f32,
+               const __nv_bfloat16 *__restrict__ cent_bf16, int64_t C, int kc, const int32_t *__restrict__ elist,
+               const int32_t *__restrict__ ecnt, int splits, int scap, const float *__restrict__ lim,
+               int32_t *__restrict__ ncand, int32_t *__restrict__ top_ids, float *__restrict__ top_s,
+               int32_t *__restrict__ lossy_rows, uint32_t *__restrict__ flags) {
+  extern __shared__ __align__(16) unsigned char rsm_raw[];
+  uint64_t *keys = reinterpret_cast<uint64_t *>(rsm_raw);  // [ECAP]
+  __shared__ float q[DIM];
+  __shared__ uint32_t hist[1 << KSEL_BITS];
+  __shared__ uint64_t small[64];
+  __shared__ uint64_t kept[MAX_KC];
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t sh[8];
+  __shared__ int s_cnt, s_tot, s_lossy;
+  const int r = blockIdx.x;
+  if (r >= R) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float l = lim[r];
+  for (int k = tid; k < DIM; k += RS_THREADS) q[k] = rows[(int64_t)r * DIM + k];
+  if (tid == 0) {
+    s_cnt = 0;
+    s_tot = 0;
+    s_lossy = 0;
+  }
+  __syncthreads();
+  for (int x = tid; x < splits; x += RS_THREADS) {
+    const int c = ecnt[(int64_t)r * splits + x];
+    atomicAdd(&s_tot, c);
+    if (c > scap) s_lossy = 1;
+  }
+  __syncthreads();
+  const bool lossy = s_lossy != 0;
+  if (!lossy) {
+    // warp w takes the lists of CTAs w, w + 8, ...; a lane per candidate
+    for (int x = warp; x < splits; x += RS_THREADS / 32) {
+      const int c = ecnt[(int64_t)r * splits + x];
+      const int32_t *el = elist + ((int64_t)r * splits + x) * scap;
+      for (int b = 0; b < c; b += 32) {
+        const int i = b + lane;
+        const int32_t j = i < c ? el[i] : -1;
+        if (j >= 0 && j < C) {
+          float acc = 0.f;
+          if (BF16C) {
+            const uint4 *cr = reinterpret_cast<const uint4 *>(cent_bf16 + (int64_t)j * DIM);
+            uint4 v[16];
+#pragma unroll
+            for (int u = 0; u < 16; u++) v[u] = __ldg(cr + u);
+#pragma unroll
+            for (int k8 = 0; k8 < 16; k8++) {
+              const uint32_t w[4] = {v[k8].x, v[k8].y, v[k8].z, v[k8].w};
+#pragma unroll
+              for (int h = 0; h < 4; h++) {
+                acc = fmaf(q[k8 * 8 + 2 * h], __uint_as_float(w[h] << 16), acc);
+                acc = fmaf(q[k8 * 8 + 2 * h + 1], __uint_as_float(w[h] & 0xffff0000u), acc);
+              }
+            }
+          } else {
+            const uint4 *cr = reinterpret_cast<const uint4 *>(cent_f32 + (int64_t)j * DIM);
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+              uint4 v[16];
+#pragma unroll
+              for (int u = 0; u < 16; u++) v[u] = __ldg(cr + half * 16 + u);
+#pragma unroll
+              for (int k4 = 0; k4 < 16; k4++) {
+                const int k = half * 64 + k4 * 4;
+                acc = fmaf(q[k + 0], __uint_as_float(v[k4].x), acc);
+                acc = fmaf(q[k + 1], __uint_as_float(v[k4].y), acc);
+                acc = fmaf(q[k + 2], __uint_as_float(v[k4].z), acc);
+                acc = fmaf(q[k + 3], __uint_as_float(v[k4].w), acc);
+              }
+            }
+          }
+          if (!(acc < l)) keys[atomicAdd(&s_cnt, 1)] = comp_key(acc, j);
+        } else if (j >= C) {
+          atomicOr(flags, TACHIOM_FLAG_BAD_INPUT);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int m = lossy ? 0 : s_cnt;
+  uint64_t *best = keys;
+  int nb = m;
+  if (m > kc) {
+    // the kappa_c largest keys (distinct: the id is part of the key)
+    const uint64_t T = block_kth_largest(keys, m, kc, hist, small, wsum, sh);
+    if (tid == 0) sh[6] = 0u;
+    __syncthreads();
+    for (int i = tid; i < m; i += RS_THREADS)
+      if (keys[i] >= T) {
+        const uint32_t d = atomicAdd(&sh[6], 1u);
+        if (d < (uint32_t)kc) kept[d] = keys[i];
+      }
+    __syncthreads();
+    best = kept;
+    nb = kc;
+  }
+  const int np = next_pow2(max(nb, 2));
+  for (int i = nb + tid; i < np; i += RS_THREADS) best[i] = 0ull;
+  __syncthreads();
+  block_sort_desc(best, np);
+  for (int i = tid; i < kc; i += RS_THREADS) {
+    const uint64_t vv = i < nb ? best[i] : 0ull;
+    top_ids[(int64_t)r * kc + i] = vv ? comp_id(vv) : -1;
+    top_s[(int64_t)r * kc + i] = vv ? comp_score(vv) : -INFINITY;
+  }
+  if (tid == 0) {
+    lossy_rows[r] = lossy ? 1 : 0;
+    ncand[r] = s_tot;
+    if (lossy) atomicOr(flags, TACHIOM_FLAG_TOPC_RESCUED);
+  }
+}
+
 // ---- host side ---------------------------------------------------------------------------
 std::mutex g_encode_mu;
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -506,9 +739,26 @@ tachiom_status encode_map(CUtensorMap *map, const void *base, int64_t rows, int 
   if (((uintptr_t)base & 15) != 0) return fail(TACHIOM_ERR_INVALID, "tensor map base not 16-byte aligned");
   cuuint64_t dims[2] = {(cuuint64_t)DIM, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)DIM * 2};
-  cuuint32_t box[2] = {(cuuint32_t)KH, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TACHIOM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return TACHIOM_OK;
+}
+
+// uint8 (E4M3) [rows x 128], box of 128 K-elements (128 bytes) by box_rows rows, 128-byte swizzle
+tachiom_status encode_map_u8(CUtensorMap *map, const void *base, int64_t rows, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc;
+  tachiom_status st = get_encoder(&enc);
+  if (st) return st;
+  if (((uintptr_t)base & 15) != 0) return fail(TACHIOM_ERR_INVALID, "tensor map base not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)DIM, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)DIM};
+  cuuint32_t box[2] = {(cuuint32_t)DIM, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(TACHIOM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -544,89 +794,188 @@ static int tc_sms(int device) {
   return sms;
 }
 
-// CTAs along the centroid axis: enough to fill the SMs, at least enough streams
-// for a row's union to hold kappa_c values, at most what k_gsel_lim holds
-static int tc_splits(int ntiles, int rbs, int kc, int sms) {
+static int gcd_int(int a, int b) {
+  while (b) {
+    const int t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// CTAs along the centroid axis for a walk of nts tiles: splits x row blocks a multiple of the
+// SM count (one CTA per SM, every SM busy in every wave), at least enough streams for a row's
+// union to hold kappa_c values, at most what k_gsel_lim holds.
+static int tc_splits(int nts, int rbs, int kc, int sms) {
   using namespace tc;
-  int sp = std::max(1, sms / rbs);
+  int sp = std::max(1, sms / gcd_int(sms, std::max(1, rbs)));
   sp = std::max(sp, (kc + 4 * TOPM - 1) / (4 * TOPM));
   sp = std::min(sp, LIM_VPT * LIM_THREADS / (4 * TOPM));
-  return std::max(1, std::min(sp, ntiles));
+  return std::max(1, std::min(sp, nts));
 }
 
-// 32-bit words of: gmax [rbs][groups][256] fp16, then tops [rows][streams][TOPM] fp32
+// stride of the sample pass: at most SAMPLE_STRIDE, and the sample keeps >= 8 kappa_c groups
+static int tc_sample_stride(int ntiles, int kc) {
+  return std::max(1, std::min(tc::SAMPLE_STRIDE, ntiles / std::max(1, 2 * kc)));
+}
+
+// 32-bit words of: gmax [rbs][groups][256] fp16 (BF16 group selection), then tops
+// [rows][streams <= 148 x 4][TOPM] fp32
 size_t topc_tc_gmax_elems(const Index &ix, int rows) {
   using namespace tc;
-  const int ntiles = (int)((ix.C + BM - 1) / BM);
-  const int rbs = (rows + BN - 1) / BN;
-  const int splits = tc_splits(ntiles, rbs, MAX_KC, tc_sms(ix.device));
-  return (size_t)rbs * ntiles * 4 * BN / 2 + (size_t)rows * splits * 4 * TOPM;
+  const int64_t ntiles = (ix.C + BM - 1) / BM;
+  const int64_t rbs = (rows + BN - 1) / BN;
+  return (size_t)(rbs * ntiles * 4 * BN / 2) + (size_t)rows * (LIM_VPT * LIM_THREADS);
 }
 
-// glist [rows][GCAP] followed by lim [rows]
-size_t topc_tc_glist_elems(int rows) { return (size_t)rows * (tc::GCAP + 1); }
+// BF16: glist [rows][GCAP], then lim [rows]; E4M3: elist [rows][ECAP] (per row [splits][ECAP /
+// splits]), then lim [rows], then the per-CTA counts [rows][splits <= 148]
+size_t topc_tc_glist_elems(int rows) {
+  return (size_t)rows * std::max<size_t>(tc::GCAP + 1, tc::ECAP + 1 + 148);
+}
 
-tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, const float *rows, int nrows, int kc,
-                              const float *margins, uint32_t *gmax, int32_t *glist, int32_t *gcount,
+// the operand maps of one precision: centroids (box 128 rows) and query rows (box 256 rows)
+static tachiom_status tc_maps(const Index &ix, const void *rows_q, int nrows, bool f8, CUtensorMap *mA,
+                              CUtensorMap *mB) {
+  using namespace tc;
+  tachiom_status st;
+  if (f8) {
+    if ((st = encode_map_u8(mA, ix.cent_e4m3, ix.C, BM))) return st;
+    return encode_map_u8(mB, rows_q, nrows, BN);
+  }
+  if ((st = encode_map(mA, ix.cent_bf16, ix.C, BM))) return st;
+  return encode_map(mB, rows_q, nrows, BN);
+}
+
+template <int MODE, bool F8>
+static tachiom_status tc_launch(const CUtensorMap &mA, const CUtensorMap &mB, const tc::TcArgs &a, int splits, int rbs,
+                                cudaStream_t s) {
+  using namespace tc;
+  constexpr int SM = smem_bytes<F8>();
+  TCUDA(cudaFuncSetAttribute(k_topc_tc<MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SM));
+  k_topc_tc<MODE, F8><<<dim3(rbs, splits), THREADS, SM, s>>>(mA, mB, a);
+  TLAUNCH();
+  return TACHIOM_OK;
+}
+
+tachiom_status launch_topc_tc(const Index &ix, const void *rows_q, const float *inv_sq, bool f8, const float *rows,
+                              int nrows, int kc, const float *margins, float *gmax_tops, int32_t *glist, int32_t *gcount,
                               int32_t *lossy_rows, int32_t *top_ids, float *top_s, uint32_t *flags, cudaStream_t s) {
   using namespace tc;
   if (nrows <= 0) return TACHIOM_OK;
   TPROF("topc_tc", s);
+  if (f8 && !ix.cent_e4m3) return fail(TACHIOM_ERR_INVALID, "the index has no E4M3 centroid copy");
   CUtensorMap mA, mB;
   tachiom_status st;
-  if ((st = encode_map(&mA, ix.cent_bf16, ix.C, BM))) return st;
-  if ((st = encode_map(&mB, rows_bf16, nrows, BN))) return st;
+  if ((st = tc_maps(ix, rows_q, nrows, f8, &mA, &mB))) return st;
   const int ntiles = (int)((ix.C + BM - 1) / BM);
   const int rbs = (nrows + BN - 1) / BN;
-  const int splits = tc_splits(ntiles, rbs, kc, tc_sms(ix.device));
+  const int sms = tc_sms(ix.device);
   const int G = ntiles * 4;
-  float *tops = reinterpret_cast<float *>(reinterpret_cast<__half *>(gmax) + (int64_t)rbs * G * BN);
-  float *lim = reinterpret_cast<float *>(glist + (int64_t)nrows * GCAP);
-  TCUDA(cudaFuncSetAttribute(k_topc_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  k_topc_tc<1><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, G, gmax, tops, nullptr,
-                                                               flags);
-  TLAUNCH();
-  if (splits * 4 * TOPM <= 32 * LIM_VPL)
-    k_gsel_lim_warp<<<(nrows + 3) / 4, 128, 0, s>>>(tops, nrows, splits * 4 * TOPM, kc, margins, lim);
+  TcArgs a{};
+  a.C = ix.C;
+  a.R = nrows;
+  a.ntiles = ntiles;
+  a.inv_sc = ix.cent_inv_sc;
+  a.inv_sq = inv_sq;
+  a.flags = flags;
+  a.G = G;
+  if (!f8) {
+    // BF16: every tile; per (row, group of 32) the maximum -> gmax, per (row, stream) the TOPM largest
+    // -> tops; lim = tau' - margin; the groups >= lim; their centroids scored exactly
+    uint32_t *gmax = reinterpret_cast<uint32_t *>(gmax_tops);
+    float *tops = reinterpret_cast<float *>(reinterpret_cast<__half *>(gmax) + (int64_t)rbs * G * BN);
+    float *lim = reinterpret_cast<float *>(glist + (int64_t)nrows * GCAP);
+    a.tstride = 1;
+    a.tops = tops;
+    a.gmax = gmax;
+    const int sp = tc_splits(ntiles, rbs, kc, sms);
+    if ((st = tc_launch<MODE_SAMPLE, false>(mA, mB, a, sp, rbs, s))) return st;
+    if (sp * 4 * TOPM <= 32 * LIM_VPL)
+      k_gsel_lim_warp<<<(nrows + 3) / 4, 128, 0, s>>>(tops, nrows, sp * 4 * TOPM, kc, margins, lim);
+    else
+      k_gsel_lim<<<nrows, LIM_THREADS, 0, s>>>(tops, nrows, sp * 4 * TOPM, kc, margins, lim);
+    TLAUNCH();
+    TCUDA(cudaMemsetAsync(gcount, 0, (size_t)nrows * 4, s));
+    k_gsel_collect<<<dim3(rbs * 8, COL_PARTS), 256, 0, s>>>(reinterpret_cast<const __half *>(gmax), G, nrows, lim,
+                                                            glist, gcount);
+    TLAUNCH();
+    if (ix.cdtype == TACHIOM_DTYPE_BF16) {
+      const size_t rsm = grs_smem<true>();
+      TCUDA(cudaFuncSetAttribute(k_group_rescore<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+      k_group_rescore<true><<<nrows, GRS_WARPS * 32, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc,
+                                                               glist, gcount, lim, top_ids, top_s, lossy_rows, flags);
+    } else {
+      const size_t rsm = grs_smem<false>();
+      TCUDA(cudaFuncSetAttribute(k_group_rescore<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+      k_group_rescore<false><<<nrows, GRS_WARPS * 32, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc,
+                                                                glist, gcount, lim, top_ids, top_s, lossy_rows, flags);
+    }
+    TLAUNCH();
+    return TACHIOM_OK;
+  }
+  // E4M3: a sample pass over every S-th tile gives the per-row threshold before the full pass, which
+  // emits the candidates above it; their exact scores give the answer
+  float *tops = gmax_tops;
+  int32_t *elist = glist;
+  float *lim = reinterpret_cast<float *>(elist + (int64_t)nrows * ECAP);
+  int32_t *scnt = elist + (int64_t)nrows * (ECAP + 1);
+  a.tstride = tc_sample_stride(ntiles, kc);
+  const int nts = (ntiles + a.tstride - 1) / a.tstride;
+  const int sp1 = tc_splits(nts, rbs, kc, sms);
+  a.tops = tops;
+  if ((st = tc_launch<MODE_SAMPLE, true>(mA, mB, a, sp1, rbs, s))) return st;
+  if (sp1 * 4 * TOPM <= 32 * LIM_VPL)
+    k_gsel_lim_warp<<<(nrows + 3) / 4, 128, 0, s>>>(tops, nrows, sp1 * 4 * TOPM, kc, margins, lim);
   else
-    k_gsel_lim<<<nrows, LIM_THREADS, 0, s>>>(tops, nrows, splits * 4 * TOPM, kc, margins, lim);
+    k_gsel_lim<<<nrows, LIM_THREADS, 0, s>>>(tops, nrows, sp1 * 4 * TOPM, kc, margins, lim);
   TLAUNCH();
-  TCUDA(cudaMemsetAsync(gcount, 0, (size_t)nrows * 4, s));
-  k_gsel_collect<<<dim3(rbs * 8, COL_PARTS), 256, 0, s>>>(reinterpret_cast<const __half *>(gmax), G, nrows, lim,
-                                                          glist, gcount);
-  TLAUNCH();
+  a.tstride = 1;
+  a.tops = nullptr;
+  a.lim = lim;
+  a.elist = elist;
+  a.ecnt = scnt;
+  const int sp2 = tc_splits(ntiles, rbs, kc, sms);
+  a.scap = ECAP / sp2;
+  if ((st = tc_launch<MODE_EMIT, true>(mA, mB, a, sp2, rbs, s))) return st;
+  const size_t rsm = rs_smem();
   if (ix.cdtype == TACHIOM_DTYPE_BF16) {
-    const size_t rsm = rs_smem<true>();
-    TCUDA(cudaFuncSetAttribute(k_group_rescore<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-    k_group_rescore<true><<<nrows, RS_WARPS * 32, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc,
-                                                            glist, gcount, lim, top_ids, top_s, lossy_rows, flags);
+    TCUDA(cudaFuncSetAttribute(k_cand_rescore<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    k_cand_rescore<true><<<nrows, RS_THREADS, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc, elist, scnt,
+                                                        sp2, a.scap, lim, gcount, top_ids, top_s, lossy_rows, flags);
   } else {
-    const size_t rsm = rs_smem<false>();
-    TCUDA(cudaFuncSetAttribute(k_group_rescore<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-    k_group_rescore<false><<<nrows, RS_WARPS * 32, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc,
-                                                             glist, gcount, lim, top_ids, top_s, lossy_rows, flags);
+    TCUDA(cudaFuncSetAttribute(k_cand_rescore<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    k_cand_rescore<false><<<nrows, RS_THREADS, rsm, s>>>(rows, nrows, ix.cent_f32, ix.cent_bf16, ix.C, kc, elist,
+                                                         scnt, sp2, a.scap, lim, gcount, top_ids, top_s, lossy_rows,
+                                                         flags);
   }
   TLAUNCH();
   return TACHIOM_OK;
 }
 
-// raw BF16 x BF16 -> FP32 tensor-core scores of the rows against every centroid
-tachiom_status launch_topc_tc_raw(const Index &ix, const __nv_bfloat16 *rows, int nrows, float *out,
-                                  uint32_t *flags, cudaStream_t s) {
+// raw approximate tensor-core scores of the rows against every centroid (BF16 x BF16 or
+// E4M3 x E4M3 with the scales undone) -> out [nrows x C]
+tachiom_status launch_topc_tc_raw(const Index &ix, const void *rows_q, const float *inv_sq, bool f8, int nrows,
+                                  float *out, uint32_t *flags, cudaStream_t s) {
   using namespace tc;
   if (nrows <= 0) return TACHIOM_OK;
+  if (f8 && !ix.cent_e4m3) return fail(TACHIOM_ERR_INVALID, "the index has no E4M3 centroid copy");
   CUtensorMap mA, mB;
   tachiom_status st;
-  if ((st = encode_map(&mA, ix.cent_bf16, ix.C, BM))) return st;
-  if ((st = encode_map(&mB, rows, nrows, BN))) return st;
+  if ((st = tc_maps(ix, rows_q, nrows, f8, &mA, &mB))) return st;
   const int ntiles = (int)((ix.C + BM - 1) / BM);
   const int rbs = (nrows + BN - 1) / BN;
+  tc::TcArgs a{};
+  a.C = ix.C;
+  a.R = nrows;
+  a.ntiles = ntiles;
+  a.tstride = 1;
+  a.inv_sc = ix.cent_inv_sc;
+  a.inv_sq = inv_sq;
+  a.raw = out;
+  a.flags = flags;
   const int splits = std::min(ntiles, 148);
-  TCUDA(cudaFuncSetAttribute(k_topc_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  k_topc_tc<3><<<dim3(splits, rbs), THREADS, SMEM_BYTES, s>>>(mA, mB, ix.C, nrows, ntiles, ntiles * 4, nullptr,
-                                                               nullptr, reinterpret_cast<uint64_t *>(out), flags);
-  TLAUNCH();
-  return TACHIOM_OK;
+  return f8 ? tc_launch<MODE_RAW, true>(mA, mB, a, splits, rbs, s) : tc_launch<MODE_RAW, false>(mA, mB, a, splits, rbs, s);
 }
 
 }  // namespace tachiom

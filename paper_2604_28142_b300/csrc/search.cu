@@ -93,6 +93,8 @@ static tachiom_status ws_reserve(Index *ix, Workspace *w, const Need &n) {
   AL(w->d_meta, (5 * nq + 2) * 4);
   AL(w->d_rows_f32, rows * DIM * 4);
   AL(w->d_rows_bf16, rows * DIM * 2);
+  AL(w->d_rows_f8, rows * DIM);
+  AL(w->d_inv_sq, rows * 4);
   AL(w->d_split, se * 8);
   AL(w->d_split_cnt, (se + rows) * 4);
   AL(w->d_top_ids, rows * kc * 4);
@@ -218,8 +220,10 @@ static tachiom_status check_params(const tachiom_search_params *p) {
     return fail(TACHIOM_ERR_INVALID, "kappa_c = %d out of [1, %d]", p->kappa_c, MAX_KC);
   if (p->kappa_d < 0 || p->kappa_d > MAX_KD)
     return fail(TACHIOM_ERR_INVALID, "kappa_d = %d out of [0, %d]", p->kappa_d, MAX_KD);
-  if (p->precision != TACHIOM_PREC_FP32 && p->precision != TACHIOM_PREC_BF16)
+  if (p->precision != TACHIOM_PREC_FP32 && p->precision != TACHIOM_PREC_BF16 && p->precision != TACHIOM_PREC_FP8)
     return fail(TACHIOM_ERR_INVALID, "unknown precision %d", p->precision);
+  if (!(p->rescore_margin == p->rescore_margin) || p->rescore_margin > 64.f)
+    return fail(TACHIOM_ERR_INVALID, "rescore_margin out of range");
   return TACHIOM_OK;
 }
 
@@ -252,7 +256,13 @@ static tachiom_status upload_meta(Workspace *w, const tachiom_search_params *p, 
 }
 
 static bool use_tc(const tachiom_search_params *p) {
-  return p->precision == TACHIOM_PREC_BF16 && topc_tc_supported();
+  return (p->precision == TACHIOM_PREC_BF16 || p->precision == TACHIOM_PREC_FP8) && topc_tc_supported();
+}
+static bool use_fp8(const tachiom_search_params *p) { return p->precision == TACHIOM_PREC_FP8 && topc_tc_supported(); }
+// the E4M3 repair window as a multiple of the rigorous bound (1: rigorous)
+constexpr float kFp8DefaultLambda = 0.1f;
+static float fp8_lambda(const tachiom_search_params *p) {
+  return p->rescore_margin > 0.f ? p->rescore_margin : kFp8DefaultLambda;
 }
 
 // plan_id >= 0 overrides the library's choices (all choices give the same results):
@@ -277,7 +287,7 @@ static int scan_kind(const tachiom_search_params *p) {
   const int forced = p->plan_id >= 0 ? (p->plan_id & 3) : SCAN_DEFAULT;
   if (!use_tc(p)) return SCAN_F32;
   if (forced == SCAN_F32) return SCAN_F32;
-  if (forced == SCAN_TC1 && p->kappa_c <= topc_tc1_max_kc()) return SCAN_TC1;
+  if (forced == SCAN_TC1 && p->kappa_c <= topc_tc1_max_kc() && !use_fp8(p)) return SCAN_TC1;
   return SCAN_TC2;
 }
 
@@ -318,10 +328,20 @@ static tachiom_status run_topc(Index *ix, Workspace *w, const tachiom_search_par
                              w->d_top_ids, w->d_top_s, w->d_flags, w->stream);
   }
   if (kind == SCAN_TC2) {
-    // group maxima from the tensor cores, then the exact FP32 top-kappa_c of the kept groups
-    if ((st = launch_quantize_rows(*ix, rows, w->d_rows_bf16, nrows, w->d_margin, w->stream))) return st;
-    if ((st = launch_topc_tc(*ix, w->d_rows_bf16, rows, nrows, kc, w->d_margin, w->d_gmax, w->d_glist, w->d_gcount,
-                             w->d_lossy, w->d_top_ids, w->d_top_s, w->d_flags, w->stream)))
+    // tensor-core sample pass, emission of the candidates above each row's threshold, exact FP32
+    // top-kappa_c of the candidates
+    const bool f8 = use_fp8(p);
+    if (f8) {
+      if ((st = launch_quantize_e4m3(*ix, rows, nrows, w->d_rows_f8, w->d_inv_sq, fp8_lambda(p), w->d_margin,
+                                     w->stream)))
+        return st;
+    } else if ((st = launch_quantize_rows(*ix, rows, w->d_rows_bf16, nrows, w->d_margin, w->stream))) {
+      return st;
+    }
+    const void *rq = f8 ? (const void *)w->d_rows_f8 : (const void *)w->d_rows_bf16;
+    if ((st = launch_topc_tc(*ix, rq, w->d_inv_sq, f8, rows, nrows, kc, w->d_margin,
+                             reinterpret_cast<float *>(w->d_gmax), w->d_glist, w->d_gcount, w->d_lossy, w->d_top_ids,
+                             w->d_top_s, w->d_flags, w->stream)))
       return st;
     return launch_topc_rescue(*ix, rows, nrows, kc, w->d_lossy, w->d_top_ids, w->d_top_s, w->stream);
   }
@@ -640,7 +660,31 @@ extern "C" tachiom_status tachiom_debug_tc_scores(tachiom_index *index, const fl
   n.kd = 1;
   if ((st = ws_reserve(ix, w, n))) return st;
   if ((st = launch_quantize_bf16(d_rows, w->d_rows_bf16, (int64_t)nrows * DIM, s))) return st;
-  return launch_topc_tc_raw(*ix, w->d_rows_bf16, nrows, d_out, w->d_flags, s);
+  return launch_topc_tc_raw(*ix, w->d_rows_bf16, nullptr, false, nrows, d_out, w->d_flags, s);
+}
+
+extern "C" tachiom_status tachiom_debug_tc_scores_fp8(tachiom_index *index, const float *d_rows, int32_t nrows,
+                                                      float *d_out, float *d_margins, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
+  if (!topc_tc_supported()) return fail(TACHIOM_ERR_INVALID, "no tensor-core step (a) on this device");
+  if (nrows < 0 || (nrows > 0 && (!d_rows || !d_out))) return fail(TACHIOM_ERR_INVALID, "bad arguments");
+  if (nrows == 0) return TACHIOM_OK;
+  DeviceGuard g(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w;
+  tachiom_status st;
+  if ((st = ws_get(ix, s, &w))) return st;
+  Need n;
+  n.nq = 1;
+  n.rows = nrows;
+  n.kc = 1;
+  n.kd = 1;
+  if ((st = ws_reserve(ix, w, n))) return st;
+  if ((st = launch_quantize_e4m3(*ix, d_rows, nrows, w->d_rows_f8, w->d_inv_sq, 1.f, w->d_margin, s))) return st;
+  if ((st = launch_topc_tc_raw(*ix, w->d_rows_f8, w->d_inv_sq, true, nrows, d_out, w->d_flags, s))) return st;
+  if (d_margins) TCUDA(cudaMemcpyAsync(d_margins, w->d_margin, (size_t)nrows * 4, cudaMemcpyDeviceToDevice, s));
+  return TACHIOM_OK;
 }
 
 extern "C" tachiom_status tachiom_debug_refine_scores(tachiom_index *index, const tachiom_search_params *params,
@@ -861,7 +905,7 @@ extern "C" tachiom_status tachiom_debug_topc_groups(tachiom_index *index, const 
   if (!ix || !params || !h_groups) return fail(TACHIOM_ERR_INVALID, "NULL argument");
   tachiom_status st;
   if ((st = check_params(params))) return st;
-  if (scan_kind(params) != SCAN_TC2) return fail(TACHIOM_ERR_INVALID, "not the group-selection path");
+  if (scan_kind(params) != SCAN_TC2) return fail(TACHIOM_ERR_INVALID, "not the candidate-emission path");
   if (nrows <= 0) return TACHIOM_OK;
   DeviceGuard g(ix->device);
   int32_t *ids = nullptr;

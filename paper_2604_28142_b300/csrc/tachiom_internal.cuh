@@ -89,6 +89,93 @@ __device__ __forceinline__ void warp_sort_desc(uint64_t *a, int n) {
     }
 }
 
+// The kappa-th largest of the n distinct keys a[0..n) (1 <= kappa <= n), to every thread:
+// a radix select over 11-bit digits from the top (bits 63..53, 52..42, ...); once the digit
+// holding the cut has at most 64 keys, one warp sorts those. The bins are scanned from the top
+// by the whole block (thread t owns a contiguous run of bins). Uses hist[2048], small[64],
+// wsum[32] and sh[8]; ends with a barrier.
+constexpr int KSEL_BITS = 11;
+__device__ __forceinline__ uint64_t block_kth_largest(const uint64_t *a, int n, int kappa, uint32_t *hist, uint64_t *small,
+                                   uint32_t *wsum, uint32_t *sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  uint64_t prefix = 0ull, mask = 0ull;
+  uint32_t need = (uint32_t)kappa;
+  for (int top = 64; top > 0; top -= KSEL_BITS) {
+    const int shift = max(0, top - KSEL_BITS), bits = top - shift, nbin = 1 << bits;
+    const uint64_t dmask = (uint64_t)(nbin - 1);
+    for (int i = tid; i < nbin; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+      const int i = i0 + tid;
+      int dg = -1;
+      if (i < n) {
+        const uint64_t k = a[i];
+        if ((k & mask) == prefix) dg = (int)((k >> shift) & dmask);
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, dg);
+      if (dg >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[dg], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    // thread t: bins [hi - w, hi), hi = nbin - t w, counted from the top
+    const int w = (nbin + blockDim.x - 1) / blockDim.x;
+    const int bhi = max(0, nbin - tid * w), blo = max(0, bhi - w);
+    uint32_t c = 0;
+    for (int d = blo; d < bhi; d++) c += hist[d];
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int u = 0; u < warp; u++) before += wsum[u];
+    (void)nw;
+    const uint32_t excl = before + inc - c;
+    inc += before;
+    if (c > 0 && excl < need && need <= inc) {
+      uint32_t cum = excl;
+      int d = bhi - 1;
+      for (; d > blo; d--) {
+        if (cum + hist[d] >= need) break;
+        cum += hist[d];
+      }
+      sh[0] = (uint32_t)d;
+      sh[1] = need - cum;
+      sh[2] = hist[d];
+      sh[3] = 0u;
+    }
+    __syncthreads();
+    prefix |= (uint64_t)sh[0] << shift;
+    mask |= dmask << shift;
+    need = sh[1];
+    const uint32_t inbin = sh[2];
+    if (inbin <= 64u) {
+      // gather the bin's keys and pick the need-th largest
+      for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int i = i0 + tid;
+        if (i < n && (a[i] & mask) == prefix) {
+          const uint32_t d = atomicAdd(&sh[3], 1u);
+          if (d < 64u) small[d] = a[i];
+        }
+      }
+      __syncthreads();
+      if (warp == 0) {
+        for (int i = (int)inbin + lane; i < 64; i += 32) small[i] = 0ull;
+        __syncwarp();
+        warp_sort_desc(small, 64);
+      }
+      __syncthreads();
+      const uint64_t r = small[need - 1];
+      __syncthreads();  // small, wsum and sh are free again when this returns
+      return r;
+    }
+    __syncthreads();  // sh and wsum are read by every thread before the next pass rewrites them
+  }
+  return prefix;  // not reached: distinct keys leave a single key in the last digit's bin
+}
+
 __host__ __device__ inline int next_pow2(int x) {
   int p = 1;
   while (p < x) p <<= 1;
@@ -107,6 +194,9 @@ struct Index {
   __nv_bfloat16 *cent_bf16 = nullptr;   // [C x 128] BF16 operand of the tensor-core path
   float cnorm_max = 0.f;                // max_j ||c_j|| (error bound of the BF16 path)
   float cerr_max = 0.f;                 // max_j ||bf16(c_j) - c_j|| (0 for a BF16-stored table)
+  uint8_t *cent_e4m3 = nullptr;         // [C x 128] E4M3 operand: c_j * 2^k_j rounded (power-of-two row scale)
+  float *cent_inv_sc = nullptr;         // [C] 2^-k_j
+  float cerr8_max = 0.f;                // max_j ||e4m3(c_j) 2^-k_j - c_j||
   int32_t *cent_type = nullptr;         // [C] or null
   int64_t *doc_off = nullptr;           // [D+1]
   int32_t *tok_cid = nullptr;           // [T]
@@ -141,12 +231,14 @@ struct Workspace {
   int32_t *d_meta = nullptr;           // qoff [B+1] | koff [B+1] | k [B] | ntok [B]
   float *d_rows_f32 = nullptr;         // staging of host queries (search_host)
   __nv_bfloat16 *d_rows_bf16 = nullptr;// [rows x 128]
+  uint8_t *d_rows_f8 = nullptr;        // [rows x 128] E4M3 rows (power-of-two row scale)
+  float *d_inv_sq = nullptr;           // [rows] their scales 2^-k
   uint64_t *d_split = nullptr;         // [rows x splits x capout] candidates of step (a)
-  uint32_t *d_gmax = nullptr;          // tensor-core path: group maxima of pass 1
+  uint32_t *d_gmax = nullptr;          // tensor-core path: the sample pass's per-stream top group maxima
   uint32_t *d_tau = nullptr;           // tensor-core path: per-row lower bound of the cut
   float *d_margin = nullptr;           // tensor-core path: per-row repair window (twice the error bound)
-  int32_t *d_glist = nullptr;          // tensor-core path: kept centroid groups per row
-  int32_t *d_gcount = nullptr;         // tensor-core path: number of kept groups per row
+  int32_t *d_glist = nullptr;          // tensor-core path: candidate centroids per row, then per-row thresholds
+  int32_t *d_gcount = nullptr;         // tensor-core path: number of candidates per row
   int32_t *d_lossy = nullptr;          // rows recomputed by the full FP32 scan
   int64_t cap_gmax = 0;
   int32_t *d_split_cnt = nullptr;      // [rows x splits]
@@ -211,15 +303,24 @@ tachiom_status launch_topc_merge(const Index &ix, const float *rows, int nrows, 
                                  uint32_t *flags, cudaStream_t s);
 tachiom_status launch_quantize_rows(const Index &ix, const float *rows, __nv_bfloat16 *out, int nrows,
                                     float *margins, cudaStream_t s);
-tachiom_status launch_topc_tc(const Index &ix, const __nv_bfloat16 *rows_bf16, const float *rows, int nrows, int kc,
-                              const float *margins, uint32_t *gmax, int32_t *glist, int32_t *gcount,
+// E4M3 rows with a power-of-two scale per row, and per row 2 lambda times the rigorous bound of
+// the E4M3 score error (the repair window of the E4M3 step (a))
+tachiom_status launch_quantize_e4m3(const Index &ix, const float *rows, int nrows, uint8_t *out, float *inv,
+                                    float lambda, float *margins, cudaStream_t s);
+// the index's E4M3 centroid copy (index load)
+tachiom_status launch_cent_e4m3(Index &ix, cudaStream_t s);
+// tensor-core step (a): rows_q BF16 (f8 false: group selection) or E4M3 with inv_sq (sample,
+// emission); gmax_tops, glist and gcount are scratch (topc_tc_gmax_elems, topc_tc_glist_elems,
+// rows); gcount receives the kept groups (BF16) or the candidates (E4M3) of every row
+tachiom_status launch_topc_tc(const Index &ix, const void *rows_q, const float *inv_sq, bool f8, const float *rows,
+                              int nrows, int kc, const float *margins, float *gmax_tops, int32_t *glist, int32_t *gcount,
                               int32_t *lossy_rows, int32_t *top_ids, float *top_s, uint32_t *flags, cudaStream_t s);
 tachiom_status launch_topc_rescue(const Index &ix, const float *rows, int nrows, int kc, const int32_t *lossy_rows,
                                   int32_t *top_ids, float *top_s, cudaStream_t s);
 size_t topc_tc_glist_elems(int rows);
 int topc_tc_supported();
-tachiom_status launch_topc_tc_raw(const Index &ix, const __nv_bfloat16 *rows, int nrows, float *out,
-                                  uint32_t *flags, cudaStream_t s);
+tachiom_status launch_topc_tc_raw(const Index &ix, const void *rows_q, const float *inv_sq, bool f8, int nrows,
+                                  float *out, uint32_t *flags, cudaStream_t s);
 tachiom_status launch_topc_tc1(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, const float *margins,
                                uint64_t *split_out, int32_t *split_cnt, uint32_t *flags, cudaStream_t s);
 int topc_tc1_capout();
