@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the k = 100 / 1000 and FP32 batched lines")
     ap.add_argument("--rescore-margin", type=float, default=0.0,
                     help="FP8 repair window of the timed path (0: the library's default)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-workload", default="msmarco-1M")
+    ap.add_argument("--serving-rates", type=float, nargs="*", default=[1000, 10000, 20000])
+    ap.add_argument("--serving-seconds", type=float, default=10.0)
     ap.add_argument("--fp8-windows", type=float, nargs="*", default=[0.1],
                     help="FP8 repair windows (multiples of the rigorous bound) timed in the sweep")
     a = ap.parse_args()
@@ -706,6 +710,11 @@ def run_ours(a):
         "rerank_only": rerank,
         "gpu_launches": _count_launches(prof),
     }
+    if not a.no_serving:
+        # the request loop on a resident index: free this workload's index first
+        torch.cuda.synchronize()
+        G.close()
+        line["serving"] = serving_record(a, T, torch, log)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -715,6 +724,33 @@ def _count_launches(prof):
     # kernels per launcher call: topc_tc 4 (GEMM, lim, collect, rescoring), topc_merge 2, the others 1
     per = {"topc_merge": 2, "topc_tc": 4}
     return sum(v[0] * per.get(k, 1) for k, v in prof.items())
+
+
+def serving_record(a, T, torch, log):
+    """Continuous batching under open-loop Poisson arrivals (8-32 tokens per request, k in {10, 100,
+    1000} with p = {0.7, 0.25, 0.05}) on the resident index of a.serving_workload: per rate the
+    achieved QPS and p50/p95/p99 latency from submission to results on the host, for the batched
+    tensor-core path and for the plain FP32 path one query per batch."""
+    from paper_2604_28142_b300 import serving
+    cfg = synth.CONFIGS[a.serving_workload]
+    ix = synth.load_or_make(a.serving_workload, device="cuda", log=log)
+    G = T.Index(ix, 0)
+    pool = serving.request_pool(synth, cfg)
+    out = {"workload": a.serving_workload, "seconds_per_rate": a.serving_seconds, "runs": []}
+    paths = [("fp32_one_query", T.PREC_FP32, 1)]
+    if T.tc_available():
+        paths = [("bf16_batched", T.PREC_BF16, 128)] + paths
+    for name, pr, mb in paths:
+        params = T.SearchParams(kappa_c=a.kc, kappa_d=0, precision=pr)
+        serving.run_rate(T, G, params, pool, 2000, 0.5, 99, 3, mb, 500)  # warm-up: scratch of every slot
+        rates = a.serving_rates if mb > 1 else [min(a.serving_rates)]
+        for r in rates:
+            res = serving.run_rate(T, G, params, pool, r, a.serving_seconds, int(r), 3, mb, 500)
+            res["path"] = name
+            out["runs"].append(res)
+            if log:
+                log(f"serving {name} {r}: {res['achieved_qps']:.0f} q/s p50 {res['p50_ms']:.2f} p99 {res['p99_ms']:.2f}")
+    return out
 
 
 def run_reference(a):

@@ -198,21 +198,33 @@ tachiom_status tachiom_refine(tachiom_index *index, const tachiom_search_params 
  * can synchronise the whole device). tachiom_refine takes its scratch from a
  * per-stream workspace that grows with cudaMalloc; this call instead uses one
  * static device array compiled into the library (2 MiB + 4 KiB, held on every
- * device that loads the library until the process exits) and calls no
- * cudaMalloc, cudaFree, pinned-host or heap allocation.
- *   Same arguments and results as tachiom_refine, with these limits:
- *   nq <= 64 and params->kappa_d given explicitly in 1..1024; larger sizes
- *   return TACHIOM_ERR_CAPACITY with a message, and nothing is launched.
+ * device that loads the library until the process exits) and one file-scope
+ * host array for its per-query metadata, and calls no cudaMalloc, cudaFree,
+ * pinned-host or heap allocation.
+ *   Same arguments as tachiom_refine. It always scores in FP32 (step (c) of
+ *   Sec. 2.2 with the lookup tables), whatever params->precision says, so its
+ *   results equal tachiom_refine's FP32 results; with TACHIOM_PREC_BF16 they
+ *   can differ from tachiom_refine's within the reduced-precision tolerance.
+ *   Limits: nq <= 64 and params->kappa_d given explicitly in 1..1024; larger
+ *   sizes return TACHIOM_ERR_CAPACITY with a message, and nothing is launched.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before capturing any stream. Every call shares the one array: calls whose
- *   work overlaps on the GPU (other streams, other host threads) race on it,
- *   so serialise them. Device-side range-check flags raised by this call are
- *   not reported by tachiom_stream_status. Asynchronous on `stream`.       */
+ *   (cudaGetSymbolAddress) with that device current. Every call shares the
+ *   two arrays: calls whose work overlaps on the GPU (other streams, other
+ *   host threads) race on them, so serialise them. Device-side range-check
+ *   flags raised by this call go to a status word in the static array, read
+ *   and cleared by tachiom_refine_noalloc_status (not by
+ *   tachiom_stream_status). Asynchronous on `stream`.                        */
 tachiom_status tachiom_refine_noalloc(tachiom_index *index, const tachiom_search_params *params,
                                       const float *d_queries, const int32_t *h_ntok,
                                       const int32_t *h_k, int32_t nq, const int32_t *d_cand_ids,
                                       int32_t *d_out_ids, float *d_out_scores, void *stream);
+
+/* Synchronise `stream`, then return and clear the TACHIOM_FLAG_* bits that
+ * tachiom_refine_noalloc calls raised on the index's device (a candidate id
+ * out of [0, n_docs) gives TACHIOM_FLAG_BAD_INPUT and is scored 0). Copies
+ * into the caller's variable and clears the word with cudaMemcpyAsync and
+ * cudaMemsetAsync; allocates nothing. Blocking.                              */
+tachiom_status tachiom_refine_noalloc_status(tachiom_index *index, void *stream, uint32_t *h_flags);
 
 /* ---- continuous-batching request loop ----
  * A server owns n_slots CUDA streams. Requests (one query each: host fp32
@@ -335,6 +347,15 @@ tachiom_status tachiom_debug_refine_scores(tachiom_index *index, const tachiom_s
  * each row. TACHIOM_ERR_INVALID when the device has no tensor-core path.     */
 tachiom_status tachiom_debug_tc_scores_fp8(tachiom_index *index, const float *d_rows, int32_t nrows,
                                            float *d_out, float *d_margins, void *stream);
+
+/* Diagnostics of the bounded waits of the tensor-core kernels: launches one CTA
+ * of the step (a) tensor-core pass whose TMA producer issues no copy and whose
+ * mbarrier waits give up after timeout_us (1..2e6) microseconds instead of the
+ * usual 2 s. The MMA issuer's first wait runs out, so the kernel raises
+ * TACHIOM_FLAG_TIMEOUT on `stream`, every role leaves its loop, TMEM is freed
+ * and the kernel returns; read the flag with tachiom_stream_status. The
+ * device stays usable. Asynchronous.                                         */
+tachiom_status tachiom_debug_wait_timeout(tachiom_index *index, int32_t timeout_us, void *stream);
 
 /* Diagnostics of the tensor-core step (a): runs it on nrows device rows on the
  * legacy default stream and copies, per row, the number of candidate centroids

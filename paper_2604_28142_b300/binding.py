@@ -166,9 +166,11 @@ def lib():
         "tachiom_gather": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P, P, P], ct.c_int),
         "tachiom_refine": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
         "tachiom_refine_noalloc": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
+        "tachiom_refine_noalloc_status": ([P, P, U32p], ct.c_int),
         "tachiom_stream_status": ([P, P, U32p], ct.c_int),
         "tachiom_debug_tc_scores": ([P, P, I32, P, P], ct.c_int),
         "tachiom_debug_tc_scores_fp8": ([P, P, I32, P, P, P], ct.c_int),
+        "tachiom_debug_wait_timeout": ([P, I32, P], ct.c_int),
         "tachiom_tc_available": ([], ct.c_int),
         "tachiom_debug_topc_groups": ([P, ct.POINTER(SearchParams), P, I32, P], ct.c_int),
         "tachiom_debug_refine_scores": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P, P], ct.c_int),
@@ -315,6 +317,9 @@ class Index:
 
     def debug_tc_scores(self, rows, out, stream=None):
         _check(lib().tachiom_debug_tc_scores(self.h, _dp(rows), int(rows.shape[0]), _dp(out), _stream(stream)))
+
+    def debug_wait_timeout(self, timeout_us, stream=None):
+        _check(lib().tachiom_debug_wait_timeout(self.h, int(timeout_us), _stream(stream)))
 
     def debug_tc_scores_fp8(self, rows, out, margins=None, stream=None):
         _check(lib().tachiom_debug_tc_scores_fp8(self.h, _dp(rows), int(rows.shape[0]), _dp(out),

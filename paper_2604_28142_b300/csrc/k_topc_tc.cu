@@ -123,6 +123,8 @@ struct TcArgs {
   int32_t *ecnt;         // MODE_EMIT: [R][splits] their counts (may exceed scap: overflow)
   int scap;
   float *raw;            // MODE_RAW: [R][C]
+  uint64_t wait_ns;      // limit of every mbarrier wait (0: TIMEOUT_NS)
+  int withhold;          // diagnostics: the producer issues no copy, so the first wait runs out
   uint32_t *flags;
 };
 
@@ -183,7 +185,7 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
-    if (lane == 0 && nt > 0) {
+    if (lane == 0 && nt > 0 && !A.withhold) {
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
       mbar_expect_tx(&ctl->bfull, G::B_BYTES);
@@ -192,7 +194,7 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       int issued = 0;
       for (int it = 0; it < nt; it++) {
         const int s = it % G::STAGES;
-        if (it >= G::STAGES && !mbar_wait(&ctl->empty[s], ((it / G::STAGES) & 1) ^ 1, abort, A.flags)) break;
+        if (it >= G::STAGES && !mbar_wait(&ctl->empty[s], ((it / G::STAGES) & 1) ^ 1, abort, A.flags, A.wait_ns)) break;
         unsigned char *a = As + s * G::A_STAGE;
         mbar_expect_tx(&ctl->full[s], G::A_STAGE);
 #pragma unroll
@@ -201,19 +203,19 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         issued = it + 1;
       }
       // drain: every copy this warp issued has landed before the CTA may exit
-      mbar_drain(&ctl->bfull, 0);
+      mbar_drain(&ctl->bfull, 0, A.wait_ns);
       for (int it = max(0, issued - G::STAGES); it < issued; it++)
-        mbar_drain(&ctl->full[it % G::STAGES], (it / G::STAGES) & 1);
+        mbar_drain(&ctl->full[it % G::STAGES], (it / G::STAGES) & 1, A.wait_ns);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0 && nt > 0) {
-      bool ok = mbar_wait(&ctl->bfull, 0, abort, A.flags);
+      bool ok = mbar_wait(&ctl->bfull, 0, abort, A.flags, A.wait_ns);
       const uint32_t b_base = smem_u32(Bs);
       for (int it = 0; ok && it < nt; it++) {
         const int s = it % G::STAGES, buf = it & 1;
-        if (!mbar_wait(&ctl->full[s], (it / G::STAGES) & 1, abort, A.flags)) break;
-        if (it >= 2 && !mbar_wait(&ctl->tempty[buf], ((it >> 1) - 1) & 1, abort, A.flags)) break;
+        if (!mbar_wait(&ctl->full[s], (it / G::STAGES) & 1, abort, A.flags, A.wait_ns)) break;
+        if (it >= 2 && !mbar_wait(&ctl->tempty[buf], ((it >> 1) - 1) & 1, abort, A.flags, A.wait_ns)) break;
         fence_after();
         const uint32_t a_base = smem_u32(As + s * G::A_STAGE);
 #pragma unroll
@@ -233,7 +235,7 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       }
       // drain: all MMAs issued by this thread are complete
       mma_commit(&ctl->drain);
-      mbar_drain(&ctl->drain, 0);
+      mbar_drain(&ctl->drain, 0, A.wait_ns);
     }
   } else {
     // ---------------- epilogue ----------------
@@ -266,7 +268,7 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const int buf = it & 1;
       // one lane waits, the whole warp follows its verdict (the TMEM loads below are warp-aligned)
       int ok = 0;
-      if (lane == 0) ok = mbar_wait(&ctl->tfull[buf], (it >> 1) & 1, abort, A.flags) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(&ctl->tfull[buf], (it >> 1) & 1, abort, A.flags, A.wait_ns) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       __syncwarp();
@@ -951,6 +953,29 @@ tachiom_status launch_topc_tc(const Index &ix, const void *rows_q, const float *
   }
   TLAUNCH();
   return TACHIOM_OK;
+}
+
+// Diagnostics of the bounded waits: one CTA of the BF16 sample pass whose producer issues no
+// copy, every mbarrier wait limited to wait_ns. The MMA warp's first wait runs out: it raises
+// TACHIOM_FLAG_TIMEOUT and the abort word, every role leaves its loop, the drains end within
+// the same limit, TMEM is freed and the kernel returns. rows_q: any BF16 [>= 256 x 128] buffer
+// (nothing is read from it).
+tachiom_status launch_topc_tc_wait_test(const Index &ix, const void *rows_q, uint64_t wait_ns, float *tops,
+                                        uint32_t *flags, cudaStream_t s) {
+  using namespace tc;
+  CUtensorMap mA, mB;
+  tachiom_status st;
+  if ((st = tc_maps(ix, rows_q, BN, false, &mA, &mB))) return st;
+  TcArgs a{};
+  a.C = ix.C;
+  a.R = BN;
+  a.ntiles = (int)((ix.C + BM - 1) / BM);
+  a.tstride = 1;
+  a.tops = tops;
+  a.wait_ns = wait_ns;
+  a.withhold = 1;
+  a.flags = flags;
+  return tc_launch<MODE_SAMPLE, false>(mA, mB, a, 1, 1, s);
 }
 
 // raw approximate tensor-core scores of the rows against every centroid (BF16 x BF16 or

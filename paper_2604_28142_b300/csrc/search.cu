@@ -663,6 +663,27 @@ extern "C" tachiom_status tachiom_debug_tc_scores(tachiom_index *index, const fl
   return launch_topc_tc_raw(*ix, w->d_rows_bf16, nullptr, false, nrows, d_out, w->d_flags, s);
 }
 
+extern "C" tachiom_status tachiom_debug_wait_timeout(tachiom_index *index, int32_t timeout_us, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
+  if (!topc_tc_supported()) return fail(TACHIOM_ERR_INVALID, "no tensor-core step (a) on this device");
+  if (timeout_us < 1 || timeout_us > 2000000) return fail(TACHIOM_ERR_INVALID, "timeout_us out of [1, 2e6]");
+  DeviceGuard g(ix->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w;
+  tachiom_status st;
+  if ((st = ws_get(ix, s, &w))) return st;
+  Need n;
+  n.nq = 1;
+  n.rows = 256;
+  n.kc = 1;
+  n.kd = 1;
+  n.gmax = (int64_t)topc_tc_gmax_elems(*ix, 256);
+  if ((st = ws_reserve(ix, w, n))) return st;
+  return launch_topc_tc_wait_test(*ix, w->d_rows_bf16, (uint64_t)timeout_us * 1000ull,
+                                  reinterpret_cast<float *>(w->d_gmax), w->d_flags, s);
+}
+
 extern "C" tachiom_status tachiom_debug_tc_scores_fp8(tachiom_index *index, const float *d_rows, int32_t nrows,
                                                       float *d_out, float *d_margins, void *stream) {
   Index *ix = as_index(index);

@@ -321,6 +321,9 @@ size_t topc_tc_glist_elems(int rows);
 int topc_tc_supported();
 tachiom_status launch_topc_tc_raw(const Index &ix, const void *rows_q, const float *inv_sq, bool f8, int nrows,
                                   float *out, uint32_t *flags, cudaStream_t s);
+// diagnostics: a tensor-core pass whose producer withholds every copy, waits limited to wait_ns
+tachiom_status launch_topc_tc_wait_test(const Index &ix, const void *rows_q, uint64_t wait_ns, float *tops,
+                                        uint32_t *flags, cudaStream_t s);
 tachiom_status launch_topc_tc1(const Index &ix, const __nv_bfloat16 *rows, int nrows, int kc, const float *margins,
                                uint64_t *split_out, int32_t *split_cnt, uint32_t *flags, cudaStream_t s);
 int topc_tc1_capout();

@@ -39,8 +39,10 @@ __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false when the CTA is aborting or the time limit passed
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort, uint32_t *flags) {
+// bounded wait: false when the CTA is aborting or the time limit (limit_ns, 0: TIMEOUT_NS) passed
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort, uint32_t *flags,
+                                          uint64_t limit_ns = 0) {
+  const uint64_t lim = limit_ns ? limit_ns : TIMEOUT_NS;
   uint64_t t0 = 0;
   for (uint32_t i = 0;; i++) {
     if (mbar_test(b, parity)) return true;
@@ -48,7 +50,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile
       if (*abort) return false;
       uint64_t t = gtimer();
       if (i == 0) t0 = t;
-      else if (t - t0 > TIMEOUT_NS) {
+      else if (t - t0 > lim) {
         *abort = 1;
         atomicOr(flags, TACHIOM_FLAG_TIMEOUT);
         return false;
@@ -57,10 +59,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile
   }
 }
 // wait with a bound and no abort check (drain at exit)
-__device__ __forceinline__ void mbar_drain(uint64_t *b, uint32_t parity) {
+__device__ __forceinline__ void mbar_drain(uint64_t *b, uint32_t parity, uint64_t limit_ns = 0) {
+  const uint64_t lim = limit_ns ? limit_ns : TIMEOUT_NS;
   uint64_t t0 = gtimer();
   while (!mbar_test(b, parity))
-    if (gtimer() - t0 > TIMEOUT_NS) break;
+    if (gtimer() - t0 > lim) break;
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {

@@ -48,9 +48,25 @@ def run_rate(T, G, params, pool, rate, seconds, seed, n_slots, max_batch, max_wa
     st = srv.stats()
     srv.close()
     lats = np.array(lats)
+    ks = np.array([k for _, k in ids])
+    by_k = {}
+    for kv in sorted(set(ks.tolist())):
+        m = ks == kv
+        by_k[str(kv)] = {"requests": int(m.sum()), "p50_ms": float(np.percentile(lats[m], 50)),
+                         "p99_ms": float(np.percentile(lats[m], 99))}
     return {"offered_qps": rate, "achieved_qps": n / wall, "requests": n,
             "p50_ms": float(np.percentile(lats, 50)), "p95_ms": float(np.percentile(lats, 95)),
-            "p99_ms": float(np.percentile(lats, 99)), "batches": st["batches"], "mean_batch": st["mean_batch"]}
+            "p99_ms": float(np.percentile(lats, 99)), "batches": st["batches"], "mean_batch": st["mean_batch"],
+            "by_k": by_k}
+
+
+def request_pool(synth, cfg, n=4096, seed_offset=3):
+    """Seeded requests: 8..32 tokens (uniform), k in {10, 100, 1000} with p = {0.7, 0.25, 0.05}."""
+    q = synth.make_queries(cfg, n_queries=n, seed=cfg.query_seed + seed_offset, ntok_min=8, ntok_max=32)
+    rng = np.random.default_rng(4)
+    ks = rng.choice([10, 100, 1000], size=n, p=[0.7, 0.25, 0.05])
+    off = np.concatenate([[0], np.cumsum(q["ntok"])])
+    return [(q["queries"][off[u]:off[u + 1]], int(ks[u])) for u in range(n)]
 
 
 def main():
@@ -74,11 +90,7 @@ def main():
     ix = synth.load_or_make(a.workload, device="cuda")
     cfg = synth.CONFIGS[a.workload]
     G = T.Index(ix, 0)
-    q = synth.make_queries(cfg, n_queries=4096, seed=cfg.query_seed + 3, ntok_min=8, ntok_max=32)
-    rng = np.random.default_rng(4)
-    ks = rng.choice([10, 100, 1000], size=4096, p=[0.7, 0.25, 0.05])
-    off = np.concatenate([[0], np.cumsum(q["ntok"])])
-    pool = [(q["queries"][off[u]:off[u + 1]], int(ks[u])) for u in range(4096)]
+    pool = request_pool(synth, cfg)
     out = []
     for prec in a.precision:
         if prec == "bf16" and not T.tc_available():
