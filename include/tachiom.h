@@ -396,9 +396,9 @@ tachiom_status tachiom_tac_allot(const int64_t *n, const double *s, int32_t n_ty
  * centroids out with tachiom_tac_allot (same parameters), then runs Lloyd's
  * kappa_j-means on every type on its own for `iters` rounds from its points at
  * positions floor((r + 1/2) n_j / kappa_j), r < kappa_j, and assigns every
- * vector once more. Squared L2 in FP32, ties to the lower centroid; means in
- * FP64 (fixed summation order, so runs repeat bit for bit) rounded to FP32; a
- * centroid left without members keeps its place.
+ * vector once more. Squared L2 in FP32, ties to the lower centroid; means and
+ * spreads in compensated FP32 (fixed summation order, so runs repeat bit for
+ * bit); a centroid left without members keeps its place.
  *   d_vectors: device fp32 [n_vectors x 128], 16-byte aligned;
  *   d_types: device int32 [n_vectors], each in [0, n_types);
  *   h_kappa: host int32 [n_types] output; h_spread: host float64 [n_types]
@@ -434,8 +434,8 @@ tachiom_status tachiom_pq_encode(const float *d_vectors, const float *d_centroid
  * floor((s + 1/2) n_vectors / sample), split into pq_m subspaces, each
  * clustered into 256 codewords by `iters` Lloyd rounds from the sample points
  * at positions floor((j + 1/2) sample / 256) (squared L2 in FP32, ties to the
- * lower codeword, FP64 means in a fixed order rounded to FP32, an empty
- * codeword keeps its place). d_codebooks: device fp32 [pq_m x 256 x
+ * lower codeword, compensated FP32 means in a fixed order, an empty codeword
+ * keeps its place). d_codebooks: device fp32 [pq_m x 256 x
  * 128 / pq_m] output, the layout tachiom_pq_encode and the index take.
  * 256 <= sample <= n_vectors. Allocates its scratch and blocks until done on
  * `stream`; TACHIOM_ERR_INVALID on a bad argument, TACHIOM_ERR_OOM. */

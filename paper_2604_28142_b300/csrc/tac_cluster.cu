@@ -77,64 +77,85 @@ __global__ void k_tac_bounds(const int32_t *__restrict__ keys, int64_t n, int64_
   }
 }
 
-// FP64 mean of the vectors X[order[mem[e]]] for e in [b, e1) (mem may be null: identity),
-// fixed order; the CTA's TC_WARPS warps end with the mean in m[128]
+// Compensated FP32 addition (Neumaier): s + c carries the sum of the added values with an error of a
+// few units in the last place of the sum, independent of how many values were added.
+__device__ __forceinline__ void kadd(float &s, float &c, float x) {
+  const float t = s + x;
+  c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+  s = t;
+}
+
+// Mean of the vectors X[order[mem[e]]] for e in [b, e1) (mem may be null: identity) in compensated
+// FP32, in a fixed order (warp w adds the members w, w + TC_WARPS, ...; the warps' sums are added in
+// warp order), so a run repeats bit for bit; the CTA's TC_WARPS warps end with the mean in m[128]
 __device__ void tac_segment_mean(const float *__restrict__ X, const int32_t *__restrict__ order,
-                                 const int32_t *__restrict__ mem, int64_t b, int64_t e1, double (*red)[128],
-                                 double *m) {
+                                 const int32_t *__restrict__ mem, int64_t b, int64_t e1, float2 (*red)[128],
+                                 float *m) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
   for (int64_t q = b + warp; q < e1; q += TC_WARPS) {
     const int64_t p = mem ? (int64_t)mem[q] : q;
     const float4 v = *reinterpret_cast<const float4 *>(X + (int64_t)order[p] * DIM + 4 * lane);
-    a0 += (double)v.x;
-    a1 += (double)v.y;
-    a2 += (double)v.z;
-    a3 += (double)v.w;
+    kadd(s0, c0, v.x);
+    kadd(s1, c1, v.y);
+    kadd(s2, c2, v.z);
+    kadd(s3, c3, v.w);
   }
-  red[warp][4 * lane] = a0;
-  red[warp][4 * lane + 1] = a1;
-  red[warp][4 * lane + 2] = a2;
-  red[warp][4 * lane + 3] = a3;
+  red[warp][4 * lane] = make_float2(s0, c0);
+  red[warp][4 * lane + 1] = make_float2(s1, c1);
+  red[warp][4 * lane + 2] = make_float2(s2, c2);
+  red[warp][4 * lane + 3] = make_float2(s3, c3);
   __syncthreads();
   if (threadIdx.x < DIM) {
-    double t = 0.0;
-    for (int w = 0; w < TC_WARPS; w++) t += red[w][threadIdx.x];
-    m[threadIdx.x] = t / (double)(e1 - b);
+    float t = 0.f, tc = 0.f;
+    for (int w = 0; w < TC_WARPS; w++) {
+      kadd(t, tc, red[w][threadIdx.x].x);
+      kadd(t, tc, red[w][threadIdx.x].y);
+    }
+    m[threadIdx.x] = (t + tc) / (float)(e1 - b);
   }
   __syncthreads();
 }
 
-// s_j = (1 / n_j) sum ||x - mean_j||^2 over the type's points (0 for an absent type)
+// s_j = (1 / n_j) sum ||x - mean_j||^2 over the type's points (0 for an absent type), compensated FP32
+// in a fixed order
 __global__ void __launch_bounds__(TC_WARPS * 32)
 k_tac_type_spread(const float *__restrict__ X, const int32_t *__restrict__ order, const int64_t *__restrict__ off,
-                  double *__restrict__ s) {
-  __shared__ double red[TC_WARPS][128];
-  __shared__ double mean[128];
-  __shared__ double wacc[TC_WARPS];
+                  float *__restrict__ s) {
+  __shared__ float2 red[TC_WARPS][128];
+  __shared__ float mean[128];
+  __shared__ float2 wacc[TC_WARPS];
   const int j = blockIdx.x;
   const int64_t b = off[j], e1 = off[j + 1];
   if (e1 == b) {
-    if (threadIdx.x == 0) s[j] = 0.0;
+    if (threadIdx.x == 0) s[j] = 0.f;
     return;
   }
   tac_segment_mean(X, order, nullptr, b, e1, red, mean);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double m0 = mean[4 * lane], m1 = mean[4 * lane + 1], m2 = mean[4 * lane + 2], m3 = mean[4 * lane + 3];
-  double q = 0.0;
+  const float m0 = mean[4 * lane], m1 = mean[4 * lane + 1], m2 = mean[4 * lane + 2], m3 = mean[4 * lane + 3];
+  float q = 0.f, qc = 0.f;
   for (int64_t p = b + warp; p < e1; p += TC_WARPS) {
     const float4 v = *reinterpret_cast<const float4 *>(X + (int64_t)order[p] * DIM + 4 * lane);
-    const double d0 = (double)v.x - m0, d1 = (double)v.y - m1, d2 = (double)v.z - m2, d3 = (double)v.w - m3;
-    q += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+    const float d0 = v.x - m0, d1 = v.y - m1, d2 = v.z - m2, d3 = v.w - m3;
+    kadd(q, qc, fmaf(d3, d3, fmaf(d2, d2, fmaf(d1, d1, d0 * d0))));
   }
+  // the lanes' compensated sums, added by a fixed butterfly
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-  if (lane == 0) wacc[warp] = q;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oq = __shfl_xor_sync(0xffffffffu, q, o), oc = __shfl_xor_sync(0xffffffffu, qc, o);
+    kadd(q, qc, oq);
+    qc += oc;
+  }
+  if (lane == 0) wacc[warp] = make_float2(q, qc);
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < TC_WARPS; w++) t += wacc[w];
-    s[j] = t / (double)(e1 - b);
+    float t = 0.f, tc = 0.f;
+    for (int w = 0; w < TC_WARPS; w++) {
+      kadd(t, tc, wacc[w].x);
+      kadd(t, tc, wacc[w].y);
+    }
+    s[j] = (t + tc) / (float)(e1 - b);
   }
 }
 
@@ -148,7 +169,7 @@ __global__ void k_tac_init(const float *__restrict__ X, const int32_t *__restric
   for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < budget; g += nw) {
     const int32_t j = ctype[g];
     const int64_t r = g - cbase[j], nj = off[j + 1] - off[j];
-    const int64_t pos = (int64_t)floor(((double)r + 0.5) * (double)nj / (double)kappa[j]);
+    const int64_t pos = ((2 * r + 1) * nj) / (2 * (int64_t)kappa[j]);  // floor((r + 1/2) n_j / kappa_j), exact
     const float4 v = *reinterpret_cast<const float4 *>(X + (int64_t)order[off[j] + pos] * DIM + 4 * lane);
     *reinterpret_cast<float4 *>(C + g * DIM + 4 * lane) = v;
   }
@@ -183,17 +204,17 @@ __global__ void k_tac_assign(const float *__restrict__ X, const int32_t *__restr
   }
 }
 
-// centroid g (one CTA each) to the FP64 mean of its members, rounded to FP32; no member: unchanged
+// centroid g (one CTA each) to the compensated FP32 mean of its members; no member: unchanged
 __global__ void __launch_bounds__(TC_WARPS * 32)
 k_tac_means(const float *__restrict__ X, const int32_t *__restrict__ order, const int32_t *__restrict__ mem,
             const int64_t *__restrict__ moff, float *__restrict__ C) {
-  __shared__ double red[TC_WARPS][128];
-  __shared__ double mean[128];
+  __shared__ float2 red[TC_WARPS][128];
+  __shared__ float mean[128];
   const int64_t g = blockIdx.x;
   const int64_t b = moff[g], e1 = moff[g + 1];
   if (e1 == b) return;
   tac_segment_mean(X, order, mem, b, e1, red, mean);
-  if (threadIdx.x < DIM) C[g * DIM + threadIdx.x] = (float)mean[threadIdx.x];
+  if (threadIdx.x < DIM) C[g * DIM + threadIdx.x] = mean[threadIdx.x];
 }
 
 __global__ void k_tac_scatter(const int32_t *__restrict__ lab, const int32_t *__restrict__ order, int64_t n,
@@ -238,7 +259,7 @@ extern "C" tachiom_status tachiom_tac_cluster(const float *d_vectors, const int3
   } while (0)
   int32_t *idx, *stype, *order, *lab, *labs, *mem, *kap_d;
   int64_t *off, *cbase_d, *moff;
-  double *spr;
+  float *spr;
   uint32_t *bad;
   TTRY(B.alloc(&idx, (size_t)N));
   TTRY(B.alloc(&stype, (size_t)N));
@@ -270,13 +291,15 @@ extern "C" tachiom_status tachiom_tac_cluster(const float *d_vectors, const int3
   k_tac_type_spread<<<n_types, TC_WARPS * 32, 0, s>>>(d_vectors, order, off, spr);
   TLAUNCH();
   std::vector<int64_t> hoff((size_t)n_types + 1);
+  std::vector<float> hsf((size_t)n_types);
   std::vector<double> hs((size_t)n_types);
   uint32_t hbad = 0;
   TCUDA(cudaMemcpyAsync(hoff.data(), off, hoff.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  TCUDA(cudaMemcpyAsync(hs.data(), spr, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TCUDA(cudaMemcpyAsync(hsf.data(), spr, hsf.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
   TCUDA(cudaMemcpyAsync(&hbad, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   TCUDA(cudaStreamSynchronize(s));
   if (hbad) return fail(TACHIOM_ERR_INVALID, "tac_cluster: a token type is outside [0, n_types)");
+  for (int32_t j = 0; j < n_types; j++) hs[j] = (double)hsf[j];
   if (h_spread) std::copy(hs.begin(), hs.end(), h_spread);
 
   // 2. the allotment (host), the centroid numbering
@@ -412,7 +435,7 @@ __global__ void k_pq_sample(const float *__restrict__ X, const float *__restrict
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < S; r += nw) {
-    const int64_t i = (int64_t)floor(((double)r + 0.5) * (double)n / (double)S);
+    const int64_t i = ((2 * (int64_t)r + 1) * n) / (2 * (int64_t)S);  // floor((r + 1/2) n / S), exact
     float rho;
     const float4 v = pq_residual(X, C, labels[i], i, lane, rho);
     const float4 u = rho > 0.f ? make_float4(v.x / rho, v.y / rho, v.z / rho, v.w / rho) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -426,7 +449,7 @@ __global__ void k_pq_init(const float *__restrict__ U, int32_t S, float *__restr
   constexpr int DS = DIM / M;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < M * 256 * DS; x += gridDim.x * blockDim.x) {
     const int m = x / (256 * DS), j = (x / DS) % 256, u = x % DS;
-    const int64_t p = (int64_t)floor(((double)j + 0.5) * (double)S / 256.0);
+    const int64_t p = ((2 * (int64_t)j + 1) * S) / 512;  // floor((j + 1/2) S / 256), exact
     books[x] = U[p * DIM + m * DS + u];
   }
 }
@@ -454,9 +477,9 @@ k_pq_assign_unit(const float *__restrict__ U, int32_t S, const float *__restrict
   }
 }
 
-// codeword k = m * 256 + j (one warp each) to the FP64 mean of its members' sub-vectors m, rounded
-// to FP32 (lane l sums members l, l + 32, ...; the lanes are added by a fixed butterfly); a
-// codeword without members keeps its place
+// codeword k = m * 256 + j (one warp each) to the compensated FP32 mean of its members' sub-vectors m
+// (lane l sums members l, l + 32, ...; the lanes are added by a fixed butterfly); a codeword without
+// members keeps its place
 template <int M>
 __global__ void k_pq_means(const float *__restrict__ U, const int32_t *__restrict__ vals,
                            const int64_t *__restrict__ off, float *__restrict__ books) {
@@ -467,20 +490,24 @@ __global__ void k_pq_means(const float *__restrict__ U, const int32_t *__restric
     const int64_t b = off[k], e1 = off[k + 1];
     if (b == e1) continue;
     const int m = (int)(k / 256);
-    double acc[DS];
+    float acc[DS], cmp[DS];
 #pragma unroll
-    for (int u = 0; u < DS; u++) acc[u] = 0.0;
+    for (int u = 0; u < DS; u++) acc[u] = cmp[u] = 0.f;
     for (int64_t q = b + lane; q < e1; q += 32) {
       const float *src = U + (int64_t)vals[q] * DIM + m * DS;
 #pragma unroll
-      for (int u = 0; u < DS; u++) acc[u] += (double)src[u];
+      for (int u = 0; u < DS; u++) kadd(acc[u], cmp[u], src[u]);
     }
 #pragma unroll
     for (int u = 0; u < DS; u++) {
-      double t = acc[u];
+      float t = acc[u], tc = cmp[u];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) books[k * DS + u] = (float)(t / (double)(e1 - b));
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ot = __shfl_xor_sync(0xffffffffu, t, o), oc = __shfl_xor_sync(0xffffffffu, tc, o);
+        kadd(t, tc, ot);
+        tc += oc;
+      }
+      if (lane == 0) books[k * DS + u] = (t + tc) / (float)(e1 - b);
     }
   }
 }

@@ -50,7 +50,7 @@ def test_tac_cluster_matches_oracle():
     budget = tail + (sum(min(PARAMS["eps"], c) for c in lo_hi) + sum(lo_hi)) // 2
     kappa, spread, cents, ctype, labels = _run(T, v, t, n_types, budget, iters, **PARAMS)
     torch.cuda.synchronize()
-    assert np.allclose(spread, s_or, rtol=1e-12, atol=0)
+    assert np.allclose(spread, s_or, rtol=1e-6, atol=0)  # compensated FP32 against FP64
     ok, oc, oct_, olab = O.cluster(v.astype(np.float64).tolist(), t.tolist(), n_types, budget,
                                    iters=iters, **PARAMS)
     assert kappa.tolist() == ok
@@ -160,8 +160,6 @@ def _pq_train_case(M, seed):
     return x.astype(np.float32), cents.astype(np.float32), lab.astype(np.int32), cid
 
 
-@pytest.mark.skipif(__import__("os").environ.get("TACHIOM_TEST_PQ_TRAIN_GPU") != "1",
-                    reason="GPU codebook training tests are opt-in (TACHIOM_TEST_PQ_TRAIN_GPU=1) until run on a GPU")
 @pytest.mark.parametrize("M", [8, 16, 32])
 def test_pq_train_closed_form(M):
     _cuda()
@@ -188,8 +186,6 @@ def test_pq_train_closed_form(M):
     assert torch.equal(T.pq_train(dx, dc, dl, M, sample=512, iters=3), books)
 
 
-@pytest.mark.skipif(__import__("os").environ.get("TACHIOM_TEST_PQ_TRAIN_GPU") != "1",
-                    reason="index building uses the GPU codebook training, opt-in until run on a GPU")
 @pytest.mark.parametrize("centroid_dtype", ["f32", "bf16"])
 def test_index_built_on_gpu_searches_like_the_oracle(centroid_dtype):
     # an index built from raw vectors by the library's kernels, searched in both precisions, gives
