@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--rescore-margin", type=float, default=0.0,
                     help="FP8 repair window of the timed path (0: the library's default)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--tune-budgets", action="store_true",
+                    help="pick kappa_c and kappa_d with the library's autotuner (default on lotte-2.8M)")
+    ap.add_argument("--tune-queries", type=int, default=64)
     ap.add_argument("--serving-workload", default="msmarco-1M")
     ap.add_argument("--serving-rates", type=float, nargs="*", default=[1000, 10000, 20000])
     ap.add_argument("--serving-seconds", type=float, default=10.0)
@@ -73,6 +76,8 @@ def parse():
     a.ntok_min, a.ntok_max = shape[1], shape[2]
     if a.oracle_queries <= 0:
         a.oracle_queries = min(16, host_cores())
+    if a.workload == "lotte-2.8M":
+        a.tune_budgets = True
     return a
 
 
@@ -488,6 +493,23 @@ def run_ours(a):
         prec = T.PREC_BF16 if T.tc_available() else T.PREC_FP32
     else:
         prec = {"bf16": T.PREC_BF16, "fp8": T.PREC_FP8, "fp32": T.PREC_FP32}[a.precision]
+    budget_tune = None
+    if a.tune_budgets:
+        # candidate budgets from the paper's grid, by cost subject to recall@10 >= 0.95 against the
+        # exhaustive top-10 (every document refined) on a tuning split of queries not in the timed ones
+        tq = synth.make_queries(cfg, n_queries=a.tune_queries, seed=cfg.query_seed + 77, ntok_min=a.ntok_min,
+                                ntok_max=a.ntok_max)
+        tdq = torch.from_numpy(tq["queries"]).cuda()
+        t0 = time.time()
+        (kc_t, kd_t), rec_t, ms_t, table = G.autotune_budgets(prec, tdq, tq["ntok"], 10, [15, 20, 40, 80, 120],
+                                                              [250, 500, 1000, 2000, 4000], min_recall=0.95)
+        a.kc, a.kd = int(kc_t), int(kd_t)
+        budget_tune = {"kappa_c": a.kc, "kappa_d": a.kd, "recall_at_10_vs_exhaustive": rec_t,
+                       "tuning_ms_per_batch": ms_t, "tuning_queries": a.tune_queries, "target_recall": 0.95,
+                       "grid": [[int(r[0]), int(r[1]), float(r[2]), float(r[3])] for r in table.reshape(-1, 4)],
+                       "tuner_seconds": time.time() - t0}
+        if log:
+            log(f"budgets: kappa_c {a.kc} kappa_d {a.kd} recall {rec_t:.3f} ({time.time() - t0:.1f} s)")
     params = T.SearchParams(kappa_c=a.kc, kappa_d=a.kd, precision=prec, rescore_margin=a.rescore_margin)
     nb = a.warmup + a.steps
     q = synth.make_queries(cfg, n_queries=nb * a.batch, seed=rank_query_seed(cfg, rank), ntok_min=a.ntok_min,
@@ -590,6 +612,32 @@ def run_ours(a):
                 sweep[nm]["topc_candidates_per_row"] = {"mean": float(kg.mean()), "p99": float(np.percentile(kg, 99)),
                                                         "max": int(kg.max())}
         T.profile_enable(False)
+    # ---- the same batches through captured CUDA graphs (tachiom_graph_*: one graph per batch shape,
+    # captured outside the events; a launch copies the batch's queries in and replays the search) ----
+    graph_rec = None
+    if not a.no_sweep:
+        idx = list(range(a.warmup, min(nb, a.warmup + 5)))
+        graphs = [G.graph(params, batches[b][1], kk) for b in idx]
+        gi_ = torch.empty(a.batch * a.k, dtype=torch.int32, device="cuda")
+        gs_ = torch.empty(a.batch * a.k, dtype=torch.float32, device="cuda")
+        for g_, b in zip(graphs, idx):
+            g_.launch(batches[b][0], gi_, gs_)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(gi_, out_i[idx[-1]]))
+        gms = []
+        for g_, b in zip(graphs, idx):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g_.launch(batches[b][0], gi_, gs_)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            gms.append(e0.elapsed_time(e1))
+        for g_ in graphs:
+            g_.close()
+        gms = np.array(gms)
+        graph_rec = {"value": float(a.batch * len(gms) / (gms.sum() / 1e3)), "unit": "queries/s",
+                     "ms_per_step": float(gms.mean()), "batches": len(gms), "ids_equal_to_stream_launch": same}
     # ---- the rerank-only use of steps (c)-(d): external candidate lists ----
     rerank = None
     if not a.no_rerank:
@@ -725,6 +773,8 @@ def run_ours(a):
         "fp32_one_query_at_a_time": single,
         "sweep": sweep,
         "rerank_only": rerank,
+        "budget_autotune": budget_tune,
+        "graph": graph_rec,
         "gpu_launches": _count_launches(prof),
     }
     if not a.no_serving:

@@ -292,6 +292,33 @@ tachiom_status tachiom_autotune(tachiom_index *index, const tachiom_search_param
                                 const float *d_queries, const int32_t *h_ntok, const int32_t *h_k,
                                 int32_t nq, int32_t *best_plan, float *best_ms, void *stream);
 
+/* The k best documents of the whole collection by the refined score of step
+ * (c), S(q, d) = sum_i max_t (<q_i, c_a(t)> + rho_t <q_i, r^_t>) (Sec. 2.2,
+ * Refine): the cascade with kappa_c = C and kappa_d = D. Every document is
+ * scored by the refine (precision as in tachiom_refine; its top-k is exact in
+ * both) in chunks of 4,096 per query; the running top-k per query is merged
+ * on the host by (score desc, doc asc). d_queries: device fp32 [sum(ntok) x
+ * 128]; h_ntok host [nq] (1..32), nq <= 4096, k in 1..1000; h_ids / h_scores:
+ * host [nq x k] outputs, padded with (-1, -inf). Blocking.                  */
+tachiom_status tachiom_exhaustive_topk(tachiom_index *index, int32_t precision, const float *d_queries,
+                                       const int32_t *h_ntok, int32_t nq, int32_t k, int32_t *h_ids,
+                                       float *h_scores, void *stream);
+
+/* The candidate budgets by measurement (the paper tunes kappa_c and kappa_d on
+ * a grid, Sec. 3): on the tuning queries, every (kappa_c, kappa_d) of the
+ * grid (n_kc x n_kd <= 256 points, kappa_d >= k) is timed (CUDA events on
+ * `stream`, median of 3 searches) and its recall@k against
+ * tachiom_exhaustive_topk is measured; *best_kc / *best_kd receive the fastest
+ * point with recall >= min_recall (none: the point of highest recall, the
+ * faster on a tie), *best_recall and *best_ms its recall and time (may be
+ * NULL). h_table (host [n_kc x n_kd x 4] floats, may be NULL) receives
+ * (kappa_c, kappa_d, recall, ms) of every point, kappa_c-major. Blocking.   */
+tachiom_status tachiom_autotune_budgets(tachiom_index *index, int32_t precision, const float *d_queries,
+                                        const int32_t *h_ntok, int32_t nq, int32_t k, const int32_t *h_grid_kc,
+                                        int32_t n_kc, const int32_t *h_grid_kd, int32_t n_kd, float min_recall,
+                                        int32_t *best_kc, int32_t *best_kd, float *best_recall, float *best_ms,
+                                        float *h_table, void *stream);
+
 /* Synchronise `stream`, then return and clear the TACHIOM_FLAG_* bits raised
  * by work on that stream. Blocking.                                         */
 tachiom_status tachiom_stream_status(tachiom_index *index, void *stream, uint32_t *h_flags);

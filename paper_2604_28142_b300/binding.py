@@ -171,6 +171,9 @@ def lib():
         "tachiom_debug_tc_scores": ([P, P, I32, P, P], ct.c_int),
         "tachiom_debug_tc_scores_fp8": ([P, P, I32, P, P, P], ct.c_int),
         "tachiom_debug_wait_timeout": ([P, I32, P], ct.c_int),
+        "tachiom_exhaustive_topk": ([P, I32, P, P, I32, I32, P, P, P], ct.c_int),
+        "tachiom_autotune_budgets": ([P, I32, P, P, I32, I32, P, I32, P, I32, ct.c_float, P, P, P, P, P, P],
+                                     ct.c_int),
         "tachiom_tc_available": ([], ct.c_int),
         "tachiom_debug_topc_groups": ([P, ct.POINTER(SearchParams), P, I32, P], ct.c_int),
         "tachiom_debug_refine_scores": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P, P], ct.c_int),
@@ -317,6 +320,30 @@ class Index:
 
     def debug_tc_scores(self, rows, out, stream=None):
         _check(lib().tachiom_debug_tc_scores(self.h, _dp(rows), int(rows.shape[0]), _dp(out), _stream(stream)))
+
+    def exhaustive_topk(self, precision, queries, ntok, k, stream=None):
+        """(ids int32 [nq x k], scores fp32 [nq x k]) of the whole collection (host arrays)."""
+        ntok = np.ascontiguousarray(ntok, np.int32)
+        nq = len(ntok)
+        ids = np.empty((nq, k), np.int32)
+        sc = np.empty((nq, k), np.float32)
+        _check(lib().tachiom_exhaustive_topk(self.h, int(precision), _dp(queries), _hp(ntok), nq, int(k), _hp(ids),
+                                             _hp(sc), _stream(stream)))
+        return ids, sc
+
+    def autotune_budgets(self, precision, queries, ntok, k, grid_kc, grid_kd, min_recall=0.95, stream=None):
+        """((kappa_c, kappa_d), recall, ms, table [n_kc x n_kd x 4]) of the budget autotuner."""
+        ntok = np.ascontiguousarray(ntok, np.int32)
+        gc = np.ascontiguousarray(grid_kc, np.int32)
+        gd = np.ascontiguousarray(grid_kd, np.int32)
+        bkc, bkd = ct.c_int32(0), ct.c_int32(0)
+        rec, ms = ct.c_float(0), ct.c_float(0)
+        table = np.zeros((len(gc), len(gd), 4), np.float32)
+        _check(lib().tachiom_autotune_budgets(self.h, int(precision), _dp(queries), _hp(ntok), len(ntok), int(k),
+                                              _hp(gc), len(gc), _hp(gd), len(gd), ct.c_float(min_recall),
+                                              ct.byref(bkc), ct.byref(bkd), ct.byref(rec), ct.byref(ms), _hp(table),
+                                              _stream(stream)))
+        return (bkc.value, bkd.value), rec.value, ms.value, table
 
     def debug_wait_timeout(self, timeout_us, stream=None):
         _check(lib().tachiom_debug_wait_timeout(self.h, int(timeout_us), _stream(stream)))

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtachiom.so")
-SOURCES = ["index.cu", "search.cu", "k_topc.cu", "k_topc_tc.cu", "k_gather.cu", "k_refine.cu", "profile.cu", "refine_noalloc.cu", "k_refine_tc.cu", "server.cu", "k_topc_tc1.cu", "k_refine_dec.cu", "tac.cu", "tac_cluster.cu"]
+SOURCES = ["index.cu", "search.cu", "k_topc.cu", "k_topc_tc.cu", "k_gather.cu", "k_refine.cu", "profile.cu", "refine_noalloc.cu", "k_refine_tc.cu", "server.cu", "k_topc_tc1.cu", "k_refine_dec.cu", "tac.cu", "tac_cluster.cu", "budgets.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

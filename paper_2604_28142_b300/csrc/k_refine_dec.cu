@@ -231,7 +231,7 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
              const float *__restrict__ cbk_err2, const __nv_bfloat16 *__restrict__ cent_bf16,
              const float *__restrict__ cent_f32, int bf16c, const float2 *__restrict__ doc_xe, float cerr, float cnorm, float *__restrict__ sa, float *__restrict__ da, float *__restrict__ thr,
              const int32_t *__restrict__ win_slot, float *__restrict__ part, int ngroups, int2 *__restrict__ wl,
-             int *__restrict__ wl_n, int wl_cap, uint32_t *__restrict__ emx, int32_t *__restrict__ wovf, int64_t D,
+             unsigned long long *__restrict__ wl_n, int wl_cap, uint32_t *__restrict__ emx, int32_t *__restrict__ wovf, int64_t D,
              uint32_t *__restrict__ flags) {
   constexpr int DS = 128 / M;
   constexpr int NT = WARPS * 32;
@@ -521,12 +521,15 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
       }
       const int tot = __shfl_sync(0xffffffffu, pre, 31);
       if (tot > 0) {
-        int base = 0;
-        if (lane == 31) base = atomicAdd(wl_n, tot);
-        base = __shfl_sync(0xffffffffu, base, 31) + pre - nf;
-        if (base + nf > wl_cap) {
+        // the counter keeps counting once the list is full (every pair of a tied window can pass
+        // the test: billions of offers), so it is 64-bit and never wraps
+        unsigned long long wb = 0ull;
+        if (lane == 31) wb = atomicAdd(wl_n, (unsigned long long)tot);
+        wb = __shfl_sync(0xffffffffu, wb, 31) + (unsigned long long)(pre - nf);
+        if (wb + (unsigned long long)nf > (unsigned long long)wl_cap) {
           if (nf) wovf[(int64_t)q * kd + P.slot] = 1;  // the list is full: this document goes to the FP32 kernel
         } else {
+          int base = (int)wb;
           const int sid = q * kd + P.slot;
           while (fl) {
             const int b = __ffs(fl) - 1;
@@ -630,8 +633,9 @@ k_dec_exact_pairs(const float *__restrict__ queries, const int32_t *__restrict__
                   const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
                   const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
                   const float *__restrict__ cent_f32, const __nv_bfloat16 *__restrict__ cent_bf16, int bf16c,
-                  const int2 *__restrict__ wl, const int *__restrict__ wl_n, int wl_cap, uint32_t *__restrict__ emx) {
-  const int n = min(*wl_n, wl_cap);
+                  const int2 *__restrict__ wl, const unsigned long long *__restrict__ wl_n, int wl_cap,
+                  uint32_t *__restrict__ emx) {
+  const int n = (int)min(*wl_n, (unsigned long long)wl_cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int2 e = wl[k];
     const int sid = e.x, q = sid / kd, i = e.y & 31;
@@ -816,7 +820,7 @@ tachiom_status launch_refine_dec_win(const Index &ix, const float *queries, cons
                                      const WinScratch &ws, uint32_t *flags, cudaStream_t s) {
   if (nq <= 0) return TACHIOM_OK;
   TPROF("refine_win", s);
-  TCUDA(cudaMemsetAsync(ws.wl_n, 0, sizeof(int), s));
+  TCUDA(cudaMemsetAsync(ws.wl_n, 0, sizeof(unsigned long long), s));
   TCUDA(cudaMemsetAsync(ws.wovf, 0, (size_t)nq * kd * sizeof(int32_t), s));
   switch (ix.M) {
     case 8: return launch_refine_dec_m<8, true>(ix, queries, meta, nq, win, kd, nullptr, nullptr, thr, win_slot, part, &ws, flags, s);

@@ -759,6 +759,19 @@ struct Graph {
   int64_t rows = 0, total_k = 0;
 };
 
+// Warm-up input of a graph's sizing run: components uniform in [-1/2, 1/2) from a hash of their
+// index (splitmix64), so the run takes the path an ordinary batch takes. All-zero rows would tie
+// every score at every stage, the slowest input of the cascade.
+__global__ void k_fill_warmup(float *__restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = (uint64_t)i + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    x[i] = (float)(z >> 40) * (1.f / 16777216.f) - 0.5f;
+  }
+}
+
 static void graph_free(Graph *g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
@@ -799,7 +812,7 @@ extern "C" tachiom_status tachiom_graph_create(tachiom_index *index, const tachi
     graph_free(g);
     return fail(TACHIOM_ERR_OOM, "graph buffers");
   }
-  cudaMemsetAsync(g->d_in, 0, (size_t)b.rows * DIM * 4, g->stream);
+  k_fill_warmup<<<256, 256, 0, g->stream>>>(g->d_in, (int64_t)b.rows * DIM);
   // first run outside the capture: scratch grows, kernel attributes are set
   if ((st = search_device(ix, params, g->d_in, h_ntok, h_k, nq, g->d_ids, g->d_s, g->stream, nullptr))) {
     graph_free(g);

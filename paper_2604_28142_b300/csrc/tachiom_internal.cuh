@@ -254,7 +254,7 @@ struct Workspace {
   int32_t *d_win_slot = nullptr;       // [B x kd] each window entry's candidate slot
   float *d_thr = nullptr;              // [B x kd x 32] per (slot, query token) thresholds of the window pass
   int2 *d_wl = nullptr;                // [B x WL_PER_QUERY] candidate pairs of the window pass
-  int *d_wl_n = nullptr;
+  unsigned long long *d_wl_n = nullptr;  // pairs offered to the list (64-bit: it keeps counting past the cap)
   uint32_t *d_emx = nullptr;           // [B x kd x 32] their exact maxima
   int32_t *d_wovf = nullptr;           // [B x kd] documents left to the all-pairs FP32 kernel
   int32_t *d_out_ids = nullptr;        // staging for search_host
@@ -363,7 +363,7 @@ tachiom_status launch_decode_tables(const Index &ix, cudaStream_t s);
 constexpr int WL_PER_QUERY = 8192;  // candidate pairs a query's window may list
 struct WinScratch {
   int2 *wl;
-  int *wl_n;
+  unsigned long long *wl_n;
   int wl_cap;
   uint32_t *emx;   // [B x kd x 32]
   int32_t *wovf;   // [B x kd]

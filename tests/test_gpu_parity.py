@@ -400,6 +400,34 @@ def test_bf16_kappa_c_above_group_count():
     assert np.array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_zero_queries_tie_every_score(prec):
+    # All-zero query tokens: every centroid score, every S~ and every refined S is 0, so every
+    # stage decides by the id rule alone. Step (a) keeps the kappa_c lowest centroid ids, step (b)
+    # the kappa_d lowest reached documents, steps (c)-(d) the k lowest non-empty ones. Every
+    # (query token, document token) pair of the top-k window passes the decode pass's test, so
+    # its pair list (8192 per query) overflows many times over and the documents go to the
+    # all-pairs FP32 kernel; the list's counter must not wrap.
+    _cuda()
+    if prec:
+        _tc()
+    c = get_case("small")
+    nq, kc, kd, k = 16, 40, 2000, 50
+    ntok = np.full(nq, 32, np.int32)
+    q = np.zeros((int(ntok.sum()), 128), np.float32)
+    ref = c.O.search(q, ntok, k, kc, kd)
+    dq = torch.from_numpy(q).cuda()
+    oi = torch.full((nq * k,), -7, dtype=torch.int32, device="cuda")
+    os_ = torch.full((nq * k,), np.nan, dtype=torch.float32, device="cuda")
+    c.G.stream_status()
+    c.G.search(c.params(prec, kd=kd, kc=kc), dq, ntok, np.full(nq, k, np.int32), oi, os_)
+    torch.cuda.synchronize()
+    gi, gs = oi.cpu().numpy(), os_.cpu().numpy()
+    assert np.array_equal(gi, ref["ids"])
+    assert np.all(gs == 0.0) and np.all(ref["scores"] == 0.0)
+    assert c.G.stream_status() & (4 | 8 | 16) == 0  # no unrescued overflow, bad input or timeout
+
+
 @pytest.mark.parametrize("name", ["small", "small32", "random_edges", "random_m8"])
 def test_refine_tc_within_error_bound(name):
     # approximate refined scores (decode + tensor cores) are within the per-document bound
