@@ -477,6 +477,9 @@ k_gather_pool(const GpArgs A) {
       }
       __syncthreads();
     }
+    // every thread has read the empty stack before thread 0 sets up the next chunk's (without
+    // this barrier a late thread could read the next chunk's s_sp = 1 and enter the loop alone)
+    __syncthreads();
   }
   // the group's exact top-kappa_d
   int n = s_lcount;

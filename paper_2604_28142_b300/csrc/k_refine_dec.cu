@@ -528,6 +528,10 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
         wb = __shfl_sync(0xffffffffu, wb, 31) + (unsigned long long)(pre - nf);
         if (wb + (unsigned long long)nf > (unsigned long long)wl_cap) {
           if (nf) wovf[(int64_t)q * kd + P.slot] = 1;  // the list is full: this document goes to the FP32 kernel
+          // a reservation that straddles the cap leaves its positions below the cap unwritten: they
+          // get the sentinel (-1), so the reader never takes a pair from an earlier batch
+          for (unsigned long long p = wb; p < (unsigned long long)wl_cap && p < wb + (unsigned long long)nf; p++)
+            wl[p] = make_int2(-1, 0);
         } else {
           int base = (int)wb;
           const int sid = q * kd + P.slot;
@@ -628,16 +632,21 @@ k_refine_dec(const float *__restrict__ queries, const int32_t *__restrict__ meta
 
 template <int M>
 __global__ void __launch_bounds__(256)
-k_dec_exact_pairs(const float *__restrict__ queries, const int32_t *__restrict__ meta, int kd,
+k_dec_exact_pairs(const float *__restrict__ queries, const int32_t *__restrict__ meta, int nq, int kd,
                   const int32_t *__restrict__ win, const int64_t *__restrict__ doc_off,
                   const int32_t *__restrict__ tok_cid, const uint8_t *__restrict__ codes,
                   const uint16_t *__restrict__ rnorm, const float *__restrict__ codebooks,
                   const float *__restrict__ cent_f32, const __nv_bfloat16 *__restrict__ cent_bf16, int bf16c,
                   const int2 *__restrict__ wl, const unsigned long long *__restrict__ wl_n, int wl_cap,
-                  uint32_t *__restrict__ emx) {
+                  uint32_t *__restrict__ emx, uint32_t *__restrict__ flags) {
   const int n = (int)min(*wl_n, (unsigned long long)wl_cap);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int2 e = wl[k];
+    if (e.x < 0) continue;  // a sentinel below the cap
+    if (e.x >= nq * kd) {   // not reachable: every entry below the cap is written by this batch
+      atomicOr(flags, TACHIOM_FLAG_CAPACITY);
+      continue;
+    }
     const int sid = e.x, q = sid / kd, i = e.y & 31;
     const int64_t t = doc_off[win[sid]] + (e.y >> 5);
     const float v = dec_exact<M>(queries + ((int64_t)meta[q] + i) * DIM, t, tok_cid, codes, rnorm, codebooks,
@@ -790,10 +799,10 @@ static tachiom_status launch_refine_dec_m(const Index &ix, const float *queries,
   if (WIN) {
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix.device);
-    k_dec_exact_pairs<M><<<sms * 4, 256, 0, s>>>(queries, meta, kd, cand, ix.doc_off, ix.tok_cid, ix.codes,
+    k_dec_exact_pairs<M><<<sms * 4, 256, 0, s>>>(queries, meta, nq, kd, cand, ix.doc_off, ix.tok_cid, ix.codes,
                                                  ix.rnorm, ix.codebooks, ix.cent_f32, ix.cent_bf16,
                                                  ix.cdtype == TACHIOM_DTYPE_BF16 ? 1 : 0, ws->wl, ws->wl_n,
-                                                 ws->wl_cap, ws->emx);
+                                                 ws->wl_cap, ws->emx, flags);
     TLAUNCH();
     k_win_sums<<<dim3((kd * 4 + 255) / 256, nq), 256, 0, s>>>(meta, nq, cand, kd, ix.doc_off, ix.D, ws->emx, ws->wovf,
                                                               128 / M, refine_groups(M), part);

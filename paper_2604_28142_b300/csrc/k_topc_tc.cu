@@ -60,9 +60,11 @@ constexpr int BN = 256;            // query rows per CTA (MMA N)
 constexpr int EPI_WARPS = 16;      // 4 per TMEM lane quarter, 64 columns each
 constexpr int THREADS = 64 + 32 * EPI_WARPS;  // TMA warp, MMA warp, epilogue
 constexpr int TMEM_COLS = 512;
-constexpr int TOPM = 8;            // group maxima kept per (query row, stream)
+constexpr int TOPM = 4;            // group maxima kept per (query row, stream): any subset of distinct
+                                   // groups gives a valid threshold; 4 of the 4 x 148 streams of a row
+                                   // nearly always hold its top kappa_c groups
 constexpr int ECAP = 16384;        // E4M3: candidates a row may emit (over all CTAs of its row block)
-constexpr int SAMPLE_STRIDE = 16;  // the sample pass walks every 16th tile
+constexpr int SAMPLE_STRIDE = 16;  // the sample pass walks at most every 16th tile
 constexpr int GCAP = 256;          // groups of 32 centroids a row may keep (group selection)
 
 enum { MODE_SAMPLE = 1, MODE_EMIT = 2, MODE_RAW = 3 };
@@ -93,6 +95,7 @@ struct Ctl {
   int abort;
   float lim[BN];  // MODE_EMIT: per query row, the emission threshold in the accumulator's scale
   int ecnt[BN];   // MODE_EMIT: per query row, the candidates this CTA has emitted
+  alignas(16) float stage[EPI_WARPS][2][32];  // MODE_SAMPLE: a warp's 32 column maxima, lane 0 -> lane c
 };
 template <bool F8>
 constexpr int smem_bytes() { return Geo<F8>::TILE_BYTES + (int)sizeof(Ctl<F8>) + 1024; }
@@ -292,8 +295,9 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         }
         if (MODE == MODE_SAMPLE) {
           // maximum score of the warp's 32 centroids, per query row (-inf: no valid centroid):
-          // one redux per column gives every lane all 32 maxima, a 5-level select tree
-          // leaves lane l the one of its row
+          // one redux per column gives every lane all 32 maxima; lane 0 stages them in shared
+          // memory and lane l reads the one of its row (two 16-byte stores per 8 columns'
+          // worth of selects otherwise spent on the ALU pipe)
           float m[32];
           if (full_tile) {
 #pragma unroll
@@ -303,13 +307,16 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             for (int c = 0; c < 32; c++)
               m[c] = redux_fmax(jv ? (F8 ? __uint_as_float(v[c]) * isc : __uint_as_float(v[c])) : -INFINITY);
           }
+          float *stg = ctl->stage[e][ch];
+          if (lane == 0) {
 #pragma unroll
-          for (int w = 16; w >= 1; w >>= 1) {
-            const bool hi = (lane & w) != 0;
-#pragma unroll
-            for (int c = 0; c < w; c++) m[c] = hi ? m[c + w] : m[c];
+            for (int u = 0; u < 8; u++)
+              reinterpret_cast<float4 *>(stg)[u] = make_float4(m[4 * u], m[4 * u + 1], m[4 * u + 2], m[4 * u + 3]);
           }
-          const float mine = F8 ? m[0] * isq[ch] : m[0];
+          __syncwarp();
+          const float mcol = stg[lane];
+          __syncwarp();  // read before lane 0 stages the next tile's maxima
+          const float mine = F8 ? mcol * isq[ch] : mcol;
           if (A.gmax) {
             __half *dst = reinterpret_cast<__half *>(A.gmax) + ((int64_t)rb * A.G + tile * 4 + quarter) * BN + cblk * 64;
             dst[ch * 32 + lane] = __float2half_ru(mine);  // rounded up: the filter stays conservative
@@ -376,7 +383,7 @@ k_topc_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 }
 
 constexpr int LIM_THREADS = 128;
-constexpr int LIM_VPT = 37;     // values per thread: up to 148 CTAs x 4 streams x TOPM per row
+constexpr int LIM_VPT = 37;     // values per thread: up to 148 CTAs x 4 streams x 8 per row
 
 // Per row: tau' = the kappa_c-th largest value of the union of its streams'
 // TOPM lists (bitwise search for the largest key with at least kappa_c keys
@@ -812,13 +819,17 @@ static int tc_splits(int nts, int rbs, int kc, int sms) {
   using namespace tc;
   int sp = std::max(1, sms / gcd_int(sms, std::max(1, rbs)));
   sp = std::max(sp, (kc + 4 * TOPM - 1) / (4 * TOPM));
-  sp = std::min(sp, LIM_VPT * LIM_THREADS / (4 * TOPM));
+  sp = std::min(sp, std::min(148, LIM_VPT * LIM_THREADS / (4 * TOPM)));  // the per-CTA count layout holds 148
   return std::max(1, std::min(sp, nts));
 }
 
-// stride of the sample pass: at most SAMPLE_STRIDE, and the sample keeps >= 8 kappa_c groups
+// stride S of the sample pass: at most SAMPLE_STRIDE, the sample keeps >= 8 kappa_c groups, and
+// S kappa_c <= 640. The sample's kappa_c-th score sits near the (S kappa_c)-th of the full row, so
+// the emission pass passes about S kappa_c centroids plus the window's: a large kappa_c takes a
+// denser sample to keep the lists inside ECAP.
 static int tc_sample_stride(int ntiles, int kc) {
-  return std::max(1, std::min(tc::SAMPLE_STRIDE, ntiles / std::max(1, 2 * kc)));
+  const int k = std::max(1, kc);
+  return std::max(1, std::min(std::min(tc::SAMPLE_STRIDE, ntiles / (2 * k)), 640 / k));
 }
 
 // 32-bit words of: gmax [rbs][groups][256] fp16 (BF16 group selection), then tops
