@@ -830,11 +830,10 @@ def run_reference(a):
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     ix = synth.load_or_make(a.workload, device=dev)
     O = Oracle(ix)
-    # the oracle runs its queries in parallel, one per thread, but on the large workloads its
-    # exhaustive step (a) streams the whole centroid table per query token and saturates the host's
-    # memory bandwidth beyond a few threads: 4 queries per step keep a step near one query's
-    # latency (about 11 s on the 8.8M-document workload), so 25 steps end in about 5 minutes
-    per_step = max(1, min(4 if a.workload in ("msmarco-8.8M", "lotte-2.8M") else 16, host_cores()))
+    # the oracle runs its queries in parallel, one per thread; a step's time is one query's latency
+    # (its exhaustive step (a) streams the whole centroid table per query token: about 22 s on the
+    # 8.8M-document workload whether 4 or 16 queries run at once), so a step takes one query per core
+    per_step = max(1, min(16, host_cores()))
     nb = a.warmup + a.steps
     q = synth.make_queries(cfg, n_queries=nb * per_step, seed=cfg.query_seed, ntok_min=a.ntok_min,
                            ntok_max=a.ntok_max)
