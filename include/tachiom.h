@@ -407,6 +407,9 @@ typedef struct {
   int64_t tau;   /* types with fewer occurrences (and >= mu) get 2 */
   int32_t eps;   /* floor of an active type's allotment */
   double theta;  /* an active type keeps at least theta vectors per centroid (> 0) */
+  int32_t gemm_min_kappa; /* tachiom_tac_cluster only: a type with at least this many centroids is
+                             assigned through a BF16 GEMM on the tensor cores and an exact FP32
+                             rescoring within a rigorous margin (the same labels); 0: 64; < 0: never */
 } tachiom_tac_params;
 
 /* n: host int64 [n_types] occurrences per type (<= 0: absent, 0 centroids);
@@ -425,7 +428,11 @@ tachiom_status tachiom_tac_allot(const int64_t *n, const double *s, int32_t n_ty
  * positions floor((r + 1/2) n_j / kappa_j), r < kappa_j, and assigns every
  * vector once more. Squared L2 in FP32, ties to the lower centroid; means and
  * spreads in compensated FP32 (fixed summation order, so runs repeat bit for
- * bit); a centroid left without members keeps its place.
+ * bit); a centroid left without members keeps its place. Types with at least
+ * p->gemm_min_kappa centroids are assigned through a cuBLAS BF16 GEMM on the
+ * tensor cores with an exact FP32 rescoring of every centroid within a
+ * rigorous margin of the approximate best (the same labels as the CUDA-core
+ * kernel); the library links cuBLAS for this call only.
  *   d_vectors: device fp32 [n_vectors x 128], 16-byte aligned;
  *   d_types: device int32 [n_vectors], each in [0, n_types);
  *   h_kappa: host int32 [n_types] output; h_spread: host float64 [n_types]

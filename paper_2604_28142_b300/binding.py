@@ -64,7 +64,8 @@ def profile_read(stream=None) -> dict:
 
 
 class TacParams(ct.Structure):
-    _fields_ = [("mu", ct.c_int64), ("tau", ct.c_int64), ("eps", ct.c_int32), ("theta", ct.c_double)]
+    _fields_ = [("mu", ct.c_int64), ("tau", ct.c_int64), ("eps", ct.c_int32), ("theta", ct.c_double),
+                ("gemm_min_kappa", ct.c_int32)]
 
 
 def tac_allot(n, s, budget: int, mu: int, tau: int, eps: int, theta: float) -> np.ndarray:
@@ -81,7 +82,7 @@ def tac_allot(n, s, budget: int, mu: int, tau: int, eps: int, theta: float) -> n
 
 
 def tac_cluster(vectors, types, n_types: int, budget: int, mu: int, tau: int, eps: int, theta: float,
-                iters: int, stream=None):
+                iters: int, gemm_min_kappa: int = 0, stream=None):
     """Token-Aware Clustering of device vectors (torch cuda fp32 [N, 128]) with device token types
     (torch cuda int32 [N]) through tachiom_tac_cluster. Returns (kappa int32 [n_types] numpy,
     spread float64 [n_types] numpy, centroids fp32 [budget, 128], centroid type int32 [budget],
@@ -93,7 +94,7 @@ def tac_cluster(vectors, types, n_types: int, budget: int, mu: int, tau: int, ep
     cents = torch.empty((budget, 128), dtype=torch.float32, device=vectors.device)
     ctype = torch.empty(budget, dtype=torch.int32, device=vectors.device)
     labels = torch.empty(n, dtype=torch.int32, device=vectors.device)
-    p = TacParams(int(mu), int(tau), int(eps), float(theta))
+    p = TacParams(int(mu), int(tau), int(eps), float(theta), int(gemm_min_kappa))
     _check(lib().tachiom_tac_cluster(_dp(vectors), _dp(types), n, int(n_types), int(budget), ct.byref(p),
                                      int(iters), _hp(kappa), _hp(spread), _dp(cents), _dp(ctype), _dp(labels),
                                      _stream(stream)))

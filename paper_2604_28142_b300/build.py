@@ -45,7 +45,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int = 8) -> str:
         if p.wait() != 0:
             raise RuntimeError("nvcc failed")
     tmp = LIB + ".tmp"
-    subprocess.check_call([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    subprocess.check_call([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcublas"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -6,16 +6,25 @@
 //
 // Layout and order (all deterministic, so a run repeats bit for bit):
 //   - points are grouped by a stable radix sort on the type (within a type: collection order);
-//   - sums run in FP64 in a fixed order: warp w of a CTA takes the segment's elements w, w + W, ...,
-//     lane l dims 4l .. 4l + 3, and the W warp partials are added in warp order;
+//   - sums run in compensated FP32 in a fixed order: warp w of a CTA takes the segment's elements
+//     w, w + W, ..., lane l dims 4l .. 4l + 3, and the W warp partials are added in warp order;
 //   - initial centroids of type j: its points at positions floor((r + 1/2) n_j / kappa_j),
 //     r < kappa_j (evenly spaced, distinct since kappa_j <= n_j);
 //   - a round: every point to the nearest centroid of its type (squared L2 in FP32, ties to the
-//     lower centroid), then every centroid to the FP64 mean of its members rounded to FP32 (a
+//     lower centroid), then every centroid to the compensated FP32 mean of its members (a
 //     centroid left without members keeps its place); after the last round, one more assignment
 //     gives the labels;
 //   - centroids are numbered type by type (type order), kappa_j each.
+// The assignment of a type with many centroids (kappa_j >= 64 by default) is a dense product: its
+// points (BF16, grouped order) times its centroids (BF16) on the tensor cores through a cuBLAS GEMM
+// with FP32 accumulation, in row chunks; then per point the approximate best centroid, and every
+// centroid whose approximate distance lies within a rigorous margin of it rescored with the FP32
+// arithmetic of the small types' kernel. The margin covers the BF16 rounding of both operands and
+// the FP32 rounding of both distance forms, so the rescored set holds every centroid whose FP32
+// distance can be the minimum and the label is the one the FP32 kernel gives.
+#include <cublas_v2.h>
 #include <cub/cub.cuh>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -47,6 +56,17 @@ struct TacBufs {
     return TACHIOM_OK;
   }
 };
+
+// a cuBLAS handle bound to one stream, destroyed on every return path
+struct Blas {
+  cublasHandle_t h = nullptr;
+  ~Blas() {
+    if (h) cublasDestroy(h);
+  }
+};
+
+constexpr int GEMM_MIN_KAPPA = 64;        // default: types with this many centroids take the GEMM path
+constexpr int64_t GEMM_SCORES = 1 << 25;  // FP32 products one GEMM chunk may hold (128 MiB)
 
 constexpr int TC_WARPS = 8;  // warps of the per-segment reduction CTAs
 
@@ -180,11 +200,12 @@ __global__ void k_tac_init(const float *__restrict__ X, const int32_t *__restric
 __global__ void k_tac_assign(const float *__restrict__ X, const int32_t *__restrict__ order,
                              const int32_t *__restrict__ stype, int64_t n, const float *__restrict__ C,
                              const int64_t *__restrict__ cbase, const int32_t *__restrict__ kappa,
-                             int32_t *__restrict__ lab) {
+                             const uint8_t *__restrict__ gemm_type, int32_t *__restrict__ lab) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < n; p += nw) {
     const int32_t j = stype[p];
+    if (gemm_type && gemm_type[j]) continue;  // assigned by the GEMM path
     const int64_t g0 = cbase[j], kj = kappa[j];
     const float4 x = *reinterpret_cast<const float4 *>(X + (int64_t)order[p] * DIM + 4 * lane);
     float best = INFINITY;
@@ -202,6 +223,95 @@ __global__ void k_tac_assign(const float *__restrict__ X, const int32_t *__restr
     }
     if (lane == 0) lab[p] = (int32_t)bg;
   }
+}
+
+// grouped-order BF16 copy of the points and their norms (one warp per point, lane l dims 4l .. 4l + 3)
+__global__ void k_tac_points_bf16(const float *__restrict__ X, const int32_t *__restrict__ order, int64_t n,
+                                  __nv_bfloat16 *__restrict__ Xb, float *__restrict__ xn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); p < n; p += nw) {
+    const float4 x = *reinterpret_cast<const float4 *>(X + (int64_t)order[p] * DIM + 4 * lane);
+    __nv_bfloat162 *d = reinterpret_cast<__nv_bfloat162 *>(Xb + p * DIM + 4 * lane);
+    d[0] = __floats2bfloat162_rn(x.x, x.y);
+    d[1] = __floats2bfloat162_rn(x.z, x.w);
+    float q = fmaf(x.w, x.w, fmaf(x.z, x.z, fmaf(x.y, x.y, x.x * x.x)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) xn[p] = sqrtf(q);
+  }
+}
+
+// per centroid: its BF16 copy, its squared norm (FP32), and the largest norm of every type
+__global__ void k_tac_cent_prep(const float *__restrict__ C, int64_t budget, const int32_t *__restrict__ ctype,
+                                __nv_bfloat16 *__restrict__ Cb, float *__restrict__ cn2,
+                                unsigned *__restrict__ cmax_type) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g < budget; g += nw) {
+    const float4 c = *reinterpret_cast<const float4 *>(C + g * DIM + 4 * lane);
+    __nv_bfloat162 *d = reinterpret_cast<__nv_bfloat162 *>(Cb + g * DIM + 4 * lane);
+    d[0] = __floats2bfloat162_rn(c.x, c.y);
+    d[1] = __floats2bfloat162_rn(c.z, c.w);
+    float q = fmaf(c.w, c.w, fmaf(c.z, c.z, fmaf(c.y, c.y, c.x * c.x)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) {
+      cn2[g] = q;
+      atomicMax(cmax_type + ctype[g], __float_as_uint(sqrtf(q)));  // non-negative floats order as uints
+    }
+  }
+}
+
+// Points [p0, p0 + R) of type j (grouped order) against its k centroids g0 ..: S [R][k] holds the
+// BF16 products <x^, c^>. One warp per point: the approximate best d~ = ||c||^2 - 2 <x^, c^>, then
+// every centroid with d~ <= best + margin rescored with k_tac_assign's FP32 arithmetic, in ascending
+// order with ties to the lower centroid. Margin: |<x^, c^> - <x, c>| <= 2^-8 ||x|| ||c|| (the BF16
+// rounding of both operands) plus the FP32 accumulation, taken as 2^-6 ||x|| cmax_j; the FP32 forms
+// of ||c||^2 and of the distance add at most 2^-16 (||x||^2 + cmax_j^2), taken as 2^-14 (...). With
+// delta and e these, every centroid whose FP32 distance can be the minimum has d~ <= best + 4 delta
+// + 2 e.
+__global__ void k_tac_assign_gemm(const float *__restrict__ X, const int32_t *__restrict__ order, int64_t p0,
+                                  int R, const float *__restrict__ S, int k, int64_t g0,
+                                  const float *__restrict__ C, const float *__restrict__ cn2,
+                                  const float *__restrict__ xn, const unsigned *__restrict__ cmax_type, int32_t j,
+                                  int32_t *__restrict__ lab) {
+  const int lane = threadIdx.x & 31;
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= R) return;
+  const int64_t p = p0 + q;
+  const float *sp = S + (int64_t)q * k;
+  float best = INFINITY;
+  for (int g = lane; g < k; g += 32) best = fminf(best, fmaf(-2.f, sp[g], cn2[g0 + g]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  const float xnorm = xn[p], cm = __uint_as_float(cmax_type[j]);
+  const float delta = ldexpf(xnorm * cm, -6);
+  const float e = ldexpf(fmaf(xnorm, xnorm, cm * cm), -14);
+  const float thr = best + 4.f * delta + 2.f * e;
+  const float4 x = *reinterpret_cast<const float4 *>(X + (int64_t)order[p] * DIM + 4 * lane);
+  float bd = INFINITY;
+  int64_t bg = -1;
+  for (int b0 = 0; b0 < k; b0 += 32) {
+    const int g = b0 + lane;
+    const bool cand = g < k && !(fmaf(-2.f, sp[g], cn2[g0 + g]) > thr);
+    unsigned m = __ballot_sync(0xffffffffu, cand);
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1u;
+      const int64_t gg = g0 + b0 + b;
+      const float4 c = *reinterpret_cast<const float4 *>(C + gg * DIM + 4 * lane);
+      const float e0 = x.x - c.x, e1 = x.y - c.y, e2 = x.z - c.z, e3 = x.w - c.w;
+      float d = fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, e0 * e0)));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (d < bd || bg < 0) {
+        bd = d;
+        bg = gg;
+      }
+    }
+  }
+  if (lane == 0) lab[p] = (int32_t)bg;
 }
 
 // centroid g (one CTA each) to the compensated FP32 mean of its members; no member: unchanged
@@ -325,9 +435,74 @@ extern "C" tachiom_status tachiom_tac_cluster(const float *d_vectors, const int3
                                                     d_centroids);
     TLAUNCH();
   }
+  // the types assigned through the GEMM path, and its buffers
+  const int32_t kmin = p->gemm_min_kappa == 0 ? GEMM_MIN_KAPPA : p->gemm_min_kappa;
+  std::vector<int32_t> gtypes;
+  std::vector<uint8_t> hgemm((size_t)n_types, 0);
+  if (kmin > 0)
+    for (int32_t j = 0; j < n_types; j++)
+      if (h_kappa[j] >= kmin && hn[j] > 0) {
+        gtypes.push_back(j);
+        hgemm[(size_t)j] = 1;
+      }
+  uint8_t *gemm_d = nullptr;
+  __nv_bfloat16 *Xb = nullptr, *Cb = nullptr;
+  float *xn = nullptr, *cn2 = nullptr, *S = nullptr;
+  unsigned *cmax_t = nullptr;
+  Blas blas;
+  if (!gtypes.empty()) {
+    // best effort: without room for the BF16 copies every type takes the CUDA-core kernel
+    TacBufs G;
+    if (G.alloc(&gemm_d, (size_t)n_types) || G.alloc(&Xb, (size_t)N * DIM) || G.alloc(&xn, (size_t)N) ||
+        G.alloc(&Cb, (size_t)budget * DIM) || G.alloc(&cn2, (size_t)budget) ||
+        G.alloc(&cmax_t, (size_t)n_types) || G.alloc(&S, (size_t)GEMM_SCORES)) {
+      gtypes.clear();  // G frees what it got
+      gemm_d = nullptr;
+    } else {
+      B.p.insert(B.p.end(), G.p.begin(), G.p.end());  // owned by the call's buffers from here
+      G.p.clear();
+    }
+  }
+  if (!gtypes.empty()) {
+    TCUDA(cudaMemcpyAsync(gemm_d, hgemm.data(), hgemm.size(), cudaMemcpyHostToDevice, s));
+    k_tac_points_bf16<<<grid_for(N, 8), 256, 0, s>>>(d_vectors, order, N, Xb, xn);
+    TLAUNCH();
+    if (cublasCreate(&blas.h) != CUBLAS_STATUS_SUCCESS) {
+      blas.h = nullptr;
+      return fail(TACHIOM_ERR_CUDA, "tac_cluster: cublasCreate failed");
+    }
+    if (cublasSetStream(blas.h, s) != CUBLAS_STATUS_SUCCESS)
+      return fail(TACHIOM_ERR_CUDA, "tac_cluster: cublasSetStream failed");
+  }
+  // every point of a GEMM-path type: S = X_j C_j^T in row chunks (column-major k_j x rows, so a
+  // point's k_j products are contiguous), then the margin rescoring
+  auto assign_gemm = [&]() -> tachiom_status {
+    TCUDA(cudaMemsetAsync(cmax_t, 0, (size_t)n_types * sizeof(unsigned), s));
+    k_tac_cent_prep<<<grid_for(budget, 8), 256, 0, s>>>(d_centroids, budget, d_centroid_type, Cb, cn2, cmax_t);
+    TLAUNCH();
+    const float one = 1.f, zero = 0.f;
+    for (int32_t j : gtypes) {
+      const int k = h_kappa[j];
+      const int64_t rows_max = std::max<int64_t>(1, GEMM_SCORES / k);
+      for (int64_t a0 = hoff[j]; a0 < hoff[j + 1]; a0 += rows_max) {
+        const int R = (int)std::min<int64_t>(rows_max, hoff[j + 1] - a0);
+        const cublasStatus_t cs =
+            cublasGemmEx(blas.h, CUBLAS_OP_T, CUBLAS_OP_N, k, R, DIM, &one, Cb + hcb[j] * DIM, CUDA_R_16BF, DIM,
+                         Xb + a0 * DIM, CUDA_R_16BF, DIM, &zero, S, CUDA_R_32F, k, CUBLAS_COMPUTE_32F,
+                         CUBLAS_GEMM_DEFAULT);
+        if (cs != CUBLAS_STATUS_SUCCESS) return fail(TACHIOM_ERR_CUDA, "tac_cluster: cublasGemmEx failed (%d)", (int)cs);
+        k_tac_assign_gemm<<<(R + 7) / 8, 256, 0, s>>>(d_vectors, order, a0, R, S, k, hcb[j], d_centroids, cn2, xn,
+                                                      cmax_t, j, lab);
+        TLAUNCH();
+      }
+    }
+    return TACHIOM_OK;
+  };
   for (int32_t it = 0; it <= iters; it++) {
     if (N > 0) {
-      k_tac_assign<<<grid_for(N, 8), 256, 0, s>>>(d_vectors, order, stype, N, d_centroids, cbase_d, kap_d, lab);
+      if (!gtypes.empty()) TTRY(assign_gemm());
+      k_tac_assign<<<grid_for(N, 8), 256, 0, s>>>(d_vectors, order, stype, N, d_centroids, cbase_d, kap_d, gemm_d,
+                                                   lab);
       TLAUNCH();
     }
     if (it == iters || N == 0 || budget == 0) break;

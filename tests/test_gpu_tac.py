@@ -64,6 +64,37 @@ def test_tac_cluster_matches_oracle():
     assert torch.equal(c2, cents) and torch.equal(ct2, ctype) and torch.equal(l2, labels)
 
 
+def test_tac_cluster_gemm_path_equals_cuda_core_path():
+    # Types with many centroids are assigned through a BF16 GEMM on the tensor cores and an exact
+    # FP32 rescoring of every centroid within a rigorous margin of the approximate best: the labels,
+    # and so the centroids of every round, must be those of the CUDA-core kernel bit for bit. Noisy
+    # blobs (noise 1.0 against centres of scale 3) put several centroids of a type near each point,
+    # so the margin holds more than one candidate for many points.
+    _cuda()
+    import paper_2604_28142_b300 as T
+    rng = np.random.default_rng(77)
+    parts_v, parts_t = [], []
+    for j, (n, k) in enumerate([(12000, 90), (3000, 12), (700, 5), (40, 1)]):
+        centers = rng.normal(size=(k, 128)) * 3.0
+        parts_v.append(centers[rng.integers(0, k, size=n)] + rng.normal(size=(n, 128)))
+        parts_t.append(np.full(n, j, np.int32))
+    perm = rng.permutation(sum(len(t) for t in parts_t))
+    v = np.concatenate(parts_v).astype(np.float32)[perm]
+    t = np.concatenate(parts_t)[perm]
+    kw = dict(mu=5, tau=20, eps=1, theta=10.0)
+    res = {}
+    for gmk in (-1, 0, 8):
+        res[gmk] = _run(T, v, t, 4, 200, 5, gemm_min_kappa=gmk, **kw)
+    torch.cuda.synchronize()
+    kappa = res[-1][0]
+    assert kappa.max() >= 64  # the default threshold sends at least one type to the GEMM path
+    for gmk in (0, 8):
+        k2, s2, c2, ct2, l2 = res[gmk]
+        assert np.array_equal(k2, kappa)
+        assert torch.equal(l2, res[-1][4]), f"labels differ (gemm_min_kappa {gmk})"
+        assert torch.equal(c2, res[-1][2]) and torch.equal(ct2, res[-1][3])
+
+
 def test_tac_cluster_type_without_centroid_and_bad_type():
     _cuda()
     import paper_2604_28142_b300 as T
