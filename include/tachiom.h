@@ -134,7 +134,9 @@ typedef struct {
                          at 4096 */
   int32_t precision;  /* TACHIOM_PREC_* for step (a) */
   int32_t plan_id;    /* -1: the library's choice of kernels; >= 0: a plan from tachiom_autotune
-                         (bits 0-1 step (a) kernel, 2-3 step (c) kernel, 4- FP32 scan slices) */
+                         (bits 0-1 step (a) kernel, 2-3 step (c) kernel, 4-23 FP32 scan slices,
+                         24 small gather pieces, 25 FP32 window over every pair, 26-28 g: 2 g
+                         gather range groups per query); every plan gives the same results */
   float rescore_margin; /* TACHIOM_PREC_FP8 only: the FP32 repair window of step (a) as a multiple
                            of the rigorous E4M3 error bound; <= 0 means 0.1 (about 4 standard
                            deviations of the typical error of unit-norm rows). Ignored otherwise. */

@@ -277,10 +277,13 @@ static float fp8_lambda(const tachiom_search_params *p) {
 //             pieces only where a range does not fit)
 //   bit 25    step (c), decode path: the window rescored over every (query token, document
 //             token) pair in FP32 (default: only the pairs that can hold a maximum)
+//   bits 26-28 step (b): range groups per query (0: the default, about 8 CTAs per SM over the
+//             batch; g: 2 g groups, within the selection's capacity)
 enum { SCAN_DEFAULT = 0, SCAN_TC1 = 1, SCAN_TC2 = 2, SCAN_F32 = 3 };
 constexpr int32_t PLAN_GATHER_SPLIT = 1 << 24;
 constexpr int32_t PLAN_WINDOW_ALL = 1 << 25;
 static bool gather_split(const tachiom_search_params *p) { return p->plan_id >= 0 && (p->plan_id & PLAN_GATHER_SPLIT); }
+static int gather_groups_of(const tachiom_search_params *p) { return p->plan_id >= 0 ? (p->plan_id >> 26) & 7 : 0; }
 enum { REFINE_DEFAULT = 0, REFINE_TC = 1, REFINE_F32 = 2, REFINE_DEC = 3 };
 
 static int scan_kind(const tachiom_search_params *p) {
@@ -444,10 +447,10 @@ static tachiom_status search_device(Index *ix, const tachiom_search_params *p, c
   if ((st = upload_meta(w, p, h_ntok, h_k, nq))) return st;
   if ((st = run_topc(ix, w, p, d_queries, b.rows, plan))) return st;
   if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, p->kappa_c, kd, w->d_pool, w->d_pool_n,
-                          gather_split(p), w->d_flags, stream)))
+                          gather_split(p), gather_groups_of(p), w->d_flags, stream)))
     return st;
-  if ((st = launch_select_kd(*ix, w->d_meta, nq, kd, w->d_pool, w->d_pool_n, w->d_cand, w->d_cand_s, w->d_ncand,
-                             stream)))
+  if ((st = launch_select_kd(*ix, w->d_meta, nq, kd, w->d_pool, w->d_pool_n, gather_groups_of(p), w->d_cand,
+                             w->d_cand_s, w->d_ncand, stream)))
     return st;
   return run_refine(ix, w, p, d_queries, nq, w->d_cand, kd, d_out_ids, d_out_scores, stream);
 }
@@ -593,9 +596,10 @@ extern "C" tachiom_status tachiom_gather(tachiom_index *index, const tachiom_sea
                                 w->d_flags, s)))
     return st;
   if ((st = launch_gather(*ix, w->d_meta, nq, w->d_top_ids, w->d_top_s, params->kappa_c, kd, w->d_pool, w->d_pool_n,
-                          gather_split(params), w->d_flags, s)))
+                          gather_split(params), gather_groups_of(params), w->d_flags, s)))
     return st;
-  return launch_select_kd(*ix, w->d_meta, nq, kd, w->d_pool, w->d_pool_n, d_cand_ids, d_cand_scores, d_ncand, s);
+  return launch_select_kd(*ix, w->d_meta, nq, kd, w->d_pool, w->d_pool_n, gather_groups_of(params), d_cand_ids,
+                          d_cand_scores, d_ncand, s);
 }
 
 extern "C" tachiom_status tachiom_refine(tachiom_index *index, const tachiom_search_params *params,
@@ -891,6 +895,8 @@ extern "C" tachiom_status tachiom_autotune(tachiom_index *index, const tachiom_s
         if (sk == SCAN_TC1 && params->kappa_c > topc_tc1_max_kc()) continue;
         plans.push_back(sk | (rk << 2));
       }
+    // the default kernels with other gather group counts (4, 8, 12 per query)
+    for (int g : {2, 4, 6}) plans.push_back(SCAN_TC2 | (REFINE_DEC << 2) | (g << 26));
   } else {
     const int sms = sm_count(ix->device);
     const int row_tiles = (b.rows + 31) / 32;

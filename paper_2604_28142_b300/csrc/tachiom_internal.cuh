@@ -334,13 +334,15 @@ tachiom_status launch_score_pairs(const Index &ix, const float *rows, int nrows,
                                   int kc, int32_t *out_ids, float *scores, uint32_t *flags, cudaStream_t s);
 // step (b): per (query, range group) the group's top-kappa_d keys into pool, then per query the
 // exact top-kappa_d of its groups' parts
-int gather_groups(const Index &ix, int nq, int kd);
+// range groups per query of step (b); groups > 0 (a plan's choice) asks for 2 x groups
+int gather_groups(const Index &ix, int nq, int kd, int groups);
 size_t gather_pool_elems(const Index &ix, int nq, int kd);
 tachiom_status launch_gather(const Index &ix, const int32_t *meta, int nq, const int32_t *top_ids, const float *top_s,
-                             int kc, int kd, uint64_t *pool, int32_t *pool_n, bool force_split, uint32_t *flags,
-                             cudaStream_t s);
+                             int kc, int kd, uint64_t *pool, int32_t *pool_n, bool force_split, int groups,
+                             uint32_t *flags, cudaStream_t s);
 tachiom_status launch_select_kd(const Index &ix, const int32_t *meta, int nq, int kd, const uint64_t *pool,
-                                const int32_t *pool_n, int32_t *cand, float *cand_s, int32_t *ncand, cudaStream_t s);
+                                const int32_t *pool_n, int groups, int32_t *cand, float *cand_s, int32_t *ncand,
+                                cudaStream_t s);
 // steps (c), (d)
 tachiom_status launch_refine_win(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                  const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s);

@@ -63,8 +63,9 @@ def test_every_plan_gives_the_same_results(env, prec):
     assert best >= 0 and ms > 0
     tok = 1 << 24  # every gather range cut into small pieces
     win_all = 1 << 25  # the FP32 window over every pair
-    plans = ([1 | 4, 1 | 8, 2 | 4, 2 | 8, 3 | 8, 2 | 12 | tok, 2 | 12 | win_all] if prec == 1
-             else [3 | 8 | (s << 4) for s in (1, 7, 40)] + [3 | 8 | tok])
+    groups = [g << 26 for g in (1, 2, 7)]  # 2 g gather range groups per query
+    plans = ([1 | 4, 1 | 8, 2 | 4, 2 | 8, 3 | 8, 2 | 12 | tok, 2 | 12 | win_all] + [2 | 12 | g for g in groups]
+             if prec == 1 else [3 | 8 | (s << 4) for s in (1, 7, 40)] + [3 | 8 | tok] + [3 | 8 | g for g in groups])
     for pl in plans + [best]:
         got = _run(T, G, params, q, kk, plan=pl)
         assert np.array_equal(got[0], want[0]), pl
