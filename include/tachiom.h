@@ -192,6 +192,21 @@ tachiom_status tachiom_refine(tachiom_index *index, const tachiom_search_params 
                               int32_t nq, const int32_t *d_cand_ids, int32_t *d_out_ids,
                               float *d_out_scores, void *stream);
 
+/* Full centroid interaction (the variant of step (b)'s scoring that Sec. 2.2
+ * contrasts with the Top_i-restricted one: every document token replaced by
+ * its assigned centroid, the max over all of the document's tokens):
+ *   S_ci(q, d) = sum_i max_{t in d} <q_i, c_a(t)>
+ * for the documents of given candidate lists (for example step (b)'s
+ * kappa_d candidates), then the k best by (S_ci desc, doc asc). Arguments,
+ * layouts and padding as tachiom_refine; always FP32 (the refine kernel with
+ * every residual norm taken as 0), whatever params->precision says; kappa_c
+ * is not used. An empty document scores 0; an id outside [0, n_docs) raises
+ * TACHIOM_FLAG_BAD_INPUT and scores 0. Asynchronous. */
+tachiom_status tachiom_centroid_interaction(tachiom_index *index, const tachiom_search_params *params,
+                                            const float *d_queries, const int32_t *h_ntok, const int32_t *h_k,
+                                            int32_t nq, const int32_t *d_cand_ids, int32_t *d_out_ids,
+                                            float *d_out_scores, void *stream);
+
 /* tachiom_refine without allocating. The paper has no counterpart: this is an
  * interface for callers that cannot allocate device memory during a call, for
  * example a process whose device memory is handed out in advance by a

@@ -166,6 +166,7 @@ def lib():
         "tachiom_top_centroids": ([P, ct.POINTER(SearchParams), P, I32, P, P, P], ct.c_int),
         "tachiom_gather": ([P, ct.POINTER(SearchParams), P, P, I32, P, P, P, P, P], ct.c_int),
         "tachiom_refine": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
+        "tachiom_centroid_interaction": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
         "tachiom_refine_noalloc": ([P, ct.POINTER(SearchParams), P, P, P, I32, P, P, P, P], ct.c_int),
         "tachiom_refine_noalloc_status": ([P, P, U32p], ct.c_int),
         "tachiom_stream_status": ([P, P, U32p], ct.c_int),
@@ -318,6 +319,15 @@ class Index:
         _check(lib().tachiom_refine(self.h, ct.byref(params), _dp(queries), _hp(ntok), _hp(k),
                                     int(ntok.shape[0]), _dp(cand_ids), _dp(out_ids), _dp(out_scores),
                                     _stream(stream)))
+
+    def centroid_interaction(self, params: SearchParams, queries, ntok, k, cand_ids, out_ids, out_scores,
+                             stream=None):
+        """Full centroid interaction of given candidate lists (tachiom_centroid_interaction)."""
+        ntok = np.ascontiguousarray(ntok, dtype=np.int32)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        _check(lib().tachiom_centroid_interaction(self.h, ct.byref(params), _dp(queries), _hp(ntok), _hp(k),
+                                                  int(ntok.shape[0]), _dp(cand_ids), _dp(out_ids),
+                                                  _dp(out_scores), _stream(stream)))
 
     def debug_tc_scores(self, rows, out, stream=None):
         _check(lib().tachiom_debug_tc_scores(self.h, _dp(rows), int(rows.shape[0]), _dp(out), _stream(stream)))

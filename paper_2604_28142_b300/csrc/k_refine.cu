@@ -112,7 +112,7 @@ k_refine(const float *__restrict__ queries, const int32_t *__restrict__ meta, in
           *reinterpret_cast<uint4 *>(cb + u * 16) = v;
         }
       }
-      const float rho = half_bits_to_float(rnorm[t]);
+      const float rho = rnorm ? half_bits_to_float(rnorm[t]) : 0.f;  // no norms: the centroid term alone
       const int32_t j = tok_cid[t];
       // centroid contribution <q_g, c_j>
       float ct[G];
@@ -209,7 +209,8 @@ k_refine(const float *__restrict__ queries, const int32_t *__restrict__ meta, in
 template <int M>
 static tachiom_status launch_refine_m(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                       const int32_t *cand, int kd, float *part, uint32_t *flags,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, bool centroid_only) {
+  const uint16_t *rn = centroid_only ? nullptr : ix.rnorm;
   constexpr int G = 128 / M;
   const int ngroups = refine_groups(M);
   size_t smem = ((size_t)M * 256 * G + (size_t)G * DIM) * 4;
@@ -217,12 +218,12 @@ static tachiom_status launch_refine_m(const Index &ix, const float *queries, con
   if (ix.cdtype == TACHIOM_DTYPE_BF16) {
     TCUDA(cudaFuncSetAttribute(k_refine<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_refine<M, true><<<grid, R_THREADS, smem, s>>>(queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid,
-                                                     ix.codes, ix.rnorm, ix.codebooks, ix.cent_f32,
+                                                     ix.codes, rn, ix.codebooks, ix.cent_f32,
                                                      ix.cent_bf16, part, ngroups, ix.D, flags);
   } else {
     TCUDA(cudaFuncSetAttribute(k_refine<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_refine<M, false><<<grid, R_THREADS, smem, s>>>(queries, meta, nq, cand, kd, ix.doc_off, ix.tok_cid,
-                                                      ix.codes, ix.rnorm, ix.codebooks, ix.cent_f32,
+                                                      ix.codes, rn, ix.codebooks, ix.cent_f32,
                                                       ix.cent_bf16, part, ngroups, ix.D, flags);
   }
   TLAUNCH();
@@ -230,13 +231,14 @@ static tachiom_status launch_refine_m(const Index &ix, const float *queries, con
 }
 
 tachiom_status launch_refine(const Index &ix, const float *queries, const int32_t *meta, int nq,
-                             const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s) {
+                             const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s,
+                             bool centroid_only) {
   if (nq <= 0) return TACHIOM_OK;
-  TPROF("refine", s);
+  TPROF(centroid_only ? "centroid_interaction" : "refine", s);
   switch (ix.M) {
-    case 8: return launch_refine_m<8>(ix, queries, meta, nq, cand, kd, part, flags, s);
-    case 16: return launch_refine_m<16>(ix, queries, meta, nq, cand, kd, part, flags, s);
-    case 32: return launch_refine_m<32>(ix, queries, meta, nq, cand, kd, part, flags, s);
+    case 8: return launch_refine_m<8>(ix, queries, meta, nq, cand, kd, part, flags, s, centroid_only);
+    case 16: return launch_refine_m<16>(ix, queries, meta, nq, cand, kd, part, flags, s, centroid_only);
+    case 32: return launch_refine_m<32>(ix, queries, meta, nq, cand, kd, part, flags, s, centroid_only);
   }
   return fail(TACHIOM_ERR_INVALID, "unsupported pq_m %d", ix.M);
 }

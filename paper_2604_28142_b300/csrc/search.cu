@@ -631,6 +631,37 @@ extern "C" tachiom_status tachiom_refine(tachiom_index *index, const tachiom_sea
   return run_refine(ix, w, params, d_queries, nq, d_cand_ids, kd, d_out_ids, d_out_scores, s);
 }
 
+extern "C" tachiom_status tachiom_centroid_interaction(tachiom_index *index, const tachiom_search_params *params,
+                                                       const float *d_queries, const int32_t *h_ntok,
+                                                       const int32_t *h_k, int32_t nq, const int32_t *d_cand_ids,
+                                                       int32_t *d_out_ids, float *d_out_scores, void *stream) {
+  Index *ix = as_index(index);
+  if (!ix) return fail(TACHIOM_ERR_INVALID, "index is NULL");
+  DeviceGuard g(ix->device);
+  tachiom_status st;
+  if ((st = check_params(params))) return st;
+  Batch b;
+  if ((st = check_batch(h_ntok, h_k, nq, 0, &b))) return st;
+  if (nq == 0) return TACHIOM_OK;
+  if (!h_k) return fail(TACHIOM_ERR_INVALID, "h_k is NULL");
+  const int kd = resolve_kd(params, b.max_k);
+  if (b.max_k > kd) return fail(TACHIOM_ERR_INVALID, "k > kappa_d");
+  if (!d_queries || !d_cand_ids || !d_out_ids || !d_out_scores) return fail(TACHIOM_ERR_INVALID, "NULL device buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace *w;
+  if ((st = ws_get(ix, s, &w))) return st;
+  Need n;
+  n.nq = nq;
+  n.rows = b.rows;
+  n.kc = params->kappa_c;
+  n.kd = kd;
+  if ((st = ws_reserve(ix, w, n))) return st;
+  if ((st = upload_meta(w, params, h_ntok, h_k, nq))) return st;
+  // the FP32 refine with every residual norm taken as 0, then the top-k
+  if ((st = launch_refine(*ix, d_queries, w->d_meta, nq, d_cand_ids, kd, w->d_part, w->d_flags, s, true))) return st;
+  return launch_final_topk(*ix, w->d_meta, nq, d_cand_ids, kd, w->d_part, d_out_ids, d_out_scores, s);
+}
+
 extern "C" tachiom_status tachiom_stream_status(tachiom_index *index, void *stream, uint32_t *h_flags) {
   Index *ix = as_index(index);
   if (!ix || !h_flags) return fail(TACHIOM_ERR_INVALID, "NULL argument");

@@ -346,9 +346,11 @@ tachiom_status launch_select_kd(const Index &ix, const int32_t *meta, int nq, in
 // steps (c), (d)
 tachiom_status launch_refine_win(const Index &ix, const float *queries, const int32_t *meta, int nq,
                                  const int32_t *cand, int kd, float *part, uint32_t *flags, cudaStream_t s);
+// centroid_only: every residual norm taken as 0, so the partial sums are the full centroid
+// interaction sum_i max_{t in d} <q_i, c_a(t)>
 tachiom_status launch_refine(const Index &ix, const float *queries, const int32_t *meta, int nq,
                              const int32_t *cand, int kd, float *part, uint32_t *flags,
-                             cudaStream_t s);
+                             cudaStream_t s, bool centroid_only = false);
 tachiom_status launch_final_topk(const Index &ix, const int32_t *meta, int nq, const int32_t *cand,
                                  int kd, const float *part, int32_t *out_ids, float *out_s,
                                  cudaStream_t s);

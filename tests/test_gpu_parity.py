@@ -215,6 +215,36 @@ def test_rerank_external_lists(name, prec):
                       exact_scores=dict(zip(cd.tolist(), rs.tolist())))
 
 
+@pytest.mark.parametrize("name", ["small", "small32", "random_edges", "random_m8"])
+def test_centroid_interaction_of_lists(name):
+    # the full centroid interaction of given lists: the oracle's refine of the same index with every
+    # residual norm zero (a pin fixes that identity), then the exact top-k of each list
+    c = get_case(name)
+    cand = _external_lists(c, seed=91)
+    kd = cand.shape[1]
+    kk = np.full(c.nq, c.k, np.int32)
+    oi = torch.empty(c.nq * c.k, dtype=torch.int32, device="cuda")
+    os_ = torch.empty(c.nq * c.k, dtype=torch.float32, device="cuda")
+    c.G.centroid_interaction(c.params(1, kd=kd), c.dq, c.ntok, kk, torch.from_numpy(cand).cuda(), oi, os_)
+    torch.cuda.synchronize()
+    gi, gs = oi.cpu().numpy(), os_.cpu().numpy()
+    from oracle import Oracle
+    ix0 = dict(c.ix)
+    ix0["residual_norms"] = np.zeros(c.ix["token_centroid"].shape[0], np.uint16)
+    O0 = Oracle(ix0)
+    for u in range(c.nq):
+        cd = cand[u][cand[u] >= 0]
+        rs = O0.refine(c.q[c.qoff[u]:c.qoff[u + 1]], cd)
+        order = np.lexsort((cd, -rs))[:c.k]
+        want_i = np.full(c.k, -1, np.int32)
+        want_s = np.full(c.k, -np.inf)
+        want_i[:len(order)], want_s[:len(order)] = cd[order], rs[order]
+        sl = slice(u * c.k, (u + 1) * c.k)
+        check_ranking(gi[sl], gs[sl], want_i, want_s, RTOL_FP32, GAP, what=f"query {u}",
+                      exact_scores=dict(zip(cd.tolist(), rs.tolist())))
+    assert c.G.stream_status() & (4 | 8 | 16) == 0
+
+
 def _search(c, prec=0, kk=None):
     kk = np.full(c.nq, c.k, np.int32) if kk is None else kk
     tot = int(kk.sum())
